@@ -1,0 +1,183 @@
+/*
+ * dd_solver.h - C ABI of the GB300 solver for sequences of Poisson problems by
+ * deflated PCG on the domain-decomposition interface problem, preconditioned by
+ * two-/three-level (and adaptive) BDDC, with Krylov subspace recycling.
+ *
+ * The method (arXiv 2412.17543):
+ *   - Sect. 2, eq. systems: one SPD matrix K (Q1 pressure Laplacian, Dirichlet
+ *     data on part of the boundary) and a sequence of right-hand sides f.
+ *   - Sect. 3.1, eq. Sug: the interface problem A x_G = b, A = sum_i R_i^T S_i R_i
+ *     with S_i = K_GG - K_GI K_II^{-1} K_IG never assembled.
+ *   - Sect. 3.2, eqs. averaging_subdomain_solves, coarse_problem, localCorr:
+ *     the BDDC preconditioner; Sect. 3.3, eqs. eig-matrix, c-def: adaptive
+ *     face constraints.
+ *   - Sect. 4.1, Algorithm 1: deflated PCG; Sect. 4.2: recycling strategies
+ *     B1-B4, harmonic Ritz vectors (eq. harmonicRitz) and the freezing
+ *     criterion (eq. harmritzstopcrit).
+ *   - Sect. 5, eqs. stopping_rhs / stopping_residual: stopping criteria.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns dd_status; no C++ exception crosses the ABI. On an
+ *     error the message of the calling thread is available from dd_last_error().
+ *   - "host" pointers are read or written synchronously before the call returns.
+ *     "device" pointers are caller-owned CUDA device memory; the library reads
+ *     and writes them in stream order on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) and never frees them.
+ *   - Vectors over the free nodes ("free vectors", length n_free) use the
+ *     lexicographic order of the free (non-Dirichlet) mesh nodes, x fastest.
+ *     Interface vectors (length n_gamma) list the interface nodes (nodes of
+ *     more than one subdomain) in increasing free-node index.
+ *   - All floating-point vectors crossing the ABI are float64.
+ */
+#ifndef DD_SOLVER_H
+#define DD_SOLVER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_ctx dd_ctx;         /* opaque: mesh, partition, preconditioner (owned by the library) */
+typedef struct dd_recycle dd_recycle; /* opaque: deflation basis and its state across solves */
+
+typedef enum {
+  DD_OK = 0,
+  DD_INVALID_ARG = 1,      /* bad sizes, NULL where not allowed, unsupported option */
+  DD_OOM = 2,              /* device or host allocation failed */
+  DD_CUDA_ERROR = 3,       /* a CUDA call failed; see dd_last_error() */
+  DD_SINGULAR_LOCAL = 4,   /* a subdomain or coarse factorization met a non-positive pivot */
+  DD_NOT_CONVERGED = 5,    /* maxit reached; the iterate and the statistics are still written */
+  DD_BREAKDOWN = 6,        /* a non-finite or non-positive PCG scalar (p^T A p, r^T z) */
+  DD_TIMEOUT = 7           /* a bounded device-side wait gave up */
+} dd_status;
+
+/* Dirichlet face bits (faces of the unit cube). */
+enum { DD_FACE_X0 = 1, DD_FACE_X1 = 2, DD_FACE_Y0 = 4, DD_FACE_Y1 = 8, DD_FACE_Z0 = 16, DD_FACE_Z1 = 32 };
+
+/* Tensor-product hexahedral mesh with a block partition (Sect. 3.1). All pointers
+ * are host pointers, copied by dd_setup. */
+typedef struct {
+  int32_t nx, ny, nz;            /* elements per axis, each >= 1 */
+  const double* xc;              /* [nx+1] increasing node coordinates; likewise yc [ny+1], zc [nz+1] */
+  const double* yc;
+  const double* zc;
+  const double* coef;            /* [nz][ny][nx] per-element coefficient k_e > 0, x fastest; NULL means 1 */
+  int32_t sub_x, sub_y, sub_z;   /* elements per subdomain per axis (must divide nx, ny, nz; each <= 8) */
+  uint32_t dirichlet_faces;      /* DD_FACE_* bits, at least one (K must be SPD, Sect. 2) */
+} dd_mesh_desc;
+
+enum { DD_WEIGHTS_CARD = 0, DD_WEIGHTS_DIAG = 1 };                 /* Sect. 3.2 interface weights D_i */
+enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_DF64 = 2 };     /* arithmetic of an operator */
+enum { DD_B1 = 1, DD_B2 = 2, DD_B3 = 3, DD_B4 = 4 };                /* Sect. 4.2 recycling strategies */
+
+typedef struct {
+  int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
+  int32_t coarse_group;     /* 3 levels: level-1 subdomains per level-2 subdomain per axis (e.g. 4) */
+  int32_t use_corners, use_edges, use_faces;  /* coarse dofs: corner values, edge and face averages */
+  int32_t adaptive;         /* 1: add face constraints from eq. eig-matrix (Sect. 3.3) */
+  double tau;               /* adaptive threshold on the face eigenvalues */
+  int32_t max_eig_per_face; /* at most this many adaptive constraints per face */
+  int32_t weights;          /* DD_WEIGHTS_CARD or DD_WEIGHTS_DIAG */
+  int32_t precond_prec;     /* DD_PREC_FP64 or DD_PREC_FP32: storage/arithmetic of the BDDC operators */
+  int32_t schur_prec;       /* DD_PREC_FP64 or DD_PREC_DF64: Schur-complement operator arithmetic
+                               (DF64 = float pairs with error-free transformations on the FP32 pipes) */
+  int32_t flexible;         /* 1: Polak-Ribiere beta (for the FP32 preconditioner) */
+  int32_t reorth;           /* 1: residual re-orthogonalization against W (Algorithm 1, greyed line) */
+  int32_t stop_rhs_norm;    /* 1: ||r_k||/||b|| (eq. stopping_rhs); 0: ||r_k||/||r_0|| (eq. stopping_residual) */
+  int32_t maxit;            /* iteration limit per solve */
+} dd_options;
+
+typedef struct {
+  int64_t n_free;           /* free nodes (unknowns of K) */
+  int64_t n_gamma;          /* interface unknowns */
+  int32_t n_sub;            /* level-1 subdomains */
+  int32_t n_coarse;         /* level-1 coarse dofs (incl. adaptive ones) */
+  int32_t n_adaptive;       /* adaptive coarse dofs among them */
+  int32_t n_sub2;           /* level-2 subdomains (3 levels), else 0 */
+  int32_t n_coarse3;        /* level-3 coarse dofs (3 levels), else 0 */
+  int64_t device_bytes;     /* device memory held by the context */
+  double setup_seconds;     /* wall time of dd_setup */
+} dd_info_t;
+
+typedef struct {
+  int32_t iters;            /* PCG iterations of the last solve */
+  double rel_res0;          /* initial residual norm over the stopping reference */
+  double rel_res;           /* final recursive residual norm over the stopping reference */
+  int32_t recycled_k;       /* columns of W used in the solve */
+  int32_t frozen;           /* 1 once eq. harmritzstopcrit has frozen W */
+  float ms;                 /* device time of the solve (CUDA events) */
+} dd_stats;
+
+/* Defaults: 3 levels, group 4, corners+edges+faces, diag weights, no adaptivity,
+ * FP64 everywhere, not flexible, stop on ||r||/||b||, maxit 500. */
+dd_status dd_default_options(dd_options* opt /* host, out */);
+
+/* Builds the partition, globs, constraints, local factorizations, coarse levels
+ * and uploads them to the current device (Sects. 3.1-3.3). Host inputs are
+ * copied; *out is owned by the caller and released with dd_destroy. Errors:
+ * DD_INVALID_ARG (sizes), DD_SINGULAR_LOCAL, DD_OOM, DD_CUDA_ERROR. */
+dd_status dd_setup(const dd_mesh_desc* mesh /* host */, const dd_options* opt /* host */,
+                   void* stream, dd_ctx** out /* host, out */);
+void dd_destroy(dd_ctx* ctx);
+const char* dd_last_error(void);      /* message of the last failing call on this thread */
+
+/* Host-only part of dd_setup (partition, globs, constraints, local and coarse
+ * factorizations) without any device work: fills the size fields of *info and,
+ * if nodes is not NULL, the free-node index of every interface unknown
+ * ([n_gamma], host, out; call once with NULL to learn n_gamma). Needs no GPU. */
+dd_status dd_plan(const dd_mesh_desc* mesh, const dd_options* opt, dd_info_t* info /* host, out */,
+                  int64_t* nodes /* host, out, nullable */, int64_t nodes_capacity);
+
+dd_status dd_get_info(const dd_ctx* ctx, dd_info_t* info /* host, out */);
+/* Free-node index of every interface unknown, in interface order (host, out, [n_gamma]). */
+dd_status dd_interface_nodes(const dd_ctx* ctx, int64_t* nodes /* host, out */);
+
+/* ---- operator-level entry points (Sect. 3.1-3.2); all vectors device, float64 ---- */
+
+/* y = A x (eq. Sug): batched subdomain Dirichlet solves with the matrix-free Q1
+ * operator, assembled over the interface. x, y: [n_gamma]. */
+dd_status dd_schur_apply(dd_ctx* ctx, const double* x, double* y, void* stream);
+/* z = M_BDDC^{-1} r (eqs. averaging_subdomain_solves, coarse_problem, localCorr). [n_gamma]. */
+dd_status dd_precond_apply(dd_ctx* ctx, const double* r, double* z, void* stream);
+/* Reduced right-hand side b = f_G - sum_i R_i^T K_GI K_II^{-1} f_I (Sect. 3.1). f: [n_free], b: [n_gamma]. */
+dd_status dd_condense(dd_ctx* ctx, const double* f, double* b, void* stream);
+/* Full solution from interface values: x_I = K_II^{-1}(f_I - K_IG x_G). f, x: [n_free], xg: [n_gamma]. */
+dd_status dd_recover(dd_ctx* ctx, const double* f, const double* xg, double* x, void* stream);
+
+/* ---- solves ---- */
+
+/* Recycle state for a sequence of solves: deflation basis of at most k columns built
+ * by `strategy` (DD_B1..DD_B4), frozen by eq. harmritzstopcrit with freeze_tol
+ * (B3/B4). k = 0 gives plain PCG. Holds x_prev (the initial guess of the next
+ * solve, Sect. 5). Owned by the caller; release with dd_recycle_destroy. */
+dd_status dd_recycle_create(dd_ctx* ctx, int32_t k, int32_t strategy, double freeze_tol,
+                            dd_recycle** out /* host, out */);
+void dd_recycle_destroy(dd_recycle* st);
+
+/* Solves K x = f for one right-hand side (Algorithm 1 on the interface problem).
+ * f: [n_free] device. x: [n_free] device, out. st: recycle state (required); its
+ * x_prev is the initial guess (zero before the first solve) and is updated, as is W
+ * (unless frozen). rtol: stopping tolerance of the selected criterion. stats: host,
+ * out, may be NULL. Returns DD_NOT_CONVERGED after maxit (x and stats still written). */
+dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, double rtol, dd_recycle* st,
+                   dd_stats* stats, void* stream);
+
+/* Adjoint of the solve x = K^{-1} f with K = sum_e k_e K_e^0 (K symmetric):
+ * lambda = K^{-1} grad_x; grad_f = lambda; grad_coef[e] = -lambda_e^T K_e^0 x_e.
+ * grad_x, x: [n_free] device in; grad_f: [n_free] device out; grad_coef:
+ * [nz][ny][nx] device out or NULL. Uses the same preconditioner; st (may be NULL)
+ * supplies a deflation basis, which is not updated. */
+dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double* grad_f,
+                     double* grad_coef, double rtol, dd_recycle* st, dd_stats* stats, void* stream);
+
+/* Checkpoint of a recycle state: writes at most *bytes bytes to host_buf; with
+ * host_buf NULL only sets *bytes to the size needed. */
+dd_status dd_recycle_export(const dd_recycle* st, void* host_buf, size_t* bytes);
+dd_status dd_recycle_import(dd_ctx* ctx, const void* host_buf, size_t bytes, dd_recycle** out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_SOLVER_H */

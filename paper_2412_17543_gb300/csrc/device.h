@@ -1,0 +1,141 @@
+// Device-side data of the DD solver and the launch wrappers of its kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace dd {
+
+constexpr int TILE = 32;  // symmetric matrices are stored as 32x32 upper tiles
+
+// Batched symmetric matrices as upper-triangular 32x32 tiles (bi <= bj, row-major
+// over the tile pairs; each tile row-major). FP64: 1024 doubles per tile;
+// FP32: 1024 floats; DF64: 1024 hi floats followed by 1024 lo floats.
+struct SymTiles {
+  int prec = DD_PREC_FP64;
+  int count = 0;
+  int max_n = 0;
+  const int* n = nullptr;         // [count] dimension of each matrix
+  const int64_t* toff = nullptr;  // [count] first tile of each matrix
+  const void* data = nullptr;
+  int64_t ntiles = 0;
+};
+
+inline size_t tile_bytes(int prec) { return prec == DD_PREC_FP32 ? 4096 : 8192; }
+
+// Batched row-major rectangular matrices (rows x cols per item), FP64 or FP32.
+struct RectMats {
+  int prec = DD_PREC_FP64;
+  const int* rows = nullptr;
+  const int* cols = nullptr;
+  const int64_t* off = nullptr;   // element offset of each item
+  const void* data = nullptr;
+};
+
+// Level-1 geometry and Schur-complement operator (Sect. 3.1).
+struct DevMesh {
+  int nx, ny, nz, sx, sy, sz, Sx, Sy, Sz, S;
+  int fx0, fx1, fy0, fy1, fz0, fz1;
+  int NLx, NLy, NLz, NL;
+  int64_t n_free, n_gamma, n_int;
+  const int16_t* lidx;
+  const int64_t* ioff;
+  const int64_t* goff;
+  const int* gmap;
+  const int* gptr;
+  const int* gidx;
+  const int64_t* gamma_free;
+  const double* ec;     // [E][3] FP64 element factors k hy hz/(36 hx), ...
+  const df64* ec_df;    // [E][3] same as float pairs
+  SymTiles KIIinv;
+  int schur_prec;
+};
+
+// One BDDC level (Sect. 3.2): weights, constrained Neumann operator N, coarse basis
+// Phi on the interface, coarse maps. Used for level 1 and level 2.
+struct DevBDDC {
+  int S;
+  int64_t n_gamma;
+  int n_coarse;
+  int64_t n_flat;          // sum of local interface sizes
+  int64_t n_cflat;         // sum of local coarse sizes
+  const int64_t* goff;
+  const int* gmap;
+  const int* gsub;         // flat local interface position -> subdomain
+  const int* gptr;
+  const int* gidx;
+  const double* D;         // flat weights
+  SymTiles N;
+  RectMats Phi;            // nG x nc per subdomain
+  const int64_t* coff;
+  const int* cmap;         // flat local coarse -> global coarse dof
+  const int* cptr;
+  const int* cidx;
+  int prec;
+};
+
+// Level-2 extras (three-level BDDC, Sect. 3.2): interior correction and extension.
+struct DevLevel2 {
+  DevBDDC b;
+  int64_t n_int;
+  const int64_t* ioff;
+  const int* imap;          // flat interior -> level-1 coarse dof
+  const int* gam_c;         // level-2 interface -> level-1 coarse dof
+  const int64_t* gam_c64;   // same, 64-bit (gather base map)
+  SymTiles KIIinv;
+  RectMats E;               // nI x nG per group
+  const void* KC3inv;       // n3 x n3 dense, prec of b
+  int n3;
+};
+
+// Scratch buffers of the operators (device).
+struct Work {
+  double* tI;      // [n_int] level-1 interior
+  double* sI;      // [n_int]
+  double* yloc;    // [n_flat] level-1 local interface
+  double* rloc;    // [n_flat]
+  double* uloc;    // [n_flat]
+  double* gloc;    // [n_cflat]
+  double* gC;      // [n_coarse]
+  double* uC;      // [n_coarse]
+  // level 2
+  double* gI2;     // [n_int2]
+  double* u0I2;    // [n_int2]
+  double* rl2;     // [n_flat2]
+  double* r2;      // [n_gamma2]
+  double* rloc2;   // [n_flat2]
+  double* uloc2;   // [n_flat2]
+  double* gloc2;   // [n_cflat2]
+  double* g3;      // [n3]
+  double* u3;      // [n3]
+  double* z2;      // [n_gamma2]
+  double* uI2;     // [n_int2]
+  int* err;        // device error word (bounded waits)
+};
+
+enum ElemMode { ELEM_SCHUR = 0, ELEM_CONDENSE = 1, ELEM_RECOVER = 2 };
+
+// ---- launch wrappers (kernels.cu) ----
+void launch_elem_interior(const DevMesh& m, int mode, const double* xg, const double* f, double* tI, cudaStream_t s);
+void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+                           cudaStream_t s);
+void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s);
+// y[g] = (base ? base[bmap ? bmap[g] : g] : 0) + sum over copies of loc[idx[k]]
+void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
+                   const int64_t* bmap, double* y, cudaStream_t s);
+void launch_scatter_recover(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
+void launch_restrict(int64_t nflat, const int* gmap, const double* D, const double* r, double* rloc, cudaStream_t s);
+void launch_phiT(const DevBDDC& b, const double* rloc, double* gloc, cudaStream_t s);
+void launch_combine(const DevBDDC& b, const double* uloc, const double* uC, double* z, cudaStream_t s);
+void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* y, cudaStream_t s);
+// per item: out[ooff+i] = alpha * sum_j M[i][j] in[ioff+j] (+ beta_add[i]) ; transposed variant
+void launch_rect_gemv(int count, const RectMats& M, bool trans, const int64_t* in_off, const int* in_map,
+                      const double* in, const int64_t* out_off, double* out, double alpha, const double* add,
+                      cudaStream_t s);
+void launch_map_gather(int64_t n, const int* map, const double* in, double* out, cudaStream_t s);
+void launch_map_scatter(int64_t n, const int* map, const double* in, double* out, cudaStream_t s);
+
+// vector kernels for the Krylov loop (vecops in kernels.cu)
+struct Scalars;  // device-resident scalars of PCG
+}  // namespace dd

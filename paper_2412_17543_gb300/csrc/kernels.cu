@@ -1,0 +1,664 @@
+// Kernels of the Schur-complement operator and the BDDC preconditioner.
+//
+//  * k_elem_interior / k_elem_interface: the matrix-free Q1 operator of a
+//    subdomain (one CTA per subdomain). Each brick's 8x8 matrix is
+//    k_e[(hy hz/hx) K1(x)M1(x)M1 + ...] (Sect. 2, Q1 pressure), whose entry for two
+//    corners depends only on which axes they differ in, so 8 values per element
+//    are formed in shared memory and every output node sums over its <= 8 bricks.
+//  * k_symv: batched symmetric GEMV over 32x32 upper tiles (K_II^{-1}, N_i, ...),
+//    one CTA per matrix; every warp streams its tiles global->shared with
+//    cp.async.bulk (TMA bulk copies completing on an mbarrier), and uses each tile
+//    twice (row block and, off the diagonal, column block) with bank-conflict-free
+//    skewed shared-memory reads, so each stored element is read from HBM once.
+//  * gathers: deterministic interface assembly sum_i R_i^T (.) (a fixed order of
+//    the <= 8 copies of an interface dof, no atomics).
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "device.h"
+
+namespace dd {
+
+// ---------------------------------------------------------------------------
+// arithmetic policies
+// ---------------------------------------------------------------------------
+struct PolF64 {
+  using V = double;
+  using Acc = double;
+  __device__ static V from_d(double d) { return d; }
+  __device__ static double to_d(V v) { return v; }
+  __device__ static V zero() { return 0.0; }
+  __device__ static V neg(V v) { return -v; }
+  __device__ static void init(Acc& a) { a = 0.0; }
+  __device__ static void fma(Acc& a, V k, V x) { a = ::fma(k, x, a); }
+  __device__ static V get(const Acc& a) { return a; }
+  __device__ static V add(V a, V b) { return a + b; }
+  // element entry for corner pair differing on axes d (bit0 x, bit1 y, bit2 z)
+  __device__ static V entry(const V* c, int d) {
+    double sx = (d & 1) ? -1.0 : 1.0, mx = (d & 1) ? 1.0 : 2.0;
+    double sy = (d & 2) ? -1.0 : 1.0, my = (d & 2) ? 1.0 : 2.0;
+    double sz = (d & 4) ? -1.0 : 1.0, mz = (d & 4) ? 1.0 : 2.0;
+    return c[0] * (sx * my * mz) + c[1] * (mx * sy * mz) + c[2] * (mx * my * sz);
+  }
+};
+
+struct PolDF {
+  using V = df64;
+  using Acc = df64_acc;
+  __device__ static V from_d(double d) { return df64_from_double(d); }
+  __device__ static double to_d(V v) { return df64_to_double(v); }
+  __device__ static V zero() { return {0.f, 0.f}; }
+  __device__ static V neg(V v) { return df64_neg(v); }
+  __device__ static void init(Acc& a) { a = df64_acc(); }
+  __device__ static void fma(Acc& a, V k, V x) { a.fma(k, x); }
+  __device__ static V get(const Acc& a) { return a.get(); }
+  __device__ static V add(V a, V b) { return df64_add(a, b); }
+  __device__ static V entry(const V* c, int d) {
+    // the scalings are +-1, +-2, +-4: exact on both halves
+    float sx = (d & 1) ? -1.f : 1.f, mx = (d & 1) ? 1.f : 2.f;
+    float sy = (d & 2) ? -1.f : 1.f, my = (d & 2) ? 1.f : 2.f;
+    float sz = (d & 4) ? -1.f : 1.f, mz = (d & 4) ? 1.f : 2.f;
+    V a = df64_scale_pow2(c[0], sx * my * mz);
+    V b = df64_scale_pow2(c[1], mx * sy * mz);
+    V e = df64_scale_pow2(c[2], mx * my * sz);
+    return df64_add(df64_add(a, b), e);
+  }
+};
+
+struct PolF32 {
+  using V = float;
+  using Acc = float;
+  __device__ static V from_d(double d) { return (float)d; }
+  __device__ static double to_d(V v) { return (double)v; }
+  __device__ static V zero() { return 0.f; }
+  __device__ static void init(Acc& a) { a = 0.f; }
+  __device__ static void fma(Acc& a, V k, V x) { a = fmaf(k, x, a); }
+  __device__ static V get(const Acc& a) { return a; }
+  __device__ static V add(V a, V b) { return a + b; }
+};
+
+template <class P>
+__device__ __forceinline__ void load_factors(const DevMesh& m, int64_t e, typename P::V* c);
+template <>
+__device__ __forceinline__ void load_factors<PolF64>(const DevMesh& m, int64_t e, double* c) {
+  c[0] = m.ec[3 * e]; c[1] = m.ec[3 * e + 1]; c[2] = m.ec[3 * e + 2];
+}
+template <>
+__device__ __forceinline__ void load_factors<PolDF>(const DevMesh& m, int64_t e, df64* c) {
+  c[0] = m.ec_df[3 * e]; c[1] = m.ec_df[3 * e + 1]; c[2] = m.ec_df[3 * e + 2];
+}
+
+__device__ __forceinline__ int64_t free_index(const DevMesh& m, int s, int l) {
+  int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
+  int a = l % m.NLx, b = (l / m.NLx) % m.NLy, c = l / (m.NLx * m.NLy);
+  int64_t x = I * m.sx + a - m.fx0, y = J * m.sy + b - m.fy0, z = K * m.sz + c - m.fz0;
+  int64_t Nfx = m.fx1 - m.fx0, Nfy = m.fy1 - m.fy0;
+  return x + Nfx * (y + Nfy * z);
+}
+
+// Element entries of the subdomain into shared memory: kd[el*8 + d].
+template <class P>
+__device__ void build_kd(const DevMesh& m, int s, typename P::V* kd) {
+  int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
+  int NE = m.sx * m.sy * m.sz;
+  for (int t = threadIdx.x; t < NE * 8; t += blockDim.x) {
+    int el = t >> 3, d = t & 7;
+    int ea = el % m.sx, eb = (el / m.sx) % m.sy, ec = el / (m.sx * m.sy);
+    int64_t e = (int64_t)(I * m.sx + ea) + (int64_t)m.nx * ((J * m.sy + eb) + (int64_t)m.ny * (K * m.sz + ec));
+    typename P::V c[3];
+    load_factors<P>(m, e, c);
+    kd[t] = P::entry(c, d);
+  }
+}
+
+// (K_loc v)_l for local node l: sum over its bricks and their corners.
+template <class P>
+__device__ __forceinline__ typename P::V apply_node(const DevMesh& m, int l, const typename P::V* xl,
+                                                    const typename P::V* kd) {
+  int a = l % m.NLx, b = (l / m.NLx) % m.NLy, c = l / (m.NLx * m.NLy);
+  typename P::Acc acc;
+  P::init(acc);
+  for (int dz = 0; dz < 2; ++dz) {
+    int ec = c - dz;
+    if (ec < 0 || ec >= m.sz) continue;
+    for (int dy = 0; dy < 2; ++dy) {
+      int eb = b - dy;
+      if (eb < 0 || eb >= m.sy) continue;
+      for (int dx = 0; dx < 2; ++dx) {
+        int ea = a - dx;
+        if (ea < 0 || ea >= m.sx) continue;
+        int el = ea + m.sx * (eb + m.sy * ec);
+        int p = dx | (dy << 1) | (dz << 2);
+        const typename P::V* k = kd + el * 8;
+        int base = ea + m.NLx * (eb + m.NLy * ec);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int lq = base + (q & 1) + m.NLx * (((q >> 1) & 1) + m.NLy * (q >> 2));
+          P::fma(acc, k[p ^ q], xl[lq]);
+        }
+      }
+    }
+  }
+  return P::get(acc);
+}
+
+// t_I = cf * f_I + ck * (K [0; x_G])_I    (SCHUR: cf=0, ck=1; CONDENSE: cf=1, ck=0; RECOVER: cf=1, ck=-1)
+template <class P>
+__global__ void __launch_bounds__(256) k_elem_interior(DevMesh m, int mode, const double* __restrict__ xg,
+                                                       const double* __restrict__ f, double* __restrict__ tI) {
+  using V = typename P::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xl = reinterpret_cast<V*>(smem_raw);
+  V* kd = xl + m.NL;
+  const int s = blockIdx.x;
+  const int16_t* code = m.lidx + (size_t)s * m.NL;
+  const bool need_k = (mode != ELEM_CONDENSE);
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    int cd = code[l];
+    V v = P::zero();
+    if (need_k && cd < 0 && cd != INT16_MIN) v = P::from_d(xg[m.gmap[m.goff[s] + (-1 - cd)]]);
+    xl[l] = v;
+  }
+  if (need_k) build_kd<P>(m, s, kd);
+  __syncthreads();
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    int cd = code[l];
+    if (cd < 0) continue;
+    double t = 0.0;
+    if (need_k) t = P::to_d(apply_node<P>(m, l, xl, kd));
+    if (mode == ELEM_CONDENSE) t = f[free_index(m, s, l)];
+    else if (mode == ELEM_RECOVER) t = f[free_index(m, s, l)] - t;
+    tI[m.ioff[s] + cd] = t;
+  }
+}
+
+// y_G = (K [-s_I; x_G])_G  (SCHUR: x_G given; CONDENSE: x_G = 0)
+template <class P>
+__global__ void __launch_bounds__(256) k_elem_interface(DevMesh m, int mode, const double* __restrict__ xg,
+                                                        const double* __restrict__ sI, double* __restrict__ yloc) {
+  using V = typename P::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xl = reinterpret_cast<V*>(smem_raw);
+  V* kd = xl + m.NL;
+  const int s = blockIdx.x;
+  const int16_t* code = m.lidx + (size_t)s * m.NL;
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    int cd = code[l];
+    V v = P::zero();
+    if (cd >= 0) v = P::from_d(-sI[m.ioff[s] + cd]);
+    else if (cd != INT16_MIN && mode == ELEM_SCHUR) v = P::from_d(xg[m.gmap[m.goff[s] + (-1 - cd)]]);
+    xl[l] = v;
+  }
+  build_kd<P>(m, s, kd);
+  __syncthreads();
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    int cd = code[l];
+    if (cd >= 0 || cd == INT16_MIN) continue;
+    yloc[m.goff[s] + (-1 - cd)] = P::to_d(apply_node<P>(m, l, xl, kd));
+  }
+}
+
+void launch_elem_interior(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
+                          cudaStream_t s) {
+  int NE = m.sx * m.sy * m.sz;
+  size_t smem = (size_t)(m.NL + NE * 8) * 8;
+  if (m.schur_prec == DD_PREC_DF64)
+    k_elem_interior<PolDF><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+  else
+    k_elem_interior<PolF64><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+  DD_CHECK_LAUNCH();
+}
+
+void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+                           cudaStream_t s) {
+  int NE = m.sx * m.sy * m.sz;
+  size_t smem = (size_t)(m.NL + NE * 8) * 8;
+  if (m.schur_prec == DD_PREC_DF64)
+    k_elem_interface<PolDF><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+  else
+    k_elem_interface<PolF64><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+  DD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr long long WAIT_LIMIT = 1ll << 24;  // try_wait attempts before giving up (seconds)
+
+// bounded wait on an mbarrier phase; returns false (and raises *err) on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, (int)DD_TIMEOUT);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// batched symmetric tile GEMV
+// ---------------------------------------------------------------------------
+template <int PREC>
+struct TileOps;
+
+template <>
+struct TileOps<DD_PREC_FP64> {
+  using P = PolF64;
+  using V = double;
+  static constexpr int BYTES = 8192;
+  __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
+    const double* A = reinterpret_cast<const double*>(T);
+    double acc = 0.0;
+#pragma unroll 8
+    for (int cc = 0; cc < 32; ++cc) {
+      int c = (cc + l) & 31;
+      acc = ::fma(A[l * 32 + c], tv[c], acc);
+    }
+    return acc;
+  }
+  __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
+    const double* A = reinterpret_cast<const double*>(T);
+    double acc = 0.0;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) acc = ::fma(A[r * 32 + l], tv[r], acc);
+    return acc;
+  }
+};
+
+template <>
+struct TileOps<DD_PREC_FP32> {
+  using P = PolF32;
+  using V = float;
+  static constexpr int BYTES = 4096;
+  __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
+    const float* A = reinterpret_cast<const float*>(T);
+    float acc = 0.f;
+#pragma unroll 8
+    for (int cc = 0; cc < 32; ++cc) {
+      int c = (cc + l) & 31;
+      acc = fmaf(A[l * 32 + c], tv[c], acc);
+    }
+    return acc;
+  }
+  __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
+    const float* A = reinterpret_cast<const float*>(T);
+    float acc = 0.f;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) acc = fmaf(A[r * 32 + l], tv[r], acc);
+    return acc;
+  }
+};
+
+template <>
+struct TileOps<DD_PREC_DF64> {
+  using P = PolDF;
+  using V = df64;
+  static constexpr int BYTES = 8192;
+  __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
+    const float* Ah = reinterpret_cast<const float*>(T);
+    const float* Al = Ah + 1024;
+    df64_acc acc;
+#pragma unroll 4
+    for (int cc = 0; cc < 32; ++cc) {
+      int c = (cc + l) & 31;
+      acc.fma(df64{Ah[l * 32 + c], Al[l * 32 + c]}, tv[c]);
+    }
+    return acc.get();
+  }
+  __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
+    const float* Ah = reinterpret_cast<const float*>(T);
+    const float* Al = Ah + 1024;
+    df64_acc acc;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) acc.fma(df64{Ah[r * 32 + l], Al[r * 32 + l]}, tv[r]);
+    return acc.get();
+  }
+};
+
+constexpr int SYMV_WARPS = 4;
+constexpr int SYMV_SLOTS = 2;
+
+__device__ __forceinline__ void tile_coords(int t, int nb, int& bi, int& bj) {
+  int b = 0, start = 0;
+  while (b < nb && t >= start + (nb - b)) {
+    start += nb - b;
+    ++b;
+  }
+  bi = b;
+  bj = b + (t - start);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int64_t* __restrict__ voff,
+                                                          const double* __restrict__ in,
+                                                          double* __restrict__ out, int* err) {
+  using Ops = TileOps<PREC>;
+  using P = typename Ops::P;
+  using V = typename Ops::V;
+  constexpr int TB = Ops::BYTES;
+  extern __shared__ __align__(128) unsigned char smem_symv[];
+  unsigned char* smem_raw = smem_symv;
+  const int m = blockIdx.x;
+  const int n = A.n[m];
+  const int nb = (n + 31) / 32;
+  const int npad = nb * 32;
+  const int maxpad = ((A.max_n + 31) / 32) * 32;
+  unsigned char* slots = smem_raw;                                            // [W][SLOTS][TB]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(slots + SYMV_WARPS * SYMV_SLOTS * TB);
+  V* tv = reinterpret_cast<V*>(bars + SYMV_WARPS * SYMV_SLOTS);              // [maxpad]
+  V* part = tv + maxpad;                                                      // [W][maxpad]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t vo = voff[m];
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) tv[i] = (i < n) ? P::from_d(in[vo + i]) : P::from_d(0.0);
+  for (int i = threadIdx.x; i < SYMV_WARPS * npad; i += blockDim.x) part[(i / npad) * maxpad + (i % npad)] = P::from_d(0.0);
+  if (lane == 0)
+    for (int k = 0; k < SYMV_SLOTS; ++k) mbar_init(&bars[warp * SYMV_SLOTS + k], 1);
+  fence_mbar_init();
+  __syncthreads();
+
+  const int ntl = nb * (nb + 1) / 2;
+  const int mine = (warp < ntl) ? (ntl - warp + SYMV_WARPS - 1) / SYMV_WARPS : 0;
+  const unsigned char* gt = reinterpret_cast<const unsigned char*>(A.data) + (size_t)A.toff[m] * TB;
+  unsigned char* wslots = slots + (size_t)warp * SYMV_SLOTS * TB;
+  uint64_t* wbars = bars + warp * SYMV_SLOTS;
+  if (lane == 0) {
+    for (int k = 0; k < SYMV_SLOTS && k < mine; ++k) {
+      int t = warp + k * SYMV_WARPS;
+      mbar_arrive_expect_tx(&wbars[k], TB);
+      bulk_g2s(wslots + (size_t)k * TB, gt + (size_t)t * TB, TB, &wbars[k]);
+    }
+  }
+  V* mypart = part + warp * maxpad;
+  bool ok = true;
+  int k = 0;
+  for (; k < mine; ++k) {
+    const int slot = k % SYMV_SLOTS;
+    if (!mbar_wait_bounded(&wbars[slot], (uint32_t)((k / SYMV_SLOTS) & 1), err)) {
+      ok = false;
+      break;
+    }
+    const int t = warp + k * SYMV_WARPS;
+    int bi, bj;
+    tile_coords(t, nb, bi, bj);
+    const unsigned char* T = wslots + (size_t)slot * TB;
+    V r = Ops::row_part(T, tv + bj * 32, lane);
+    mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
+    if (bi != bj) {
+      V c = Ops::col_part(T, tv + bi * 32, lane);
+      mypart[bj * 32 + lane] = P::add(mypart[bj * 32 + lane], c);
+    }
+    __syncwarp();
+    if (lane == 0 && k + SYMV_SLOTS < mine) {
+      fence_proxy_async();
+      int tn = warp + (k + SYMV_SLOTS) * SYMV_WARPS;
+      mbar_arrive_expect_tx(&wbars[slot], TB);
+      bulk_g2s(wslots + (size_t)slot * TB, gt + (size_t)tn * TB, TB, &wbars[slot]);
+    }
+  }
+  if (!ok) {
+    // drain the copies this warp still has in flight (bounded), then leave
+    for (int kk = k; kk < mine && kk < k + SYMV_SLOTS; ++kk)
+      mbar_wait_bounded(&wbars[kk % SYMV_SLOTS], (uint32_t)((kk / SYMV_SLOTS) & 1), nullptr);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    V s = part[i];
+    for (int w = 1; w < SYMV_WARPS; ++w) s = P::add(s, part[w * maxpad + i]);
+    out[vo + i] = P::to_d(s);
+  }
+}
+
+void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s) {
+  if (A.count == 0) return;
+  int maxpad = ((A.max_n + 31) / 32) * 32;
+  size_t vb = (A.prec == DD_PREC_FP32) ? 4 : 8;
+  size_t tb = tile_bytes(A.prec);
+  size_t smem = SYMV_WARPS * SYMV_SLOTS * tb + SYMV_WARPS * SYMV_SLOTS * 8 + (size_t)maxpad * vb * (1 + SYMV_WARPS);
+  dim3 grid(A.count), block(SYMV_WARPS * 32);
+  switch (A.prec) {
+    case DD_PREC_FP64:
+      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_symv<DD_PREC_FP64><<<grid, block, smem, s>>>(A, voff, in, out, err);
+      break;
+    case DD_PREC_FP32:
+      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_symv<DD_PREC_FP32><<<grid, block, smem, s>>>(A, voff, in, out, err);
+      break;
+    default:
+      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_symv<DD_PREC_DF64><<<grid, block, smem, s>>>(A, voff, in, out, err);
+  }
+  DD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// gathers, scatters, BDDC pieces
+// ---------------------------------------------------------------------------
+__global__ void k_gather(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
+                         const double* __restrict__ loc, const double* __restrict__ base,
+                         const int64_t* __restrict__ bmap, double* __restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (base) s = base[bmap ? bmap[g] : g];
+    for (int k = ptr[g]; k < ptr[g + 1]; ++k) s += loc[idx[k]];
+    y[g] = s;
+  }
+}
+
+static int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
+                   const int64_t* bmap, double* y, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, ptr, idx, loc, base, bmap, y);
+  DD_CHECK_LAUNCH();
+}
+
+__global__ void k_scatter_recover(DevMesh m, const double* __restrict__ xg, const double* __restrict__ sI,
+                                  double* __restrict__ x) {
+  const int s = blockIdx.x;
+  const int16_t* code = m.lidx + (size_t)s * m.NL;
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    int cd = code[l];
+    if (cd >= 0) x[free_index(m, s, l)] = sI[m.ioff[s] + cd];
+  }
+  // interface values: each global interface dof written by its first copy's subdomain
+  for (int j = threadIdx.x; j < (int)(m.goff[s + 1] - m.goff[s]); j += blockDim.x) {
+    int64_t k = m.goff[s] + j;
+    int g = m.gmap[k];
+    if (m.gidx[m.gptr[g]] == (int)k) x[m.gamma_free[g]] = xg[g];
+  }
+}
+
+void launch_scatter_recover(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s) {
+  k_scatter_recover<<<m.S, 256, 0, s>>>(m, xg, sI, x);
+  DD_CHECK_LAUNCH();
+}
+
+__global__ void k_restrict(int64_t nflat, const int* __restrict__ gmap, const double* __restrict__ D,
+                           const double* __restrict__ r, double* __restrict__ rloc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nflat; k += (int64_t)gridDim.x * blockDim.x)
+    rloc[k] = D[k] * r[gmap[k]];
+}
+
+void launch_restrict(int64_t nflat, const int* gmap, const double* D, const double* r, double* rloc,
+                     cudaStream_t s) {
+  if (nflat == 0) return;
+  k_restrict<<<grid_for(nflat, 256), 256, 0, s>>>(nflat, gmap, D, r, rloc);
+  DD_CHECK_LAUNCH();
+}
+
+template <class T>
+__device__ __forceinline__ double ldv(const T* p, int64_t i) {
+  return (double)p[i];
+}
+
+// gloc[coff[s]+c] = sum_j Phi_s[j][c] rloc[goff[s]+j]   (coarse right-hand side, eq. coarse_problem)
+template <class T>
+__global__ void k_phiT(DevBDDC b, const double* __restrict__ rloc, double* __restrict__ gloc) {
+  const int s = blockIdx.x;
+  const int nG = (int)(b.goff[s + 1] - b.goff[s]);
+  const int nc = (int)(b.coff[s + 1] - b.coff[s]);
+  const T* Phi = reinterpret_cast<const T*>(b.Phi.data) + b.Phi.off[s];
+  const double* r = rloc + b.goff[s];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < nG; j += 32) acc += ldv(Phi, (int64_t)j * nc + c) * r[j];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) gloc[b.coff[s] + c] = acc;
+  }
+}
+
+void launch_phiT(const DevBDDC& b, const double* rloc, double* gloc, cudaStream_t s) {
+  if (b.Phi.prec == DD_PREC_FP32)
+    k_phiT<float><<<b.S, 256, 0, s>>>(b, rloc, gloc);
+  else
+    k_phiT<double><<<b.S, 256, 0, s>>>(b, rloc, gloc);
+  DD_CHECK_LAUNCH();
+}
+
+// z[g] = sum over copies k=(s,j): D[k] (uloc[k] + Phi_s[j,:] . uC[cmap_s])   (eq. averaging_subdomain_solves)
+template <class T>
+__global__ void k_combine(DevBDDC b, const double* __restrict__ uloc, const double* __restrict__ uC,
+                          double* __restrict__ z) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < b.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int t = b.gptr[g]; t < b.gptr[g + 1]; ++t) {
+      int k = b.gidx[t];
+      int s = b.gsub[k];
+      int j = (int)(k - b.goff[s]);
+      int nc = (int)(b.coff[s + 1] - b.coff[s]);
+      const T* row = reinterpret_cast<const T*>(b.Phi.data) + b.Phi.off[s] + (int64_t)j * nc;
+      const int* cm = b.cmap + b.coff[s];
+      double v = uloc[k];
+      for (int c = 0; c < nc; ++c) v += ldv(row, c) * uC[cm[c]];
+      acc += b.D[k] * v;
+    }
+    z[g] = acc;
+  }
+}
+
+void launch_combine(const DevBDDC& b, const double* uloc, const double* uC, double* z, cudaStream_t s) {
+  if (b.Phi.prec == DD_PREC_FP32)
+    k_combine<float><<<grid_for(b.n_gamma, 128), 128, 0, s>>>(b, uloc, uC, z);
+  else
+    k_combine<double><<<grid_for(b.n_gamma, 128), 128, 0, s>>>(b, uloc, uC, z);
+  DD_CHECK_LAUNCH();
+}
+
+// y = A x for a dense row-major n x n matrix (warp per row)
+template <class T>
+__global__ void k_dense_gemv(int n, const T* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    const T* a = A + (int64_t)row * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += (double)a[j] * x[j];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = acc;
+  }
+}
+
+void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* y, cudaStream_t s) {
+  if (n == 0) return;
+  int blocks = (n * 32 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (prec == DD_PREC_FP32)
+    k_dense_gemv<float><<<blocks, 256, 0, s>>>(n, (const float*)A, x, y);
+  else
+    k_dense_gemv<double><<<blocks, 256, 0, s>>>(n, (const double*)A, x, y);
+  DD_CHECK_LAUNCH();
+}
+
+// Batched rectangular GEMV: for item m, y = alpha * M x (+ add) or y = alpha * M^T x (+ add).
+// Input element j of item m: in[in_map ? in_map[in_off[m]+j] : in_off[m]+j].
+template <class T>
+__global__ void k_rect_gemv(RectMats M, bool trans, const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
+                            const double* __restrict__ in, const int64_t* __restrict__ out_off,
+                            double* __restrict__ out, double alpha, const double* __restrict__ add) {
+  const int m = blockIdx.x;
+  const int R = M.rows[m], C = M.cols[m];
+  const T* A = reinterpret_cast<const T*>(M.data) + M.off[m];
+  const int64_t io = in_off[m], oo = out_off[m];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nout = trans ? C : R, nin = trans ? R : C;
+  for (int o = warp; o < nout; o += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < nin; j += 32) {
+      double a = trans ? (double)A[(int64_t)j * C + o] : (double)A[(int64_t)o * C + j];
+      double xv = in[in_map ? in_map[io + j] : io + j];
+      acc += a * xv;
+    }
+    for (int sft = 16; sft; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
+    if (lane == 0) out[oo + o] = alpha * acc + (add ? add[oo + o] : 0.0);
+  }
+}
+
+void launch_rect_gemv(int count, const RectMats& M, bool trans, const int64_t* in_off, const int* in_map,
+                      const double* in, const int64_t* out_off, double* out, double alpha, const double* add,
+                      cudaStream_t s) {
+  if (count == 0) return;
+  if (M.prec == DD_PREC_FP32)
+    k_rect_gemv<float><<<count, 256, 0, s>>>(M, trans, in_off, in_map, in, out_off, out, alpha, add);
+  else
+    k_rect_gemv<double><<<count, 256, 0, s>>>(M, trans, in_off, in_map, in, out_off, out, alpha, add);
+  DD_CHECK_LAUNCH();
+}
+
+__global__ void k_map_gather(int64_t n, const int* __restrict__ map, const double* __restrict__ in,
+                             double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[map[i]];
+}
+__global__ void k_map_scatter(int64_t n, const int* __restrict__ map, const double* __restrict__ in,
+                              double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[map[i]] = in[i];
+}
+void launch_map_gather(int64_t n, const int* map, const double* in, double* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_map_gather<<<grid_for(n, 256), 256, 0, s>>>(n, map, in, out);
+  DD_CHECK_LAUNCH();
+}
+void launch_map_scatter(int64_t n, const int* map, const double* in, double* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_map_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, map, in, out);
+  DD_CHECK_LAUNCH();
+}
+
+}  // namespace dd

@@ -1,0 +1,515 @@
+// Host-side setup (Sect. 3): partition of a tensor-product Q1 mesh into blocks,
+// interior/interface split, globs and coarse dofs, dense local factorizations,
+// coarse levels. Runs once per matrix; everything per subdomain is independent
+// and parallelised with OpenMP.
+#include "setup.h"
+
+#include <omp.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <map>
+#include <string>
+
+#include "common.h"
+#include "hostla.h"
+
+namespace dd {
+
+namespace {
+
+enum { GLOB_FACE = 0, GLOB_EDGE = 1, GLOB_CORNER = 2 };
+
+int glob_kind(int mult) { return mult <= 2 ? GLOB_FACE : (mult < 8 ? GLOB_EDGE : GLOB_CORNER); }
+
+struct Globs {
+  std::vector<std::vector<int>> subs;     // sharing set (sorted subdomain ids)
+  std::vector<std::vector<int64_t>> dofs; // global interface dofs (ascending)
+  std::vector<int> kind;
+};
+
+// Globs = interface dofs grouped by their sharing set, ordered by first dof (Sect. 3.2).
+template <class F>
+Globs make_globs(int64_t n_gamma, F sharing) {
+  Globs gl;
+  std::map<std::vector<int>, int> id;
+  std::vector<int> s;
+  for (int64_t g = 0; g < n_gamma; ++g) {
+    s.clear();
+    sharing(g, s);
+    auto it = id.find(s);
+    int k;
+    if (it == id.end()) {
+      k = (int)gl.subs.size();
+      id.emplace(s, k);
+      gl.subs.push_back(s);
+      gl.dofs.emplace_back();
+      gl.kind.push_back(glob_kind((int)s.size()));
+    } else {
+      k = it->second;
+    }
+    gl.dofs[k].push_back(g);
+  }
+  return gl;
+}
+
+struct CoarseDof {
+  int glob;
+  std::vector<double> row;  // over the glob's dofs
+};
+
+// Constraint rows of subdomain s (nc_s x nG_s) from the coarse dofs touching it.
+void subdomain_constraints(const Level& L, int s, const Globs& gl, const std::vector<CoarseDof>& cd,
+                           const std::vector<std::vector<int>>& cdofs_of_sub, std::vector<double>& C) {
+  int nG = (int)(L.goff[s + 1] - L.goff[s]);
+  const int* gm = L.gmap.data() + L.goff[s];
+  const auto& mine = cdofs_of_sub[s];
+  C.assign((size_t)mine.size() * nG, 0.0);
+  for (size_t r = 0; r < mine.size(); ++r) {
+    const CoarseDof& c = cd[mine[r]];
+    const auto& dofs = gl.dofs[c.glob];
+    for (size_t t = 0; t < dofs.size(); ++t) {
+      int pos = (int)(std::lower_bound(gm, gm + nG, (int)dofs[t]) - gm);
+      if (pos >= nG || gm[pos] != dofs[t]) throw Error(DD_INVALID_ARG, "glob dof not in subdomain interface");
+      C[r * nG + pos] = c.row[t];
+    }
+  }
+}
+
+// Dense pipeline of one subdomain: K_II^{-1}, S = K_GG - K_GI K_II^{-1} K_IG, and with
+// S^ = S + rho C^T C (equal to S on ker C): N = S^{-1} - S^{-1}C^T (C S^{-1} C^T)^{-1} C S^{-1},
+// Phi = S^{-1} C^T (C S^{-1} C^T)^{-1}, KC = Phi^T S Phi = (C S^{-1} C^T)^{-1} - rho I.
+bool dense_sub(int nloc, const double* K, const std::vector<int>& I, const std::vector<int>& G,
+               const std::vector<double>& C, int nc, bool needE, DenseSub& out) {
+  int nI = (int)I.size(), nG = (int)G.size();
+  out.nI = nI;
+  out.nG = nG;
+  out.nc = nc;
+  std::vector<double> KII((size_t)nI * nI), KIG((size_t)nI * nG), S((size_t)nG * nG);
+  for (int a = 0; a < nI; ++a) {
+    for (int b = 0; b < nI; ++b) KII[(size_t)a * nI + b] = K[(size_t)I[a] * nloc + I[b]];
+    for (int b = 0; b < nG; ++b) KIG[(size_t)a * nG + b] = K[(size_t)I[a] * nloc + G[b]];
+  }
+  for (int a = 0; a < nG; ++a)
+    for (int b = 0; b < nG; ++b) S[(size_t)a * nG + b] = K[(size_t)G[a] * nloc + G[b]];
+  if (nI > 0) {
+    if (!la::cholesky(nI, KII.data())) return false;
+    std::vector<double> Linv((size_t)nI * nI);
+    la::tri_inv_lower(nI, KII.data(), Linv.data());
+    std::vector<double> LT((size_t)nI * nI);
+    for (int a = 0; a < nI; ++a)
+      for (int b = 0; b < nI; ++b) LT[(size_t)a * nI + b] = Linv[(size_t)b * nI + a];
+    out.KIIinv.assign((size_t)nI * nI, 0.0);
+    for (int a = 0; a < nI; ++a)
+      for (int b = 0; b <= a; ++b) {
+        const double* ra = LT.data() + (size_t)a * nI;
+        const double* rb = LT.data() + (size_t)b * nI;
+        double s = 0.0;
+        for (int k = a; k < nI; ++k) s += ra[k] * rb[k];
+        out.KIIinv[(size_t)a * nI + b] = s;
+        out.KIIinv[(size_t)b * nI + a] = s;
+      }
+    std::vector<double> X((size_t)nI * nG), XT((size_t)nG * nI);
+    la::trmm_lower(nI, nG, Linv.data(), KIG.data(), X.data());
+    for (int a = 0; a < nI; ++a)
+      for (int b = 0; b < nG; ++b) XT[(size_t)b * nI + a] = X[(size_t)a * nG + b];
+    la::gemm_nt(nG, nG, nI, -1.0, XT.data(), XT.data(), 1.0, S.data());
+    if (needE) {
+      out.E.resize((size_t)nI * nG);
+      la::gemm_nn(nI, nG, nI, LT.data(), X.data(), out.E.data());
+    }
+  }
+  for (int a = 0; a < nG; ++a)  // symmetrize
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (S[(size_t)a * nG + b] + S[(size_t)b * nG + a]);
+      S[(size_t)a * nG + b] = S[(size_t)b * nG + a] = v;
+    }
+  std::vector<double> Sh = S;
+  double rho = 0.0;
+  if (nc > 0) {
+    double trS = 0.0, trC = 0.0;
+    for (int a = 0; a < nG; ++a) trS += S[(size_t)a * nG + a];
+    for (size_t t = 0; t < C.size(); ++t) trC += C[t] * C[t];
+    rho = trS / std::max(trC, 1e-300);
+    for (int r = 0; r < nc; ++r) {
+      const double* cr = C.data() + (size_t)r * nG;
+      for (int a = 0; a < nG; ++a) {
+        if (cr[a] == 0.0) continue;
+        double ca = rho * cr[a];
+        for (int b = 0; b < nG; ++b) Sh[(size_t)a * nG + b] += ca * cr[b];
+      }
+    }
+  }
+  std::vector<double> Shinv((size_t)nG * nG);
+  if (!la::spd_inverse(nG, Sh.data(), Shinv.data())) return false;
+  if (nc == 0) {
+    out.N = Shinv;
+    return true;
+  }
+  std::vector<double> Xc((size_t)nG * nc), Y((size_t)nc * nc), Yinv((size_t)nc * nc);
+  la::gemm_nt(nG, nc, nG, 1.0, Shinv.data(), C.data(), 0.0, Xc.data());  // S^{-1} C^T
+  la::gemm_nn(nc, nc, nG, C.data(), Xc.data(), Y.data());                // C S^{-1} C^T
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (Y[(size_t)a * nc + b] + Y[(size_t)b * nc + a]);
+      Y[(size_t)a * nc + b] = Y[(size_t)b * nc + a] = v;
+    }
+  if (!la::spd_inverse(nc, Y.data(), Yinv.data())) return false;
+  out.Phi.resize((size_t)nG * nc);
+  la::gemm_nn(nG, nc, nc, Xc.data(), Yinv.data(), out.Phi.data());
+  out.N = Shinv;
+  la::gemm_nt(nG, nG, nc, -1.0, out.Phi.data(), Xc.data(), 1.0, out.N.data());
+  for (int a = 0; a < nG; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (out.N[(size_t)a * nG + b] + out.N[(size_t)b * nG + a]);
+      out.N[(size_t)a * nG + b] = out.N[(size_t)b * nG + a] = v;
+    }
+  out.KC = Yinv;
+  for (int a = 0; a < nc; ++a) out.KC[(size_t)a * nc + a] -= rho;
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (out.KC[(size_t)a * nc + b] + out.KC[(size_t)b * nc + a]);
+      out.KC[(size_t)a * nc + b] = out.KC[(size_t)b * nc + a] = v;
+    }
+  return true;
+}
+
+// CSR listing, for every global dof, the flat local positions of its copies (subdomains ascending).
+void build_copy_csr(int64_t n, const std::vector<int64_t>& off, const std::vector<int>& map, std::vector<int>& ptr,
+                    std::vector<int>& idx) {
+  ptr.assign(n + 1, 0);
+  for (size_t k = 0; k < map.size(); ++k) ptr[map[k] + 1]++;
+  for (int64_t g = 0; g < n; ++g) ptr[g + 1] += ptr[g];
+  idx.assign(map.size(), 0);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t k = 0; k < map.size(); ++k) idx[fill[map[k]]++] = (int)k;  // k ascending => subdomains ascending
+  (void)off;
+}
+
+// Select coarse dofs from globs by kind (Sect. 3.2: corners = point values, edges/faces = averages).
+std::vector<CoarseDof> select_coarse(const Globs& gl, bool corners, bool edges, bool faces) {
+  std::vector<CoarseDof> cd;
+  for (size_t g = 0; g < gl.kind.size(); ++g) {
+    int k = gl.kind[g];
+    if ((k == GLOB_CORNER && corners) || (k == GLOB_EDGE && edges) || (k == GLOB_FACE && faces)) {
+      size_t m = gl.dofs[g].size();
+      cd.push_back({(int)g, std::vector<double>(m, 1.0 / (double)m)});
+    }
+  }
+  return cd;
+}
+
+// Weights, coarse maps and dense pipelines of a level whose subdomain matrices are given.
+void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, int weights,
+                  const std::vector<std::vector<double>>& Kloc, const std::vector<int>& nloc,
+                  const std::vector<std::vector<int>>& Iloc, const std::vector<std::vector<int>>& Gloc, bool needE,
+                  const char* what) {
+  L.n_coarse = (int)cd.size();
+  std::vector<std::vector<int>> cdofs_of_sub(L.S);
+  for (size_t c = 0; c < cd.size(); ++c)
+    for (int s : gl.subs[cd[c].glob]) cdofs_of_sub[s].push_back((int)c);
+  L.sub.assign(L.S, DenseSub());
+  // weights
+  std::vector<double> dsum(L.n_gamma, 0.0);
+  if (weights == DD_WEIGHTS_DIAG) {
+    for (int s = 0; s < L.S; ++s)
+      for (size_t j = 0; j < Gloc[s].size(); ++j) {
+        int p = Gloc[s][j];
+        dsum[L.gmap[L.goff[s] + j]] += Kloc[s][(size_t)p * nloc[s] + p];
+      }
+  }
+  int failed = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < L.S; ++s) {
+    std::vector<double> C;
+    subdomain_constraints(L, s, gl, cd, cdofs_of_sub, C);
+    DenseSub& ds = L.sub[s];
+    bool ok = dense_sub(nloc[s], Kloc[s].data(), Iloc[s], Gloc[s], C, (int)cdofs_of_sub[s].size(), needE, ds);
+    if (!ok) {
+#pragma omp critical
+      failed = s;
+    }
+    ds.cmap = cdofs_of_sub[s];
+    ds.D.resize(Gloc[s].size());
+    for (size_t j = 0; j < Gloc[s].size(); ++j) {
+      int g = L.gmap[L.goff[s] + j];
+      if (weights == DD_WEIGHTS_DIAG) {
+        int p = Gloc[s][j];
+        ds.D[j] = Kloc[s][(size_t)p * nloc[s] + p] / dsum[g];
+      } else {
+        ds.D[j] = 0.0;  // filled below (needs multiplicities)
+      }
+    }
+  }
+  if (failed >= 0)
+    throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": non-positive pivot in subdomain " + std::to_string(failed));
+  if (weights != DD_WEIGHTS_DIAG) {
+    for (int s = 0; s < L.S; ++s)
+      for (size_t j = 0; j < L.sub[s].D.size(); ++j) {
+        int g = L.gmap[L.goff[s] + j];
+        L.sub[s].D[j] = 1.0 / (double)(L.gptr[g + 1] - L.gptr[g]);
+      }
+  }
+  // coarse copy CSR
+  L.coff.assign(L.S + 1, 0);
+  for (int s = 0; s < L.S; ++s) L.coff[s + 1] = L.coff[s] + L.sub[s].nc;
+  std::vector<int> cflat(L.coff[L.S]);
+  for (int s = 0; s < L.S; ++s)
+    for (int c = 0; c < L.sub[s].nc; ++c) cflat[L.coff[s] + c] = L.sub[s].cmap[c];
+  build_copy_csr(L.n_coarse, L.coff, cflat, L.cptr, L.cidx);
+}
+
+std::vector<double> assemble_coarse(const Level& L) {
+  size_t n = L.n_coarse;
+  std::vector<double> KC(n * n, 0.0);
+  for (int s = 0; s < L.S; ++s) {
+    const DenseSub& d = L.sub[s];
+    for (int a = 0; a < d.nc; ++a)
+      for (int b = 0; b < d.nc; ++b) KC[(size_t)d.cmap[a] * n + d.cmap[b]] += d.KC[(size_t)a * d.nc + b];
+  }
+  return KC;
+}
+
+}  // namespace
+
+void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& H) {
+  auto t0 = std::chrono::steady_clock::now();
+  DD_REQUIRE(md.nx >= 1 && md.ny >= 1 && md.nz >= 1, "mesh sizes must be positive");
+  DD_REQUIRE(md.xc && md.yc && md.zc, "coordinate arrays required");
+  DD_REQUIRE(md.sub_x >= 1 && md.sub_y >= 1 && md.sub_z >= 1 && md.sub_x <= 8 && md.sub_y <= 8 && md.sub_z <= 8,
+             "subdomain sizes must be in [1, 8]");
+  DD_REQUIRE(md.nx % md.sub_x == 0 && md.ny % md.sub_y == 0 && md.nz % md.sub_z == 0,
+             "subdomain sizes must divide the mesh");
+  DD_REQUIRE((md.dirichlet_faces & 63u) != 0, "at least one Dirichlet face is required (SPD matrix)");
+  DD_REQUIRE(opt.levels == 2 || opt.levels == 3, "levels must be 2 or 3");
+  DD_REQUIRE(opt.weights == DD_WEIGHTS_CARD || opt.weights == DD_WEIGHTS_DIAG, "weights must be card or diag");
+  Mesh1& M = H.mesh;
+  M.nx = md.nx; M.ny = md.ny; M.nz = md.nz;
+  M.sx = md.sub_x; M.sy = md.sub_y; M.sz = md.sub_z;
+  M.Sx = M.nx / M.sx; M.Sy = M.ny / M.sy; M.Sz = M.nz / M.sz;
+  M.S = M.Sx * M.Sy * M.Sz;
+  uint32_t df = md.dirichlet_faces;
+  M.fx0 = (df & DD_FACE_X0) ? 1 : 0; M.fx1 = (df & DD_FACE_X1) ? M.nx : M.nx + 1;
+  M.fy0 = (df & DD_FACE_Y0) ? 1 : 0; M.fy1 = (df & DD_FACE_Y1) ? M.ny : M.ny + 1;
+  M.fz0 = (df & DD_FACE_Z0) ? 1 : 0; M.fz1 = (df & DD_FACE_Z1) ? M.nz : M.nz + 1;
+  const int64_t Nfx = M.fx1 - M.fx0, Nfy = M.fy1 - M.fy0, Nfz = M.fz1 - M.fz0;
+  DD_REQUIRE(Nfx > 0 && Nfy > 0 && Nfz > 0, "no free nodes");
+  M.n_free = Nfx * Nfy * Nfz;
+  M.NLx = M.sx + 1; M.NLy = M.sy + 1; M.NLz = M.sz + 1;
+  M.NL = M.NLx * M.NLy * M.NLz;
+  M.xc.assign(md.xc, md.xc + M.nx + 1);
+  M.yc.assign(md.yc, md.yc + M.ny + 1);
+  M.zc.assign(md.zc, md.zc + M.nz + 1);
+  for (int i = 0; i < M.nx; ++i) DD_REQUIRE(M.xc[i + 1] > M.xc[i], "x coordinates must increase");
+  for (int i = 0; i < M.ny; ++i) DD_REQUIRE(M.yc[i + 1] > M.yc[i], "y coordinates must increase");
+  for (int i = 0; i < M.nz; ++i) DD_REQUIRE(M.zc[i + 1] > M.zc[i], "z coordinates must increase");
+  const int64_t E = (int64_t)M.nx * M.ny * M.nz;
+  M.ecx.resize(E); M.ecy.resize(E); M.ecz.resize(E);
+  for (int ez = 0; ez < M.nz; ++ez)
+    for (int ey = 0; ey < M.ny; ++ey)
+      for (int ex = 0; ex < M.nx; ++ex) {
+        int64_t e = ex + (int64_t)M.nx * (ey + (int64_t)M.ny * ez);
+        double k = md.coef ? md.coef[e] : 1.0;
+        DD_REQUIRE(k > 0.0 && std::isfinite(k), "coefficients must be positive and finite");
+        double hx = M.xc[ex + 1] - M.xc[ex], hy = M.yc[ey + 1] - M.yc[ey], hz = M.zc[ez + 1] - M.zc[ez];
+        M.ecx[e] = k * hy * hz / (36.0 * hx);
+        M.ecy[e] = k * hx * hz / (36.0 * hy);
+        M.ecz[e] = k * hx * hy / (36.0 * hz);
+      }
+
+  // ---- interface numbering (free nodes shared by more than one subdomain) ----
+  auto cut = [](int p, int n, int s) { return p % s == 0 && p > 0 && p < n; };
+  auto is_free = [&](int x, int y, int z) {
+    return x >= M.fx0 && x < M.fx1 && y >= M.fy0 && y < M.fy1 && z >= M.fz0 && z < M.fz1;
+  };
+  auto free_idx = [&](int x, int y, int z) -> int64_t {
+    return (x - M.fx0) + Nfx * ((y - M.fy0) + Nfy * (int64_t)(z - M.fz0));
+  };
+  std::vector<int> gamma_of_free(M.n_free, -1);
+  int64_t nG = 0;
+  for (int z = M.fz0; z < M.fz1; ++z)
+    for (int y = M.fy0; y < M.fy1; ++y)
+      for (int x = M.fx0; x < M.fx1; ++x)
+        if (cut(x, M.nx, M.sx) || cut(y, M.ny, M.sy) || cut(z, M.nz, M.sz)) {
+          gamma_of_free[free_idx(x, y, z)] = (int)nG++;
+          M.gamma_free.push_back(free_idx(x, y, z));
+        }
+  Level& L1 = H.l1;
+  L1.S = M.S;
+  L1.n_gamma = nG;
+  DD_REQUIRE(nG > 0, "partition has no interface (one subdomain)");
+  DD_REQUIRE(M.NL <= 729, "local node grid too large");
+
+  // ---- per-subdomain local numbering ----
+  M.lidx.assign((size_t)M.S * M.NL, INT16_MIN);
+  L1.goff.assign(M.S + 1, 0);
+  L1.ioff.assign(M.S + 1, 0);
+  std::vector<std::vector<int>> Iloc(M.S), Gloc(M.S);  // positions in the local free-node list
+  std::vector<int> nloc(M.S);
+  std::vector<std::vector<int>> lfree(M.S);            // local node id of each local free node
+  for (int s = 0; s < M.S; ++s) {
+    int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
+    int ni = 0, ng = 0, nl = 0;
+    for (int c = 0; c < M.NLz; ++c)
+      for (int b = 0; b < M.NLy; ++b)
+        for (int a = 0; a < M.NLx; ++a) {
+          int x = I * M.sx + a, y = J * M.sy + b, z = Kk * M.sz + c;
+          int l = a + M.NLx * (b + M.NLy * c);
+          if (!is_free(x, y, z)) continue;
+          lfree[s].push_back(l);
+          if (gamma_of_free[free_idx(x, y, z)] >= 0) {
+            M.lidx[(size_t)s * M.NL + l] = (int16_t)(-1 - ng);
+            Gloc[s].push_back(nl);
+            L1.gmap.push_back(gamma_of_free[free_idx(x, y, z)]);
+            ng++;
+          } else {
+            M.lidx[(size_t)s * M.NL + l] = (int16_t)ni;
+            Iloc[s].push_back(nl);
+            ni++;
+          }
+          nl++;
+        }
+    nloc[s] = nl;
+    L1.goff[s + 1] = L1.goff[s] + ng;
+    L1.ioff[s + 1] = L1.ioff[s] + ni;
+  }
+  build_copy_csr(nG, L1.goff, L1.gmap, L1.gptr, L1.gidx);
+
+  // ---- globs from sharing sets ----
+  auto axis_subs = [](int p, int n, int s, int* out) -> int {
+    if (p % s == 0 && p > 0 && p < n) { out[0] = p / s - 1; out[1] = p / s; return 2; }
+    out[0] = std::min(p / s, n / s - 1);
+    return 1;
+  };
+  Globs gl = make_globs(nG, [&](int64_t g, std::vector<int>& subs) {
+    int64_t f = M.gamma_free[g];
+    int x = (int)(f % Nfx) + M.fx0, y = (int)((f / Nfx) % Nfy) + M.fy0, z = (int)(f / (Nfx * Nfy)) + M.fz0;
+    int ax[2], ay[2], az[2];
+    int nxs = axis_subs(x, M.nx, M.sx, ax), nys = axis_subs(y, M.ny, M.sy, ay), nzs = axis_subs(z, M.nz, M.sz, az);
+    for (int k = 0; k < nzs; ++k)
+      for (int j = 0; j < nys; ++j)
+        for (int i = 0; i < nxs; ++i) subs.push_back(ax[i] + M.Sx * (ay[j] + M.Sy * az[k]));
+    std::sort(subs.begin(), subs.end());
+  });
+  std::vector<CoarseDof> cd = select_coarse(gl, opt.use_corners, opt.use_edges, opt.use_faces);
+  DD_REQUIRE(!cd.empty(), "no coarse degrees of freedom selected");
+
+  // ---- local stiffness matrices (closed-form Kronecker form of the Q1 brick) ----
+  std::vector<std::vector<double>> Kloc(M.S);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int s = 0; s < M.S; ++s) {
+    int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
+    int nl = nloc[s];
+    std::vector<int> pos(M.NL, -1);
+    for (int t = 0; t < nl; ++t) pos[lfree[s][t]] = t;
+    std::vector<double>& K = Kloc[s];
+    K.assign((size_t)nl * nl, 0.0);
+    for (int ec = 0; ec < M.sz; ++ec)
+      for (int eb = 0; eb < M.sy; ++eb)
+        for (int ea = 0; ea < M.sx; ++ea) {
+          int64_t e = (I * M.sx + ea) + (int64_t)M.nx * ((J * M.sy + eb) + (int64_t)M.ny * (Kk * M.sz + ec));
+          double cx = M.ecx[e], cy = M.ecy[e], cz = M.ecz[e];
+          for (int p = 0; p < 8; ++p) {
+            int lp = (ea + (p & 1)) + M.NLx * ((eb + ((p >> 1) & 1)) + M.NLy * (ec + (p >> 2)));
+            int ip = pos[lp];
+            if (ip < 0) continue;
+            for (int q = 0; q < 8; ++q) {
+              int lq = (ea + (q & 1)) + M.NLx * ((eb + ((q >> 1) & 1)) + M.NLy * (ec + (q >> 2)));
+              int iq = pos[lq];
+              if (iq < 0) continue;
+              int d = p ^ q;
+              double sx = (d & 1) ? -1.0 : 1.0, mx = (d & 1) ? 1.0 : 2.0;
+              double sy = (d & 2) ? -1.0 : 1.0, my = (d & 2) ? 1.0 : 2.0;
+              double sz = (d & 4) ? -1.0 : 1.0, mz = (d & 4) ? 1.0 : 2.0;
+              K[(size_t)ip * nl + iq] += cx * sx * my * mz + cy * mx * sy * mz + cz * mx * my * sz;
+            }
+          }
+        }
+  }
+  finish_level(L1, gl, cd, opt.weights, Kloc, nloc, Iloc, Gloc, false, "level 1");
+  Kloc.clear();
+  Kloc.shrink_to_fit();
+
+  H.levels = opt.levels;
+  if (opt.levels == 2) {
+    std::vector<double> KC = assemble_coarse(L1);
+    H.KCinv.resize(KC.size());
+    if (!la::spd_inverse(L1.n_coarse, KC.data(), H.KCinv.data()))
+      throw Error(DD_SINGULAR_LOCAL, "coarse matrix is not SPD");
+  } else {
+    // ---- level 2: groups of g^3 subdomains, subdomains acting as elements (Sect. 3.2) ----
+    int g = std::max(1, opt.coarse_group);
+    int Gx = (M.Sx + g - 1) / g, Gy = (M.Sy + g - 1) / g, Gz = (M.Sz + g - 1) / g;
+    int S2 = Gx * Gy * Gz;
+    std::vector<std::vector<int>> members(S2);
+    for (int s = 0; s < M.S; ++s) {
+      int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
+      members[(I / g) + Gx * ((J / g) + Gy * (Kk / g))].push_back(s);
+    }
+    int nC = L1.n_coarse;
+    std::vector<std::vector<int>> groups_of_c(nC);
+    std::vector<std::vector<int>> ldofs(S2);
+    for (int j = 0; j < S2; ++j) {
+      std::vector<int> d;
+      for (int s : members[j]) d.insert(d.end(), L1.sub[s].cmap.begin(), L1.sub[s].cmap.end());
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      ldofs[j] = d;
+      for (int c : d) groups_of_c[c].push_back(j);
+    }
+    Level& L2 = H.l2;
+    L2.S = S2;
+    std::vector<int> gam2_of_c(nC, -1);
+    int64_t nG2 = 0;
+    for (int c = 0; c < nC; ++c)
+      if (groups_of_c[c].size() >= 2) {
+        gam2_of_c[c] = (int)nG2++;
+        H.gam2_c.push_back(c);
+      }
+    L2.n_gamma = nG2;
+    DD_REQUIRE(nG2 > 0, "three levels need more than one coarse subdomain");
+    std::vector<std::vector<double>> K2(S2);
+    std::vector<int> nloc2(S2);
+    std::vector<std::vector<int>> I2(S2), G2(S2);
+    L2.goff.assign(S2 + 1, 0);
+    L2.ioff.assign(S2 + 1, 0);
+    for (int j = 0; j < S2; ++j) {
+      const auto& d = ldofs[j];
+      int n = (int)d.size();
+      nloc2[j] = n;
+      K2[j].assign((size_t)n * n, 0.0);
+      for (int s : members[j]) {
+        const DenseSub& ds = L1.sub[s];
+        std::vector<int> p(ds.nc);
+        for (int a = 0; a < ds.nc; ++a) p[a] = (int)(std::lower_bound(d.begin(), d.end(), ds.cmap[a]) - d.begin());
+        for (int a = 0; a < ds.nc; ++a)
+          for (int b = 0; b < ds.nc; ++b) K2[j][(size_t)p[a] * n + p[b]] += ds.KC[(size_t)a * ds.nc + b];
+      }
+      for (int t = 0; t < n; ++t) {
+        if (gam2_of_c[d[t]] >= 0) {
+          G2[j].push_back(t);
+          L2.gmap.push_back(gam2_of_c[d[t]]);
+        } else {
+          I2[j].push_back(t);
+          H.imap2.push_back(d[t]);
+        }
+      }
+      L2.goff[j + 1] = L2.goff[j] + (int64_t)G2[j].size();
+      L2.ioff[j + 1] = L2.ioff[j] + (int64_t)I2[j].size();
+    }
+    build_copy_csr(nG2, L2.goff, L2.gmap, L2.gptr, L2.gidx);
+    Globs gl2 = make_globs(nG2, [&](int64_t gg, std::vector<int>& subs) { subs = groups_of_c[H.gam2_c[gg]]; });
+    std::vector<CoarseDof> cd2 = select_coarse(gl2, true, true, true);
+    DD_REQUIRE(!cd2.empty(), "no level-2 coarse dofs");
+    finish_level(L2, gl2, cd2, opt.weights, K2, nloc2, I2, G2, true, "level 2");
+    std::vector<double> KC3 = assemble_coarse(L2);
+    H.KC3inv.resize(KC3.size());
+    if (!la::spd_inverse(L2.n_coarse, KC3.data(), H.KC3inv.data()))
+      throw Error(DD_SINGULAR_LOCAL, "level-3 coarse matrix is not SPD");
+  }
+  H.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace dd

@@ -1,0 +1,913 @@
+// Context, device uploads, operator applications and the deflated PCG solve
+// (Algorithm 1) with Krylov subspace recycling (Sect. 4.2), behind the C ABI of
+// include/dd_solver.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "common.h"
+#include "device.h"
+#include "hostla.h"
+#include "setup.h"
+#include "vecops.h"
+
+using namespace dd;
+
+static thread_local std::string g_last_error;
+
+struct dd_ctx {
+  dd_options opt{};
+  dd_info_t info{};
+  DeviceArena arena;
+  std::vector<int64_t> gamma_free_host;
+  int64_t n_free = 0, n_gamma = 0;
+  int levels = 2;
+  DevMesh mesh{};
+  DevBDDC b1{};
+  DevLevel2 l2{};
+  const void* KCinv = nullptr;
+  Work w{};
+  // Krylov buffers
+  double *xg = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr;
+  double* tmp = nullptr;
+  double* sc = nullptr;        // device scalars [SC_COUNT]
+  double* sc_host = nullptr;   // pinned mirror
+  double* partials = nullptr;  // [NBLK*MAXDOT]
+  double* wpart = nullptr;     // [NBLK*MAXK]
+  double* mu = nullptr;        // [MAXK]
+  double* gram_part = nullptr; // [NBLK*4096]
+  double* gram_out = nullptr;  // [4096]
+  double* ybuf = nullptr;      // [128*128] combination coefficients
+  const double** ptrs = nullptr;  // device pointer table for gram / lincomb
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~dd_ctx() {
+    if (sc_host) cudaFreeHost(sc_host);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+struct dd_recycle {
+  dd_ctx* ctx = nullptr;
+  int kmax = 0, strategy = DD_B4;
+  double freeze_tol = 1e-5;
+  int k = 0;
+  bool frozen = false;
+  int step = 0;
+  DeviceArena arena;
+  double *W = nullptr, *AW = nullptr, *MAW = nullptr;       // [kmax][n_gamma]
+  double *W2 = nullptr, *AW2 = nullptr, *MAW2 = nullptr;    // next basis
+  double* Ginv = nullptr;                                   // [kmax*kmax] (W^T A W)^{-1}
+  double* WWinv = nullptr;                                  // [kmax*kmax] (W^T W)^{-1}
+  std::vector<double> theta;
+  double* xg_prev = nullptr;                                // [n_gamma]
+  bool have_prev = false;
+  int hmax = 0;
+  double *P = nullptr, *AP = nullptr, *Z = nullptr, *MAP = nullptr;  // histories [hmax][n_gamma]
+  std::vector<double> alphas;
+};
+
+// ---------------------------------------------------------------------------
+// uploads
+// ---------------------------------------------------------------------------
+namespace {
+
+SymTiles upload_sym(DeviceArena& A, const std::vector<const double*>& mats, const std::vector<int>& dims, int prec,
+                    cudaStream_t s) {
+  SymTiles T;
+  T.prec = prec;
+  T.count = (int)mats.size();
+  std::vector<int64_t> toff(T.count);
+  int64_t nt = 0;
+  int maxn = 0;
+  for (int m = 0; m < T.count; ++m) {
+    int nb = (dims[m] + 31) / 32;
+    toff[m] = nt;
+    nt += (int64_t)nb * (nb + 1) / 2;
+    maxn = std::max(maxn, dims[m]);
+  }
+  T.ntiles = nt;
+  T.max_n = maxn;
+  size_t tb = tile_bytes(prec);
+  std::vector<unsigned char> buf((size_t)nt * tb, 0);
+  for (int m = 0; m < T.count; ++m) {
+    int n = dims[m], nb = (n + 31) / 32;
+    const double* M = mats[m];
+    int64_t t = toff[m];
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj, ++t) {
+        unsigned char* tile = buf.data() + (size_t)t * tb;
+        for (int r = 0; r < 32; ++r)
+          for (int c = 0; c < 32; ++c) {
+            int i = bi * 32 + r, j = bj * 32 + c;
+            double v = (i < n && j < n) ? M[(size_t)i * n + j] : 0.0;
+            if (prec == DD_PREC_FP64) {
+              reinterpret_cast<double*>(tile)[r * 32 + c] = v;
+            } else if (prec == DD_PREC_FP32) {
+              reinterpret_cast<float*>(tile)[r * 32 + c] = (float)v;
+            } else {
+              df64 d = df64_from_double(v);
+              reinterpret_cast<float*>(tile)[r * 32 + c] = d.hi;
+              reinterpret_cast<float*>(tile)[1024 + r * 32 + c] = d.lo;
+            }
+          }
+      }
+  }
+  T.n = A.upload(dims, s);
+  T.toff = A.upload(toff, s);
+  unsigned char* d = A.alloc<unsigned char>(buf.size());
+  DD_CUDA(cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  T.data = d;
+  return T;
+}
+
+RectMats upload_rect(DeviceArena& A, const std::vector<const double*>& mats, const std::vector<int>& rows,
+                     const std::vector<int>& cols, int prec, cudaStream_t s) {
+  RectMats R;
+  R.prec = prec;
+  std::vector<int64_t> off(mats.size());
+  int64_t tot = 0;
+  for (size_t m = 0; m < mats.size(); ++m) {
+    off[m] = tot;
+    tot += (int64_t)rows[m] * cols[m];
+  }
+  if (prec == DD_PREC_FP32) {
+    std::vector<float> buf(tot);
+    for (size_t m = 0; m < mats.size(); ++m)
+      for (int64_t t = 0; t < (int64_t)rows[m] * cols[m]; ++t) buf[off[m] + t] = (float)mats[m][t];
+    float* d = A.alloc<float>(buf.size());
+    DD_CUDA(cudaMemcpy(d, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice));
+    R.data = d;
+  } else {
+    std::vector<double> buf(tot);
+    for (size_t m = 0; m < mats.size(); ++m)
+      std::copy(mats[m], mats[m] + (size_t)rows[m] * cols[m], buf.begin() + off[m]);
+    double* d = A.alloc<double>(buf.size());
+    DD_CUDA(cudaMemcpy(d, buf.data(), buf.size() * 8, cudaMemcpyHostToDevice));
+    R.data = d;
+  }
+  R.rows = A.upload(rows, s);
+  R.cols = A.upload(cols, s);
+  R.off = A.upload(off, s);
+  return R;
+}
+
+void upload_bddc(DeviceArena& A, const Level& L, int prec, DevBDDC& b, cudaStream_t s) {
+  b.S = L.S;
+  b.n_gamma = L.n_gamma;
+  b.n_coarse = L.n_coarse;
+  b.n_flat = L.goff[L.S];
+  b.n_cflat = L.coff[L.S];
+  b.prec = prec;
+  b.goff = A.upload(L.goff, s);
+  b.gmap = A.upload(L.gmap, s);
+  std::vector<int> gsub(b.n_flat);
+  std::vector<double> D(b.n_flat);
+  std::vector<int> cmap(b.n_cflat);
+  for (int i = 0; i < L.S; ++i) {
+    for (int64_t k = L.goff[i]; k < L.goff[i + 1]; ++k) {
+      gsub[k] = i;
+      D[k] = L.sub[i].D[k - L.goff[i]];
+    }
+    for (int c = 0; c < L.sub[i].nc; ++c) cmap[L.coff[i] + c] = L.sub[i].cmap[c];
+  }
+  b.gsub = A.upload(gsub, s);
+  b.D = A.upload(D, s);
+  b.gptr = A.upload(L.gptr, s);
+  b.gidx = A.upload(L.gidx, s);
+  b.coff = A.upload(L.coff, s);
+  b.cmap = A.upload(cmap, s);
+  b.cptr = A.upload(L.cptr, s);
+  b.cidx = A.upload(L.cidx, s);
+  std::vector<const double*> Ns, Ps;
+  std::vector<int> nG, nc;
+  for (int i = 0; i < L.S; ++i) {
+    Ns.push_back(L.sub[i].N.data());
+    Ps.push_back(L.sub[i].Phi.data());
+    nG.push_back(L.sub[i].nG);
+    nc.push_back(L.sub[i].nc);
+  }
+  b.N = upload_sym(A, Ns, nG, prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+  b.Phi = upload_rect(A, Ps, nG, nc, prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+}
+
+const void* upload_dense(DeviceArena& A, const std::vector<double>& M, int prec) {
+  if (prec == DD_PREC_FP32) {
+    std::vector<float> f(M.begin(), M.end());
+    float* d = A.alloc<float>(f.size());
+    DD_CUDA(cudaMemcpy(d, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    return d;
+  }
+  double* d = A.alloc<double>(M.size());
+  DD_CUDA(cudaMemcpy(d, M.data(), M.size() * 8, cudaMemcpyHostToDevice));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+void schur_apply(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
+  launch_elem_interior(c->mesh, ELEM_SCHUR, x, nullptr, c->w.tI, s);
+  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  launch_elem_interface(c->mesh, ELEM_SCHUR, x, c->w.sI, c->w.yloc, s);
+  launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, nullptr, nullptr, y, s);
+}
+
+void condense(dd_ctx* c, const double* f, double* b, cudaStream_t s) {
+  launch_elem_interior(c->mesh, ELEM_CONDENSE, nullptr, f, c->w.tI, s);
+  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  launch_elem_interface(c->mesh, ELEM_CONDENSE, nullptr, c->w.sI, c->w.yloc, s);
+  launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, f, c->mesh.gamma_free, b, s);
+}
+
+void recover(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream_t s) {
+  launch_elem_interior(c->mesh, ELEM_RECOVER, xg, f, c->w.tI, s);
+  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  launch_scatter_recover(c->mesh, xg, c->w.sI, x, s);
+}
+
+// BDDC of one level on an interface residual r -> z, with a coarse solver callback
+template <class CoarseFn>
+void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* gloc,
+                double* gC, double* uC, CoarseFn coarse, cudaStream_t s) {
+  launch_restrict(b.n_flat, b.gmap, b.D, r, rloc, s);
+  launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
+  launch_phiT(b, rloc, gloc, s);
+  launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
+  coarse(gC, uC);
+  launch_combine(b, uloc, uC, z, s);
+}
+
+// three-level: BDDC for the whole coarse system K_C u = g (interior correction, interface BDDC, extension)
+void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
+  DevLevel2& L = c->l2;
+  Work& w = c->w;
+  launch_map_gather(L.n_int, L.imap, g, w.gI2, s);
+  launch_symv(L.KIIinv, L.ioff, w.gI2, w.u0I2, w.err, s);
+  launch_rect_gemv(L.b.S, L.E, true, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);
+  launch_gather(L.b.n_gamma, L.b.gptr, L.b.gidx, w.rl2, g, L.gam_c64, w.r2, s);  // g[gam_c] + sum of copies
+  bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.gloc2, w.g3, w.u3,
+             [&](const double* g3, double* u3) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, s); }, s);
+  launch_rect_gemv(L.b.S, L.E, false, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2, s);
+  launch_map_scatter(L.n_int, L.imap, w.uI2, u, s);
+  launch_map_scatter(L.b.n_gamma, L.gam_c, w.z2, u, s);
+}
+
+void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+  Work& w = c->w;
+  bddc_apply(c, c->b1, r, z, w.rloc, w.uloc, w.gloc, w.gC, w.uC,
+             [&](const double* g, double* u) {
+               if (c->levels == 2)
+                 launch_dense_gemv(c->b1.n_coarse, c->b1.prec, c->KCinv, g, u, s);
+               else
+                 level2_apply(c, g, u, s);
+             },
+             s);
+}
+
+void check_err(dd_ctx* c, cudaStream_t s) {
+  int e = 0;
+  DD_CUDA(cudaMemcpyAsync(&e, c->w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  if (e) throw Error((dd_status)e, "a bounded device-side wait timed out");
+}
+
+template <class F>
+dd_status guard(F&& f) {
+  try {
+    f();
+    return DD_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return DD_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return DD_INVALID_ARG;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dd_last_error(void) { return g_last_error.c_str(); }
+
+dd_status dd_default_options(dd_options* o) {
+  if (!o) return DD_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->levels = 3;
+  o->coarse_group = 4;
+  o->use_corners = o->use_edges = o->use_faces = 1;
+  o->adaptive = 0;
+  o->tau = 10.0;
+  o->max_eig_per_face = 10;
+  o->weights = DD_WEIGHTS_DIAG;
+  o->precond_prec = DD_PREC_FP64;
+  o->schur_prec = DD_PREC_FP64;
+  o->flexible = 0;
+  o->reorth = 0;
+  o->stop_rhs_norm = 1;
+  o->maxit = 500;
+  return DD_OK;
+}
+
+dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, dd_ctx** out) {
+  if (!md || !opt || !out) {
+    g_last_error = "dd_setup: NULL argument";
+    return DD_INVALID_ARG;
+  }
+  *out = nullptr;
+  return guard([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    DD_REQUIRE(opt->precond_prec == DD_PREC_FP64 || opt->precond_prec == DD_PREC_FP32,
+               "precond_prec must be FP64 or FP32");
+    DD_REQUIRE(opt->schur_prec == DD_PREC_FP64 || opt->schur_prec == DD_PREC_DF64, "schur_prec must be FP64 or DF64");
+    DD_REQUIRE(opt->maxit >= 1, "maxit must be positive");
+    DD_REQUIRE(!opt->adaptive, "adaptive constraints are not available in this build");
+    auto H = std::make_unique<HostSetup>();
+    build_host_setup(*md, *opt, *H);
+    auto c = std::make_unique<dd_ctx>();
+    c->opt = *opt;
+    c->levels = H->levels;
+    const Mesh1& M = H->mesh;
+    DeviceArena& A = c->arena;
+    c->n_free = M.n_free;
+    c->n_gamma = H->l1.n_gamma;
+    c->gamma_free_host = M.gamma_free;
+    // ---- level-1 mesh / Schur operator ----
+    DevMesh& dm = c->mesh;
+    dm.nx = M.nx; dm.ny = M.ny; dm.nz = M.nz; dm.sx = M.sx; dm.sy = M.sy; dm.sz = M.sz;
+    dm.Sx = M.Sx; dm.Sy = M.Sy; dm.Sz = M.Sz; dm.S = M.S;
+    dm.fx0 = M.fx0; dm.fx1 = M.fx1; dm.fy0 = M.fy0; dm.fy1 = M.fy1; dm.fz0 = M.fz0; dm.fz1 = M.fz1;
+    dm.NLx = M.NLx; dm.NLy = M.NLy; dm.NLz = M.NLz; dm.NL = M.NL;
+    dm.n_free = M.n_free;
+    dm.n_gamma = H->l1.n_gamma;
+    dm.n_int = H->l1.ioff[M.S];
+    dm.schur_prec = opt->schur_prec;
+    dm.lidx = A.upload(M.lidx, s);
+    dm.ioff = A.upload(H->l1.ioff, s);
+    dm.goff = A.upload(H->l1.goff, s);
+    dm.gmap = A.upload(H->l1.gmap, s);
+    dm.gptr = A.upload(H->l1.gptr, s);
+    dm.gidx = A.upload(H->l1.gidx, s);
+    dm.gamma_free = A.upload(M.gamma_free, s);
+    {
+      size_t E = M.ecx.size();
+      std::vector<double> ec(3 * E);
+      std::vector<df64> ecd(3 * E);
+      for (size_t e = 0; e < E; ++e) {
+        ec[3 * e] = M.ecx[e]; ec[3 * e + 1] = M.ecy[e]; ec[3 * e + 2] = M.ecz[e];
+        for (int t = 0; t < 3; ++t) ecd[3 * e + t] = df64_from_double(ec[3 * e + t]);
+      }
+      dm.ec = A.upload(ec, s);
+      dm.ec_df = A.upload(ecd, s);
+    }
+    {
+      std::vector<const double*> mats;
+      std::vector<int> dims;
+      for (int i = 0; i < M.S; ++i) {
+        mats.push_back(H->l1.sub[i].KIIinv.data());
+        dims.push_back(H->l1.sub[i].nI);
+      }
+      dm.KIIinv = upload_sym(A, mats, dims, opt->schur_prec == DD_PREC_DF64 ? DD_PREC_DF64 : DD_PREC_FP64, s);
+    }
+    // ---- level-1 BDDC ----
+    upload_bddc(A, H->l1, opt->precond_prec, c->b1, s);
+    int pp = opt->precond_prec;
+    Work& w = c->w;
+    w.tI = A.alloc<double>(dm.n_int);
+    w.sI = A.alloc<double>(dm.n_int);
+    w.yloc = A.alloc<double>(c->b1.n_flat);
+    w.rloc = A.alloc<double>(c->b1.n_flat);
+    w.uloc = A.alloc<double>(c->b1.n_flat);
+    w.gloc = A.alloc<double>(c->b1.n_cflat);
+    w.gC = A.alloc<double>(c->b1.n_coarse);
+    w.uC = A.alloc<double>(c->b1.n_coarse);
+    w.err = A.alloc<int>(1);
+    DD_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+    if (c->levels == 2) {
+      c->KCinv = upload_dense(A, H->KCinv, pp);
+    } else {
+      DevLevel2& L = c->l2;
+      upload_bddc(A, H->l2, pp, L.b, s);
+      L.n_int = H->l2.ioff[H->l2.S];
+      L.ioff = A.upload(H->l2.ioff, s);
+      L.imap = A.upload(H->imap2, s);
+      L.gam_c = A.upload(H->gam2_c, s);
+      L.gam_c64 = A.upload(std::vector<int64_t>(H->gam2_c.begin(), H->gam2_c.end()), s);
+      std::vector<const double*> Ks, Es;
+      std::vector<int> nI, nG;
+      for (int j = 0; j < H->l2.S; ++j) {
+        Ks.push_back(H->l2.sub[j].KIIinv.data());
+        Es.push_back(H->l2.sub[j].E.data());
+        nI.push_back(H->l2.sub[j].nI);
+        nG.push_back(H->l2.sub[j].nG);
+      }
+      L.KIIinv = upload_sym(A, Ks, nI, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+      L.E = upload_rect(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+      L.n3 = H->l2.n_coarse;
+      L.KC3inv = upload_dense(A, H->KC3inv, pp);
+      w.gI2 = A.alloc<double>(L.n_int);
+      w.u0I2 = A.alloc<double>(L.n_int);
+      w.uI2 = A.alloc<double>(L.n_int);
+      w.rl2 = A.alloc<double>(L.b.n_flat);
+      w.rloc2 = A.alloc<double>(L.b.n_flat);
+      w.uloc2 = A.alloc<double>(L.b.n_flat);
+      w.r2 = A.alloc<double>(L.b.n_gamma);
+      w.z2 = A.alloc<double>(L.b.n_gamma);
+      w.gloc2 = A.alloc<double>(L.b.n_cflat);
+      w.g3 = A.alloc<double>(L.n3);
+      w.u3 = A.alloc<double>(L.n3);
+    }
+    // ---- Krylov buffers ----
+    int64_t nG = c->n_gamma;
+    c->xg = A.alloc<double>(nG);
+    c->r = A.alloc<double>(nG);
+    c->z = A.alloc<double>(nG);
+    c->zold = A.alloc<double>(nG);
+    c->p = A.alloc<double>(nG);
+    c->q = A.alloc<double>(nG);
+    c->bvec = A.alloc<double>(nG);
+    c->tmp = A.alloc<double>(nG);
+    c->sc = A.alloc<double>(SC_COUNT);
+    c->partials = A.alloc<double>(NBLK * MAXDOT);
+    c->wpart = A.alloc<double>((size_t)NBLK * MAXK);
+    c->mu = A.alloc<double>(MAXK);
+    c->gram_part = A.alloc<double>((size_t)NBLK * 4096);
+    c->gram_out = A.alloc<double>(4096);
+    c->ybuf = A.alloc<double>(128 * 128);
+    c->ptrs = A.alloc<const double*>(512);
+    DD_CUDA(cudaMallocHost(&c->sc_host, SC_COUNT * sizeof(double)));
+    DD_CUDA(cudaEventCreate(&c->ev0));
+    DD_CUDA(cudaEventCreate(&c->ev1));
+    DD_CUDA(cudaStreamSynchronize(s));
+    c->info.n_free = c->n_free;
+    c->info.n_gamma = c->n_gamma;
+    c->info.n_sub = M.S;
+    c->info.n_coarse = H->l1.n_coarse;
+    c->info.n_adaptive = H->l1.n_adaptive;
+    c->info.n_sub2 = c->levels == 3 ? H->l2.S : 0;
+    c->info.n_coarse3 = c->levels == 3 ? H->l2.n_coarse : 0;
+    c->info.device_bytes = (int64_t)A.bytes;
+    c->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = c.release();
+  });
+}
+
+void dd_destroy(dd_ctx* c) { delete c; }
+
+dd_status dd_plan(const dd_mesh_desc* md, const dd_options* opt, dd_info_t* info, int64_t* nodes,
+                  int64_t capacity) {
+  if (!md || !opt || !info) {
+    g_last_error = "dd_plan: NULL argument";
+    return DD_INVALID_ARG;
+  }
+  return guard([&] {
+    HostSetup H;
+    build_host_setup(*md, *opt, H);
+    std::memset(info, 0, sizeof(*info));
+    info->n_free = H.mesh.n_free;
+    info->n_gamma = H.l1.n_gamma;
+    info->n_sub = H.mesh.S;
+    info->n_coarse = H.l1.n_coarse;
+    info->n_adaptive = H.l1.n_adaptive;
+    info->n_sub2 = H.levels == 3 ? H.l2.S : 0;
+    info->n_coarse3 = H.levels == 3 ? H.l2.n_coarse : 0;
+    info->setup_seconds = H.setup_seconds;
+    if (nodes) {
+      DD_REQUIRE(capacity >= H.l1.n_gamma, "dd_plan: node buffer too small");
+      std::copy(H.mesh.gamma_free.begin(), H.mesh.gamma_free.end(), nodes);
+    }
+  });
+}
+
+dd_status dd_get_info(const dd_ctx* c, dd_info_t* info) {
+  if (!c || !info) return DD_INVALID_ARG;
+  *info = c->info;
+  return DD_OK;
+}
+
+dd_status dd_interface_nodes(const dd_ctx* c, int64_t* nodes) {
+  if (!c || !nodes) return DD_INVALID_ARG;
+  std::copy(c->gamma_free_host.begin(), c->gamma_free_host.end(), nodes);
+  return DD_OK;
+}
+
+dd_status dd_schur_apply(dd_ctx* c, const double* x, double* y, void* stream) {
+  if (!c || !x || !y) return DD_INVALID_ARG;
+  return guard([&] { schur_apply(c, x, y, (cudaStream_t)stream); check_err(c, (cudaStream_t)stream); });
+}
+
+dd_status dd_precond_apply(dd_ctx* c, const double* r, double* z, void* stream) {
+  if (!c || !r || !z) return DD_INVALID_ARG;
+  return guard([&] { precond_apply(c, r, z, (cudaStream_t)stream); check_err(c, (cudaStream_t)stream); });
+}
+
+dd_status dd_condense(dd_ctx* c, const double* f, double* b, void* stream) {
+  if (!c || !f || !b) return DD_INVALID_ARG;
+  return guard([&] { condense(c, f, b, (cudaStream_t)stream); check_err(c, (cudaStream_t)stream); });
+}
+
+dd_status dd_recover(dd_ctx* c, const double* f, const double* xg, double* x, void* stream) {
+  if (!c || !f || !xg || !x) return DD_INVALID_ARG;
+  return guard([&] { recover(c, f, xg, x, (cudaStream_t)stream); check_err(c, (cudaStream_t)stream); });
+}
+
+dd_status dd_recycle_create(dd_ctx* c, int32_t k, int32_t strategy, double freeze_tol, dd_recycle** out) {
+  if (!c || !out || k < 0 || k > MAXK - 1 || strategy < DD_B1 || strategy > DD_B4) {
+    g_last_error = "dd_recycle_create: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  return guard([&] {
+    auto st = std::make_unique<dd_recycle>();
+    st->ctx = c;
+    st->kmax = k;
+    st->strategy = strategy;
+    st->freeze_tol = freeze_tol;
+    int64_t n = c->n_gamma;
+    st->xg_prev = st->arena.alloc<double>(n);
+    DD_CUDA(cudaMemset(st->xg_prev, 0, n * sizeof(double)));
+    if (k > 0) {
+      st->W = st->arena.alloc<double>((size_t)k * n);
+      st->AW = st->arena.alloc<double>((size_t)k * n);
+      st->MAW = st->arena.alloc<double>((size_t)k * n);
+      st->W2 = st->arena.alloc<double>((size_t)k * n);
+      st->AW2 = st->arena.alloc<double>((size_t)k * n);
+      st->MAW2 = st->arena.alloc<double>((size_t)k * n);
+      st->Ginv = st->arena.alloc<double>((size_t)k * k);
+      st->WWinv = st->arena.alloc<double>((size_t)k * k);
+      st->hmax = std::min(c->opt.maxit + 1, std::max(16, 128 - k));
+      st->P = st->arena.alloc<double>((size_t)st->hmax * n);
+      st->AP = st->arena.alloc<double>((size_t)st->hmax * n);
+      st->Z = st->arena.alloc<double>((size_t)(st->hmax + 1) * n);
+      st->MAP = st->arena.alloc<double>((size_t)st->hmax * n);
+    }
+    *out = st.release();
+  });
+}
+
+void dd_recycle_destroy(dd_recycle* st) { delete st; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// deflated PCG (Algorithm 1) and the recycling update
+// ---------------------------------------------------------------------------
+namespace {
+
+void set_ptrs(dd_ctx* c, const std::vector<const double*>& v, int at, cudaStream_t s) {
+  DD_CUDA(cudaMemcpyAsync(c->ptrs + at, v.data(), v.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
+}
+
+// C[a][b] = X_a . Y_b, computed in column blocks of at most 64 x 64
+std::vector<double> gram_host(dd_ctx* c, const std::vector<const double*>& X, const std::vector<const double*>& Y,
+                              cudaStream_t s) {
+  int na = (int)X.size(), nb = (int)Y.size();
+  std::vector<double> C((size_t)na * nb, 0.0);
+  if (!na || !nb) return C;
+  DD_REQUIRE(na <= 256 && nb <= 256, "gram: at most 256 columns");
+  set_ptrs(c, X, 0, s);
+  set_ptrs(c, Y, 256, s);
+  std::vector<double> blk(64 * 64);
+  for (int a0 = 0; a0 < na; a0 += 64)
+    for (int b0 = 0; b0 < nb; b0 += 64) {
+      int ma = std::min(64, na - a0), mb = std::min(64, nb - b0);
+      gram(c->n_gamma, ma, c->ptrs + a0, mb, c->ptrs + 256 + b0, c->gram_part, c->gram_out, s);
+      DD_CUDA(cudaMemcpyAsync(blk.data(), c->gram_out, (size_t)ma * mb * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DD_CUDA(cudaStreamSynchronize(s));
+      for (int a = 0; a < ma; ++a)
+        for (int b = 0; b < mb; ++b) C[(size_t)(a0 + a) * nb + b0 + b] = blk[(size_t)a * mb + b];
+    }
+  return C;
+}
+
+void lincomb_dev(dd_ctx* c, const std::vector<const double*>& V, const std::vector<double>& Y, int kc,
+                 const std::vector<double*>& out, cudaStream_t s) {
+  std::vector<const double*> o(out.begin(), out.end());
+  set_ptrs(c, V, 0, s);
+  set_ptrs(c, o, 256, s);
+  DD_REQUIRE(V.size() <= 256 && kc <= 256 && Y.size() <= (size_t)128 * 128, "lincomb: too many columns");
+  double* Yd = c->ybuf;
+  DD_CUDA(cudaMemcpyAsync(Yd, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  lincomb(c->n_gamma, (int)V.size(), c->ptrs, Yd, kc, (double* const*)(c->ptrs + 256), s);
+  DD_CUDA(cudaStreamSynchronize(s));
+}
+
+// G = W^T A W and its inverse (k x k, FP64, on the host)
+void refresh_gram(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
+  int k = st->k;
+  if (k == 0) return;
+  int64_t n = c->n_gamma;
+  std::vector<const double*> Wc, AWc;
+  for (int j = 0; j < k; ++j) {
+    Wc.push_back(st->W + (size_t)j * n);
+    AWc.push_back(st->AW + (size_t)j * n);
+  }
+  std::vector<double> G = gram_host(c, Wc, AWc, s);
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (G[a * k + b] + G[b * k + a]);
+      G[a * k + b] = G[b * k + a] = v;
+    }
+  std::vector<double> Gi((size_t)k * k);
+  if (!la::spd_inverse(k, G.data(), Gi.data())) {
+    // basis numerically dependent: drop it (plain PCG until it is rebuilt)
+    st->k = 0;
+    return;
+  }
+  DD_CUDA(cudaMemcpyAsync(st->Ginv, Gi.data(), Gi.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (c->opt.reorth) {
+    std::vector<double> WW = gram_host(c, Wc, Wc, s), WWi((size_t)k * k);
+    if (!la::spd_inverse(k, WW.data(), WWi.data())) {
+      st->k = 0;
+      return;
+    }
+    DD_CUDA(cudaMemcpyAsync(st->WWinv, WWi.data(), WWi.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  DD_CUDA(cudaStreamSynchronize(s));
+}
+
+// Recycling after a solve with l search vectors (Sect. 4.2).
+void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
+  st->step++;
+  if (st->kmax == 0 || st->frozen || l == 0) return;
+  int64_t n = c->n_gamma;
+  int R = st->kmax;
+  l = std::min(l, st->hmax);
+  if (st->strategy == DD_B1 || st->strategy == DD_B2) {
+    // basis of search vectors (B1: first R, then frozen; B2: last R)
+    std::vector<const double*> Vs, AVs;
+    for (int j = 0; j < st->k; ++j) {
+      Vs.push_back(st->W + (size_t)j * n);
+      AVs.push_back(st->AW + (size_t)j * n);
+    }
+    for (int j = 0; j < l; ++j) {
+      Vs.push_back(st->P + (size_t)j * n);
+      AVs.push_back(st->AP + (size_t)j * n);
+    }
+    int m = (int)Vs.size();
+    int first = (st->strategy == DD_B1) ? 0 : std::max(0, m - R);
+    int last = (st->strategy == DD_B1) ? std::min(m, R) : m;
+    int kn = last - first;
+    for (int j = 0; j < kn; ++j) {
+      DD_CUDA(cudaMemcpyAsync(st->W2 + (size_t)j * n, Vs[first + j], n * 8, cudaMemcpyDeviceToDevice, s));
+      DD_CUDA(cudaMemcpyAsync(st->AW2 + (size_t)j * n, AVs[first + j], n * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    std::swap(st->W, st->W2);
+    std::swap(st->AW, st->AW2);
+    st->k = kn;
+    if (st->strategy == DD_B1 && kn >= R) st->frozen = true;
+    refresh_gram(c, st, s);
+    return;
+  }
+  // B3 / B4: harmonic Ritz vectors of V = [W, P]  (eq. harmonicRitz)
+  // M^{-1} A p_j = (z_j - z_{j+1}) / alpha_j, and for the last one one extra preconditioner solve
+  for (int j = 0; j < l; ++j) {
+    if (j + 1 < l)
+      zdiff(n, st->Z + (size_t)j * n, st->Z + (size_t)(j + 1) * n, 1.0 / st->alphas[j], st->MAP + (size_t)j * n, s);
+    else
+      precond_apply(c, st->AP + (size_t)j * n, st->MAP + (size_t)j * n, s);
+  }
+  std::vector<const double*> V, AV, MAV;
+  for (int j = 0; j < st->k; ++j) {
+    V.push_back(st->W + (size_t)j * n);
+    AV.push_back(st->AW + (size_t)j * n);
+    MAV.push_back(st->MAW + (size_t)j * n);
+  }
+  for (int j = 0; j < l; ++j) {
+    V.push_back(st->P + (size_t)j * n);
+    AV.push_back(st->AP + (size_t)j * n);
+    MAV.push_back(st->MAP + (size_t)j * n);
+  }
+  int m = (int)V.size();
+  std::vector<double> F = gram_host(c, V, AV, s);    // V^T A V
+  std::vector<double> Gh = gram_host(c, AV, MAV, s); // (AV)^T M^{-1} (AV)
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (F[a * m + b] + F[b * m + a]);
+      F[a * m + b] = F[b * m + a] = v;
+      v = 0.5 * (Gh[a * m + b] + Gh[b * m + a]);
+      Gh[a * m + b] = Gh[b * m + a] = v;
+    }
+  // restrict to the numerically nonsingular part of F: F = Q L Q^T, T = Q_r L_r^{-1/2}
+  std::vector<double> Fw(F), lam(m), Q((size_t)m * m);
+  la::sym_eig(m, Fw.data(), lam.data(), Q.data());
+  double lmax = lam[m - 1];
+  std::vector<int> keep;
+  for (int a = 0; a < m; ++a)
+    if (lam[a] > 1e-12 * lmax) keep.push_back(a);
+  int r = (int)keep.size();
+  if (r == 0) return;
+  std::vector<double> T((size_t)m * r);
+  for (int a = 0; a < m; ++a)
+    for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = Q[(size_t)a * m + keep[j]] / std::sqrt(lam[keep[j]]);
+  // C = T^T Gh T
+  std::vector<double> GT((size_t)m * r), Cm((size_t)r * r);
+  la::gemm_nn(m, r, m, Gh.data(), T.data(), GT.data());
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      double sacc = 0.0;
+      for (int a = 0; a < m; ++a) sacc += T[(size_t)a * r + i] * GT[(size_t)a * r + j];
+      Cm[(size_t)i * r + j] = sacc;
+    }
+  std::vector<double> th(r), U((size_t)r * r);
+  la::sym_eig(r, Cm.data(), th.data(), U.data());
+  int kn = std::min(R, r);
+  std::vector<int> sel(kn);
+  for (int j = 0; j < kn; ++j) sel[j] = (st->strategy == DD_B4) ? (r - 1 - j) : j;
+  std::vector<double> theta(kn);
+  for (int j = 0; j < kn; ++j) theta[j] = th[sel[j]];
+  if ((int)st->theta.size() == R && kn == R) {
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < R; ++j) {
+      num += (theta[j] - st->theta[j]) * (theta[j] - st->theta[j]);
+      den += theta[j] * theta[j];
+    }
+    if (std::sqrt(num) <= st->freeze_tol * std::sqrt(den)) st->frozen = true;  // eq. harmritzstopcrit
+  }
+  st->theta = theta;
+  // Y = T U_sel (m x kn)
+  std::vector<double> Y((size_t)m * kn, 0.0);
+  for (int a = 0; a < m; ++a)
+    for (int j = 0; j < kn; ++j) {
+      double sacc = 0.0;
+      for (int i = 0; i < r; ++i) sacc += T[(size_t)a * r + i] * U[(size_t)i * r + sel[j]];
+      Y[(size_t)a * kn + j] = sacc;
+    }
+  std::vector<double*> oW, oAW, oMAW;
+  for (int j = 0; j < kn; ++j) {
+    oW.push_back(st->W2 + (size_t)j * n);
+    oAW.push_back(st->AW2 + (size_t)j * n);
+    oMAW.push_back(st->MAW2 + (size_t)j * n);
+  }
+  lincomb_dev(c, V, Y, kn, oW, s);
+  lincomb_dev(c, AV, Y, kn, oAW, s);
+  lincomb_dev(c, MAV, Y, kn, oMAW, s);
+  std::swap(st->W, st->W2);
+  std::swap(st->AW, st->AW2);
+  std::swap(st->MAW, st->MAW2);
+  st->k = kn;
+  refresh_gram(c, st, s);
+}
+
+
+// Algorithm 1 on A x_G = b with initial guess in c->xg; returns iterations.
+dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stats* stats, cudaStream_t s) {
+  const int64_t n = c->n_gamma;
+  const dd_options& o = c->opt;
+  const int k = st ? st->k : 0;
+  const double* W = k ? st->W : nullptr;
+  const double* AW = k ? st->AW : nullptr;
+  DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
+  if (k) {
+    // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
+    schur_apply(c, c->xg, c->q, s);
+    vec_sub(n, c->bvec, c->q, c->r, s);
+    defl_mu(n, k, W, n, c->r, st->Ginv, c->wpart, c->mu, s);
+    defl_update(n, k, W, n, c->mu, nullptr, c->xg, c->sc, -1, 1.0, s);
+  }
+  schur_apply(c, c->xg, c->q, s);
+  vec_sub(n, c->bvec, c->q, c->r, s);
+  vec_dots(n, c->bvec, c->bvec, c->r, c->r, nullptr, nullptr, c->partials, s);
+  vec_finalize(c->partials, c->sc, FIN_BB, 0, s);
+  DD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(c->sc_host[SC_BB]);
+  const double r0 = std::sqrt(c->sc_host[SC_RR]);
+  double ref = o.stop_rhs_norm ? bnorm : r0;
+  if (ref == 0.0) ref = 1.0;
+  double rel = r0 / ref;
+  int its = 0;
+  dd_status status = DD_OK;
+  if (stats) stats->rel_res0 = rel;
+  if (st) st->alphas.clear();
+  if (rel >= rtol) {
+    precond_apply(c, c->r, c->z, s);
+    if (record && st && st->hmax > 0)
+      DD_CUDA(cudaMemcpyAsync(st->Z, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
+    vec_dots(n, c->r, c->z, nullptr, nullptr, nullptr, nullptr, c->partials, s);
+    vec_finalize(c->partials, c->sc, FIN_RZ0, 0, s);
+    if (k) {
+      defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
+      defl_update(n, k, W, n, c->mu, c->z, c->p, c->sc, -1, -1.0, s);
+    } else {
+      DD_CUDA(cudaMemcpyAsync(c->p, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    while (true) {
+      schur_apply(c, c->p, c->q, s);
+      vec_dots(n, c->p, c->q, nullptr, nullptr, nullptr, nullptr, c->partials, s);
+      vec_finalize(c->partials, c->sc, FIN_PQ, 0, s);
+      bool rec = record && st && its < st->hmax;
+      if (rec) {
+        DD_CUDA(cudaMemcpyAsync(st->P + (size_t)its * n, c->p, n * 8, cudaMemcpyDeviceToDevice, s));
+        DD_CUDA(cudaMemcpyAsync(st->AP + (size_t)its * n, c->q, n * 8, cudaMemcpyDeviceToDevice, s));
+      }
+      vec_axpy2(n, c->sc, c->xg, c->p, c->r, c->q, c->partials, s);
+      vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
+      if (k && o.reorth) {
+        // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
+        defl_mu(n, k, W, n, c->r, st->WWinv, c->wpart, c->mu, s);
+        defl_update(n, k, W, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, s);
+        vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, s);
+        vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
+      }
+      its++;
+      DD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DD_CUDA(cudaStreamSynchronize(s));
+      if (st) st->alphas.push_back(c->sc_host[SC_ALPHA]);
+      if (c->sc_host[SC_FLAG] != 0.0) {
+        status = DD_BREAKDOWN;
+        break;
+      }
+      rel = std::sqrt(c->sc_host[SC_RR]) / ref;
+      if (rel < rtol) break;
+      if (its >= o.maxit) {
+        status = DD_NOT_CONVERGED;
+        break;
+      }
+      std::swap(c->z, c->zold);
+      precond_apply(c, c->r, c->z, s);
+      if (record && st && its <= st->hmax)
+        DD_CUDA(cudaMemcpyAsync(st->Z + (size_t)its * n, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
+      vec_dots(n, c->r, c->z, o.flexible ? c->r : nullptr, o.flexible ? c->zold : nullptr, nullptr, nullptr,
+               c->partials, s);
+      vec_finalize(c->partials, c->sc, FIN_RZ, o.flexible, s);
+      if (k) defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
+      defl_update(n, k, W, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, s);
+    }
+  }
+  if (stats) {
+    stats->iters = its;
+    stats->rel_res = rel;
+    stats->recycled_k = k;
+    stats->frozen = st ? (int)st->frozen : 0;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycle* st, dd_stats* stats, void* stream) {
+  if (!c || !f || !x || !st || st->ctx != c || !(rtol > 0.0)) {
+    g_last_error = "dd_solve: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  dd_status result = DD_OK;
+  dd_status gs = guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    DD_CUDA(cudaEventRecord(c->ev0, s));
+    condense(c, f, c->bvec, s);
+    DD_CUDA(cudaMemcpyAsync(c->xg, st->xg_prev, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
+    bool record = st->kmax > 0 && !st->frozen;
+    result = pcg_solve(c, st, rtol, record, stats, s);
+    recover(c, f, c->xg, x, s);
+    DD_CUDA(cudaMemcpyAsync(st->xg_prev, c->xg, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
+    if (record && (result == DD_OK || result == DD_NOT_CONVERGED)) {
+      recycle_update(c, st, (int)st->alphas.size(), s);
+    } else {
+      st->step++;
+    }
+    DD_CUDA(cudaEventRecord(c->ev1, s));
+    check_err(c, s);
+    if (stats) {
+      float ms = 0.f;
+      DD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      stats->ms = ms;
+      stats->frozen = (int)st->frozen;
+    }
+  });
+  if (gs != DD_OK) return gs;
+  if (result != DD_OK) g_last_error = result == DD_NOT_CONVERGED ? "maxit reached" : "PCG breakdown";
+  return result;
+}
+
+dd_status dd_adjoint(dd_ctx*, const double*, const double*, double*, double*, double, dd_recycle*, dd_stats*, void*) {
+  g_last_error = "dd_adjoint: not available in this build";
+  return DD_INVALID_ARG;
+}
+
+dd_status dd_recycle_export(const dd_recycle*, void*, size_t*) {
+  g_last_error = "dd_recycle_export: not available in this build";
+  return DD_INVALID_ARG;
+}
+
+dd_status dd_recycle_import(dd_ctx*, const void*, size_t, dd_recycle**) {
+  g_last_error = "dd_recycle_import: not available in this build";
+  return DD_INVALID_ARG;
+}
+
+}  // extern "C"

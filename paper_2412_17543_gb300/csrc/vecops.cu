@@ -1,0 +1,309 @@
+// Krylov-vector kernels: deterministic dot products (fixed grid, fixed-order
+// two-stage reduction, no floating-point atomics), fused PCG updates, the
+// deflation projection (Algorithm 1: mu = (W^T A W)^{-1} (AW)^T z, p = z + beta p - W mu),
+// and tall-skinny Gram / combination kernels for the recycling update
+// (eq. harmonicRitz).
+#include "vecops.h"
+
+namespace dd {
+
+constexpr int RB = 256;  // threads per reduction block
+
+template <int ND>
+__device__ __forceinline__ void block_reduce_store(double (&v)[ND], double* partials) {
+  __shared__ double sh[ND][RB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    double x = v[d];
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[d][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < ND) {
+    double s = 0.0;
+    for (int w = 0; w < RB / 32; ++w) s += sh[threadIdx.x][w];
+    partials[blockIdx.x * MAXDOT + threadIdx.x] = s;
+  }
+}
+
+// partial dots: d0 = a0.b0, d1 = a1.b1, d2 = a2.b2 (null pairs skipped)
+__global__ void __launch_bounds__(RB) k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
+                                             const double* __restrict__ a1, const double* __restrict__ b1,
+                                             const double* __restrict__ a2, const double* __restrict__ b2,
+                                             double* partials) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    v[0] = fma(a0[i], b0[i], v[0]);
+    if (a1) v[1] = fma(a1[i], b1[i], v[1]);
+    if (a2) v[2] = fma(a2[i], b2[i], v[2]);
+  }
+  block_reduce_store<3>(v, partials);
+}
+
+// x += alpha p ; r -= alpha q ; partial ||r||^2
+__global__ void __launch_bounds__(RB) k_axpy2(int64_t n, const double* __restrict__ sc, double* __restrict__ x,
+                                              const double* __restrict__ p, double* __restrict__ r,
+                                              const double* __restrict__ q, double* partials) {
+  const double alpha = sc[SC_ALPHA];
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    x[i] = fma(alpha, p[i], x[i]);
+    double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  block_reduce_store<1>(v, partials);
+}
+
+// single-block finalization: sums the partials in a fixed order and updates the scalars
+__global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible) {
+  __shared__ double tot[3];
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partials[b * MAXDOT + threadIdx.x];
+    tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  switch (op) {
+    case FIN_PQ: {
+      double pq = tot[0];
+      sc[SC_PQ] = pq;
+      if (!(pq > 0.0) || !isfinite(pq) || !isfinite(sc[SC_RZ])) {
+        sc[SC_FLAG] = 1.0;
+        sc[SC_ALPHA] = 0.0;
+      } else {
+        sc[SC_ALPHA] = sc[SC_RZ] / pq;
+      }
+      break;
+    }
+    case FIN_RR:
+      sc[SC_RR] = tot[0];
+      if (!isfinite(tot[0])) sc[SC_FLAG] = 1.0;
+      break;
+    case FIN_RZ0:
+      sc[SC_RZ] = tot[0];
+      if (!(tot[0] > 0.0) || !isfinite(tot[0])) sc[SC_FLAG] = 1.0;
+      break;
+    case FIN_RZ: {
+      double rz_new = tot[0], rz_old_z = tot[1];
+      double num = flexible ? (rz_new - rz_old_z) : rz_new;
+      double rz = sc[SC_RZ];
+      sc[SC_BETA] = (rz != 0.0) ? num / rz : 0.0;
+      sc[SC_RZ] = rz_new;
+      if (!(rz_new > 0.0) || !isfinite(rz_new)) sc[SC_FLAG] = 1.0;
+      break;
+    }
+    case FIN_BB:
+      sc[SC_BB] = tot[0];
+      sc[SC_RR] = tot[1];
+      break;
+    default:
+      break;
+  }
+}
+
+void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, const double* a2,
+              const double* b2, double* partials, cudaStream_t s) {
+  k_dots<<<NBLK, RB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, partials);
+  DD_CHECK_LAUNCH();
+}
+void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s) {
+  k_finalize<<<1, 32, 0, s>>>(NBLK, partials, sc, op, flexible);
+  DD_CHECK_LAUNCH();
+}
+void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
+               cudaStream_t s) {
+  k_axpy2<<<NBLK, RB, 0, s>>>(n, sc, x, p, r, q, partials);
+  DD_CHECK_LAUNCH();
+}
+
+// y = a - b
+__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] - b[i];
+}
+void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s) {
+  k_sub<<<NBLK, RB, 0, s>>>(n, a, b, y);
+  DD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// deflation
+// ---------------------------------------------------------------------------
+// partial dots of the k columns of W (column-major, leading dimension ld) with v
+__global__ void __launch_bounds__(RB) k_wdots(int64_t n, int k, const double* __restrict__ W, int64_t ld,
+                                              const double* __restrict__ v, double* wpart) {
+  __shared__ double sh[RB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < k; ++c) {
+    const double* w = W + (int64_t)c * ld;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB)
+      acc = fma(w[i], v[i], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sh[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w2 = 0; w2 < RB / 32; ++w2) s += sh[w2];
+      wpart[(int64_t)blockIdx.x * MAXK + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// mu = Ginv * (sum of partials)   (k x k, one block)
+__global__ void k_wfinal(int nblk, int k, const double* __restrict__ wpart, const double* __restrict__ Ginv,
+                         double* mu) {
+  __shared__ double d[MAXK];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += wpart[(int64_t)b * MAXK + c];
+    d[c] = s;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s += Ginv[a * k + c] * d[c];
+    mu[a] = s;
+  }
+}
+
+void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, const double* Ginv, double* wpart,
+             double* mu, cudaStream_t s) {
+  if (k == 0) return;
+  k_wdots<<<NBLK, RB, 0, s>>>(n, k, W, ld, v, wpart);
+  DD_CHECK_LAUNCH();
+  k_wfinal<<<1, 64, 0, s>>>(NBLK, k, wpart, Ginv, mu);
+  DD_CHECK_LAUNCH();
+}
+
+// y = alpha_z * z + beta * y - W mu   (beta taken from sc[beta_idx] if beta_idx >= 0, else 0)
+__global__ void k_pupdate(int64_t n, int k, const double* __restrict__ W, int64_t ld, const double* __restrict__ mu,
+                          const double* __restrict__ z, double* __restrict__ y, const double* __restrict__ sc,
+                          int beta_idx, double sign_w) {
+  __shared__ double m[MAXK];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) m[c] = mu[c];
+  __syncthreads();
+  const double beta = beta_idx >= 0 ? sc[beta_idx] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (z ? z[i] : 0.0) + (beta_idx >= 0 ? beta * y[i] : (z ? 0.0 : y[i]));
+    double wm = 0.0;
+    for (int c = 0; c < k; ++c) wm = fma(W[(int64_t)c * ld + i], m[c], wm);
+    y[i] = v + sign_w * wm;
+  }
+}
+
+void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
+                 const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
+  k_pupdate<<<NBLK, RB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  DD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// tall-skinny products for the recycling update
+// ---------------------------------------------------------------------------
+// partial C[a][b] = sum_i X_a[i] Y_b[i] over this block's rows (na, nb <= 128)
+constexpr int GR = 16;  // rows per smem stage (2 x 16 x 129 doubles of static shared memory)
+__global__ void __launch_bounds__(256) k_gram(int64_t n, int na, const double* const* __restrict__ X, int nb,
+                                              const double* const* __restrict__ Y, double* part) {
+  __shared__ double xs[GR][129];
+  __shared__ double ys[GR][129];
+  const int npair = na * nb;
+  double acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+  for (int64_t base = i0; base < i1; base += GR) {
+    int rows = (int)min((int64_t)GR, i1 - base);
+    for (int t = threadIdx.x; t < GR * na; t += blockDim.x) {
+      int r = t % GR, a = t / GR;
+      xs[r][a] = r < rows ? X[a][base + r] : 0.0;
+    }
+    for (int t = threadIdx.x; t < GR * nb; t += blockDim.x) {
+      int r = t % GR, b = t / GR;
+      ys[r][b] = r < rows ? Y[b][base + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      int pr = threadIdx.x + t * 256;
+      if (pr < npair) {
+        int a = pr / nb, b = pr % nb;
+        double s = acc[t];
+        for (int r = 0; r < GR; ++r) s = fma(xs[r][a], ys[r][b], s);
+        acc[t] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    int pr = threadIdx.x + t * 256;
+    if (pr < npair) part[(int64_t)blockIdx.x * npair + pr] = acc[t];
+  }
+}
+
+__global__ void k_gram_reduce(int nblk, int npair, const double* __restrict__ part, double* C) {
+  for (int pr = blockIdx.x * blockDim.x + threadIdx.x; pr < npair; pr += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * npair + pr];
+    C[pr] = s;
+  }
+}
+
+void gram(int64_t n, int na, const double* const* X, int nb, const double* const* Y, double* part, double* C,
+          cudaStream_t s) {
+  if (na == 0 || nb == 0) return;
+  if (na > 128 || nb > 128 || na * nb > 16 * 256) throw Error(DD_INVALID_ARG, "gram: too many columns");
+  k_gram<<<NBLK, 256, 0, s>>>(n, na, X, nb, Y, part);
+  DD_CHECK_LAUNCH();
+  k_gram_reduce<<<(na * nb + 255) / 256, 256, 0, s>>>(NBLK, na * nb, part, C);
+  DD_CHECK_LAUNCH();
+}
+
+// out_c[i] = sum_a V_a[i] Y[a][c]   (Y row-major m x kc)
+__global__ void k_lincomb(int64_t n, int m, const double* const* __restrict__ V, const double* __restrict__ Yc, int kc,
+                          double* const* __restrict__ out) {
+  extern __shared__ double ysm[];
+  for (int t = threadIdx.x; t < m * kc; t += blockDim.x) ysm[t] = Yc[t];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int c0 = 0; c0 < kc; c0 += 8) {
+      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int a = 0; a < m; ++a) {
+        double v = V[a][i];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (c0 + t < kc) acc[t] = fma(v, ysm[a * kc + c0 + t], acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (c0 + t < kc) out[c0 + t][i] = acc[t];
+    }
+  }
+}
+
+void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s) {
+  if (kc == 0) return;
+  size_t smem = (size_t)m * kc * sizeof(double);
+  if (smem > 48 * 1024) DD_CUDA(cudaFuncSetAttribute(k_lincomb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_lincomb<<<NBLK, RB, smem, s>>>(n, m, V, Yc, kc, out);
+  DD_CHECK_LAUNCH();
+}
+
+// MAP_j = (z_j - z_{j+1}) / alpha_j
+__global__ void k_zdiff(int64_t n, const double* __restrict__ z0, const double* __restrict__ z1, double inv_alpha,
+                        double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (z0[i] - z1[i]) * inv_alpha;
+}
+void zdiff(int64_t n, const double* z0, const double* z1, double inv_alpha, double* out, cudaStream_t s) {
+  k_zdiff<<<NBLK, RB, 0, s>>>(n, z0, z1, inv_alpha, out);
+  DD_CHECK_LAUNCH();
+}
+
+}  // namespace dd

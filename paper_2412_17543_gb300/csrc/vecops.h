@@ -1,0 +1,36 @@
+// Krylov-vector kernels (vecops.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace dd {
+
+constexpr int NBLK = 304;   // reduction grid: 2 blocks per SM of GB300 (fixed => deterministic sums)
+constexpr int MAXDOT = 4;   // dot products per partial record
+constexpr int MAXK = 128;   // maximum deflation basis size
+
+// device scalar slots of PCG
+enum {
+  SC_RZ = 0, SC_PQ, SC_ALPHA, SC_RR, SC_BETA, SC_BB, SC_FLAG, SC_COUNT = 16
+};
+enum { FIN_PQ = 1, FIN_RR, FIN_RZ0, FIN_RZ, FIN_BB };
+
+void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, const double* a2,
+              const double* b2, double* partials, cudaStream_t s);
+void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s);
+void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
+               cudaStream_t s);
+void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, const double* Ginv, double* wpart,
+             double* mu, cudaStream_t s);
+// y = z + beta*y + sign_w * W mu  (beta from sc[beta_idx] if beta_idx >= 0; with z == NULL and beta_idx < 0: y += sign_w W mu)
+void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
+                 const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+void gram(int64_t n, int na, const double* const* X, int nb, const double* const* Y, double* part, double* C,
+          cudaStream_t s);
+void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s);
+void zdiff(int64_t n, const double* z0, const double* z1, double inv_alpha, double* out, cudaStream_t s);
+
+}  // namespace dd

@@ -1,0 +1,163 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived from the arithmetic):
+  * FP64 operators: a sum of <= ~800 products per output in a different order than
+    the oracle's LAPACK-based dense path: |y - y_oracle| <= 1e-12 * max|y_oracle|.
+  * DF64 Schur operator (float pairs, ~2^-44 per operation): 1e-11 * max|y|.
+  * FP32 preconditioner: 1e-4 * max|z| (single-precision storage, FP32 sums).
+  * Solutions (spec tolerance): relative 2-norm error vs the sparse Cholesky
+    solution <= 1e-7 at rtol 1e-9.
+"""
+import numpy as np
+import pytest
+
+from oracle import cholesky, dd, pcg
+from workload import load_sequence, make_mesh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2412_17543_gb300 as P  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+CASES = {
+    # name: (n, sub, ratio, aspect, levels, kinds)
+    "cube16_cf": (16, 4, 1.0, None, 2, (dd.CORNER, dd.FACE)),
+    "graded16_s8": (16, 8, 1.08, 20.0, 2, (dd.CORNER, dd.EDGE, dd.FACE)),
+    "graded24_s8": (24, 8, 1.3, 20.0, 2, (dd.CORNER, dd.EDGE, dd.FACE)),
+    "graded16_s2_3l": (16, 2, 1.08, 20.0, 3, (dd.CORNER, dd.EDGE, dd.FACE)),
+}
+
+
+def _opts(levels, kinds, **kw):
+    o = dict(levels=levels, coarse_group=4, use_corners=int(dd.CORNER in kinds), use_edges=int(dd.EDGE in kinds),
+             use_faces=int(dd.FACE in kinds), weights="diag")
+    o.update(kw)
+    return o
+
+
+_oracles = {}
+
+
+def oracle_case(name):
+    if name not in _oracles:
+        n, sub, ratio, aspect, levels, kinds = CASES[name]
+        m = make_mesh(n, sub, ratio, aspect)
+        subs = dd.q1_substructures(m)
+        _oracles[name] = (m, subs, kinds, levels)
+    return _oracles[name]
+
+
+@pytest.mark.parametrize("name", ["cube16_cf", "graded16_s8", "graded24_s8"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-11)])
+def test_schur_apply(name, prec, tol):
+    m, subs, kinds, levels = oracle_case(name)
+    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec))
+    assert np.array_equal(S.interface_nodes(), subs.gamma)
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        x = rng.standard_normal(len(subs.gamma))
+        y = N(S.schur_apply(T(x)))
+        yo = subs.schur_apply(x)
+        assert np.abs(y - yo).max() <= tol * np.abs(yo).max()
+
+
+@pytest.mark.parametrize("name", ["cube16_cf", "graded24_s8"])
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_condense_and_recover(name, prec):
+    m, subs, kinds, levels = oracle_case(name)
+    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec))
+    f = load_sequence(m, 1, 1)[0]
+    b = N(S.condense(T(f)))
+    bo = subs.condense(f)
+    assert np.abs(b - bo).max() <= 1e-11 * np.abs(bo).max()
+    xg = np.random.default_rng(2).standard_normal(len(subs.gamma))
+    x = N(S.recover(T(f), T(xg)))
+    xo = subs.recover(f, xg)
+    assert np.abs(x - xo).max() <= 1e-11 * np.abs(xo).max()
+
+
+@pytest.mark.parametrize("name", ["cube16_cf", "graded16_s8", "graded16_s2_3l"])
+@pytest.mark.parametrize("weights", ["card", "diag"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_precond_apply(name, weights, prec, tol):
+    m, subs, kinds, levels = oracle_case(name)
+    S = P.Solver(m, **_opts(levels, kinds, weights=weights, precond_prec=prec))
+    Po = dd.Preconditioner(subs, levels, kinds, weights, group=4)
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(len(subs.gamma))
+    z = N(S.precond_apply(T(r)))
+    zo = Po.apply(r)
+    assert np.abs(z - zo).max() <= tol * np.abs(zo).max()
+
+
+def _direct(m, F):
+    ch = cholesky.factor_mesh(m)
+    return [ch.solve(f) for f in F]
+
+
+@pytest.mark.parametrize("schur,pre,flex", [("fp64", "fp64", 0), ("df64", "fp32", 1)])
+def test_solve_sequence_plain(schur, pre, flex):
+    m, subs, kinds, levels = oracle_case("cube16_cf")
+    F = load_sequence(m, 1, 10)
+    X = _direct(m, F)
+    S = P.Solver(m, **_opts(2, kinds, schur_prec=schur, precond_prec=pre, flexible=flex))
+    rec = S.recycler(0)
+    Po = dd.Preconditioner(subs, 2, kinds, "diag")
+    xs_o, infos_o, _ = pcg.solve_sequence(subs.schur_apply, Po.apply, [subs.condense(f) for f in F], R=0, rtol=1e-9)
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        x = N(x)
+        err = np.linalg.norm(x - X[t]) / np.linalg.norm(X[t])
+        assert err <= 1e-7, (t, err)
+        assert st["rel_res"] < 1e-9
+        if schur == "fp64" and pre == "fp64":
+            assert abs(st["iters"] - infos_o[t].iters) <= 1, (t, st["iters"], infos_o[t].iters)
+
+
+@pytest.mark.parametrize("strategy", ["B4", "B3", "B2", "B1"])
+def test_solve_sequence_recycled(strategy):
+    m, subs, kinds, levels = oracle_case("graded16_s8")
+    F = load_sequence(m, 2, 8)
+    X = _direct(m, F)
+    S = P.Solver(m, **_opts(2, (dd.CORNER,), schur_prec="fp64", precond_prec="fp64"))
+    rec = S.recycler(6, strategy)
+    Po = dd.Preconditioner(subs, 2, (dd.CORNER,), "diag")
+    _, infos_o, _ = pcg.solve_sequence(subs.schur_apply, Po.apply, [subs.condense(f) for f in F], R=6,
+                                       strategy=strategy, rtol=1e-9)
+    its = []
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        x = N(x)
+        err = np.linalg.norm(x - X[t]) / np.linalg.norm(X[t])
+        assert err <= 1e-7, (t, err)
+        its.append(st["iters"])
+    its_o = [i.iters for i in infos_o]
+    assert its[0] == its_o[0]
+    assert sum(its) <= sum(its_o) + len(F), (its, its_o)
+
+
+def test_solve_mixed_recycled_three_level():
+    m, subs, kinds, levels = oracle_case("graded16_s2_3l")
+    F = load_sequence(m, 3, 6)
+    X = _direct(m, F)
+    S = P.Solver(m, **_opts(3, kinds, schur_prec="df64", precond_prec="fp32", flexible=1))
+    rec = S.recycler(8, "B4")
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        err = np.linalg.norm(N(x) - X[t]) / np.linalg.norm(X[t])
+        assert err <= 1e-7, (t, err)

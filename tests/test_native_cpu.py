@@ -1,0 +1,75 @@
+"""CPU-side checks of the native library: exports and host-side setup against the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dd
+from workload import FACE_X1, make_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_2412_17543_gb300 as P
+    try:
+        return P.load()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+
+
+def _declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(dd_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib()
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2412_17543_gb300 import _native
+    assert set(names) == set(_native.SIGNATURES), "binding must declare exactly the header's functions"
+
+
+@pytest.mark.parametrize("n,sub,levels,kinds", [(16, 4, 2, dict(use_edges=0)), (16, 2, 3, {}), (12, 4, 2, {})])
+def test_plan_matches_oracle_partition(n, sub, levels, kinds):
+    _lib()
+    import paper_2412_17543_gb300 as P
+    m = make_mesh(n, sub, 1.08, 20.0)
+    info, nodes = P.plan(m, levels=levels, coarse_group=4, **kinds)
+    subs = dd.q1_substructures(m)
+    assert info["n_free"] == m.n_free
+    assert info["n_gamma"] == len(subs.gamma)
+    assert np.array_equal(nodes, subs.gamma)
+    sel = (dd.CORNER, dd.FACE) if kinds.get("use_edges", 1) == 0 else (dd.CORNER, dd.EDGE, dd.FACE)
+    nC = sum(1 for k in subs.glob_kind if k in sel)
+    assert info["n_coarse"] == nC
+    if levels == 3:
+        Pc = dd.Preconditioner(subs, 3, sel, group=4)
+        assert info["n_sub2"] == Pc.subs2.S
+        assert info["n_coarse3"] == Pc.l2.nC
+
+
+def test_plan_rejects_bad_input():
+    _lib()
+    import paper_2412_17543_gb300 as P
+    m = make_mesh(10, 4)  # 4 does not divide 10
+    with pytest.raises(P.DDError) as e:
+        P.plan(m, levels=2)
+    assert e.value.code == 1
+    m = make_mesh(8, 4, dirichlet=0)  # pure Neumann: K singular
+    with pytest.raises(P.DDError):
+        P.plan(m, levels=2)
+    m = make_mesh(8, 4, coef=-np.ones((8, 8, 8)))
+    with pytest.raises(P.DDError):
+        P.plan(m, levels=2)
