@@ -172,6 +172,26 @@ dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, double rtol, dd_recy
 dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double* grad_f,
                      double* grad_coef, double rtol, dd_recycle* st, dd_stats* stats, void* stream);
 
+/* ---- profiling (CUDA events on the launching stream) ---- */
+enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} GEMV of the Schur operator (Sect. 3.1) */
+       DD_PROF_SYMV_N = 1,     /* batched constrained-Neumann GEMV of BDDC (eq. localCorr) */
+       DD_PROF_SCHUR = 2,      /* whole Schur-complement applications */
+       DD_PROF_PRECOND = 3,    /* whole BDDC applications */
+       DD_PROF_RECYCLE = 4,    /* recycling updates between solves (Sect. 4.2) */
+       DD_PROF_COUNT = 5 };
+typedef struct {
+  double ms;                /* summed device time of the timed launches/regions */
+  int64_t launches;         /* number of timed launches/regions */
+  double alg_bytes;         /* algorithmic bytes of one launch (matrix entries once, vectors in and out) */
+} dd_kernel_prof;
+/* enable != 0 starts event timing of the classes above (adds two event records
+ * per timed launch); enable == 0 stops it. If prof is not NULL, writes the totals
+ * accumulated since the last read ([DD_PROF_COUNT], host) and resets them
+ * (synchronizes `stream`). *kernel_launches (nullable) receives the number of
+ * kernels this context launched since the last read. */
+dd_status dd_profile(dd_ctx* ctx, int32_t enable, dd_kernel_prof* prof /* host, out, nullable */,
+                     int64_t* kernel_launches /* host, out, nullable */, void* stream);
+
 /* Checkpoint of a recycle state: writes at most *bytes bytes to host_buf; with
  * host_buf NULL only sets *bytes to the size needed. */
 dd_status dd_recycle_export(const dd_recycle* st, void* host_buf, size_t* bytes);

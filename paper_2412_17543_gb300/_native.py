@@ -38,6 +38,13 @@ class Info(ctypes.Structure):
                 ("n_coarse3", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("setup_seconds", ctypes.c_double)]
 
 
+class KernelProf(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("alg_bytes", ctypes.c_double)]
+
+
+PROF_CLASSES = ["symv_KIIinv", "symv_N", "schur_apply", "precond_apply", "recycle_update"]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("rel_res0", ctypes.c_double), ("rel_res", ctypes.c_double),
                 ("recycled_k", ctypes.c_int32), ("frozen", ctypes.c_int32), ("ms", ctypes.c_float)]
@@ -63,6 +70,7 @@ SIGNATURES = {
     "dd_recycle_destroy": (None, [_P]),
     "dd_solve": (ctypes.c_int, [_P, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),
     "dd_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),
+    "dd_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(KernelProf), ctypes.POINTER(ctypes.c_int64), _P]),
     "dd_recycle_export": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "dd_recycle_import": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
 }

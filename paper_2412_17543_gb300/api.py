@@ -136,6 +136,17 @@ class Solver:
         nat.check(self.lib.dd_recover(self.handle, _dptr(f), _dptr(xg), _dptr(x), _stream_ptr()), "dd_recover")
         return x
 
+    def profile(self, enable: bool, read: bool = True):
+        """Starts/stops kernel timing; returns ({class: (ms, launches, alg_bytes)}, kernel launches) if read."""
+        if not read:
+            nat.check(self.lib.dd_profile(self.handle, int(enable), None, None, _stream_ptr()), "dd_profile")
+            return None
+        prof = (nat.KernelProf * len(nat.PROF_CLASSES))()
+        nl = ctypes.c_int64()
+        nat.check(self.lib.dd_profile(self.handle, int(enable), prof, ctypes.byref(nl), _stream_ptr()), "dd_profile")
+        out = {name: (prof[i].ms, prof[i].launches, prof[i].alg_bytes) for i, name in enumerate(nat.PROF_CLASSES)}
+        return out, nl.value
+
     def recycler(self, k=0, strategy="B4", freeze_tol=1e-5) -> "Recycler":
         return Recycler(self, k, strategy, freeze_tol)
 

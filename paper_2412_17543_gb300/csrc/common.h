@@ -27,7 +27,12 @@ struct Error : std::runtime_error {
                         ":" + std::to_string(__LINE__));                                      \
   } while (0)
 
-#define DD_CHECK_LAUNCH() DD_CUDA(cudaGetLastError())
+void count_launch();  // process-wide counter of kernel launches (profiling)
+#define DD_CHECK_LAUNCH() \
+  do {                    \
+    ::dd::count_launch(); \
+    DD_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define DD_REQUIRE(cond, msg) \
   do {                        \

@@ -202,10 +202,10 @@ std::vector<CoarseDof> select_coarse(const Globs& gl, bool corners, bool edges, 
 }
 
 // Weights, coarse maps and dense pipelines of a level whose subdomain matrices are given.
-void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, int weights,
-                  const std::vector<std::vector<double>>& Kloc, const std::vector<int>& nloc,
-                  const std::vector<std::vector<int>>& Iloc, const std::vector<std::vector<int>>& Gloc, bool needE,
-                  const char* what) {
+template <class KFn, class DiagFn>
+void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, int weights, KFn kloc_fn,
+                  DiagFn diag_fn, const std::vector<int>& nloc, const std::vector<std::vector<int>>& Iloc,
+                  const std::vector<std::vector<int>>& Gloc, bool needE, const char* what) {
   L.n_coarse = (int)cd.size();
   std::vector<std::vector<int>> cdofs_of_sub(L.S);
   for (size_t c = 0; c < cd.size(); ++c)
@@ -213,20 +213,20 @@ void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, i
   L.sub.assign(L.S, DenseSub());
   // weights
   std::vector<double> dsum(L.n_gamma, 0.0);
-  if (weights == DD_WEIGHTS_DIAG) {
-    for (int s = 0; s < L.S; ++s)
-      for (size_t j = 0; j < Gloc[s].size(); ++j) {
-        int p = Gloc[s][j];
-        dsum[L.gmap[L.goff[s] + j]] += Kloc[s][(size_t)p * nloc[s] + p];
-      }
+  std::vector<std::vector<double>> diag(L.S);
+  for (int s = 0; s < L.S; ++s) {
+    diag_fn(s, diag[s]);
+    if (weights == DD_WEIGHTS_DIAG)
+      for (size_t j = 0; j < Gloc[s].size(); ++j) dsum[L.gmap[L.goff[s] + j]] += diag[s][Gloc[s][j]];
   }
   int failed = -1;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int s = 0; s < L.S; ++s) {
-    std::vector<double> C;
+    std::vector<double> C, K;
     subdomain_constraints(L, s, gl, cd, cdofs_of_sub, C);
+    kloc_fn(s, K);
     DenseSub& ds = L.sub[s];
-    bool ok = dense_sub(nloc[s], Kloc[s].data(), Iloc[s], Gloc[s], C, (int)cdofs_of_sub[s].size(), needE, ds);
+    bool ok = dense_sub(nloc[s], K.data(), Iloc[s], Gloc[s], C, (int)cdofs_of_sub[s].size(), needE, ds);
     if (!ok) {
 #pragma omp critical
       failed = s;
@@ -236,8 +236,7 @@ void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, i
     for (size_t j = 0; j < Gloc[s].size(); ++j) {
       int g = L.gmap[L.goff[s] + j];
       if (weights == DD_WEIGHTS_DIAG) {
-        int p = Gloc[s][j];
-        ds.D[j] = Kloc[s][(size_t)p * nloc[s] + p] / dsum[g];
+        ds.D[j] = diag[s][Gloc[s][j]] / dsum[g];
       } else {
         ds.D[j] = 0.0;  // filled below (needs multiplicities)
       }
@@ -396,15 +395,12 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
   std::vector<CoarseDof> cd = select_coarse(gl, opt.use_corners, opt.use_edges, opt.use_faces);
   DD_REQUIRE(!cd.empty(), "no coarse degrees of freedom selected");
 
-  // ---- local stiffness matrices (closed-form Kronecker form of the Q1 brick) ----
-  std::vector<std::vector<double>> Kloc(M.S);
-#pragma omp parallel for schedule(dynamic, 4)
-  for (int s = 0; s < M.S; ++s) {
+  // ---- local stiffness matrices (closed-form Kronecker form of the Q1 brick), built per subdomain ----
+  auto kloc_fn = [&](int s, std::vector<double>& K) {
     int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
     int nl = nloc[s];
     std::vector<int> pos(M.NL, -1);
     for (int t = 0; t < nl; ++t) pos[lfree[s][t]] = t;
-    std::vector<double>& K = Kloc[s];
     K.assign((size_t)nl * nl, 0.0);
     for (int ec = 0; ec < M.sz; ++ec)
       for (int eb = 0; eb < M.sy; ++eb)
@@ -427,10 +423,25 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
             }
           }
         }
-  }
-  finish_level(L1, gl, cd, opt.weights, Kloc, nloc, Iloc, Gloc, false, "level 1");
-  Kloc.clear();
-  Kloc.shrink_to_fit();
+  };
+  auto kdiag_fn = [&](int s, std::vector<double>& d) {  // diagonal: every corner of a brick adds 4(cx+cy+cz)
+    int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
+    int nl = nloc[s];
+    std::vector<int> pos(M.NL, -1);
+    for (int t = 0; t < nl; ++t) pos[lfree[s][t]] = t;
+    d.assign(nl, 0.0);
+    for (int ec = 0; ec < M.sz; ++ec)
+      for (int eb = 0; eb < M.sy; ++eb)
+        for (int ea = 0; ea < M.sx; ++ea) {
+          int64_t e = (I * M.sx + ea) + (int64_t)M.nx * ((J * M.sy + eb) + (int64_t)M.ny * (Kk * M.sz + ec));
+          double v = 4.0 * (M.ecx[e] + M.ecy[e] + M.ecz[e]);
+          for (int p = 0; p < 8; ++p) {
+            int lp = (ea + (p & 1)) + M.NLx * ((eb + ((p >> 1) & 1)) + M.NLy * (ec + (p >> 2)));
+            if (pos[lp] >= 0) d[pos[lp]] += v;
+          }
+        }
+  };
+  finish_level(L1, gl, cd, opt.weights, kloc_fn, kdiag_fn, nloc, Iloc, Gloc, false, "level 1");
 
   H.levels = opt.levels;
   if (opt.levels == 2) {
@@ -503,7 +514,13 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
     Globs gl2 = make_globs(nG2, [&](int64_t gg, std::vector<int>& subs) { subs = groups_of_c[H.gam2_c[gg]]; });
     std::vector<CoarseDof> cd2 = select_coarse(gl2, true, true, true);
     DD_REQUIRE(!cd2.empty(), "no level-2 coarse dofs");
-    finish_level(L2, gl2, cd2, opt.weights, K2, nloc2, I2, G2, true, "level 2");
+    finish_level(
+        L2, gl2, cd2, opt.weights, [&](int j, std::vector<double>& K) { K = K2[j]; },
+        [&](int j, std::vector<double>& d) {
+          d.resize(nloc2[j]);
+          for (int t = 0; t < nloc2[j]; ++t) d[t] = K2[j][(size_t)t * nloc2[j] + t];
+        },
+        nloc2, I2, G2, true, "level 2");
     std::vector<double> KC3 = assemble_coarse(L2);
     H.KC3inv.resize(KC3.size());
     if (!la::spd_inverse(L2.n_coarse, KC3.data(), H.KC3inv.data()))

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -19,6 +20,10 @@
 using namespace dd;
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+namespace dd {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace dd
 
 struct dd_ctx {
   dd_options opt{};
@@ -45,12 +50,73 @@ struct dd_ctx {
   double* ybuf = nullptr;      // [128*128] combination coefficients
   const double** ptrs = nullptr;  // device pointer table for gram / lincomb
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // profiling: events around timed launches, harvested after a synchronization
+  bool prof_on = false;
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[DD_PROF_COUNT] = {0};
+  int64_t prof_n[DD_PROF_COUNT] = {0};
+  double prof_bytes[DD_PROF_COUNT] = {0};
+  cudaEvent_t get_event() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    DD_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  void harvest() {  // caller has synchronized the stream
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        prof_ms[p.cls] += ms;
+        prof_n[p.cls] += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
   ~dd_ctx() {
     if (sc_host) cudaFreeHost(sc_host);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
   }
 };
+
+namespace {
+// times the launches issued on `s` during its lifetime when profiling is on
+struct ProfScope {
+  dd_ctx* c;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(dd_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    if (c->prof_on && cls >= 0 && cls < DD_PROF_COUNT) {
+      a = c->get_event();
+      b = c->get_event();
+      DD_CUDA(cudaEventRecord(a, s));
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEventRecord(b, s);
+      c->pending.push_back({cls, a, b});
+    }
+  }
+};
+}  // namespace
 
 struct dd_recycle {
   dd_ctx* ctx = nullptr;
@@ -212,8 +278,12 @@ const void* upload_dense(DeviceArena& A, const std::vector<double>& M, int prec)
 // operators
 // ---------------------------------------------------------------------------
 void schur_apply(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
+  ProfScope ps(c, DD_PROF_SCHUR, s);
   launch_elem_interior(c->mesh, ELEM_SCHUR, x, nullptr, c->w.tI, s);
-  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  {
+    ProfScope pk(c, DD_PROF_SYMV_KII, s);
+    launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  }
   launch_elem_interface(c->mesh, ELEM_SCHUR, x, c->w.sI, c->w.yloc, s);
   launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, nullptr, nullptr, y, s);
 }
@@ -236,7 +306,10 @@ template <class CoarseFn>
 void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* gloc,
                 double* gC, double* uC, CoarseFn coarse, cudaStream_t s) {
   launch_restrict(b.n_flat, b.gmap, b.D, r, rloc, s);
-  launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
+  {
+    ProfScope pk(c, &b == &c->b1 ? DD_PROF_SYMV_N : DD_PROF_COUNT, s);
+    launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
+  }
   launch_phiT(b, rloc, gloc, s);
   launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
   coarse(gC, uC);
@@ -259,6 +332,7 @@ void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
 }
 
 void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+  ProfScope ps(c, DD_PROF_PRECOND, s);
   Work& w = c->w;
   bddc_apply(c, c->b1, r, z, w.rloc, w.uloc, w.gloc, w.gC, w.uC,
              [&](const double* g, double* u) {
@@ -453,6 +527,16 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     DD_CUDA(cudaEventCreate(&c->ev0));
     DD_CUDA(cudaEventCreate(&c->ev1));
     DD_CUDA(cudaStreamSynchronize(s));
+    {
+      double kii = 0, nn = 0;
+      for (int i = 0; i < M.S; ++i) {
+        double a = H->l1.sub[i].nI, g = H->l1.sub[i].nG;
+        kii += a * (a + 1) / 2 * 8.0 + 2 * a * 8.0;
+        nn += g * (g + 1) / 2 * (pp == DD_PREC_FP32 ? 4.0 : 8.0) + 2 * g * 8.0;
+      }
+      c->prof_bytes[DD_PROF_SYMV_KII] = kii;
+      c->prof_bytes[DD_PROF_SYMV_N] = nn;
+    }
     c->info.n_free = c->n_free;
     c->info.n_gamma = c->n_gamma;
     c->info.n_sub = M.S;
@@ -877,12 +961,14 @@ dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycl
     recover(c, f, c->xg, x, s);
     DD_CUDA(cudaMemcpyAsync(st->xg_prev, c->xg, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
     if (record && (result == DD_OK || result == DD_NOT_CONVERGED)) {
+      ProfScope pr(c, DD_PROF_RECYCLE, s);
       recycle_update(c, st, (int)st->alphas.size(), s);
     } else {
       st->step++;
     }
     DD_CUDA(cudaEventRecord(c->ev1, s));
     check_err(c, s);
+    if (c->prof_on) c->harvest();
     if (stats) {
       float ms = 0.f;
       DD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
@@ -893,6 +979,28 @@ dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycl
   if (gs != DD_OK) return gs;
   if (result != DD_OK) g_last_error = result == DD_NOT_CONVERGED ? "maxit reached" : "PCG breakdown";
   return result;
+}
+
+dd_status dd_profile(dd_ctx* c, int32_t enable, dd_kernel_prof* prof, int64_t* launches, void* stream) {
+  if (!c) return DD_INVALID_ARG;
+  return guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prof || launches) {
+      DD_CUDA(cudaStreamSynchronize(s));
+      c->harvest();
+    }
+    if (prof) {
+      for (int k = 0; k < DD_PROF_COUNT; ++k) {
+        prof[k].ms = c->prof_ms[k];
+        prof[k].launches = c->prof_n[k];
+        prof[k].alg_bytes = c->prof_bytes[k];
+        c->prof_ms[k] = 0;
+        c->prof_n[k] = 0;
+      }
+    }
+    if (launches) *launches = g_launches.exchange(0);
+    c->prof_on = enable != 0;
+  });
 }
 
 dd_status dd_adjoint(dd_ctx*, const double*, const double*, double*, double*, double, dd_recycle*, dd_stats*, void*) {
