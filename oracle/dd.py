@@ -327,7 +327,7 @@ class Preconditioner:
 # ---------------------------------------------------------------------------
 
 def face_schur(subs: Substructures, i: int, face_dofs: np.ndarray) -> np.ndarray:
-    """Schur complement of subdomain matrix K_i onto the given face dofs (all other local dofs eliminated)."""
+    """Schur complement of subdomain matrix K_i onto the given dofs (all other local dofs eliminated)."""
     d = subs.dofs[i]
     F = np.searchsorted(d, face_dofs)
     R = np.setdiff1d(np.arange(len(d)), F)
@@ -338,17 +338,20 @@ def face_schur(subs: Substructures, i: int, face_dofs: np.ndarray) -> np.ndarray
 
 
 def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: float, max_per_face: int = 10,
-                              drop_tol: float = 1e-10):
-    """Extra face constraints from eq. eig-matrix, one problem per face shared by two subdomains.
+                              drop_tol: float = 1e-10, kinds=(CORNER, EDGE, FACE)):
+    """Extra face constraints from eq. eig-matrix, one problem per face shared by two subdomains s, t.
 
-    Reading used here: A_s, A_t are the Schur complements of the two subdomain
-    matrices onto the face dofs; Pi is the orthogonal projection onto the space
-    where the face arithmetic averages of the two copies agree; E averages the
-    two copies with the BDDC weights. Eigenvectors with lambda > tau (at most
-    max_per_face, largest first) give rows c = w^T Pi (I-E)^T A (I-E) Pi
-    (eq. c-def), restricted to the s-copy of the face. Rows are orthogonalized
-    against the face average and each other; rows whose remaining relative
-    norm is below drop_tol are dropped. Returns {glob index: [rows]}.
+    Reading used here: the pair problem lives on the common interface of s and t
+    (the face together with the edges and corners it touches, i.e. every glob whose
+    sharing set contains both). A_s, A_t are the Schur complements of the two
+    subdomain matrices onto those dofs; Pi is the orthogonal projection onto the
+    space where the two copies agree in every initial coarse dof of the common
+    interface (corner values, edge and face averages); E averages the two copies
+    with the BDDC weights. Eigenvectors with lambda > tau (at most max_per_face,
+    largest first) give c = w^T Pi (I-E)^T A (I-E) Pi (eq. c-def); its entries on
+    the face itself, first copy, form the new row, orthogonalized against the face
+    average and the rows before it (rows whose remaining relative norm is below
+    drop_tol are dropped). Returns {face glob index: [rows]}.
     Parity unpinned against the paper (which uses a limited LOBPCG).
     """
     out = {}
@@ -356,16 +359,23 @@ def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: floa
         if kind != FACE or len(sset) != 2 or len(gd) < 2:
             continue
         s, t = sset
-        m = len(gd)
-        As, At = face_schur(subs, s, gd), face_schur(subs, t, gd)
+        closure = [g2 for g2, ss in enumerate(subs.glob_subs) if s in ss and t in ss]
+        dofs = np.sort(np.concatenate([subs.glob_dofs[g2] for g2 in closure]))
+        m = len(dofs)
+        As, At = face_schur(subs, s, dofs), face_schur(subs, t, dofs)
         A = sla.block_diag(As, At)
-        ws = bddc_weights[s][np.searchsorted(subs.dofs[s][subs.locG[s]], gd)]
-        wt = bddc_weights[t][np.searchsorted(subs.dofs[t][subs.locG[t]], gd)]
+        ws = bddc_weights[s][np.searchsorted(subs.dofs[s][subs.locG[s]], dofs)]
+        wt = bddc_weights[t][np.searchsorted(subs.dofs[t][subs.locG[t]], dofs)]
         E = np.block([[np.diag(ws), np.diag(wt)], [np.diag(ws), np.diag(wt)]])
         IE = np.eye(2 * m) - E
-        a = np.full(m, 1.0 / m)
-        q = np.concatenate([a, -a])
-        Pi = np.eye(2 * m) - np.outer(q, q) / (q @ q)
+        Q = []
+        for g2 in closure:
+            if subs.glob_kind[g2] in kinds:
+                a = np.zeros(m)
+                a[np.searchsorted(dofs, subs.glob_dofs[g2])] = 1.0 / len(subs.glob_dofs[g2])
+                Q.append(np.concatenate([a, -a]))
+        Qo, _ = np.linalg.qr(np.array(Q).T)
+        Pi = np.eye(2 * m) - Qo @ Qo.T
         Lhs = Pi @ IE.T @ A @ IE @ Pi
         Rhs = Pi @ A @ Pi
         Lhs, Rhs = 0.5 * (Lhs + Lhs.T), 0.5 * (Rhs + Rhs.T)
@@ -375,20 +385,20 @@ def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: floa
         T = U[:, keep] / np.sqrt(lam_r[keep])
         lam, V = np.linalg.eigh(T.T @ Lhs @ T)
         sel = np.nonzero(lam > tau)[0][::-1][:max_per_face]
+        fpos = np.searchsorted(dofs, gd)
         rows = []
-        basis = [a / np.linalg.norm(a)]
+        basis = [np.full(len(gd), 1.0 / np.sqrt(len(gd)))]
         for k in sel:
             w = T @ V[:, k]
-            c = w @ Lhs
-            r = c[:m].copy()
+            r = (w @ Lhs)[:m][fpos]
             nr0 = np.linalg.norm(r)
             if nr0 == 0:
                 continue
             for bvec in basis:
-                r -= (bvec @ r) * bvec
+                r = r - (bvec @ r) * bvec
             if np.linalg.norm(r) < drop_tol * nr0:
                 continue
-            r /= np.linalg.norm(r)
+            r = r / np.linalg.norm(r)
             basis.append(r)
             rows.append(r)
         if rows:

@@ -114,40 +114,95 @@ void trmm_lower(int n, int m, const double* L, const double* X, double* Y) {
 }
 
 void sym_eig(int n, double* A, double* w, double* V) {
-  // cyclic Jacobi rotations (Golub & Van Loan, Alg. 8.5.3); converges quadratically
+  // 1) Householder reduction A = Q T Q^T (T tridiagonal), Q accumulated in V (Golub & Van Loan Sect. 8.3.1)
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
   std::fill(V, V + (size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
-  double fro = 0.0;
-  for (size_t t = 0; t < (size_t)n * n; ++t) fro += A[t] * A[t];
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) off += a(i, j) * a(i, j);
-    if (off <= 1e-30 * fro || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double apq = a(p, q);
-        if (std::fabs(apq) < 1e-300) continue;
-        double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
-        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          double akp = a(k, p), akq = a(k, q);
-          a(k, p) = c * akp - s * akq;
-          a(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          double apk = a(p, k), aqk = a(q, k);
-          a(p, k) = c * apk - s * aqk;
-          a(q, k) = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - s * vkq;
-          V[(size_t)k * n + q] = s * vkp + c * vkq;
-        }
+  std::vector<double> v(n), p(n), q(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    int m = n - k - 1;  // trailing size
+    double alpha = 0.0;
+    for (int i = 0; i < m; ++i) {
+      v[i] = a(k + 1 + i, k);
+      alpha += v[i] * v[i];
+    }
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    if (v[0] > 0) alpha = -alpha;
+    v[0] -= alpha;
+    double vn2 = 0.0;
+    for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+    if (vn2 == 0.0) continue;
+    double beta = 2.0 / vn2;
+    for (int i = 0; i < m; ++i) {  // p = beta B v
+      const double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      double sacc = 0.0;
+      for (int j = 0; j < m; ++j) sacc += row[j] * v[j];
+      p[i] = beta * sacc;
+    }
+    double K = 0.0;
+    for (int i = 0; i < m; ++i) K += v[i] * p[i];
+    K *= 0.5 * beta;
+    for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+    for (int i = 0; i < m; ++i) {  // B -= v q^T + q v^T
+      double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+      for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+    }
+    a(k + 1, k) = alpha;
+    a(k, k + 1) = alpha;
+    for (int i = 1; i < m; ++i) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
+    for (int r = 0; r < n; ++r) {  // V = V H
+      double* row = V + (size_t)r * n + (k + 1);
+      double sacc = 0.0;
+      for (int j = 0; j < m; ++j) sacc += row[j] * v[j];
+      sacc *= beta;
+      for (int j = 0; j < m; ++j) row[j] -= sacc * v[j];
+    }
+  }
+  // 2) implicit symmetric QR steps with Wilkinson shifts, bulge chased by Givens rotations
+  //    applied as similarities on the band (Golub & Van Loan Alg. 8.3.2), rotations accumulated in V
+  auto rot = [&](int k, int lo, int hi, double c, double sn) {
+    for (int j = std::max(lo, k - 1); j <= std::min(hi, k + 2); ++j) {  // rows k, k+1
+      double x = a(k, j), y = a(k + 1, j);
+      a(k, j) = c * x + sn * y;
+      a(k + 1, j) = -sn * x + c * y;
+    }
+    for (int i = std::max(lo, k - 1); i <= std::min(hi, k + 2); ++i) {  // columns k, k+1
+      double x = a(i, k), y = a(i, k + 1);
+      a(i, k) = c * x + sn * y;
+      a(i, k + 1) = -sn * x + c * y;
+    }
+    for (int r = 0; r < n; ++r) {
+      double x = V[(size_t)r * n + k], y = V[(size_t)r * n + k + 1];
+      V[(size_t)r * n + k] = c * x + sn * y;
+      V[(size_t)r * n + k + 1] = -sn * x + c * y;
+    }
+  };
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, iter = 0;
+  while (hi > 0 && iter < 60 * n) {
+    if (std::fabs(a(hi, hi - 1)) <= eps * (std::fabs(a(hi, hi)) + std::fabs(a(hi - 1, hi - 1)))) {
+      a(hi, hi - 1) = a(hi - 1, hi) = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(a(lo, lo - 1)) > eps * (std::fabs(a(lo, lo)) + std::fabs(a(lo - 1, lo - 1)))) --lo;
+    if (lo > 0) a(lo, lo - 1) = a(lo - 1, lo) = 0.0;
+    double dd = 0.5 * (a(hi - 1, hi - 1) - a(hi, hi)), eh = a(hi, hi - 1);
+    double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + eh * eh);
+    double mu = a(hi, hi) - (den != 0.0 ? eh * eh / den : 0.0);
+    double x = a(lo, lo) - mu, z = a(lo + 1, lo);
+    for (int k = lo; k < hi; ++k) {
+      double r = std::hypot(x, z);
+      double c = r > 0 ? x / r : 1.0, sn = r > 0 ? z / r : 0.0;
+      rot(k, lo, hi, c, sn);
+      if (k + 1 < hi) {
+        x = a(k + 1, k);
+        z = a(k + 2, k);
       }
+    }
+    ++iter;
   }
   std::vector<int> idx(n);
   std::iota(idx.begin(), idx.end(), 0);

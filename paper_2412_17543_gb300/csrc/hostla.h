@@ -20,7 +20,8 @@ void gemm_nt(int n, int m, int k, double alpha, const double* A, const double* B
 void gemm_nn(int n, int m, int k, const double* A, const double* B, double* C);
 // Y (n x m) = L (n x n lower) * X (n x m)
 void trmm_lower(int n, int m, const double* L, const double* X, double* Y);
-// Symmetric eigen-decomposition by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w
+// Symmetric eigen-decomposition (Householder tridiagonalization, implicit shifted QR):
+// A (n x n, destroyed) -> eigenvalues w
 // (ascending) and eigenvectors as columns of V (n x n row-major).
 void sym_eig(int n, double* A, double* w, double* V);
 

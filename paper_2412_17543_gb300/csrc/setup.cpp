@@ -78,16 +78,15 @@ void subdomain_constraints(const Level& L, int s, const Globs& gl, const std::ve
   }
 }
 
-// Dense pipeline of one subdomain: K_II^{-1}, S = K_GG - K_GI K_II^{-1} K_IG, and with
-// S^ = S + rho C^T C (equal to S on ker C): N = S^{-1} - S^{-1}C^T (C S^{-1} C^T)^{-1} C S^{-1},
-// Phi = S^{-1} C^T (C S^{-1} C^T)^{-1}, KC = Phi^T S Phi = (C S^{-1} C^T)^{-1} - rho I.
-bool dense_sub(int nloc, const double* K, const std::vector<int>& I, const std::vector<int>& G,
-               const std::vector<double>& C, int nc, bool needE, DenseSub& out) {
+// Phase A of one subdomain: K_II^{-1} and the local Schur complement
+// S = K_GG - K_GI K_II^{-1} K_IG (Sect. 3.1); E = K_II^{-1} K_IG on coarse levels.
+bool dense_schur(int nloc, const double* K, const std::vector<int>& I, const std::vector<int>& G, bool needE,
+                 DenseSub& out, std::vector<double>& S) {
   int nI = (int)I.size(), nG = (int)G.size();
   out.nI = nI;
   out.nG = nG;
-  out.nc = nc;
-  std::vector<double> KII((size_t)nI * nI), KIG((size_t)nI * nG), S((size_t)nG * nG);
+  std::vector<double> KII((size_t)nI * nI), KIG((size_t)nI * nG);
+  S.assign((size_t)nG * nG, 0.0);
   for (int a = 0; a < nI; ++a) {
     for (int b = 0; b < nI; ++b) KII[(size_t)a * nI + b] = K[(size_t)I[a] * nloc + I[b]];
     for (int b = 0; b < nG; ++b) KIG[(size_t)a * nG + b] = K[(size_t)I[a] * nloc + G[b]];
@@ -106,10 +105,10 @@ bool dense_sub(int nloc, const double* K, const std::vector<int>& I, const std::
       for (int b = 0; b <= a; ++b) {
         const double* ra = LT.data() + (size_t)a * nI;
         const double* rb = LT.data() + (size_t)b * nI;
-        double s = 0.0;
-        for (int k = a; k < nI; ++k) s += ra[k] * rb[k];
-        out.KIIinv[(size_t)a * nI + b] = s;
-        out.KIIinv[(size_t)b * nI + a] = s;
+        double sacc = 0.0;
+        for (int k = a; k < nI; ++k) sacc += ra[k] * rb[k];
+        out.KIIinv[(size_t)a * nI + b] = sacc;
+        out.KIIinv[(size_t)b * nI + a] = sacc;
       }
     std::vector<double> X((size_t)nI * nG), XT((size_t)nG * nI);
     la::trmm_lower(nI, nG, Linv.data(), KIG.data(), X.data());
@@ -126,6 +125,16 @@ bool dense_sub(int nloc, const double* K, const std::vector<int>& I, const std::
       double v = 0.5 * (S[(size_t)a * nG + b] + S[(size_t)b * nG + a]);
       S[(size_t)a * nG + b] = S[(size_t)b * nG + a] = v;
     }
+  return true;
+}
+
+// Phase C of one subdomain: the constrained Neumann problem of eq. localCorr with a
+// right-hand side on G. With S^ = S + rho C^T C (equal to S on ker C):
+// N = S^{-1} - S^{-1}C^T (C S^{-1} C^T)^{-1} C S^{-1}, Phi = S^{-1} C^T (C S^{-1} C^T)^{-1},
+// KC = Phi^T S Phi = (C S^{-1} C^T)^{-1} - rho I.
+bool dense_bddc(const std::vector<double>& S, const std::vector<double>& C, int nc, DenseSub& out) {
+  int nG = out.nG;
+  out.nc = nc;
   std::vector<double> Sh = S;
   double rho = 0.0;
   if (nc > 0) {
@@ -201,17 +210,213 @@ std::vector<CoarseDof> select_coarse(const Globs& gl, bool corners, bool edges, 
   return cd;
 }
 
-// Weights, coarse maps and dense pipelines of a level whose subdomain matrices are given.
+// Local positions (in subdomain s's interface list) of a glob's dofs.
+std::vector<int> glob_positions(const Level& L, int s, const std::vector<int64_t>& dofs) {
+  int nG = (int)(L.goff[s + 1] - L.goff[s]);
+  const int* gm = L.gmap.data() + L.goff[s];
+  std::vector<int> pos(dofs.size());
+  for (size_t t = 0; t < dofs.size(); ++t) {
+    int p = (int)(std::lower_bound(gm, gm + nG, (int)dofs[t]) - gm);
+    if (p >= nG || gm[p] != dofs[t]) throw Error(DD_INVALID_ARG, "glob dof not in subdomain interface");
+    pos[t] = p;
+  }
+  return pos;
+}
+
+// Schur complement of S onto the positions F (all other rows/columns eliminated).
+bool face_schur(int nG, const std::vector<double>& S, const std::vector<int>& F, std::vector<double>& A) {
+  int m = (int)F.size();
+  std::vector<char> inF(nG, 0);
+  for (int p : F) inF[p] = 1;
+  std::vector<int> R;
+  for (int p = 0; p < nG; ++p)
+    if (!inF[p]) R.push_back(p);
+  int r = (int)R.size();
+  A.assign((size_t)m * m, 0.0);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) A[(size_t)a * m + b] = S[(size_t)F[a] * nG + F[b]];
+  if (r == 0) return true;
+  std::vector<double> SRR((size_t)r * r), SRF((size_t)r * m), Linv((size_t)r * r), X((size_t)r * m),
+      XT((size_t)m * r);
+  for (int a = 0; a < r; ++a) {
+    for (int b = 0; b < r; ++b) SRR[(size_t)a * r + b] = S[(size_t)R[a] * nG + R[b]];
+    for (int b = 0; b < m; ++b) SRF[(size_t)a * m + b] = S[(size_t)R[a] * nG + F[b]];
+  }
+  if (!la::cholesky(r, SRR.data())) return false;
+  la::tri_inv_lower(r, SRR.data(), Linv.data());
+  la::trmm_lower(r, m, Linv.data(), SRF.data(), X.data());
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < m; ++b) XT[(size_t)b * r + a] = X[(size_t)a * m + b];
+  la::gemm_nt(m, m, r, -1.0, XT.data(), XT.data(), 1.0, A.data());
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (A[(size_t)a * m + b] + A[(size_t)b * m + a]);
+      A[(size_t)a * m + b] = A[(size_t)b * m + a] = v;
+    }
+  return true;
+}
+
+// Adaptive constraints of one face shared by two subdomains (Sect. 3.3, eqs. eig-matrix and c-def),
+// posed on their common interface (the face with the edges and corners it touches).
+// As, At: Schur complements of the two subdomains onto the common interface; ws, wt: BDDC weights
+// there; cq: the initial coarse dofs of the common interface (rows over its dofs). Pi projects onto
+// the space where both copies agree in every initial coarse dof, E averages the copies with the
+// weights. Eigenvectors with lambda > tau (largest first, at most maxr) give c = w^T Pi (I-E)^T A
+// (I-E) Pi; its entries on the face (positions fpos, first copy) form a row, orthogonalized against
+// the face average and the rows before it.
+std::vector<std::vector<double>> face_eigen_rows(const std::vector<double>& As, const std::vector<double>& At,
+                                                 const std::vector<double>& ws, const std::vector<double>& wt,
+                                                 const std::vector<std::vector<double>>& cq,
+                                                 const std::vector<int>& fpos, double tau, int maxr) {
+  const int m = (int)ws.size(), n = 2 * m;
+  std::vector<double> A((size_t)n * n, 0.0), IE((size_t)n * n, 0.0), Pi((size_t)n * n, 0.0);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      A[(size_t)a * n + b] = As[(size_t)a * m + b];
+      A[(size_t)(m + a) * n + m + b] = At[(size_t)a * m + b];
+    }
+  for (int a = 0; a < m; ++a) {  // I - E, E = [[Ws, Wt], [Ws, Wt]]
+    IE[(size_t)a * n + a] += 1.0;
+    IE[(size_t)(m + a) * n + m + a] += 1.0;
+    IE[(size_t)a * n + a] -= ws[a];
+    IE[(size_t)a * n + m + a] -= wt[a];
+    IE[(size_t)(m + a) * n + a] -= ws[a];
+    IE[(size_t)(m + a) * n + m + a] -= wt[a];
+  }
+  // orthonormal basis of the jumps (c, -c) of the initial coarse dofs (modified Gram-Schmidt)
+  std::vector<std::vector<double>> Qo;
+  for (const auto& c : cq) {
+    std::vector<double> q(n);
+    for (int a = 0; a < m; ++a) {
+      q[a] = c[a];
+      q[m + a] = -c[a];
+    }
+    double n0 = 0.0;
+    for (double v : q) n0 += v * v;
+    n0 = std::sqrt(n0);
+    for (const auto& b : Qo) {
+      double d = 0.0;
+      for (int a = 0; a < n; ++a) d += b[a] * q[a];
+      for (int a = 0; a < n; ++a) q[a] -= d * b[a];
+    }
+    double n1 = 0.0;
+    for (double v : q) n1 += v * v;
+    n1 = std::sqrt(n1);
+    if (n1 <= 1e-12 * n0) continue;
+    for (double& v : q) v /= n1;
+    Qo.push_back(q);
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double v = (a == b ? 1.0 : 0.0);
+      for (const auto& q : Qo) v -= q[a] * q[b];
+      Pi[(size_t)a * n + b] = v;
+    }
+  std::vector<double> T1((size_t)n * n), T2((size_t)n * n), Lhs((size_t)n * n), Rhs((size_t)n * n);
+  // Lhs = Pi IE^T A IE Pi ; Rhs = Pi A Pi
+  std::vector<double> IEPi((size_t)n * n);
+  la::gemm_nn(n, n, n, IE.data(), Pi.data(), IEPi.data());
+  la::gemm_nn(n, n, n, A.data(), IEPi.data(), T1.data());           // A IE Pi
+  std::vector<double> IEPiT((size_t)n * n);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) IEPiT[(size_t)a * n + b] = IEPi[(size_t)b * n + a];
+  la::gemm_nn(n, n, n, IEPiT.data(), T1.data(), Lhs.data());
+  la::gemm_nn(n, n, n, A.data(), Pi.data(), T1.data());
+  la::gemm_nn(n, n, n, Pi.data(), T1.data(), Rhs.data());
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < a; ++b) {
+      double v = 0.5 * (Lhs[(size_t)a * n + b] + Lhs[(size_t)b * n + a]);
+      Lhs[(size_t)a * n + b] = Lhs[(size_t)b * n + a] = v;
+      v = 0.5 * (Rhs[(size_t)a * n + b] + Rhs[(size_t)b * n + a]);
+      Rhs[(size_t)a * n + b] = Rhs[(size_t)b * n + a] = v;
+    }
+  // restrict to the range of Rhs (drops ker Pi and the common null space)
+  std::vector<double> lam(n), U((size_t)n * n), Rw = Rhs;
+  la::sym_eig(n, Rw.data(), lam.data(), U.data());
+  std::vector<int> keep;
+  for (int a = 0; a < n; ++a)
+    if (lam[a] > 1e-12 * lam[n - 1]) keep.push_back(a);
+  int r = (int)keep.size();
+  std::vector<std::vector<double>> rows;
+  if (r == 0) return rows;
+  std::vector<double> T((size_t)n * r);
+  for (int a = 0; a < n; ++a)
+    for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = U[(size_t)a * n + keep[j]] / std::sqrt(lam[keep[j]]);
+  std::vector<double> LT((size_t)n * r), Cm((size_t)r * r);
+  la::gemm_nn(n, r, n, Lhs.data(), T.data(), LT.data());
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      double sacc = 0.0;
+      for (int a = 0; a < n; ++a) sacc += T[(size_t)a * r + i] * LT[(size_t)a * r + j];
+      Cm[(size_t)i * r + j] = sacc;
+    }
+  std::vector<double> mu(r), V((size_t)r * r);
+  la::sym_eig(r, Cm.data(), mu.data(), V.data());
+  const int mf = (int)fpos.size();
+  std::vector<std::vector<double>> basis;
+  {
+    std::vector<double> a0(mf, 1.0 / std::sqrt((double)mf));
+    basis.push_back(a0);
+  }
+  for (int j = r - 1; j >= 0 && (int)rows.size() < maxr; --j) {
+    if (!(mu[j] > tau)) break;
+    std::vector<double> w(n, 0.0);
+    for (int a = 0; a < n; ++a)
+      for (int i = 0; i < r; ++i) w[a] += T[(size_t)a * r + i] * V[(size_t)i * r + j];
+    std::vector<double> row(mf, 0.0);  // c = w^T Lhs on the face, first copy
+    for (int b = 0; b < mf; ++b) {
+      double sacc = 0.0;
+      for (int a = 0; a < n; ++a) sacc += w[a] * Lhs[(size_t)a * n + fpos[b]];
+      row[b] = sacc;
+    }
+    double n0 = 0.0;
+    for (double v : row) n0 += v * v;
+    n0 = std::sqrt(n0);
+    if (n0 == 0.0) continue;
+    for (const auto& bv : basis) {
+      double d = 0.0;
+      for (int b = 0; b < mf; ++b) d += bv[b] * row[b];
+      for (int b = 0; b < mf; ++b) row[b] -= d * bv[b];
+    }
+    double n1 = 0.0;
+    for (double v : row) n1 += v * v;
+    n1 = std::sqrt(n1);
+    if (n1 < 1e-10 * n0) continue;
+    for (double& v : row) v /= n1;
+    basis.push_back(row);
+    rows.push_back(row);
+  }
+  return rows;
+}
+
+struct AdaptiveOpts {
+  bool on = false;
+  double tau = 10.0;
+  int max_per_face = 10;
+};
+
+// Weights, constraints and dense pipelines of a level whose subdomain matrices are given:
+// phase A (Schur complements), weights, optional adaptive face constraints, phase C (BDDC).
 template <class KFn, class DiagFn>
-void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, int weights, KFn kloc_fn,
-                  DiagFn diag_fn, const std::vector<int>& nloc, const std::vector<std::vector<int>>& Iloc,
-                  const std::vector<std::vector<int>>& Gloc, bool needE, const char* what) {
-  L.n_coarse = (int)cd.size();
-  std::vector<std::vector<int>> cdofs_of_sub(L.S);
-  for (size_t c = 0; c < cd.size(); ++c)
-    for (int s : gl.subs[cd[c].glob]) cdofs_of_sub[s].push_back((int)c);
+void finish_level(Level& L, const Globs& gl, std::vector<CoarseDof> cd, int weights, KFn kloc_fn, DiagFn diag_fn,
+                  const std::vector<int>& nloc, const std::vector<std::vector<int>>& Iloc,
+                  const std::vector<std::vector<int>>& Gloc, bool needE, const AdaptiveOpts& ad, const char* what) {
   L.sub.assign(L.S, DenseSub());
-  // weights
+  std::vector<std::vector<double>> S(L.S);
+  int failed = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < L.S; ++s) {
+    std::vector<double> K;
+    kloc_fn(s, K);
+    if (!dense_schur(nloc[s], K.data(), Iloc[s], Gloc[s], needE, L.sub[s], S[s])) {
+#pragma omp critical
+      failed = s;
+    }
+  }
+  if (failed >= 0)
+    throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": non-positive pivot in K_II of subdomain " +
+                                       std::to_string(failed));
+  // weights D_i (Sect. 3.2): card = inverse multiplicity, diag = share of the diagonal entries
   std::vector<double> dsum(L.n_gamma, 0.0);
   std::vector<std::vector<double>> diag(L.S);
   for (int s = 0; s < L.S; ++s) {
@@ -219,38 +424,95 @@ void finish_level(Level& L, const Globs& gl, const std::vector<CoarseDof>& cd, i
     if (weights == DD_WEIGHTS_DIAG)
       for (size_t j = 0; j < Gloc[s].size(); ++j) dsum[L.gmap[L.goff[s] + j]] += diag[s][Gloc[s][j]];
   }
-  int failed = -1;
+  for (int s = 0; s < L.S; ++s) {
+    DenseSub& ds = L.sub[s];
+    ds.D.resize(Gloc[s].size());
+    for (size_t j = 0; j < Gloc[s].size(); ++j) {
+      int g = L.gmap[L.goff[s] + j];
+      ds.D[j] = weights == DD_WEIGHTS_DIAG ? diag[s][Gloc[s][j]] / dsum[g]
+                                           : 1.0 / (double)(L.gptr[g + 1] - L.gptr[g]);
+    }
+  }
+  // adaptive face constraints (Sect. 3.3), inserted after each face's average
+  if (ad.on) {
+    std::vector<int> faces;
+    for (size_t g = 0; g < gl.kind.size(); ++g)
+      if (gl.kind[g] == GLOB_FACE && gl.subs[g].size() == 2 && gl.dofs[g].size() >= 2) faces.push_back((int)g);
+    std::vector<std::vector<int>> globs_of_sub(L.S);
+    for (size_t g = 0; g < gl.subs.size(); ++g)
+      for (int s : gl.subs[g]) globs_of_sub[s].push_back((int)g);
+    std::vector<char> initial(gl.kind.size(), 0);
+    for (const CoarseDof& c : cd) initial[c.glob] = 1;
+    std::vector<std::vector<std::vector<double>>> extra(faces.size());
+    int bad = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int f = 0; f < (int)faces.size(); ++f) {
+      int g = faces[f];
+      int s = gl.subs[g][0], t = gl.subs[g][1];
+      // common interface of s and t: every glob whose sharing set holds both
+      std::vector<int> closure;
+      for (int g2 : globs_of_sub[s])
+        if (std::binary_search(gl.subs[g2].begin(), gl.subs[g2].end(), t)) closure.push_back(g2);
+      std::vector<int64_t> dofs;
+      for (int g2 : closure) dofs.insert(dofs.end(), gl.dofs[g2].begin(), gl.dofs[g2].end());
+      std::sort(dofs.begin(), dofs.end());
+      std::vector<int> Fs = glob_positions(L, s, dofs), Ft = glob_positions(L, t, dofs);
+      std::vector<double> As, At;
+      if (!face_schur(L.sub[s].nG, S[s], Fs, As) || !face_schur(L.sub[t].nG, S[t], Ft, At)) {
+#pragma omp critical
+        bad = g;
+        continue;
+      }
+      const int m = (int)dofs.size();
+      std::vector<double> ws(m), wt(m);
+      for (int a = 0; a < m; ++a) {
+        ws[a] = L.sub[s].D[Fs[a]];
+        wt[a] = L.sub[t].D[Ft[a]];
+      }
+      std::vector<std::vector<double>> cq;
+      for (int g2 : closure) {
+        if (!initial[g2]) continue;
+        std::vector<double> c(m, 0.0);
+        for (int64_t d : gl.dofs[g2])
+          c[std::lower_bound(dofs.begin(), dofs.end(), d) - dofs.begin()] = 1.0 / (double)gl.dofs[g2].size();
+        cq.push_back(c);
+      }
+      std::vector<int> fpos;
+      for (int64_t d : gl.dofs[g]) fpos.push_back((int)(std::lower_bound(dofs.begin(), dofs.end(), d) - dofs.begin()));
+      extra[f] = face_eigen_rows(As, At, ws, wt, cq, fpos, ad.tau, ad.max_per_face);
+    }
+    if (bad >= 0) throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": singular face Schur complement");
+    std::vector<std::vector<std::vector<double>>> by_glob(gl.kind.size());
+    for (size_t f = 0; f < faces.size(); ++f) by_glob[faces[f]] = std::move(extra[f]);
+    std::vector<CoarseDof> cd2;
+    for (const CoarseDof& c : cd) {
+      cd2.push_back(c);
+      for (auto& row : by_glob[c.glob]) {
+        cd2.push_back({c.glob, row});
+        L.n_adaptive++;
+      }
+    }
+    cd.swap(cd2);
+  }
+  L.n_coarse = (int)cd.size();
+  std::vector<std::vector<int>> cdofs_of_sub(L.S);
+  for (size_t c = 0; c < cd.size(); ++c)
+    for (int s : gl.subs[cd[c].glob]) cdofs_of_sub[s].push_back((int)c);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int s = 0; s < L.S; ++s) {
-    std::vector<double> C, K;
+    std::vector<double> C;
     subdomain_constraints(L, s, gl, cd, cdofs_of_sub, C);
-    kloc_fn(s, K);
     DenseSub& ds = L.sub[s];
-    bool ok = dense_sub(nloc[s], K.data(), Iloc[s], Gloc[s], C, (int)cdofs_of_sub[s].size(), needE, ds);
-    if (!ok) {
+    if (!dense_bddc(S[s], C, (int)cdofs_of_sub[s].size(), ds)) {
 #pragma omp critical
       failed = s;
     }
     ds.cmap = cdofs_of_sub[s];
-    ds.D.resize(Gloc[s].size());
-    for (size_t j = 0; j < Gloc[s].size(); ++j) {
-      int g = L.gmap[L.goff[s] + j];
-      if (weights == DD_WEIGHTS_DIAG) {
-        ds.D[j] = diag[s][Gloc[s][j]] / dsum[g];
-      } else {
-        ds.D[j] = 0.0;  // filled below (needs multiplicities)
-      }
-    }
+    std::vector<double>().swap(S[s]);
   }
   if (failed >= 0)
-    throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": non-positive pivot in subdomain " + std::to_string(failed));
-  if (weights != DD_WEIGHTS_DIAG) {
-    for (int s = 0; s < L.S; ++s)
-      for (size_t j = 0; j < L.sub[s].D.size(); ++j) {
-        int g = L.gmap[L.goff[s] + j];
-        L.sub[s].D[j] = 1.0 / (double)(L.gptr[g + 1] - L.gptr[g]);
-      }
-  }
+    throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": singular constrained problem in subdomain " +
+                                       std::to_string(failed));
   // coarse copy CSR
   L.coff.assign(L.S + 1, 0);
   for (int s = 0; s < L.S; ++s) L.coff[s + 1] = L.coff[s] + L.sub[s].nc;
@@ -441,7 +703,12 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
           }
         }
   };
-  finish_level(L1, gl, cd, opt.weights, kloc_fn, kdiag_fn, nloc, Iloc, Gloc, false, "level 1");
+  AdaptiveOpts ad;
+  ad.on = opt.adaptive != 0;
+  ad.tau = opt.tau;
+  ad.max_per_face = opt.max_eig_per_face > 0 ? opt.max_eig_per_face : 10;
+  DD_REQUIRE(!ad.on || opt.tau > 1.0, "adaptive threshold tau must exceed 1");
+  finish_level(L1, gl, cd, opt.weights, kloc_fn, kdiag_fn, nloc, Iloc, Gloc, false, ad, "level 1");
 
   H.levels = opt.levels;
   if (opt.levels == 2) {
@@ -520,7 +787,7 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
           d.resize(nloc2[j]);
           for (int t = 0; t < nloc2[j]; ++t) d[t] = K2[j][(size_t)t * nloc2[j] + t];
         },
-        nloc2, I2, G2, true, "level 2");
+        nloc2, I2, G2, true, AdaptiveOpts(), "level 2");
     std::vector<double> KC3 = assemble_coarse(L2);
     H.KC3inv.resize(KC3.size());
     if (!la::spd_inverse(L2.n_coarse, KC3.data(), H.KC3inv.data()))

@@ -409,7 +409,6 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
                "precond_prec must be FP64 or FP32");
     DD_REQUIRE(opt->schur_prec == DD_PREC_FP64 || opt->schur_prec == DD_PREC_DF64, "schur_prec must be FP64 or DF64");
     DD_REQUIRE(opt->maxit >= 1, "maxit must be positive");
-    DD_REQUIRE(!opt->adaptive, "adaptive constraints are not available in this build");
     auto H = std::make_unique<HostSetup>();
     build_host_setup(*md, *opt, *H);
     auto c = std::make_unique<dd_ctx>();

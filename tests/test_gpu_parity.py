@@ -161,3 +161,23 @@ def test_solve_mixed_recycled_three_level():
         x, st = S.solve(T(f), rec, rtol=1e-9)
         err = np.linalg.norm(N(x) - X[t]) / np.linalg.norm(X[t])
         assert err <= 1e-7, (t, err)
+
+
+@pytest.mark.parametrize("tau", [1.5, 3.0])
+def test_precond_apply_adaptive(tau):
+    # random coefficients make some faces need extra constraints (Sect. 3.3)
+    rng = np.random.default_rng(5)
+    n = 8
+    coef = np.exp(2.0 * rng.standard_normal((n, n, n)))
+    m = make_mesh(n, 4, 1.08, 20.0, coef=coef)
+    subs = dd.q1_substructures(m)
+    kinds = (dd.CORNER, dd.EDGE, dd.FACE)
+    base = dd.Preconditioner(subs, 2, kinds, "diag")
+    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau)
+    Po = dd.Preconditioner(subs, 2, kinds, "diag", extra_rows=rows)
+    S = P.Solver(m, **_opts(2, kinds, adaptive=1, tau=tau))
+    assert S.info["n_adaptive"] == sum(len(r) for r in rows.values()) > 0
+    r = np.random.default_rng(3).standard_normal(len(subs.gamma))
+    z = N(S.precond_apply(T(r)))
+    zo = Po.apply(r)
+    assert np.abs(z - zo).max() <= 1e-9 * np.abs(zo).max()

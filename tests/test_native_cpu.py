@@ -73,3 +73,18 @@ def test_plan_rejects_bad_input():
     m = make_mesh(8, 4, coef=-np.ones((8, 8, 8)))
     with pytest.raises(P.DDError):
         P.plan(m, levels=2)
+
+
+@pytest.mark.parametrize("tau", [1.5, 3.0])
+def test_plan_adaptive_count_matches_oracle(tau):
+    _lib()
+    import paper_2412_17543_gb300 as P
+    rng = np.random.default_rng(5)
+    n = 8
+    coef = np.exp(2.0 * rng.standard_normal((n, n, n)))
+    m = make_mesh(n, 4, 1.08, 20.0, coef=coef)
+    subs = dd.q1_substructures(m)
+    base = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag")
+    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau)
+    info, _ = P.plan(m, levels=2, adaptive=1, tau=tau, weights="diag")
+    assert info["n_adaptive"] == sum(len(r) for r in rows.values())

@@ -121,7 +121,7 @@ def test_adaptive_constraints_invariants():
     N = len(subs.gamma)
     base = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag")
     e0 = np.linalg.eigvalsh(L.T @ base.dense(N) @ L)
-    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=1.5)
+    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=3.0)
     assert sum(len(r) for r in rows.values()) > 0
     ad = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag", extra_rows=rows)
     e1 = np.linalg.eigvalsh(L.T @ ad.dense(N) @ L)
