@@ -101,10 +101,17 @@ def dist_env():
     return world, rank, local
 
 
-OPTS_MIXED = dict(levels=3, coarse_group=4, use_corners=1, use_edges=1, use_faces=1, weights="diag",
-                  schur_prec="df64", precond_prec="fp32", flexible=1, maxit=500)
-OPTS_PLAIN = dict(levels=3, coarse_group=4, use_corners=1, use_edges=1, use_faces=1, weights="diag",
-                  schur_prec="fp64", precond_prec="fp64", flexible=0, maxit=500)
+def solver_options(wl, mixed: bool) -> dict:
+    """Options of a workload: the mixed-precision arm and the plain FP64 arm share mesh,
+    partition and constraints (adaptive ones included)."""
+    o = dict(levels=wl["levels"], coarse_group=4, use_corners=wl["corners"], use_edges=wl["edges"],
+             use_faces=wl["faces"], weights="diag", adaptive=wl.get("adaptive", 0), tau=wl.get("tau", 10.0),
+             max_eig_per_face=10, maxit=500)
+    if mixed:
+        o.update(schur_prec="df64", precond_prec="fp32", flexible=1)
+    else:
+        o.update(schur_prec="fp64", precond_prec="fp64", flexible=0)
+    return o
 
 
 def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist, prof=False):
@@ -256,7 +263,7 @@ def main():
     F_dev = F_host.to(dev)
 
     t0 = time.perf_counter()
-    mixed = pkg.Solver(mesh, **OPTS_MIXED)
+    mixed = pkg.Solver(mesh, **solver_options(wl, True))
     setup_mixed = time.perf_counter() - t0
     hbm, peak_kind = peaks()
     with ClockSampler(local) as clk:
@@ -270,7 +277,7 @@ def main():
     plain = None
     if not args.no_plain:
         t0 = time.perf_counter()
-        ps = pkg.Solver(mesh, **OPTS_PLAIN)
+        ps = pkg.Solver(mesh, **solver_options(wl, False))
         setup_plain = time.perf_counter() - t0
         psec, pstats, _ = run_arm(torch, ps, F_dev, args.warmup, args.steps, 0, "B4", rtol, world, dist)
         pits = [s["iters"] for s in pstats]
@@ -305,8 +312,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64 (df64 Schur, f32 BDDC)", "data": "synthetic",
                 "config": {"workload": args.workload, "n": wl["n"], "subdomains": (wl["n"] // wl["sub"]) ** 3,
-                           "levels": 3, "coarse_group": 4, "k": k, "strategy": "B4", "rtol": rtol,
-                           "adaptive": False, "grading_ratio": mesh.info["ratio"],
+                           "levels": wl["levels"], "coarse_group": 4, "k": k, "strategy": "B4", "rtol": rtol,
+                           "adaptive": bool(wl.get("adaptive", 0)), "tau": wl.get("tau"),
+                           "n_adaptive": mixed.info["n_adaptive"], "grading_ratio": mesh.info["ratio"],
                            "max_aspect": mesh.info["max_aspect"], "n_free": mixed.n_free,
                            "n_gamma": mixed.n_gamma, "n_coarse": mixed.info["n_coarse"],
                            "l2": "operators of 3.1 GB stream from HBM every iteration (inputs larger than L2)",

@@ -24,12 +24,16 @@ struct SymTiles {
 
 inline size_t tile_bytes(int prec) { return prec == DD_PREC_FP32 ? 4096 : 8192; }
 
-// Batched row-major rectangular matrices (rows x cols per item), FP64 or FP32.
-struct RectMats {
+// A batch of row-major matrices addressed through a flat row space (for batched GEMVs):
+// item m owns rows row0[m] .. row0[m] + rows_m - 1; its matrix starts at element moff[m].
+struct BatchedRows {
   int prec = DD_PREC_FP64;
-  const int* rows = nullptr;
+  int64_t nrows = 0;
+  int max_cols = 0;
+  const int* item_of_row = nullptr;
+  const int64_t* row0 = nullptr;
   const int* cols = nullptr;
-  const int64_t* off = nullptr;   // element offset of each item
+  const int64_t* moff = nullptr;
   const void* data = nullptr;
 };
 
@@ -67,7 +71,8 @@ struct DevBDDC {
   const int* gidx;
   const double* D;         // flat weights
   SymTiles N;
-  RectMats Phi;            // nG x nc per subdomain
+  BatchedRows Phi;         // nG x nc per subdomain (rows = local interface dofs)
+  BatchedRows PhiT;        // nc x nG per subdomain (rows = local coarse dofs)
   const int64_t* coff;
   const int* cmap;         // flat local coarse -> global coarse dof
   const int* cptr;
@@ -84,7 +89,8 @@ struct DevLevel2 {
   const int* gam_c;         // level-2 interface -> level-1 coarse dof
   const int64_t* gam_c64;   // same, 64-bit (gather base map)
   SymTiles KIIinv;
-  RectMats E;               // nI x nG per group
+  BatchedRows E;            // nI x nG per group (K_II^{-1} K_IG)
+  BatchedRows ET;           // nG x nI per group
   const void* KC3inv;       // n3 x n3 dense, prec of b
   int n3;
 };
@@ -96,6 +102,7 @@ struct Work {
   double* yloc;    // [n_flat] level-1 local interface
   double* rloc;    // [n_flat]
   double* uloc;    // [n_flat]
+  double* vloc;    // [n_flat]
   double* gloc;    // [n_cflat]
   double* gC;      // [n_coarse]
   double* uC;      // [n_coarse]
@@ -106,6 +113,7 @@ struct Work {
   double* r2;      // [n_gamma2]
   double* rloc2;   // [n_flat2]
   double* uloc2;   // [n_flat2]
+  double* vloc2;   // [n_flat2]
   double* gloc2;   // [n_cflat2]
   double* g3;      // [n3]
   double* u3;      // [n3]
@@ -126,13 +134,14 @@ void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc,
                    const int64_t* bmap, double* y, cudaStream_t s);
 void launch_scatter_recover(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
 void launch_restrict(int64_t nflat, const int* gmap, const double* D, const double* r, double* rloc, cudaStream_t s);
-void launch_phiT(const DevBDDC& b, const double* rloc, double* gloc, cudaStream_t s);
-void launch_combine(const DevBDDC& b, const double* uloc, const double* uC, double* z, cudaStream_t s);
 void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* y, cudaStream_t s);
-// per item: out[ooff+i] = alpha * sum_j M[i][j] in[ioff+j] (+ beta_add[i]) ; transposed variant
-void launch_rect_gemv(int count, const RectMats& M, bool trans, const int64_t* in_off, const int* in_map,
-                      const double* in, const int64_t* out_off, double* out, double alpha, const double* add,
-                      cudaStream_t s);
+// per item m: out[out_off[m]+i] = alpha * sum_j M_m[i][j] x_j (+ add[out_off[m]+i]),
+// x_j = in[in_map ? in_map[in_off[m]+j] : in_off[m]+j]
+void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                  const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s);
+// z[g] = sum over copies k of D[k] (uloc[k] + vloc[k])
+void launch_wgather(int64_t n, const int* ptr, const int* idx, const double* D, const double* uloc,
+                    const double* vloc, double* z, cudaStream_t s);
 void launch_map_gather(int64_t n, const int* map, const double* in, double* out, cudaStream_t s);
 void launch_map_scatter(int64_t n, const int* map, const double* in, double* out, cudaStream_t s);
 

@@ -179,15 +179,26 @@ void sym_eig(int n, double* A, double* w, double* V) {
     }
   };
   const double eps = 2.220446049250313e-16;
+  // an off-diagonal entry is negligible relative to its diagonal neighbours or to the norm of T
+  // (the latter deflates blocks of numerically zero eigenvalues, whose neighbours are ~0 too)
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double rs = std::fabs(a(i, i)) + (i > 0 ? std::fabs(a(i, i - 1)) : 0.0) + (i + 1 < n ? std::fabs(a(i + 1, i)) : 0.0);
+    tnorm = std::max(tnorm, rs);
+  }
+  auto small = [&](int i) {  // entry (i, i-1)
+    double e = std::fabs(a(i, i - 1));
+    return e <= eps * (std::fabs(a(i, i)) + std::fabs(a(i - 1, i - 1))) || e <= 4 * eps * tnorm;
+  };
   int hi = n - 1, iter = 0;
-  while (hi > 0 && iter < 60 * n) {
-    if (std::fabs(a(hi, hi - 1)) <= eps * (std::fabs(a(hi, hi)) + std::fabs(a(hi - 1, hi - 1)))) {
+  while (hi > 0 && iter < 100 * n) {
+    if (small(hi)) {
       a(hi, hi - 1) = a(hi - 1, hi) = 0.0;
       --hi;
       continue;
     }
     int lo = hi - 1;
-    while (lo > 0 && std::fabs(a(lo, lo - 1)) > eps * (std::fabs(a(lo, lo)) + std::fabs(a(lo - 1, lo - 1)))) --lo;
+    while (lo > 0 && !small(lo)) --lo;
     if (lo > 0) a(lo, lo - 1) = a(lo - 1, lo) = 0.0;
     double dd = 0.5 * (a(hi - 1, hi - 1) - a(hi, hi)), eh = a(hi, hi - 1);
     double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + eh * eh);

@@ -14,6 +14,7 @@
 //    the <= 8 copies of an interface dof, no atomics).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "device.h"
@@ -117,8 +118,9 @@ template <class P>
 __device__ __forceinline__ typename P::V apply_node(const DevMesh& m, int l, const typename P::V* xl,
                                                     const typename P::V* kd) {
   int a = l % m.NLx, b = (l / m.NLx) % m.NLy, c = l / (m.NLx * m.NLy);
-  typename P::Acc acc;
-  P::init(acc);
+  typename P::Acc acc[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) P::init(acc[t]);
   for (int dz = 0; dz < 2; ++dz) {
     int ec = c - dz;
     if (ec < 0 || ec >= m.sz) continue;
@@ -135,12 +137,12 @@ __device__ __forceinline__ typename P::V apply_node(const DevMesh& m, int l, con
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           int lq = base + (q & 1) + m.NLx * (((q >> 1) & 1) + m.NLy * (q >> 2));
-          P::fma(acc, k[p ^ q], xl[lq]);
+          P::fma(acc[q & 3], k[p ^ q], xl[lq]);
         }
       }
     }
   }
-  return P::get(acc);
+  return P::add(P::add(P::get(acc[0]), P::get(acc[1])), P::add(P::get(acc[2]), P::get(acc[3])));
 }
 
 // t_I = cf * f_I + ck * (K [0; x_G])_I    (SCHUR: cf=0, ck=1; CONDENSE: cf=1, ck=0; RECOVER: cf=1, ck=-1)
@@ -274,22 +276,31 @@ struct TileOps<DD_PREC_FP64> {
   using P = PolF64;
   using V = double;
   static constexpr int BYTES = 8192;
+  // four independent accumulation chains per part (instruction-level parallelism)
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
     const double* A = reinterpret_cast<const double*>(T);
-    double acc = 0.0;
-#pragma unroll 8
-    for (int cc = 0; cc < 32; ++cc) {
-      int c = (cc + l) & 31;
-      acc = ::fma(A[l * 32 + c], tv[c], acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 32; cc += 4) {
+      int c0 = (cc + l) & 31, c1 = (cc + 1 + l) & 31, c2 = (cc + 2 + l) & 31, c3 = (cc + 3 + l) & 31;
+      a0 = ::fma(A[l * 32 + c0], tv[c0], a0);
+      a1 = ::fma(A[l * 32 + c1], tv[c1], a1);
+      a2 = ::fma(A[l * 32 + c2], tv[c2], a2);
+      a3 = ::fma(A[l * 32 + c3], tv[c3], a3);
     }
-    return acc;
+    return (a0 + a1) + (a2 + a3);
   }
   __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
     const double* A = reinterpret_cast<const double*>(T);
-    double acc = 0.0;
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) acc = ::fma(A[r * 32 + l], tv[r], acc);
-    return acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+    for (int r = 0; r < 32; r += 4) {
+      a0 = ::fma(A[r * 32 + l], tv[r], a0);
+      a1 = ::fma(A[(r + 1) * 32 + l], tv[r + 1], a1);
+      a2 = ::fma(A[(r + 2) * 32 + l], tv[r + 2], a2);
+      a3 = ::fma(A[(r + 3) * 32 + l], tv[r + 3], a3);
+    }
+    return (a0 + a1) + (a2 + a3);
   }
 };
 
@@ -300,20 +311,28 @@ struct TileOps<DD_PREC_FP32> {
   static constexpr int BYTES = 4096;
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
     const float* A = reinterpret_cast<const float*>(T);
-    float acc = 0.f;
-#pragma unroll 8
-    for (int cc = 0; cc < 32; ++cc) {
-      int c = (cc + l) & 31;
-      acc = fmaf(A[l * 32 + c], tv[c], acc);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 32; cc += 4) {
+      int c0 = (cc + l) & 31, c1 = (cc + 1 + l) & 31, c2 = (cc + 2 + l) & 31, c3 = (cc + 3 + l) & 31;
+      a0 = fmaf(A[l * 32 + c0], tv[c0], a0);
+      a1 = fmaf(A[l * 32 + c1], tv[c1], a1);
+      a2 = fmaf(A[l * 32 + c2], tv[c2], a2);
+      a3 = fmaf(A[l * 32 + c3], tv[c3], a3);
     }
-    return acc;
+    return (a0 + a1) + (a2 + a3);
   }
   __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
     const float* A = reinterpret_cast<const float*>(T);
-    float acc = 0.f;
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) acc = fmaf(A[r * 32 + l], tv[r], acc);
-    return acc;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; r += 4) {
+      a0 = fmaf(A[r * 32 + l], tv[r], a0);
+      a1 = fmaf(A[(r + 1) * 32 + l], tv[r + 1], a1);
+      a2 = fmaf(A[(r + 2) * 32 + l], tv[r + 2], a2);
+      a3 = fmaf(A[(r + 3) * 32 + l], tv[r + 3], a3);
+    }
+    return (a0 + a1) + (a2 + a3);
   }
 };
 
@@ -325,21 +344,29 @@ struct TileOps<DD_PREC_DF64> {
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
     const float* Ah = reinterpret_cast<const float*>(T);
     const float* Al = Ah + 1024;
-    df64_acc acc;
-#pragma unroll 4
-    for (int cc = 0; cc < 32; ++cc) {
-      int c = (cc + l) & 31;
-      acc.fma(df64{Ah[l * 32 + c], Al[l * 32 + c]}, tv[c]);
+    df64_acc a0, a1, a2, a3;
+#pragma unroll
+    for (int cc = 0; cc < 32; cc += 4) {
+      int c0 = (cc + l) & 31, c1 = (cc + 1 + l) & 31, c2 = (cc + 2 + l) & 31, c3 = (cc + 3 + l) & 31;
+      a0.fma(df64{Ah[l * 32 + c0], Al[l * 32 + c0]}, tv[c0]);
+      a1.fma(df64{Ah[l * 32 + c1], Al[l * 32 + c1]}, tv[c1]);
+      a2.fma(df64{Ah[l * 32 + c2], Al[l * 32 + c2]}, tv[c2]);
+      a3.fma(df64{Ah[l * 32 + c3], Al[l * 32 + c3]}, tv[c3]);
     }
-    return acc.get();
+    return df64_add(df64_add(a0.get(), a1.get()), df64_add(a2.get(), a3.get()));
   }
   __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
     const float* Ah = reinterpret_cast<const float*>(T);
     const float* Al = Ah + 1024;
-    df64_acc acc;
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) acc.fma(df64{Ah[r * 32 + l], Al[r * 32 + l]}, tv[r]);
-    return acc.get();
+    df64_acc a0, a1, a2, a3;
+#pragma unroll
+    for (int r = 0; r < 32; r += 4) {
+      a0.fma(df64{Ah[r * 32 + l], Al[r * 32 + l]}, tv[r]);
+      a1.fma(df64{Ah[(r + 1) * 32 + l], Al[(r + 1) * 32 + l]}, tv[r + 1]);
+      a2.fma(df64{Ah[(r + 2) * 32 + l], Al[(r + 2) * 32 + l]}, tv[r + 2]);
+      a3.fma(df64{Ah[(r + 3) * 32 + l], Al[(r + 3) * 32 + l]}, tv[r + 3]);
+    }
+    return df64_add(df64_add(a0.get(), a1.get()), df64_add(a2.get(), a3.get()));
   }
 };
 
@@ -521,63 +548,92 @@ void launch_restrict(int64_t nflat, const int* gmap, const double* D, const doub
   DD_CHECK_LAUNCH();
 }
 
-template <class T>
-__device__ __forceinline__ double ldv(const T* p, int64_t i) {
-  return (double)p[i];
-}
-
-// gloc[coff[s]+c] = sum_j Phi_s[j][c] rloc[goff[s]+j]   (coarse right-hand side, eq. coarse_problem)
-template <class T>
-__global__ void k_phiT(DevBDDC b, const double* __restrict__ rloc, double* __restrict__ gloc) {
-  const int s = blockIdx.x;
-  const int nG = (int)(b.goff[s + 1] - b.goff[s]);
-  const int nc = (int)(b.coff[s + 1] - b.coff[s]);
-  const T* Phi = reinterpret_cast<const T*>(b.Phi.data) + b.Phi.off[s];
-  const double* r = rloc + b.goff[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c = warp; c < nc; c += nw) {
+// Batched row-major GEMV over a flat row space: row r of the batch belongs to item
+// item_of_row[r] (local row r - row0[item]); out[out_off[m] + i] = alpha * sum_j M_m[i][j] * x_j
+// (+ add[out_off[m] + i]), x_j = in[in_map ? in_map[in_off[m] + j] : in_off[m] + j].
+// Wide rows: a warp per row with lanes along the row (coalesced); narrow rows: a thread per row.
+template <class T, bool WIDE>
+__global__ void __launch_bounds__(256) k_bgemv(int64_t nrows, const int* __restrict__ item_of_row,
+                                               const int64_t* __restrict__ row0, const int* __restrict__ cols,
+                                               const int64_t* __restrict__ moff, const T* __restrict__ M,
+                                               const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
+                                               const double* __restrict__ in, const int64_t* __restrict__ out_off,
+                                               double* __restrict__ out, double alpha,
+                                               const double* __restrict__ add) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = WIDE ? ((int64_t)gridDim.x * blockDim.x) >> 5 : (int64_t)gridDim.x * blockDim.x;
+  int64_t r = WIDE ? (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5 : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; r < nrows; r += stride) {
+    const int m = item_of_row[r];
+    const int i = (int)(r - row0[m]);
+    const int C = cols[m];
+    const T* a = M + moff[m] + (int64_t)i * C;
+    const int64_t io = in_off[m];
     double acc = 0.0;
-    for (int j = lane; j < nG; j += 32) acc += ldv(Phi, (int64_t)j * nc + c) * r[j];
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) gloc[b.coff[s] + c] = acc;
+    if (WIDE) {
+      for (int j = lane; j < C; j += 32) acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane != 0) continue;
+    } else {
+      double a2 = 0.0;
+      int j = 0;
+      for (; j + 1 < C; j += 2) {
+        acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
+        a2 = fma((double)a[j + 1], in[in_map ? in_map[io + j + 1] : io + j + 1], a2);
+      }
+      if (j < C) acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
+      acc += a2;
+    }
+    const int64_t oi = out_off[m] + i;
+    out[oi] = alpha * acc + (add ? add[oi] : 0.0);
   }
 }
 
-void launch_phiT(const DevBDDC& b, const double* rloc, double* gloc, cudaStream_t s) {
-  if (b.Phi.prec == DD_PREC_FP32)
-    k_phiT<float><<<b.S, 256, 0, s>>>(b, rloc, gloc);
-  else
-    k_phiT<double><<<b.S, 256, 0, s>>>(b, rloc, gloc);
+void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                  const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
+  if (B.nrows == 0) return;
+  const bool wide = B.max_cols >= 64;
+  int64_t threads = wide ? B.nrows * 32 : B.nrows;
+  int grid = (int)std::min<int64_t>((threads + 255) / 256, 152 * 16);
+  if (grid < 1) grid = 1;
+  if (B.prec == DD_PREC_FP32) {
+    const float* M = static_cast<const float*>(B.data);
+    if (wide)
+      k_bgemv<float, true><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map, in,
+                                                out_off, out, alpha, add);
+    else
+      k_bgemv<float, false><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
+                                                 in, out_off, out, alpha, add);
+  } else {
+    const double* M = static_cast<const double*>(B.data);
+    if (wide)
+      k_bgemv<double, true><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
+                                                 in, out_off, out, alpha, add);
+    else
+      k_bgemv<double, false><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
+                                                  in, out_off, out, alpha, add);
+  }
   DD_CHECK_LAUNCH();
 }
 
-// z[g] = sum over copies k=(s,j): D[k] (uloc[k] + Phi_s[j,:] . uC[cmap_s])   (eq. averaging_subdomain_solves)
-template <class T>
-__global__ void k_combine(DevBDDC b, const double* __restrict__ uloc, const double* __restrict__ uC,
-                          double* __restrict__ z) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < b.n_gamma;
-       g += (int64_t)gridDim.x * blockDim.x) {
+// z[g] = sum over copies k of D[k] (uloc[k] + vloc[k])   (eq. averaging_subdomain_solves)
+__global__ void k_wgather(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
+                          const double* __restrict__ D, const double* __restrict__ uloc,
+                          const double* __restrict__ vloc, double* __restrict__ z) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int t = b.gptr[g]; t < b.gptr[g + 1]; ++t) {
-      int k = b.gidx[t];
-      int s = b.gsub[k];
-      int j = (int)(k - b.goff[s]);
-      int nc = (int)(b.coff[s + 1] - b.coff[s]);
-      const T* row = reinterpret_cast<const T*>(b.Phi.data) + b.Phi.off[s] + (int64_t)j * nc;
-      const int* cm = b.cmap + b.coff[s];
-      double v = uloc[k];
-      for (int c = 0; c < nc; ++c) v += ldv(row, c) * uC[cm[c]];
-      acc += b.D[k] * v;
+    for (int t = ptr[g]; t < ptr[g + 1]; ++t) {
+      int k = idx[t];
+      acc = fma(D[k], uloc[k] + vloc[k], acc);
     }
     z[g] = acc;
   }
 }
 
-void launch_combine(const DevBDDC& b, const double* uloc, const double* uC, double* z, cudaStream_t s) {
-  if (b.Phi.prec == DD_PREC_FP32)
-    k_combine<float><<<grid_for(b.n_gamma, 128), 128, 0, s>>>(b, uloc, uC, z);
-  else
-    k_combine<double><<<grid_for(b.n_gamma, 128), 128, 0, s>>>(b, uloc, uC, z);
+void launch_wgather(int64_t n, const int* ptr, const int* idx, const double* D, const double* uloc,
+                    const double* vloc, double* z, cudaStream_t s) {
+  if (n == 0) return;
+  k_wgather<<<grid_for(n, 256), 256, 0, s>>>(n, ptr, idx, D, uloc, vloc, z);
   DD_CHECK_LAUNCH();
 }
 
@@ -602,41 +658,6 @@ void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* 
     k_dense_gemv<float><<<blocks, 256, 0, s>>>(n, (const float*)A, x, y);
   else
     k_dense_gemv<double><<<blocks, 256, 0, s>>>(n, (const double*)A, x, y);
-  DD_CHECK_LAUNCH();
-}
-
-// Batched rectangular GEMV: for item m, y = alpha * M x (+ add) or y = alpha * M^T x (+ add).
-// Input element j of item m: in[in_map ? in_map[in_off[m]+j] : in_off[m]+j].
-template <class T>
-__global__ void k_rect_gemv(RectMats M, bool trans, const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
-                            const double* __restrict__ in, const int64_t* __restrict__ out_off,
-                            double* __restrict__ out, double alpha, const double* __restrict__ add) {
-  const int m = blockIdx.x;
-  const int R = M.rows[m], C = M.cols[m];
-  const T* A = reinterpret_cast<const T*>(M.data) + M.off[m];
-  const int64_t io = in_off[m], oo = out_off[m];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nout = trans ? C : R, nin = trans ? R : C;
-  for (int o = warp; o < nout; o += nw) {
-    double acc = 0.0;
-    for (int j = lane; j < nin; j += 32) {
-      double a = trans ? (double)A[(int64_t)j * C + o] : (double)A[(int64_t)o * C + j];
-      double xv = in[in_map ? in_map[io + j] : io + j];
-      acc += a * xv;
-    }
-    for (int sft = 16; sft; sft >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sft);
-    if (lane == 0) out[oo + o] = alpha * acc + (add ? add[oo + o] : 0.0);
-  }
-}
-
-void launch_rect_gemv(int count, const RectMats& M, bool trans, const int64_t* in_off, const int* in_map,
-                      const double* in, const int64_t* out_off, double* out, double alpha, const double* add,
-                      cudaStream_t s) {
-  if (count == 0) return;
-  if (M.prec == DD_PREC_FP32)
-    k_rect_gemv<float><<<count, 256, 0, s>>>(M, trans, in_off, in_map, in, out_off, out, alpha, add);
-  else
-    k_rect_gemv<double><<<count, 256, 0, s>>>(M, trans, in_off, in_map, in, out_off, out, alpha, add);
   DD_CHECK_LAUNCH();
 }
 

@@ -192,35 +192,54 @@ SymTiles upload_sym(DeviceArena& A, const std::vector<const double*>& mats, cons
   return T;
 }
 
-RectMats upload_rect(DeviceArena& A, const std::vector<const double*>& mats, const std::vector<int>& rows,
-                     const std::vector<int>& cols, int prec, cudaStream_t s) {
-  RectMats R;
-  R.prec = prec;
-  std::vector<int64_t> off(mats.size());
+// Row batch of row-major matrices (rows x cols per item); transposed: stores M^T of every item.
+BatchedRows upload_rows(DeviceArena& A, const std::vector<const double*>& mats, const std::vector<int>& rows,
+                        const std::vector<int>& cols, int prec, bool transpose, cudaStream_t s) {
+  BatchedRows B;
+  B.prec = prec;
+  const size_t cnt = mats.size();
+  std::vector<int64_t> row0(cnt + 1, 0), moff(cnt);
+  std::vector<int> ncol(cnt);
   int64_t tot = 0;
-  for (size_t m = 0; m < mats.size(); ++m) {
-    off[m] = tot;
-    tot += (int64_t)rows[m] * cols[m];
+  for (size_t m = 0; m < cnt; ++m) {
+    int R = transpose ? cols[m] : rows[m], C = transpose ? rows[m] : cols[m];
+    row0[m + 1] = row0[m] + R;
+    ncol[m] = C;
+    moff[m] = tot;
+    tot += (int64_t)R * C;
+    B.max_cols = std::max(B.max_cols, C);
+  }
+  B.nrows = row0[cnt];
+  std::vector<int> item((size_t)B.nrows);
+  for (size_t m = 0; m < cnt; ++m)
+    for (int64_t r = row0[m]; r < row0[m + 1]; ++r) item[r] = (int)m;
+  std::vector<double> buf(tot);
+  for (size_t m = 0; m < cnt; ++m) {
+    int R0 = rows[m], C0 = cols[m];
+    for (int i = 0; i < R0; ++i)
+      for (int j = 0; j < C0; ++j) {
+        double v = mats[m][(size_t)i * C0 + j];
+        if (transpose)
+          buf[moff[m] + (int64_t)j * R0 + i] = v;
+        else
+          buf[moff[m] + (int64_t)i * C0 + j] = v;
+      }
   }
   if (prec == DD_PREC_FP32) {
-    std::vector<float> buf(tot);
-    for (size_t m = 0; m < mats.size(); ++m)
-      for (int64_t t = 0; t < (int64_t)rows[m] * cols[m]; ++t) buf[off[m] + t] = (float)mats[m][t];
-    float* d = A.alloc<float>(buf.size());
-    DD_CUDA(cudaMemcpy(d, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice));
-    R.data = d;
+    std::vector<float> f(buf.begin(), buf.end());
+    float* d = A.alloc<float>(f.size());
+    DD_CUDA(cudaMemcpy(d, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    B.data = d;
   } else {
-    std::vector<double> buf(tot);
-    for (size_t m = 0; m < mats.size(); ++m)
-      std::copy(mats[m], mats[m] + (size_t)rows[m] * cols[m], buf.begin() + off[m]);
     double* d = A.alloc<double>(buf.size());
     DD_CUDA(cudaMemcpy(d, buf.data(), buf.size() * 8, cudaMemcpyHostToDevice));
-    R.data = d;
+    B.data = d;
   }
-  R.rows = A.upload(rows, s);
-  R.cols = A.upload(cols, s);
-  R.off = A.upload(off, s);
-  return R;
+  B.item_of_row = A.upload(item, s);
+  B.row0 = A.upload(row0, s);
+  B.cols = A.upload(ncol, s);
+  B.moff = A.upload(moff, s);
+  return B;
 }
 
 void upload_bddc(DeviceArena& A, const Level& L, int prec, DevBDDC& b, cudaStream_t s) {
@@ -259,7 +278,9 @@ void upload_bddc(DeviceArena& A, const Level& L, int prec, DevBDDC& b, cudaStrea
     nc.push_back(L.sub[i].nc);
   }
   b.N = upload_sym(A, Ns, nG, prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
-  b.Phi = upload_rect(A, Ps, nG, nc, prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+  int rp = prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64;
+  b.Phi = upload_rows(A, Ps, nG, nc, rp, false, s);
+  b.PhiT = upload_rows(A, Ps, nG, nc, rp, true, s);
 }
 
 const void* upload_dense(DeviceArena& A, const std::vector<double>& M, int prec) {
@@ -303,17 +324,18 @@ void recover(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream
 
 // BDDC of one level on an interface residual r -> z, with a coarse solver callback
 template <class CoarseFn>
-void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* gloc,
-                double* gC, double* uC, CoarseFn coarse, cudaStream_t s) {
+void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* vloc,
+                double* gloc, double* gC, double* uC, CoarseFn coarse, cudaStream_t s) {
   launch_restrict(b.n_flat, b.gmap, b.D, r, rloc, s);
   {
     ProfScope pk(c, &b == &c->b1 ? DD_PROF_SYMV_N : DD_PROF_COUNT, s);
     launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
   }
-  launch_phiT(b, rloc, gloc, s);
+  launch_bgemv(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);  // Phi_i^T D_i R_i r
   launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
   coarse(gC, uC);
-  launch_combine(b, uloc, uC, z, s);
+  launch_bgemv(b.Phi, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);  // Phi_i R_Ci u_C
+  launch_wgather(b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
 }
 
 // three-level: BDDC for the whole coarse system K_C u = g (interior correction, interface BDDC, extension)
@@ -322,11 +344,11 @@ void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
   Work& w = c->w;
   launch_map_gather(L.n_int, L.imap, g, w.gI2, s);
   launch_symv(L.KIIinv, L.ioff, w.gI2, w.u0I2, w.err, s);
-  launch_rect_gemv(L.b.S, L.E, true, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);
+  launch_bgemv(L.ET, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather(L.b.n_gamma, L.b.gptr, L.b.gidx, w.rl2, g, L.gam_c64, w.r2, s);  // g[gam_c] + sum of copies
-  bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.gloc2, w.g3, w.u3,
+  bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.vloc2, w.gloc2, w.g3, w.u3,
              [&](const double* g3, double* u3) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, s); }, s);
-  launch_rect_gemv(L.b.S, L.E, false, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2, s);
+  launch_bgemv(L.E, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2, s);  // u0 - K_II^{-1} K_IG z
   launch_map_scatter(L.n_int, L.imap, w.uI2, u, s);
   launch_map_scatter(L.b.n_gamma, L.gam_c, w.z2, u, s);
 }
@@ -334,7 +356,7 @@ void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
 void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_PRECOND, s);
   Work& w = c->w;
-  bddc_apply(c, c->b1, r, z, w.rloc, w.uloc, w.gloc, w.gC, w.uC,
+  bddc_apply(c, c->b1, r, z, w.rloc, w.uloc, w.vloc, w.gloc, w.gC, w.uC,
              [&](const double* g, double* u) {
                if (c->levels == 2)
                  launch_dense_gemv(c->b1.n_coarse, c->b1.prec, c->KCinv, g, u, s);
@@ -465,6 +487,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     w.yloc = A.alloc<double>(c->b1.n_flat);
     w.rloc = A.alloc<double>(c->b1.n_flat);
     w.uloc = A.alloc<double>(c->b1.n_flat);
+    w.vloc = A.alloc<double>(c->b1.n_flat);
     w.gloc = A.alloc<double>(c->b1.n_cflat);
     w.gC = A.alloc<double>(c->b1.n_coarse);
     w.uC = A.alloc<double>(c->b1.n_coarse);
@@ -489,7 +512,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
         nG.push_back(H->l2.sub[j].nG);
       }
       L.KIIinv = upload_sym(A, Ks, nI, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
-      L.E = upload_rect(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
+      L.E = upload_rows(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, false, s);
+      L.ET = upload_rows(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, true, s);
       L.n3 = H->l2.n_coarse;
       L.KC3inv = upload_dense(A, H->KC3inv, pp);
       w.gI2 = A.alloc<double>(L.n_int);
@@ -498,6 +522,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       w.rl2 = A.alloc<double>(L.b.n_flat);
       w.rloc2 = A.alloc<double>(L.b.n_flat);
       w.uloc2 = A.alloc<double>(L.b.n_flat);
+      w.vloc2 = A.alloc<double>(L.b.n_flat);
       w.r2 = A.alloc<double>(L.b.n_gamma);
       w.z2 = A.alloc<double>(L.b.n_gamma);
       w.gloc2 = A.alloc<double>(L.b.n_cflat);

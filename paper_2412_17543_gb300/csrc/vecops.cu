@@ -56,13 +56,16 @@ __global__ void __launch_bounds__(RB) k_axpy2(int64_t n, const double* __restric
   block_reduce_store<1>(v, partials);
 }
 
-// single-block finalization: sums the partials in a fixed order and updates the scalars
+// single-block finalization: sums the partials in a fixed order (a warp per dot product,
+// fixed lane assignment and shuffle tree) and updates the scalars
 __global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible) {
   __shared__ double tot[3];
-  if (threadIdx.x < 3) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 3) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partials[b * MAXDOT + threadIdx.x];
-    tot[threadIdx.x] = s;
+    for (int b = lane; b < nblk; b += 32) s += partials[b * MAXDOT + warp];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) tot[warp] = s;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -110,7 +113,7 @@ void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, c
   DD_CHECK_LAUNCH();
 }
 void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s) {
-  k_finalize<<<1, 32, 0, s>>>(NBLK, partials, sc, op, flexible);
+  k_finalize<<<1, 96, 0, s>>>(NBLK, partials, sc, op, flexible);
   DD_CHECK_LAUNCH();
 }
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
