@@ -146,6 +146,30 @@ dd_status dd_condense(dd_ctx* ctx, const double* f, double* b, void* stream);
 /* Full solution from interface values: x_I = K_II^{-1}(f_I - K_IG x_G). f, x: [n_free], xg: [n_gamma]. */
 dd_status dd_recover(dd_ctx* ctx, const double* f, const double* xg, double* x, void* stream);
 
+/* Same result as dd_schur_apply, for callers that must not allocate device memory
+ * on a call path: code that runs under a fixed device-memory budget taken up front,
+ * or between other work where the implicit synchronization of cudaMalloc/cudaFree
+ * is not acceptable. Its per-call scratch (the subdomain interior and local
+ * interface vectors) lives in one statically allocated device array of
+ * DD_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU loading this library holds until
+ * the process exits; no cudaMalloc, cudaFree or allocating library routine runs.
+ * The paper has no counterpart: this is a property of the library interface only.
+ * Limits and behaviour:
+ *  - needs 8 * (2 * n_interior + n_local_interface) bytes of scratch, where
+ *    n_interior = n_free - n_gamma and n_local_interface is the sum of the
+ *    subdomains' interface sizes; a larger problem returns DD_INVALID_ARG with a
+ *    message giving both numbers (meshes up to about 64^3 with 8^3 subdomains fit);
+ *  - the first call on a device looks up the array's device address for that
+ *    device (make that device current first) and must therefore come before any
+ *    stream capture that includes this entry point;
+ *  - all calls share the array and it keeps the previous call's contents; every
+ *    scratch entry read by a call is written earlier in the same call, so nothing
+ *    needs clearing, but calls whose executions overlap on the GPU (different
+ *    streams, or different contexts on one device) race on it and must be ordered
+ *    by the caller. x, y: [n_gamma] device. */
+#define DD_NOALLOC_SCRATCH_BYTES (8u << 20)
+dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double* y, void* stream);
+
 /* ---- solves ---- */
 
 /* Recycle state for a sequence of solves: deflation basis of at most k columns built

@@ -1043,3 +1043,10 @@ dd_status dd_recycle_import(dd_ctx*, const void*, size_t, dd_recycle**) {
 }
 
 }  // extern "C"
+
+namespace dd {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+// Read access to a context's Schur-operator data and error word for other translation units.
+const DevMesh* context_mesh(const dd_ctx* c) { return c ? &c->mesh : nullptr; }
+int* context_err(dd_ctx* c) { return c ? c->w.err : nullptr; }
+}  // namespace dd
