@@ -71,6 +71,7 @@ typedef struct {
 enum { DD_WEIGHTS_CARD = 0, DD_WEIGHTS_DIAG = 1 };                 /* Sect. 3.2 interface weights D_i */
 enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_DF64 = 2 };     /* arithmetic of an operator */
 enum { DD_B1 = 1, DD_B2 = 2, DD_B3 = 3, DD_B4 = 4 };                /* Sect. 4.2 recycling strategies */
+enum { DD_LOCAL_AUTO = 0, DD_LOCAL_DENSE = 1, DD_LOCAL_FDM = 2 };   /* K_II^{-1} representation */
 
 typedef struct {
   int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
@@ -87,6 +88,8 @@ typedef struct {
   int32_t reorth;           /* 1: residual re-orthogonalization against W (Algorithm 1, greyed line) */
   int32_t stop_rhs_norm;    /* 1: ||r_k||/||b|| (eq. stopping_rhs); 0: ||r_k||/||r_0|| (eq. stopping_residual) */
   int32_t maxit;            /* iteration limit per solve */
+  int32_t local_solver;     /* K_II^{-1} representation: DD_LOCAL_AUTO (fast diagonalization when every
+                               subdomain has a constant coefficient, else dense), DD_LOCAL_DENSE, DD_LOCAL_FDM */
 } dd_options;
 
 typedef struct {
@@ -97,6 +100,7 @@ typedef struct {
   int32_t n_adaptive;       /* adaptive coarse dofs among them */
   int32_t n_sub2;           /* level-2 subdomains (3 levels), else 0 */
   int32_t n_coarse3;        /* level-3 coarse dofs (3 levels), else 0 */
+  int32_t local_solver;     /* DD_LOCAL_DENSE or DD_LOCAL_FDM: the representation in use */
   int64_t device_bytes;     /* device memory held by the context */
   double setup_seconds;     /* wall time of dd_setup */
 } dd_info_t;
@@ -197,7 +201,7 @@ dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double*
                      double* grad_coef, double rtol, dd_recycle* st, dd_stats* stats, void* stream);
 
 /* ---- profiling (CUDA events on the launching stream) ---- */
-enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} GEMV of the Schur operator (Sect. 3.1) */
+enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} application of the Schur operator (Sect. 3.1) */
        DD_PROF_SYMV_N = 1,     /* batched constrained-Neumann GEMV of BDDC (eq. localCorr) */
        DD_PROF_SCHUR = 2,      /* whole Schur-complement applications */
        DD_PROF_PRECOND = 3,    /* whole BDDC applications */

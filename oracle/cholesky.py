@@ -150,6 +150,23 @@ class NDCholesky:
         return int(sum(f.L11.shape[0] * (f.L11.shape[0] + 1) // 2 + f.L21.size for f in self.postorder))
 
 
+def symbolic_counts(dims, leaf: int = 64):
+    """(nnz(L), multiply-adds of the factorization) of the nested-dissection multifrontal
+    Cholesky of a structured (Nx, Ny, Nz) grid, from the front sizes alone (no numeric work)."""
+    class _Sym(NDCholesky):
+        def __init__(self, dims, leaf):
+            self.dims = tuple(int(d) for d in dims)
+            self.leaf = leaf
+            self.root = self._build((0, self.dims[0], 0, self.dims[1], 0, self.dims[2]))
+            self.postorder = []
+            self._post(self.root)
+    sym = _Sym(dims, leaf)
+    nnz = sum(len(f.vars) * (len(f.vars) + 1) // 2 + len(f.vars) * len(f.bnd) for f in sym.postorder)
+    madds = sum(len(f.vars) ** 3 / 3 + len(f.vars) ** 2 * len(f.bnd) + len(f.vars) * len(f.bnd) ** 2 / 2
+                for f in sym.postorder)
+    return int(nnz), float(madds)
+
+
 def factor_mesh(mesh, K=None, leaf: int = 64) -> NDCholesky:
     """Factor the assembled Q1 matrix of `mesh` (free nodes)."""
     from . import q1

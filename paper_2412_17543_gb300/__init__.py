@@ -7,5 +7,5 @@ CUDA kernels behind the C ABI of include/dd_solver.h); this package is its thin
 binding. Build it with `python -m paper_2412_17543_gb300.build` or
 `__graft_entry__.build()`.
 """
-from .api import Recycler, Solver, make_options, plan  # noqa: F401
+from .api import PoissonSolve, Recycler, Solver, make_options, plan  # noqa: F401
 from ._native import DDError, load  # noqa: F401

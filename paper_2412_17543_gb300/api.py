@@ -37,6 +37,8 @@ def make_options(**kw) -> nat.Options:
             v = nat.WEIGHTS[v]
         if k in ("precond_prec", "schur_prec") and isinstance(v, str):
             v = nat.PREC[v]
+        if k == "local_solver" and isinstance(v, str):
+            v = nat.LOCAL[v]
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)
@@ -94,6 +96,7 @@ class Solver:
         self.info = _info_dict(info)
         self.n_free = int(info.n_free)
         self.n_gamma = int(info.n_gamma)
+        self.n_elem = int(mesh.nx) * int(mesh.ny) * int(mesh.nz)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -162,6 +165,53 @@ class Solver:
         return x, stats
 
 
+    def adjoint(self, grad_x, x=None, rec: "Recycler" = None, rtol=1e-10, coef_grad=True):
+        """lambda = K^{-1} grad_x (K symmetric); returns (dL/df = lambda, dL/dk per element or None, stats)."""
+        import torch
+        gf = self._vec(self.n_free, grad_x)
+        gk = None
+        if coef_grad:
+            if x is None:
+                raise ValueError("the coefficient gradient needs the forward solution x")
+            gk = torch.empty(self.n_elem, dtype=torch.float64, device=grad_x.device)
+        st = nat.Stats()
+        nat.check(self.lib.dd_adjoint(self.handle, _dptr(grad_x), _dptr(x) if x is not None else None, _dptr(gf),
+                                      _dptr(gk) if gk is not None else None, ctypes.c_double(rtol),
+                                      rec.handle if rec is not None else None, ctypes.byref(st), _stream_ptr()),
+                  "dd_adjoint")
+        return gf, gk, {f: getattr(st, f) for f, _ in nat.Stats._fields_}
+
+
+class PoissonSolve:
+    """x = K(k)^{-1} f as a differentiable operation (torch.autograd.Function).
+
+    forward(f, g): solves with the set-up solver (whose coefficient field is k = exp(g));
+    backward: the adjoint solve with the same operator, preconditioner and deflation
+    basis returns dL/df = lambda and dL/dg_e = k_e * (-lambda_e^T K_e^0 x_e).
+    """
+
+    @staticmethod
+    def apply(f, g, solver: "Solver", rec: "Recycler", rtol: float = 1e-10, adjoint_rtol: float = 1e-10):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, f_, g_):
+                x, _ = solver.solve(f_.detach().contiguous(), rec, rtol)
+                ctx.save_for_backward(x, g_)
+                return x
+
+            @staticmethod
+            def backward(ctx, grad_x):
+                x, g_ = ctx.saved_tensors
+                gf, gk, _ = solver.adjoint(grad_x.contiguous(), x, rec, adjoint_rtol,
+                                           coef_grad=ctx.needs_input_grad[1])
+                gg = gk * torch.exp(g_.reshape(-1)).reshape(gk.shape) if gk is not None else None
+                return gf, (gg.reshape(g_.shape) if gg is not None else None)
+
+        return _Fn.apply(f, g)
+
+
 class Recycler:
     """Recycle state of a sequence of solves (dd_recycle_create / dd_recycle_destroy)."""
 
@@ -171,6 +221,25 @@ class Recycler:
         nat.check(solver.lib.dd_recycle_create(solver.handle, int(k), nat.STRATEGY[strategy],
                                                ctypes.c_double(freeze_tol), ctypes.byref(h)), "dd_recycle_create")
         self.handle = h
+
+    def export(self) -> bytes:
+        """Checkpoint of the recycle state (host bytes)."""
+        lib = self.solver.lib
+        n = ctypes.c_size_t(0)
+        nat.check(lib.dd_recycle_export(self.handle, None, ctypes.byref(n)), "dd_recycle_export")
+        buf = ctypes.create_string_buffer(n.value)
+        nat.check(lib.dd_recycle_export(self.handle, buf, ctypes.byref(n)), "dd_recycle_export")
+        return buf.raw[: n.value]
+
+    @classmethod
+    def restore(cls, solver: "Solver", data: bytes) -> "Recycler":
+        obj = cls.__new__(cls)
+        obj.solver = solver
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(data, len(data))
+        nat.check(solver.lib.dd_recycle_import(solver.handle, buf, len(data), ctypes.byref(h)), "dd_recycle_import")
+        obj.handle = h
+        return obj
 
     def close(self):
         if getattr(self, "handle", None):

@@ -11,7 +11,7 @@ constexpr int TILE = 32;  // symmetric matrices are stored as 32x32 upper tiles
 
 // Batched symmetric matrices as upper-triangular 32x32 tiles (bi <= bj, row-major
 // over the tile pairs; each tile row-major). FP64: 1024 doubles per tile;
-// FP32: 1024 floats; DF64: 1024 hi floats followed by 1024 lo floats.
+// FP32: 1024 floats; DF64: 1024 (hi, lo) float pairs.
 struct SymTiles {
   int prec = DD_PREC_FP64;
   int count = 0;
@@ -29,7 +29,9 @@ inline size_t tile_bytes(int prec) { return prec == DD_PREC_FP32 ? 4096 : 8192; 
 struct BatchedRows {
   int prec = DD_PREC_FP64;
   int64_t nrows = 0;
+  int count = 0;
   int max_cols = 0;
+  int max_rows = 0;
   const int* item_of_row = nullptr;
   const int64_t* row0 = nullptr;
   const int* cols = nullptr;
@@ -44,6 +46,11 @@ struct DevMesh {
   int NLx, NLy, NLz, NL;
   int64_t n_free, n_gamma, n_int;
   const int16_t* lidx;
+  const int* sub_type;      // [S] work-list type of each subdomain
+  const int* type_off;      // [types][6]: first/last item of the interior pass, of the interface pass,
+                            //             first/last boundary-layer element
+  const int16_t* type_items;  // items: node, then 8 slots (element * 8 + corner, -1 = none)
+  const int16_t* type_bl;     // boundary-layer element ids
   const int64_t* ioff;
   const int64_t* goff;
   const int* gmap;
@@ -51,9 +58,14 @@ struct DevMesh {
   const int* gidx;
   const int64_t* gamma_free;
   const double* ec;     // [E][3] FP64 element factors k hy hz/(36 hx), ...
+  const double* coef;   // [E] element coefficients k_e (FP64)
   const df64* ec_df;    // [E][3] same as float pairs
-  SymTiles KIIinv;
+  SymTiles KIIinv;         // dense representation (local_solver == DD_LOCAL_DENSE)
   int schur_prec;
+  int local_solver;         // DD_LOCAL_DENSE or DD_LOCAL_FDM
+  const int* fdm_n;         // [S][3] sizes of the interior index sets per axis (<= 9)
+  const void* fdm_V;        // [S][3][81] 1D generalized eigenvectors, stride 9 (df64 or double)
+  const void* fdm_Dinv;     // [n_int] inverse eigenvalue sums, indexed like interior vectors
 };
 
 // One BDDC level (Sect. 3.2): weights, constrained Neumann operator N, coarse basis
@@ -71,8 +83,7 @@ struct DevBDDC {
   const int* gidx;
   const double* D;         // flat weights
   SymTiles N;
-  BatchedRows Phi;         // nG x nc per subdomain (rows = local interface dofs)
-  BatchedRows PhiT;        // nc x nG per subdomain (rows = local coarse dofs)
+  BatchedRows PhiT;        // Phi_i^T: nc x nG per subdomain (rows = local coarse dofs)
   const int64_t* coff;
   const int* cmap;         // flat local coarse -> global coarse dof
   const int* cptr;
@@ -90,7 +101,6 @@ struct DevLevel2 {
   const int64_t* gam_c64;   // same, 64-bit (gather base map)
   SymTiles KIIinv;
   BatchedRows E;            // nI x nG per group (K_II^{-1} K_IG)
-  BatchedRows ET;           // nG x nI per group
   const void* KC3inv;       // n3 x n3 dense, prec of b
   int n3;
 };
@@ -128,10 +138,14 @@ enum ElemMode { ELEM_SCHUR = 0, ELEM_CONDENSE = 1, ELEM_RECOVER = 2 };
 void launch_elem_interior(const DevMesh& m, int mode, const double* xg, const double* f, double* tI, cudaStream_t s);
 void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
                            cudaStream_t s);
+// s_I = K_II^{-1} t_I for every subdomain (dense tiles or fast diagonalization)
+void launch_kii_apply(const DevMesh& m, const double* tI, double* sI, int* err, cudaStream_t s);
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s);
 // y[g] = (base ? base[bmap ? bmap[g] : g] : 0) + sum over copies of loc[idx[k]]
 void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
                    const int64_t* bmap, double* y, cudaStream_t s);
+// grad[e] = -lambda_e^T K_e^0 x_e (coefficient gradient of the adjoint)
+void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, cudaStream_t s);
 void launch_scatter_recover(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
 void launch_restrict(int64_t nflat, const int* gmap, const double* D, const double* r, double* rloc, cudaStream_t s);
 void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* y, cudaStream_t s);
@@ -139,6 +153,9 @@ void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* 
 // x_j = in[in_map ? in_map[in_off[m]+j] : in_off[m]+j]
 void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                   const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s);
+// per item m: out[out_off[m]+j] = alpha * sum_i M_m[i][j] x_i (+ add[out_off[m]+j]) (transposed product)
+void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                    const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s);
 // z[g] = sum over copies k of D[k] (uloc[k] + vloc[k])
 void launch_wgather(int64_t n, const int* ptr, const int* idx, const double* D, const double* uloc,
                     const double* vloc, double* z, cudaStream_t s);

@@ -98,55 +98,61 @@ __device__ __forceinline__ int64_t free_index(const DevMesh& m, int s, int l) {
   return x + Nfx * (y + Nfy * z);
 }
 
-// Element entries of the subdomain into shared memory: kd[el*8 + d].
-template <class P>
-__device__ void build_kd(const DevMesh& m, int s, typename P::V* kd) {
-  int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
-  int NE = m.sx * m.sy * m.sz;
-  for (int t = threadIdx.x; t < NE * 8; t += blockDim.x) {
-    int el = t >> 3, d = t & 7;
-    int ea = el % m.sx, eb = (el / m.sx) % m.sy, ec = el / (m.sx * m.sy);
-    int64_t e = (int64_t)(I * m.sx + ea) + (int64_t)m.nx * ((J * m.sy + eb) + (int64_t)m.ny * (K * m.sz + ec));
+// ---------------------------------------------------------------------------
+// Element passes driven by per-subdomain-type work lists. Subdomains with the same
+// pattern of interior / interface / absent nodes share lists built on the host:
+//   * the boundary-layer elements (those with an interface corner): only they contribute
+//     when the input vanishes in the interior (first pass) or the output is taken on the
+//     interface (second pass);
+//   * output items: node l and up to 8 slots (element * 8 + corner of l in it), sorted by
+//     slot count so that the lanes of a warp do the same amount of work.
+// S is the subdomain edge in elements (0: taken from the mesh at run time).
+// ---------------------------------------------------------------------------
+template <class P, int S>
+__device__ __forceinline__ void build_kd_list(const DevMesh& m, int s, const int16_t* bll, int nbl,
+                                              typename P::V* kd) {
+  const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
+  const int NE = sx * sy * sz;
+  const int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
+  for (int t = threadIdx.x; t < nbl; t += blockDim.x) {
+    const int el = bll[t];
+    const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
+    const int64_t e = (int64_t)(I * sx + ea) + (int64_t)m.nx * ((J * sy + eb) + (int64_t)m.ny * (K * sz + ec));
     typename P::V c[3];
     load_factors<P>(m, e, c);
-    kd[t] = P::entry(c, d);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) kd[d * NE + el] = P::entry(c, d);
   }
 }
 
-// (K_loc v)_l for local node l: sum over its bricks and their corners.
-template <class P>
-__device__ __forceinline__ typename P::V apply_node(const DevMesh& m, int l, const typename P::V* xl,
+template <class P, int S>
+__device__ __forceinline__ typename P::V apply_item(const DevMesh& m, const int16_t* it, const typename P::V* xl,
                                                     const typename P::V* kd) {
-  int a = l % m.NLx, b = (l / m.NLx) % m.NLy, c = l / (m.NLx * m.NLy);
+  const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
+  const int NE = sx * sy * sz;
+  const int NLx = sx + 1, NLy = sy + 1;
   typename P::Acc acc[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) P::init(acc[t]);
-  for (int dz = 0; dz < 2; ++dz) {
-    int ec = c - dz;
-    if (ec < 0 || ec >= m.sz) continue;
-    for (int dy = 0; dy < 2; ++dy) {
-      int eb = b - dy;
-      if (eb < 0 || eb >= m.sy) continue;
-      for (int dx = 0; dx < 2; ++dx) {
-        int ea = a - dx;
-        if (ea < 0 || ea >= m.sx) continue;
-        int el = ea + m.sx * (eb + m.sy * ec);
-        int p = dx | (dy << 1) | (dz << 2);
-        const typename P::V* k = kd + el * 8;
-        int base = ea + m.NLx * (eb + m.NLy * ec);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int v = it[1 + k];
+    if (v < 0) break;
+    const int el = v >> 3, p = v & 7;
+    const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
+    const int base = ea + NLx * (eb + NLy * ec);
+    const typename P::V* kp = kd + el;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          int lq = base + (q & 1) + m.NLx * (((q >> 1) & 1) + m.NLy * (q >> 2));
-          P::fma(acc[q & 3], k[p ^ q], xl[lq]);
-        }
-      }
+    for (int q = 0; q < 8; ++q) {
+      const int lq = base + (q & 1) + NLx * (((q >> 1) & 1) + NLy * (q >> 2));
+      P::fma(acc[q & 3], kp[(p ^ q) * NE], xl[lq]);
     }
   }
   return P::add(P::add(P::get(acc[0]), P::get(acc[1])), P::add(P::get(acc[2]), P::get(acc[3])));
 }
 
-// t_I = cf * f_I + ck * (K [0; x_G])_I    (SCHUR: cf=0, ck=1; CONDENSE: cf=1, ck=0; RECOVER: cf=1, ck=-1)
-template <class P>
+// t_I = f_I - ck * (K [0; x_G])_I   (SCHUR: t = (K x)_I; CONDENSE: t = f_I; RECOVER: t = f_I - (K x)_I)
+template <class P, int S>
 __global__ void __launch_bounds__(256) k_elem_interior(DevMesh m, int mode, const double* __restrict__ xg,
                                                        const double* __restrict__ f, double* __restrict__ tI) {
   using V = typename P::V;
@@ -155,28 +161,34 @@ __global__ void __launch_bounds__(256) k_elem_interior(DevMesh m, int mode, cons
   V* kd = xl + m.NL;
   const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
-  const bool need_k = (mode != ELEM_CONDENSE);
+  const int* to = m.type_off + 6 * m.sub_type[s];
+  const int64_t io = m.ioff[s];
+  // every interior output first gets its base value (0 or f_I)
   for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
     int cd = code[l];
-    V v = P::zero();
-    if (need_k && cd < 0 && cd != INT16_MIN) v = P::from_d(xg[m.gmap[m.goff[s] + (-1 - cd)]]);
-    xl[l] = v;
+    if (cd >= 0) tI[io + cd] = (mode == ELEM_SCHUR) ? 0.0 : f[free_index(m, s, l)];
   }
-  if (need_k) build_kd<P>(m, s, kd);
-  __syncthreads();
+  if (mode == ELEM_CONDENSE) return;
   for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
     int cd = code[l];
-    if (cd < 0) continue;
-    double t = 0.0;
-    if (need_k) t = P::to_d(apply_node<P>(m, l, xl, kd));
-    if (mode == ELEM_CONDENSE) t = f[free_index(m, s, l)];
-    else if (mode == ELEM_RECOVER) t = f[free_index(m, s, l)] - t;
-    tI[m.ioff[s] + cd] = t;
+    xl[l] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[m.gmap[m.goff[s] + (-1 - cd)]]) : P::zero();
+  }
+  build_kd_list<P, S>(m, s, m.type_bl + to[4], to[5] - to[4], kd);
+  __syncthreads();
+  for (int i = to[0] + threadIdx.x; i < to[1]; i += blockDim.x) {
+    const int16_t* it = m.type_items + 9 * (size_t)i;
+    const int l = it[0];
+    const double v = P::to_d(apply_item<P, S>(m, it, xl, kd));
+    const int cd = code[l];
+    if (mode == ELEM_SCHUR)
+      tI[io + cd] = v;
+    else
+      tI[io + cd] = f[free_index(m, s, l)] - v;
   }
 }
 
 // y_G = (K [-s_I; x_G])_G  (SCHUR: x_G given; CONDENSE: x_G = 0)
-template <class P>
+template <class P, int S>
 __global__ void __launch_bounds__(256) k_elem_interface(DevMesh m, int mode, const double* __restrict__ xg,
                                                         const double* __restrict__ sI, double* __restrict__ yloc) {
   using V = typename P::V;
@@ -185,6 +197,7 @@ __global__ void __launch_bounds__(256) k_elem_interface(DevMesh m, int mode, con
   V* kd = xl + m.NL;
   const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
+  const int* to = m.type_off + 6 * m.sub_type[s];
   for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
     int cd = code[l];
     V v = P::zero();
@@ -192,13 +205,34 @@ __global__ void __launch_bounds__(256) k_elem_interface(DevMesh m, int mode, con
     else if (cd != INT16_MIN && mode == ELEM_SCHUR) v = P::from_d(xg[m.gmap[m.goff[s] + (-1 - cd)]]);
     xl[l] = v;
   }
-  build_kd<P>(m, s, kd);
+  build_kd_list<P, S>(m, s, m.type_bl + to[4], to[5] - to[4], kd);
   __syncthreads();
-  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
-    int cd = code[l];
-    if (cd >= 0 || cd == INT16_MIN) continue;
-    yloc[m.goff[s] + (-1 - cd)] = P::to_d(apply_node<P>(m, l, xl, kd));
+  for (int i = to[2] + threadIdx.x; i < to[3]; i += blockDim.x) {
+    const int16_t* it = m.type_items + 9 * (size_t)i;
+    const int cd = code[it[0]];
+    yloc[m.goff[s] + (-1 - cd)] = P::to_d(apply_item<P, S>(m, it, xl, kd));
   }
+}
+
+template <class P>
+static void elem_interior_dispatch(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
+                                   size_t smem, cudaStream_t s) {
+  if (m.sx == 8 && m.sy == 8 && m.sz == 8)
+    k_elem_interior<P, 8><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+  else if (m.sx == 4 && m.sy == 4 && m.sz == 4)
+    k_elem_interior<P, 4><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+  else
+    k_elem_interior<P, 0><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+}
+template <class P>
+static void elem_interface_dispatch(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+                                    size_t smem, cudaStream_t s) {
+  if (m.sx == 8 && m.sy == 8 && m.sz == 8)
+    k_elem_interface<P, 8><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+  else if (m.sx == 4 && m.sy == 4 && m.sz == 4)
+    k_elem_interface<P, 4><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+  else
+    k_elem_interface<P, 0><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
 }
 
 void launch_elem_interior(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
@@ -206,9 +240,9 @@ void launch_elem_interior(const DevMesh& m, int mode, const double* xg, const do
   int NE = m.sx * m.sy * m.sz;
   size_t smem = (size_t)(m.NL + NE * 8) * 8;
   if (m.schur_prec == DD_PREC_DF64)
-    k_elem_interior<PolDF><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+    elem_interior_dispatch<PolDF>(m, mode, xg, f, tI, smem, s);
   else
-    k_elem_interior<PolF64><<<m.S, 256, smem, s>>>(m, mode, xg, f, tI);
+    elem_interior_dispatch<PolF64>(m, mode, xg, f, tI, smem, s);
   DD_CHECK_LAUNCH();
 }
 
@@ -217,9 +251,9 @@ void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const d
   int NE = m.sx * m.sy * m.sz;
   size_t smem = (size_t)(m.NL + NE * 8) * 8;
   if (m.schur_prec == DD_PREC_DF64)
-    k_elem_interface<PolDF><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+    elem_interface_dispatch<PolDF>(m, mode, xg, sI, yloc, smem, s);
   else
-    k_elem_interface<PolF64><<<m.S, 256, smem, s>>>(m, mode, xg, sI, yloc);
+    elem_interface_dispatch<PolF64>(m, mode, xg, sI, yloc, smem, s);
   DD_CHECK_LAUNCH();
 }
 
@@ -276,6 +310,10 @@ struct TileOps<DD_PREC_FP64> {
   using P = PolF64;
   using V = double;
   static constexpr int BYTES = 8192;
+  __device__ static void both_parts(const unsigned char* T, const V* ti, const V* tj, int l, V& row, V& col) {
+    row = row_part(T, tj, l);
+    col = col_part(T, ti, l);
+  }
   // four independent accumulation chains per part (instruction-level parallelism)
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
     const double* A = reinterpret_cast<const double*>(T);
@@ -309,6 +347,10 @@ struct TileOps<DD_PREC_FP32> {
   using P = PolF32;
   using V = float;
   static constexpr int BYTES = 4096;
+  __device__ static void both_parts(const unsigned char* T, const V* ti, const V* tj, int l, V& row, V& col) {
+    row = row_part(T, tj, l);
+    col = col_part(T, ti, l);
+  }
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
     const float* A = reinterpret_cast<const float*>(T);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -341,32 +383,54 @@ struct TileOps<DD_PREC_DF64> {
   using P = PolDF;
   using V = df64;
   static constexpr int BYTES = 8192;
+  // tile element (r, c) is the float pair at float2 index r * 32 + c
   __device__ static V row_part(const unsigned char* T, const V* tv, int l) {
-    const float* Ah = reinterpret_cast<const float*>(T);
-    const float* Al = Ah + 1024;
+    const float2* A = reinterpret_cast<const float2*>(T);
     df64_acc a0, a1, a2, a3;
 #pragma unroll
     for (int cc = 0; cc < 32; cc += 4) {
       int c0 = (cc + l) & 31, c1 = (cc + 1 + l) & 31, c2 = (cc + 2 + l) & 31, c3 = (cc + 3 + l) & 31;
-      a0.fma(df64{Ah[l * 32 + c0], Al[l * 32 + c0]}, tv[c0]);
-      a1.fma(df64{Ah[l * 32 + c1], Al[l * 32 + c1]}, tv[c1]);
-      a2.fma(df64{Ah[l * 32 + c2], Al[l * 32 + c2]}, tv[c2]);
-      a3.fma(df64{Ah[l * 32 + c3], Al[l * 32 + c3]}, tv[c3]);
+      float2 e0 = A[l * 32 + c0], e1 = A[l * 32 + c1], e2 = A[l * 32 + c2], e3 = A[l * 32 + c3];
+      a0.fma(df64{e0.x, e0.y}, tv[c0]);
+      a1.fma(df64{e1.x, e1.y}, tv[c1]);
+      a2.fma(df64{e2.x, e2.y}, tv[c2]);
+      a3.fma(df64{e3.x, e3.y}, tv[c3]);
     }
     return df64_add(df64_add(a0.get(), a1.get()), df64_add(a2.get(), a3.get()));
   }
   __device__ static V col_part(const unsigned char* T, const V* tv, int l) {
-    const float* Ah = reinterpret_cast<const float*>(T);
-    const float* Al = Ah + 1024;
+    const float2* A = reinterpret_cast<const float2*>(T);
     df64_acc a0, a1, a2, a3;
 #pragma unroll
     for (int r = 0; r < 32; r += 4) {
-      a0.fma(df64{Ah[r * 32 + l], Al[r * 32 + l]}, tv[r]);
-      a1.fma(df64{Ah[(r + 1) * 32 + l], Al[(r + 1) * 32 + l]}, tv[r + 1]);
-      a2.fma(df64{Ah[(r + 2) * 32 + l], Al[(r + 2) * 32 + l]}, tv[r + 2]);
-      a3.fma(df64{Ah[(r + 3) * 32 + l], Al[(r + 3) * 32 + l]}, tv[r + 3]);
+      float2 e0 = A[r * 32 + l], e1 = A[(r + 1) * 32 + l], e2 = A[(r + 2) * 32 + l], e3 = A[(r + 3) * 32 + l];
+      a0.fma(df64{e0.x, e0.y}, tv[r]);
+      a1.fma(df64{e1.x, e1.y}, tv[r + 1]);
+      a2.fma(df64{e2.x, e2.y}, tv[r + 2]);
+      a3.fma(df64{e3.x, e3.y}, tv[r + 3]);
     }
     return df64_add(df64_add(a0.get(), a1.get()), df64_add(a2.get(), a3.get()));
+  }
+  // both parts of an off-diagonal tile in one pass: eight independent chains
+  __device__ static void both_parts(const unsigned char* T, const V* ti, const V* tj, int l, V& row, V& col) {
+    const float2* A = reinterpret_cast<const float2*>(T);
+    df64_acc r0, r1, r2, r3, q0, q1, q2, q3;
+#pragma unroll
+    for (int cc = 0; cc < 32; cc += 4) {
+      int c0 = (cc + l) & 31, c1 = (cc + 1 + l) & 31, c2 = (cc + 2 + l) & 31, c3 = (cc + 3 + l) & 31;
+      float2 e0 = A[l * 32 + c0], e1 = A[l * 32 + c1], e2 = A[l * 32 + c2], e3 = A[l * 32 + c3];
+      float2 f0 = A[cc * 32 + l], f1 = A[(cc + 1) * 32 + l], f2 = A[(cc + 2) * 32 + l], f3 = A[(cc + 3) * 32 + l];
+      r0.fma(df64{e0.x, e0.y}, tj[c0]);
+      q0.fma(df64{f0.x, f0.y}, ti[cc]);
+      r1.fma(df64{e1.x, e1.y}, tj[c1]);
+      q1.fma(df64{f1.x, f1.y}, ti[cc + 1]);
+      r2.fma(df64{e2.x, e2.y}, tj[c2]);
+      q2.fma(df64{f2.x, f2.y}, ti[cc + 2]);
+      r3.fma(df64{e3.x, e3.y}, tj[c3]);
+      q3.fma(df64{f3.x, f3.y}, ti[cc + 3]);
+    }
+    row = df64_add(df64_add(r0.get(), r1.get()), df64_add(r2.get(), r3.get()));
+    col = df64_add(df64_add(q0.get(), q1.get()), df64_add(q2.get(), q3.get()));
   }
 };
 
@@ -436,11 +500,14 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
     int bi, bj;
     tile_coords(t, nb, bi, bj);
     const unsigned char* T = wslots + (size_t)slot * TB;
-    V r = Ops::row_part(T, tv + bj * 32, lane);
-    mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
     if (bi != bj) {
-      V c = Ops::col_part(T, tv + bi * 32, lane);
+      V r, c;
+      Ops::both_parts(T, tv + bi * 32, tv + bj * 32, lane, r, c);
+      mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
       mypart[bj * 32 + lane] = P::add(mypart[bj * 32 + lane], c);
+    } else {
+      V r = Ops::row_part(T, tv + bj * 32, lane);
+      mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
     }
     __syncwarp();
     if (lane == 0 && k + SYMV_SLOTS < mine) {
@@ -487,6 +554,91 @@ void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Fast diagonalization: s = V D^{-1} V^T t with V = Vz (x) Vy (x) Vx, one CTA per subdomain,
+// six contractions along one axis each in shared memory (about 14k multiply-adds per
+// 8^3 subdomain instead of a 343^2 matrix).
+// ---------------------------------------------------------------------------
+template <class P>
+__device__ __forceinline__ typename P::V ld_fdm(const void* base, int64_t i);
+template <>
+__device__ __forceinline__ double ld_fdm<PolF64>(const void* base, int64_t i) {
+  return static_cast<const double*>(base)[i];
+}
+template <>
+__device__ __forceinline__ df64 ld_fdm<PolDF>(const void* base, int64_t i) {
+  return static_cast<const df64*>(base)[i];
+}
+
+// out[..j..] = sum_i A(i, j) in[..i..] (transposed) or sum_i A(j, i) in[..i..] along axis `ax`
+template <class P>
+__device__ __forceinline__ void fdm_contract(const typename P::V* A, int ax, bool trans, const int* n,
+                                             const typename P::V* in, typename P::V* out) {
+  const int N = n[0] * n[1] * n[2];
+  const int na = n[ax];
+  const int stride = ax == 0 ? 1 : (ax == 1 ? n[0] : n[0] * n[1]);
+  for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    const int j = (idx / stride) % na;
+    const int base = idx - j * stride;
+    typename P::Acc acc[2];
+    P::init(acc[0]);
+    P::init(acc[1]);
+    for (int i = 0; i < na; ++i) {
+      typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
+      P::fma(acc[i & 1], a, in[base + i * stride]);
+    }
+    out[idx] = P::add(P::get(acc[0]), P::get(acc[1]));
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(128) k_fdm_apply(DevMesh m, const double* __restrict__ tI, double* __restrict__ sI) {
+  using V = typename P::V;
+  __shared__ V Vs[3][81];
+  __shared__ V b0[729], b1[729];
+  __shared__ int n[3];
+  const int s = blockIdx.x;
+  if (threadIdx.x < 3) n[threadIdx.x] = m.fdm_n[3 * s + threadIdx.x];
+  for (int t = threadIdx.x; t < 243; t += blockDim.x) Vs[t / 81][t % 81] = ld_fdm<P>(m.fdm_V, (int64_t)s * 243 + t);
+  __syncthreads();
+  const int N = n[0] * n[1] * n[2];
+  const int64_t off = m.ioff[s];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) b0[i] = P::from_d(tI[off + i]);
+  __syncthreads();
+  fdm_contract<P>(Vs[0], 0, true, n, b0, b1);
+  __syncthreads();
+  fdm_contract<P>(Vs[1], 1, true, n, b1, b0);
+  __syncthreads();
+  fdm_contract<P>(Vs[2], 2, true, n, b0, b1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    typename P::Acc acc;
+    P::init(acc);
+    P::fma(acc, b1[i], ld_fdm<P>(m.fdm_Dinv, off + i));
+    b1[i] = P::get(acc);
+  }
+  __syncthreads();
+  fdm_contract<P>(Vs[0], 0, false, n, b1, b0);
+  __syncthreads();
+  fdm_contract<P>(Vs[1], 1, false, n, b0, b1);
+  __syncthreads();
+  fdm_contract<P>(Vs[2], 2, false, n, b1, b0);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sI[off + i] = P::to_d(b0[i]);
+}
+
+void launch_kii_apply(const DevMesh& m, const double* tI, double* sI, int* err, cudaStream_t s) {
+  if (m.local_solver == DD_LOCAL_FDM) {
+    if (m.schur_prec == DD_PREC_DF64)
+      k_fdm_apply<PolDF><<<m.S, 128, 0, s>>>(m, tI, sI);
+    else
+      k_fdm_apply<PolF64><<<m.S, 128, 0, s>>>(m, tI, sI);
+    DD_CHECK_LAUNCH();
+  } else {
+    launch_symv(m.KIIinv, m.ioff, tI, sI, err, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // gathers, scatters, BDDC pieces
 // ---------------------------------------------------------------------------
 __global__ void k_gather(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
@@ -511,6 +663,46 @@ void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc,
                    const int64_t* bmap, double* y, cudaStream_t s) {
   if (n == 0) return;
   k_gather<<<grid_for(n, 256), 256, 0, s>>>(n, ptr, idx, loc, base, bmap, y);
+  DD_CHECK_LAUNCH();
+}
+
+// dL/dk_e = -lambda_e^T K_e^0 x_e with K_e^0 = K_e / k_e; Dirichlet nodes carry 0
+__global__ void k_coef_grad(DevMesh m, const double* __restrict__ x, const double* __restrict__ lam,
+                            double* __restrict__ grad) {
+  const int64_t E = (int64_t)m.nx * m.ny * m.nz;
+  const int64_t Nfx = m.fx1 - m.fx0, Nfy = m.fy1 - m.fy0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ex = (int)(e % m.nx), ey = (int)((e / m.nx) % m.ny), ez = (int)(e / ((int64_t)m.nx * m.ny));
+    double xv[8], lv[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      int gx = ex + (a & 1), gy = ey + ((a >> 1) & 1), gz = ez + (a >> 2);
+      bool fr = gx >= m.fx0 && gx < m.fx1 && gy >= m.fy0 && gy < m.fy1 && gz >= m.fz0 && gz < m.fz1;
+      int64_t f = (gx - m.fx0) + Nfx * ((gy - m.fy0) + Nfy * (int64_t)(gz - m.fz0));
+      xv[a] = fr ? x[f] : 0.0;
+      lv[a] = fr ? lam[f] : 0.0;
+    }
+    double c[3];
+    const double k = m.coef[e];
+    c[0] = m.ec[3 * e] / k; c[1] = m.ec[3 * e + 1] / k; c[2] = m.ec[3 * e + 2] / k;
+    double kd[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) kd[d] = PolF64::entry(c, d);
+    double s = 0.0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      double row = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) row = fma(kd[p ^ q], xv[q], row);
+      s = fma(lv[p], row, s);
+    }
+    grad[e] = -s;
+  }
+}
+
+void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, cudaStream_t s) {
+  int64_t E = (int64_t)m.nx * m.ny * m.nz;
+  k_coef_grad<<<grid_for(E, 256), 256, 0, s>>>(m, x, lam, grad);
   DD_CHECK_LAUNCH();
 }
 
@@ -612,6 +804,54 @@ void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map
     else
       k_bgemv<double, false><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
                                                   in, out_off, out, alpha, add);
+  }
+  DD_CHECK_LAUNCH();
+}
+
+// Batched transposed GEMV: one block per item, x staged in shared memory, thread per output
+// column j reading row i of M at consecutive addresses across the block (coalesced).
+template <class T>
+__global__ void __launch_bounds__(256) k_bgemv_t(const int64_t* __restrict__ row0, const int* __restrict__ cols,
+                                                 const int64_t* __restrict__ moff, const T* __restrict__ M,
+                                                 const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
+                                                 const double* __restrict__ in, const int64_t* __restrict__ out_off,
+                                                 double* __restrict__ out, double alpha,
+                                                 const double* __restrict__ add) {
+  extern __shared__ double xs[];
+  const int m = blockIdx.x;
+  const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
+  const int64_t io = in_off[m];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) xs[i] = in[in_map ? in_map[io + i] : io + i];
+  __syncthreads();
+  const T* A = M + moff[m];
+  const int64_t oo = out_off[m];
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int i = 0;
+    for (; i + 1 < R; i += 2) {
+      a0 = fma((double)A[(int64_t)i * C + j], xs[i], a0);
+      a1 = fma((double)A[(int64_t)(i + 1) * C + j], xs[i + 1], a1);
+    }
+    if (i < R) a0 = fma((double)A[(int64_t)i * C + j], xs[i], a0);
+    out[oo + j] = alpha * (a0 + a1) + (add ? add[oo + j] : 0.0);
+  }
+}
+
+void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                    const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
+  if (B.count == 0) return;
+  size_t smem = (size_t)std::max(B.max_rows, 1) * sizeof(double);
+  int threads = B.max_cols >= 256 ? 256 : 128;
+  if (B.prec == DD_PREC_FP32) {
+    if (smem > 48 * 1024)
+      DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bgemv_t<float><<<B.count, threads, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const float*>(B.data), in_off,
+                                                    in_map, in, out_off, out, alpha, add);
+  } else {
+    if (smem > 48 * 1024)
+      DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bgemv_t<double><<<B.count, threads, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const double*>(B.data),
+                                                     in_off, in_map, in, out_off, out, alpha, add);
   }
   DD_CHECK_LAUNCH();
 }

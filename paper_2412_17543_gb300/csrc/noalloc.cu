@@ -66,7 +66,7 @@ extern "C" dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double
     double* sI = base + n_int;
     double* yloc = base + 2 * n_int;
     dd::launch_elem_interior(m, dd::ELEM_SCHUR, x, nullptr, tI, s);
-    dd::launch_symv(m.KIIinv, m.ioff, tI, sI, dd::context_err(ctx), s);
+    dd::launch_kii_apply(m, tI, sI, dd::context_err(ctx), s);
     dd::launch_elem_interface(m, dd::ELEM_SCHUR, x, sI, yloc, s);
     dd::launch_gather(m.n_gamma, m.gptr, m.gidx, yloc, nullptr, nullptr, y, s);
     int e = 0;

@@ -710,6 +710,116 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
   DD_REQUIRE(!ad.on || opt.tau > 1.0, "adaptive threshold tau must exceed 1");
   finish_level(L1, gl, cd, opt.weights, kloc_fn, kdiag_fn, nloc, Iloc, Gloc, false, ad, "level 1");
 
+  // ---- fast diagonalization of K_II (constant coefficient per subdomain, tensor mesh) ----
+  {
+    bool constant = true;
+    std::vector<double> ksub(M.S, 1.0);
+    if (md.coef) {
+      for (int s = 0; s < M.S && constant; ++s) {
+        int I = s % M.Sx, J = (s / M.Sx) % M.Sy, Kk = s / (M.Sx * M.Sy);
+        int64_t e0 = (I * M.sx) + (int64_t)M.nx * ((J * M.sy) + (int64_t)M.ny * (Kk * M.sz));
+        ksub[s] = md.coef[e0];
+        for (int ec = 0; ec < M.sz && constant; ++ec)
+          for (int eb = 0; eb < M.sy && constant; ++eb)
+            for (int ea = 0; ea < M.sx; ++ea) {
+              int64_t e = (I * M.sx + ea) + (int64_t)M.nx * ((J * M.sy + eb) + (int64_t)M.ny * (Kk * M.sz + ec));
+              if (md.coef[e] != ksub[s]) {
+                constant = false;
+                break;
+              }
+            }
+      }
+    }
+    DD_REQUIRE(opt.local_solver != DD_LOCAL_FDM || constant,
+               "local_solver FDM needs a constant coefficient in every subdomain");
+    H.local_solver = (opt.local_solver == DD_LOCAL_DENSE || !constant) ? DD_LOCAL_DENSE : DD_LOCAL_FDM;
+    if (H.local_solver == DD_LOCAL_FDM) {
+      H.fdm.assign(M.S, FdmSub());
+      const int ns[3] = {M.sx, M.sy, M.sz}, nn[3] = {M.nx, M.ny, M.nz};
+      const int f0[3] = {M.fx0, M.fy0, M.fz0}, f1[3] = {M.fx1, M.fy1, M.fz1};
+      const std::vector<double>* cs[3] = {&M.xc, &M.yc, &M.zc};
+      int failed = -1;
+#pragma omp parallel for schedule(dynamic, 8)
+      for (int s = 0; s < M.S; ++s) {
+        const int blk[3] = {s % M.Sx, (s / M.Sx) % M.Sy, s / (M.Sx * M.Sy)};
+        FdmSub& F = H.fdm[s];
+        std::vector<double> lam[3];
+        for (int a = 0; a < 3; ++a) {
+          const int sa = ns[a], nl = sa + 1, g0 = blk[a] * sa;
+          std::vector<double> K1((size_t)nl * nl, 0.0), M1((size_t)nl * nl, 0.0);
+          for (int e = 0; e < sa; ++e) {  // 1D stiffness (1/h)[1 -1; -1 1] and mass h[1/3 1/6; 1/6 1/3]
+            double h = (*cs[a])[g0 + e + 1] - (*cs[a])[g0 + e];
+            K1[(size_t)e * nl + e] += 1.0 / h;
+            K1[(size_t)(e + 1) * nl + e + 1] += 1.0 / h;
+            K1[(size_t)e * nl + e + 1] -= 1.0 / h;
+            K1[(size_t)(e + 1) * nl + e] -= 1.0 / h;
+            M1[(size_t)e * nl + e] += h / 3.0;
+            M1[(size_t)(e + 1) * nl + e + 1] += h / 3.0;
+            M1[(size_t)e * nl + e + 1] += h / 6.0;
+            M1[(size_t)(e + 1) * nl + e] += h / 6.0;
+          }
+          std::vector<int> P;  // interior positions along this axis: not on a cut plane, not Dirichlet
+          for (int p = 0; p < nl; ++p) {
+            int g = g0 + p;
+            bool cutp = g % sa == 0 && g > 0 && g < nn[a];
+            if (!cutp && g >= f0[a] && g < f1[a]) P.push_back(p);
+          }
+          const int n = (int)P.size();
+          F.n[a] = n;
+          std::vector<double> Ka((size_t)n * n), Ma((size_t)n * n), Linv((size_t)n * n), C((size_t)n * n),
+              T((size_t)n * n), U((size_t)n * n);
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+              Ka[(size_t)i * n + j] = K1[(size_t)P[i] * nl + P[j]];
+              Ma[(size_t)i * n + j] = M1[(size_t)P[i] * nl + P[j]];
+            }
+          lam[a].resize(n);
+          if (!la::cholesky(n, Ma.data())) {
+#pragma omp critical
+            failed = s;
+            continue;
+          }
+          la::tri_inv_lower(n, Ma.data(), Linv.data());
+          // C = L^{-1} K L^{-T}
+          la::gemm_nt(n, n, n, 1.0, Ka.data(), Linv.data(), 0.0, T.data());   // K L^{-T}
+          la::gemm_nn(n, n, n, Linv.data(), T.data(), C.data());
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j) {
+              double v = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+              C[(size_t)i * n + j] = C[(size_t)j * n + i] = v;
+            }
+          la::sym_eig(n, C.data(), lam[a].data(), U.data());
+          // V = L^{-T} U
+          F.V[a].assign((size_t)n * n, 0.0);
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+              double sacc = 0.0;
+              for (int k2 = i; k2 < n; ++k2) sacc += Linv[(size_t)k2 * n + i] * U[(size_t)k2 * n + j];
+              F.V[a][(size_t)i * n + j] = sacc;
+            }
+        }
+        const double k = ksub[s];
+        F.Dinv.resize((size_t)F.n[0] * F.n[1] * F.n[2]);
+        for (int iz = 0; iz < F.n[2]; ++iz)
+          for (int iy = 0; iy < F.n[1]; ++iy)
+            for (int ix = 0; ix < F.n[0]; ++ix) {
+              double d = k * (lam[0][ix] + lam[1][iy] + lam[2][iz]);
+              if (!(d > 0.0)) {
+#pragma omp critical
+                failed = s;
+              }
+              F.Dinv[((size_t)iz * F.n[1] + iy) * F.n[0] + ix] = 1.0 / d;
+            }
+        if ((int64_t)F.Dinv.size() != L1.ioff[s + 1] - L1.ioff[s]) {
+#pragma omp critical
+          failed = s;
+        }
+      }
+      if (failed >= 0)
+        throw Error(DD_SINGULAR_LOCAL, "fast diagonalization failed in subdomain " + std::to_string(failed));
+    }
+  }
+
   H.levels = opt.levels;
   if (opt.levels == 2) {
     std::vector<double> KC = assemble_coarse(L1);

@@ -50,9 +50,21 @@ struct Mesh1 {
   std::vector<int64_t> gamma_free;    // global interface index -> free node index
 };
 
+// Fast diagonalization of K_II for a constant-coefficient subdomain on a tensor mesh:
+// interior nodes = P_x x P_y x P_z, K_II = k (Kz(x)My(x)Mx + Mz(x)Ky(x)Mx + Mz(x)My(x)Kx),
+// K_a V_a = M_a V_a L_a with V_a^T M_a V_a = I, so K_II^{-1} = V D^{-1} V^T with
+// V = Vz(x)Vy(x)Vx and D = k (Lz + Ly + Lx).
+struct FdmSub {
+  int n[3] = {0, 0, 0};             // |P_x|, |P_y|, |P_z|
+  std::vector<double> V[3];         // n_a x n_a, row-major (V[a][i * n_a + j] = (V_a)_{ij})
+  std::vector<double> Dinv;         // n_z * n_y * n_x, x fastest
+};
+
 struct HostSetup {
   Mesh1 mesh;
   Level l1;
+  int local_solver = DD_LOCAL_DENSE;  // representation of K_II^{-1} on the device
+  std::vector<FdmSub> fdm;             // per level-1 subdomain (local_solver == DD_LOCAL_FDM)
   // two-level coarse solve
   std::vector<double> KCinv;          // n_coarse^2 (levels == 2)
   // three-level

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
+#include <map>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -176,10 +178,10 @@ SymTiles upload_sym(DeviceArena& A, const std::vector<const double*>& mats, cons
               reinterpret_cast<double*>(tile)[r * 32 + c] = v;
             } else if (prec == DD_PREC_FP32) {
               reinterpret_cast<float*>(tile)[r * 32 + c] = (float)v;
-            } else {
+            } else {  // float pair (hi, lo) per element
               df64 d = df64_from_double(v);
-              reinterpret_cast<float*>(tile)[r * 32 + c] = d.hi;
-              reinterpret_cast<float*>(tile)[1024 + r * 32 + c] = d.lo;
+              reinterpret_cast<float*>(tile)[2 * (r * 32 + c)] = d.hi;
+              reinterpret_cast<float*>(tile)[2 * (r * 32 + c) + 1] = d.lo;
             }
           }
       }
@@ -208,8 +210,10 @@ BatchedRows upload_rows(DeviceArena& A, const std::vector<const double*>& mats, 
     moff[m] = tot;
     tot += (int64_t)R * C;
     B.max_cols = std::max(B.max_cols, C);
+    B.max_rows = std::max(B.max_rows, R);
   }
   B.nrows = row0[cnt];
+  B.count = (int)cnt;
   std::vector<int> item((size_t)B.nrows);
   for (size_t m = 0; m < cnt; ++m)
     for (int64_t r = row0[m]; r < row0[m + 1]; ++r) item[r] = (int)m;
@@ -279,7 +283,6 @@ void upload_bddc(DeviceArena& A, const Level& L, int prec, DevBDDC& b, cudaStrea
   }
   b.N = upload_sym(A, Ns, nG, prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
   int rp = prec == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64;
-  b.Phi = upload_rows(A, Ps, nG, nc, rp, false, s);
   b.PhiT = upload_rows(A, Ps, nG, nc, rp, true, s);
 }
 
@@ -303,7 +306,7 @@ void schur_apply(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
   launch_elem_interior(c->mesh, ELEM_SCHUR, x, nullptr, c->w.tI, s);
   {
     ProfScope pk(c, DD_PROF_SYMV_KII, s);
-    launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+    launch_kii_apply(c->mesh, c->w.tI, c->w.sI, c->w.err, s);
   }
   launch_elem_interface(c->mesh, ELEM_SCHUR, x, c->w.sI, c->w.yloc, s);
   launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, nullptr, nullptr, y, s);
@@ -311,14 +314,14 @@ void schur_apply(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
 
 void condense(dd_ctx* c, const double* f, double* b, cudaStream_t s) {
   launch_elem_interior(c->mesh, ELEM_CONDENSE, nullptr, f, c->w.tI, s);
-  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  launch_kii_apply(c->mesh, c->w.tI, c->w.sI, c->w.err, s);
   launch_elem_interface(c->mesh, ELEM_CONDENSE, nullptr, c->w.sI, c->w.yloc, s);
   launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, f, c->mesh.gamma_free, b, s);
 }
 
 void recover(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream_t s) {
   launch_elem_interior(c->mesh, ELEM_RECOVER, xg, f, c->w.tI, s);
-  launch_symv(c->mesh.KIIinv, c->mesh.ioff, c->w.tI, c->w.sI, c->w.err, s);
+  launch_kii_apply(c->mesh, c->w.tI, c->w.sI, c->w.err, s);
   launch_scatter_recover(c->mesh, xg, c->w.sI, x, s);
 }
 
@@ -334,7 +337,7 @@ void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double*
   launch_bgemv(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);  // Phi_i^T D_i R_i r
   launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
   coarse(gC, uC);
-  launch_bgemv(b.Phi, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);  // Phi_i R_Ci u_C
+  launch_bgemv_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);  // Phi_i R_Ci u_C
   launch_wgather(b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
 }
 
@@ -344,7 +347,7 @@ void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
   Work& w = c->w;
   launch_map_gather(L.n_int, L.imap, g, w.gI2, s);
   launch_symv(L.KIIinv, L.ioff, w.gI2, w.u0I2, w.err, s);
-  launch_bgemv(L.ET, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
+  launch_bgemv_t(L.E, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather(L.b.n_gamma, L.b.gptr, L.b.gidx, w.rl2, g, L.gam_c64, w.r2, s);  // g[gam_c] + sum of copies
   bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.vloc2, w.gloc2, w.g3, w.u3,
              [&](const double* g3, double* u3) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, s); }, s);
@@ -390,6 +393,85 @@ dd_status guard(F&& f) {
   }
 }
 
+// Work lists of the element passes, one set per distinct pattern of interior /
+// interface / absent nodes among the subdomains (a handful: interior subdomains and
+// those touching each part of the Dirichlet boundary).
+struct WorkLists {
+  std::vector<int> sub_type;          // [S]
+  std::vector<int> type_off;          // [types][6]
+  std::vector<int16_t> items;         // [items][9]
+  std::vector<int16_t> bl;            // boundary-layer element ids
+};
+
+WorkLists build_work_lists(const Mesh1& M) {
+  const int sx = M.sx, sy = M.sy, sz = M.sz, NE = sx * sy * sz;
+  DD_REQUIRE(8 * NE <= 32767, "subdomain too large for the element work lists (8 * elements > 32767)");
+  WorkLists W;
+  W.sub_type.resize(M.S);
+  std::map<std::vector<int8_t>, int> types;
+  std::vector<int8_t> pat(M.NL);
+  for (int s = 0; s < M.S; ++s) {
+    const int16_t* code = M.lidx.data() + (size_t)s * M.NL;
+    for (int l = 0; l < M.NL; ++l) pat[l] = code[l] >= 0 ? 1 : (code[l] == INT16_MIN ? 0 : 2);
+    auto it = types.find(pat);
+    if (it != types.end()) {
+      W.sub_type[s] = it->second;
+      continue;
+    }
+    const int t = (int)types.size();
+    types.emplace(pat, t);
+    W.sub_type[s] = t;
+    auto node = [&](int a, int b, int c) { return a + M.NLx * (b + M.NLy * c); };
+    // boundary-layer elements: at least one interface corner
+    std::vector<char> isbl(NE, 0);
+    const int bl0 = (int)W.bl.size();
+    for (int el = 0; el < NE; ++el) {
+      const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
+      for (int q = 0; q < 8 && !isbl[el]; ++q)
+        if (pat[node(ea + (q & 1), eb + ((q >> 1) & 1), ec + (q >> 2))] == 2) isbl[el] = 1;
+      if (isbl[el]) W.bl.push_back((int16_t)el);
+    }
+    // output items of one pass: nodes of kind `want` with their boundary-layer slots
+    auto pass = [&](int want, int& b, int& e) {
+      std::vector<std::array<int16_t, 9>> its;
+      for (int c = 0; c < M.NLz; ++c)
+        for (int bb = 0; bb < M.NLy; ++bb)
+          for (int a = 0; a < M.NLx; ++a) {
+            const int l = node(a, bb, c);
+            if (pat[l] != want) continue;
+            std::array<int16_t, 9> it;
+            it.fill(-1);
+            it[0] = (int16_t)l;
+            int k = 0;
+            for (int p = 0; p < 8; ++p) {
+              const int ea = a - (p & 1), eb = bb - ((p >> 1) & 1), ec = c - (p >> 2);
+              if (ea < 0 || eb < 0 || ec < 0 || ea >= sx || eb >= sy || ec >= sz) continue;
+              const int el = ea + sx * (eb + sy * ec);
+              if (!isbl[el]) continue;
+              it[1 + k++] = (int16_t)(el * 8 + p);
+            }
+            if (k > 0) its.push_back(it);
+          }
+      auto cnt = [](const std::array<int16_t, 9>& x) {
+        int k = 0;
+        while (k < 8 && x[1 + k] >= 0) ++k;
+        return k;
+      };
+      std::stable_sort(its.begin(), its.end(), [&](const auto& x, const auto& y) { return cnt(x) > cnt(y); });
+      b = (int)(W.items.size() / 9);
+      for (auto& x : its) W.items.insert(W.items.end(), x.begin(), x.end());
+      e = (int)(W.items.size() / 9);
+    };
+    int o[6];
+    pass(1, o[0], o[1]);
+    pass(2, o[2], o[3]);
+    o[4] = bl0;
+    o[5] = (int)W.bl.size();
+    W.type_off.insert(W.type_off.end(), o, o + 6);
+  }
+  return W;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -415,6 +497,7 @@ dd_status dd_default_options(dd_options* o) {
   o->reorth = 0;
   o->stop_rhs_norm = 1;
   o->maxit = 500;
+  o->local_solver = DD_LOCAL_AUTO;
   return DD_OK;
 }
 
@@ -452,6 +535,13 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     dm.n_int = H->l1.ioff[M.S];
     dm.schur_prec = opt->schur_prec;
     dm.lidx = A.upload(M.lidx, s);
+    {
+      WorkLists W = build_work_lists(M);
+      dm.sub_type = A.upload(W.sub_type, s);
+      dm.type_off = A.upload(W.type_off, s);
+      dm.type_items = A.upload(W.items, s);
+      dm.type_bl = A.upload(W.bl, s);
+    }
     dm.ioff = A.upload(H->l1.ioff, s);
     dm.goff = A.upload(H->l1.goff, s);
     dm.gmap = A.upload(H->l1.gmap, s);
@@ -468,8 +558,37 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       }
       dm.ec = A.upload(ec, s);
       dm.ec_df = A.upload(ecd, s);
+      std::vector<double> kc(E, 1.0);  // E = number of elements
+      if (md->coef) std::copy(md->coef, md->coef + E, kc.begin());
+      dm.coef = A.upload(kc, s);
     }
-    {
+    dm.local_solver = H->local_solver;
+    if (H->local_solver == DD_LOCAL_FDM) {
+      // 1D eigenbases padded to 9x9 per axis, and D^{-1} indexed like the interior vectors
+      std::vector<int> fn((size_t)3 * M.S);
+      std::vector<double> Vd((size_t)243 * M.S, 0.0), Dd((size_t)dm.n_int);
+      for (int i = 0; i < M.S; ++i) {
+        const FdmSub& F = H->fdm[i];
+        for (int a = 0; a < 3; ++a) {
+          fn[3 * i + a] = F.n[a];
+          for (int r = 0; r < F.n[a]; ++r)
+            for (int q = 0; q < F.n[a]; ++q) Vd[(size_t)243 * i + 81 * a + 9 * r + q] = F.V[a][(size_t)r * F.n[a] + q];
+        }
+        std::copy(F.Dinv.begin(), F.Dinv.end(), Dd.begin() + H->l1.ioff[i]);
+      }
+      dm.fdm_n = A.upload(fn, s);
+      if (opt->schur_prec == DD_PREC_DF64) {
+        std::vector<df64> Vf(Vd.size()), Df(Dd.size());
+        for (size_t t = 0; t < Vd.size(); ++t) Vf[t] = df64_from_double(Vd[t]);
+        for (size_t t = 0; t < Dd.size(); ++t) Df[t] = df64_from_double(Dd[t]);
+        dm.fdm_V = A.upload(Vf, s);
+        dm.fdm_Dinv = A.upload(Df, s);
+      } else {
+        dm.fdm_V = A.upload(Vd, s);
+        dm.fdm_Dinv = A.upload(Dd, s);
+      }
+      dm.KIIinv.count = 0;
+    } else {
       std::vector<const double*> mats;
       std::vector<int> dims;
       for (int i = 0; i < M.S; ++i) {
@@ -513,7 +632,6 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       }
       L.KIIinv = upload_sym(A, Ks, nI, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, s);
       L.E = upload_rows(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, false, s);
-      L.ET = upload_rows(A, Es, nI, nG, pp == DD_PREC_FP32 ? DD_PREC_FP32 : DD_PREC_FP64, true, s);
       L.n3 = H->l2.n_coarse;
       L.KC3inv = upload_dense(A, H->KC3inv, pp);
       w.gI2 = A.alloc<double>(L.n_int);
@@ -552,10 +670,17 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     DD_CUDA(cudaEventCreate(&c->ev1));
     DD_CUDA(cudaStreamSynchronize(s));
     {
+      // algorithmic bytes of one K_II^{-1} application: the operator data read once and the
+      // vectors in and out (dense: packed triangles; FDM: 1D eigenbases and D^{-1})
       double kii = 0, nn = 0;
       for (int i = 0; i < M.S; ++i) {
         double a = H->l1.sub[i].nI, g = H->l1.sub[i].nG;
-        kii += a * (a + 1) / 2 * 8.0 + 2 * a * 8.0;
+        if (H->local_solver == DD_LOCAL_FDM) {
+          const FdmSub& F = H->fdm[i];
+          kii += (F.n[0] * F.n[0] + F.n[1] * F.n[1] + F.n[2] * F.n[2]) * 8.0 + a * 8.0 + 2 * a * 8.0;
+        } else {
+          kii += a * (a + 1) / 2 * 8.0 + 2 * a * 8.0;
+        }
         nn += g * (g + 1) / 2 * (pp == DD_PREC_FP32 ? 4.0 : 8.0) + 2 * g * 8.0;
       }
       c->prof_bytes[DD_PROF_SYMV_KII] = kii;
@@ -568,6 +693,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->info.n_adaptive = H->l1.n_adaptive;
     c->info.n_sub2 = c->levels == 3 ? H->l2.S : 0;
     c->info.n_coarse3 = c->levels == 3 ? H->l2.n_coarse : 0;
+    c->info.local_solver = H->local_solver;
     c->info.device_bytes = (int64_t)A.bytes;
     c->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = c.release();
@@ -593,6 +719,7 @@ dd_status dd_plan(const dd_mesh_desc* md, const dd_options* opt, dd_info_t* info
     info->n_adaptive = H.l1.n_adaptive;
     info->n_sub2 = H.levels == 3 ? H.l2.S : 0;
     info->n_coarse3 = H.levels == 3 ? H.l2.n_coarse : 0;
+    info->local_solver = H.local_solver;
     info->setup_seconds = H.setup_seconds;
     if (nodes) {
       DD_REQUIRE(capacity >= H.l1.n_gamma, "dd_plan: node buffer too small");
@@ -1027,19 +1154,137 @@ dd_status dd_profile(dd_ctx* c, int32_t enable, dd_kernel_prof* prof, int64_t* l
   });
 }
 
-dd_status dd_adjoint(dd_ctx*, const double*, const double*, double*, double*, double, dd_recycle*, dd_stats*, void*) {
-  g_last_error = "dd_adjoint: not available in this build";
-  return DD_INVALID_ARG;
+dd_status dd_adjoint(dd_ctx* c, const double* grad_x, const double* x, double* grad_f, double* grad_coef,
+                     double rtol, dd_recycle* st, dd_stats* stats, void* stream) {
+  if (!c || !grad_x || !grad_f || (grad_coef && !x) || !(rtol > 0.0) || (st && st->ctx != c)) {
+    g_last_error = "dd_adjoint: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  dd_status result = DD_OK;
+  dd_status gs = guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    DD_CUDA(cudaEventRecord(c->ev0, s));
+    // lambda = K^{-1} grad_x: the same condensation, deflated PCG (basis of st, not updated) and recovery
+    condense(c, grad_x, c->bvec, s);
+    DD_CUDA(cudaMemsetAsync(c->xg, 0, c->n_gamma * sizeof(double), s));
+    result = pcg_solve(c, st, rtol, false, stats, s);
+    recover(c, grad_x, c->xg, grad_f, s);
+    if (grad_coef) launch_coef_grad(c->mesh, x, grad_f, grad_coef, s);
+    DD_CUDA(cudaEventRecord(c->ev1, s));
+    check_err(c, s);
+    if (c->prof_on) c->harvest();
+    if (stats) {
+      float ms = 0.f;
+      DD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      stats->ms = ms;
+    }
+  });
+  if (gs != DD_OK) return gs;
+  if (result != DD_OK) g_last_error = result == DD_NOT_CONVERGED ? "maxit reached" : "PCG breakdown";
+  return result;
 }
 
-dd_status dd_recycle_export(const dd_recycle*, void*, size_t*) {
-  g_last_error = "dd_recycle_export: not available in this build";
-  return DD_INVALID_ARG;
+// Checkpoint layout (host bytes): header, theta[ntheta], x_prev[n_gamma], then for k > 0
+// W, AW, MAW [k][n_gamma] and Ginv, WWinv [k][k] (all FP64, little-endian as in memory).
+struct RecycleHeader {
+  char magic[8];
+  int64_t n_gamma;
+  int32_t kmax, strategy, k, frozen, step, ntheta;
+  double freeze_tol;
+};
+
+static size_t recycle_bytes(const dd_recycle* st) {
+  size_t n = (size_t)st->ctx->n_gamma, k = (size_t)st->k;
+  return sizeof(RecycleHeader) + st->theta.size() * 8 + n * 8 + (k ? (3 * k * n + 2 * k * k) * 8 : 0);
 }
 
-dd_status dd_recycle_import(dd_ctx*, const void*, size_t, dd_recycle**) {
-  g_last_error = "dd_recycle_import: not available in this build";
-  return DD_INVALID_ARG;
+dd_status dd_recycle_export(const dd_recycle* st, void* host_buf, size_t* bytes) {
+  if (!st || !bytes) {
+    g_last_error = "dd_recycle_export: NULL argument";
+    return DD_INVALID_ARG;
+  }
+  return guard([&] {
+    size_t need = recycle_bytes(st);
+    if (!host_buf) {
+      *bytes = need;
+      return;
+    }
+    DD_REQUIRE(*bytes >= need, "dd_recycle_export: buffer too small");
+    *bytes = need;
+    unsigned char* p = static_cast<unsigned char*>(host_buf);
+    RecycleHeader h{};
+    std::memcpy(h.magic, "DDRCY01", 8);
+    h.n_gamma = st->ctx->n_gamma;
+    h.kmax = st->kmax; h.strategy = st->strategy; h.k = st->k; h.frozen = st->frozen; h.step = st->step;
+    h.ntheta = (int32_t)st->theta.size();
+    h.freeze_tol = st->freeze_tol;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    std::memcpy(p, st->theta.data(), st->theta.size() * 8);
+    p += st->theta.size() * 8;
+    const size_t n = (size_t)h.n_gamma, k = (size_t)st->k;
+    DD_CUDA(cudaMemcpy(p, st->xg_prev, n * 8, cudaMemcpyDeviceToHost));
+    p += n * 8;
+    if (k) {
+      for (const double* src : {st->W, st->AW, st->MAW}) {
+        DD_CUDA(cudaMemcpy(p, src, k * n * 8, cudaMemcpyDeviceToHost));
+        p += k * n * 8;
+      }
+      DD_CUDA(cudaMemcpy(p, st->Ginv, k * k * 8, cudaMemcpyDeviceToHost));
+      p += k * k * 8;
+      if (st->ctx->opt.reorth) DD_CUDA(cudaMemcpy(p, st->WWinv, k * k * 8, cudaMemcpyDeviceToHost));
+      else std::memset(p, 0, k * k * 8);
+    }
+  });
+}
+
+dd_status dd_recycle_import(dd_ctx* c, const void* host_buf, size_t bytes, dd_recycle** out) {
+  if (!c || !host_buf || !out) {
+    g_last_error = "dd_recycle_import: NULL argument";
+    return DD_INVALID_ARG;
+  }
+  *out = nullptr;
+  RecycleHeader h;
+  if (bytes < sizeof h) {
+    g_last_error = "dd_recycle_import: buffer too small";
+    return DD_INVALID_ARG;
+  }
+  std::memcpy(&h, host_buf, sizeof h);
+  if (std::memcmp(h.magic, "DDRCY01", 8) != 0 || h.n_gamma != c->n_gamma || h.k < 0 || h.k > h.kmax) {
+    g_last_error = "dd_recycle_import: not a checkpoint of this problem";
+    return DD_INVALID_ARG;
+  }
+  dd_recycle* st = nullptr;
+  dd_status rc = dd_recycle_create(c, h.kmax, h.strategy, h.freeze_tol, &st);
+  if (rc != DD_OK) return rc;
+  rc = guard([&] {
+    st->k = h.k;
+    st->frozen = h.frozen != 0;
+    st->step = h.step;
+    DD_REQUIRE(bytes >= recycle_bytes(st) + (size_t)h.ntheta * 8 - st->theta.size() * 8,
+               "dd_recycle_import: truncated checkpoint");
+    const unsigned char* p = static_cast<const unsigned char*>(host_buf) + sizeof h;
+    st->theta.assign(reinterpret_cast<const double*>(p), reinterpret_cast<const double*>(p) + h.ntheta);
+    p += (size_t)h.ntheta * 8;
+    const size_t n = (size_t)h.n_gamma, k = (size_t)h.k;
+    DD_CUDA(cudaMemcpy(st->xg_prev, p, n * 8, cudaMemcpyHostToDevice));
+    p += n * 8;
+    if (k) {
+      for (double* dst : {st->W, st->AW, st->MAW}) {
+        DD_CUDA(cudaMemcpy(dst, p, k * n * 8, cudaMemcpyHostToDevice));
+        p += k * n * 8;
+      }
+      DD_CUDA(cudaMemcpy(st->Ginv, p, k * k * 8, cudaMemcpyHostToDevice));
+      p += k * k * 8;
+      DD_CUDA(cudaMemcpy(st->WWinv, p, k * k * 8, cudaMemcpyHostToDevice));
+    }
+  });
+  if (rc != DD_OK) {
+    delete st;
+    return rc;
+  }
+  *out = st;
+  return DD_OK;
 }
 
 }  // extern "C"

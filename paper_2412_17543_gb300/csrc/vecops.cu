@@ -135,23 +135,32 @@ void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_
 // ---------------------------------------------------------------------------
 // deflation
 // ---------------------------------------------------------------------------
-// partial dots of the k columns of W (column-major, leading dimension ld) with v
+// partial dots of the k columns of W (column-major, leading dimension ld) with v; eight
+// columns per sweep so that v is read k/8 times and every W element once
 __global__ void __launch_bounds__(RB) k_wdots(int64_t n, int k, const double* __restrict__ W, int64_t ld,
                                               const double* __restrict__ v, double* wpart) {
-  __shared__ double sh[RB / 32];
+  __shared__ double sh[8][RB / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = 0; c < k; ++c) {
-    const double* w = W + (int64_t)c * ld;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB)
-      acc = fma(w[i], v[i], acc);
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sh[warp] = acc;
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int nc = min(8, k - c0);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+      const double vi = v[i];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < nc) acc[t] = fma(W[(int64_t)(c0 + t) * ld + i], vi, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      double x = acc[t];
+      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) sh[t][warp] = x;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nc) {
       double s = 0.0;
-      for (int w2 = 0; w2 < RB / 32; ++w2) s += sh[w2];
-      wpart[(int64_t)blockIdx.x * MAXK + c] = s;
+      for (int w2 = 0; w2 < RB / 32; ++w2) s += sh[threadIdx.x][w2];
+      wpart[(int64_t)blockIdx.x * MAXK + c0 + threadIdx.x] = s;
     }
     __syncthreads();
   }

@@ -64,9 +64,11 @@ def oracle_case(name):
 
 @pytest.mark.parametrize("name", ["cube16_cf", "graded16_s8", "graded24_s8"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("df64", 1e-11)])
-def test_schur_apply(name, prec, tol):
+@pytest.mark.parametrize("local", ["dense", "fdm"])
+def test_schur_apply(name, prec, tol, local):
     m, subs, kinds, levels = oracle_case(name)
-    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec))
+    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec, local_solver=local))
+    assert S.info["local_solver"] == (1 if local == "dense" else 2)
     assert np.array_equal(S.interface_nodes(), subs.gamma)
     rng = np.random.default_rng(0)
     for _ in range(2):
@@ -78,9 +80,10 @@ def test_schur_apply(name, prec, tol):
 
 @pytest.mark.parametrize("name", ["cube16_cf", "graded24_s8"])
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
-def test_condense_and_recover(name, prec):
+@pytest.mark.parametrize("local", ["dense", "fdm"])
+def test_condense_and_recover(name, prec, local):
     m, subs, kinds, levels = oracle_case(name)
-    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec))
+    S = P.Solver(m, **_opts(2, kinds, schur_prec=prec, local_solver=local))
     f = load_sequence(m, 1, 1)[0]
     b = N(S.condense(T(f)))
     bo = subs.condense(f)
@@ -151,11 +154,12 @@ def test_solve_sequence_recycled(strategy):
     assert sum(its) <= sum(its_o) + len(F), (its, its_o)
 
 
-def test_solve_mixed_recycled_three_level():
+@pytest.mark.parametrize("local", ["dense", "fdm"])
+def test_solve_mixed_recycled_three_level(local):
     m, subs, kinds, levels = oracle_case("graded16_s2_3l")
     F = load_sequence(m, 3, 6)
     X = _direct(m, F)
-    S = P.Solver(m, **_opts(3, kinds, schur_prec="df64", precond_prec="fp32", flexible=1))
+    S = P.Solver(m, **_opts(3, kinds, schur_prec="df64", precond_prec="fp32", flexible=1, local_solver=local))
     rec = S.recycler(8, "B4")
     for t, f in enumerate(F):
         x, st = S.solve(T(f), rec, rtol=1e-9)
@@ -181,3 +185,48 @@ def test_precond_apply_adaptive(tau):
     z = N(S.precond_apply(T(r)))
     zo = Po.apply(r)
     assert np.abs(z - zo).max() <= 1e-9 * np.abs(zo).max()
+
+
+def test_adjoint_and_autograd_match_oracle():
+    from oracle import adjoint
+    rng = np.random.default_rng(11)
+    n = 16
+    from workload import gaussian_random_field
+    g = gaussian_random_field(n, 40)
+    m = make_mesh(n, 4, 1.08, 20.0, coef=np.exp(g))
+    f = load_sequence(m, 4, 1)[0]
+    target = rng.standard_normal(m.n_free)
+    ch = cholesky.factor_mesh(m)
+    x_o = ch.solve(f)
+    gf_o, gk_o = adjoint.adjoint(m, ch, x_o, 2 * (x_o - target))
+    S = P.Solver(m, levels=2, use_edges=1, schur_prec="fp64", precond_prec="fp64")
+    rec = S.recycler(0)
+    # C ABI adjoint
+    gf, gk, st = S.adjoint(T(2 * (x_o - target)), T(x_o), None, 1e-12)
+    assert np.abs(N(gf) - gf_o).max() <= 1e-9 * np.abs(gf_o).max()
+    assert np.abs(N(gk) - gk_o).max() <= 1e-9 * np.abs(gk_o).max()
+    # autograd through the binding: loss = ||x - target||^2, gradients w.r.t. f and g = log k
+    fT = T(f).requires_grad_(True)
+    gT = T(g).requires_grad_(True)
+    x = P.PoissonSolve.apply(fT, gT, S, rec, 1e-12, 1e-12)
+    loss = ((x - T(target)) ** 2).sum()
+    loss.backward()
+    gg_o = (np.exp(g).ravel() * gk_o).reshape(g.shape)
+    assert np.abs(N(fT.grad) - gf_o).max() <= 1e-8 * np.abs(gf_o).max()
+    assert np.abs(N(gT.grad) - gg_o).max() <= 1e-8 * np.abs(gg_o).max()
+
+
+def test_recycle_checkpoint_resume_is_bitwise_identical():
+    m, subs, kinds, levels = oracle_case("graded16_s8")
+    F = load_sequence(m, 5, 10)
+    S = P.Solver(m, **_opts(2, kinds, schur_prec="df64", precond_prec="fp32", flexible=1))
+    recA = S.recycler(6, "B4")
+    xa = [N(S.solve(T(f), recA, rtol=1e-9)[0]) for f in F]
+    recB = S.recycler(6, "B4")
+    xb = [N(S.solve(T(f), recB, rtol=1e-9)[0]) for f in F[:5]]
+    blob = recB.export()
+    recB.close()
+    recC = P.Recycler.restore(S, blob)
+    xb += [N(S.solve(T(f), recC, rtol=1e-9)[0]) for f in F[5:]]
+    for t in range(10):
+        assert np.array_equal(xa[t], xb[t]), t
