@@ -220,6 +220,41 @@ typedef struct {
 dd_status dd_profile(dd_ctx* ctx, int32_t enable, dd_kernel_prof* prof /* host, out, nullable */,
                      int64_t* kernel_launches /* host, out, nullable */, void* stream);
 
+/* ---- ensembles (independent right-hand-side sequences solved as one block) ----
+ * Up to DD_ENSEMBLE_WIDTH sequences that share the matrix, the BDDC preconditioner
+ * and one recycled deflation basis advance together: every operator application
+ * streams the local operators once for all members. Each member runs its own
+ * deflated PCG (Algorithm 1: own alpha, beta and stopping test, decided on the
+ * device); the shared basis W is updated from the search vectors of member 0 with
+ * the strategy of the state (Sect. 4.2) and deflates every member. The paper solves
+ * one sequence; the ensemble is this library's batching of independent sequences.
+ * Residual re-orthogonalization (options.reorth) is not applied to ensembles, and a
+ * dense K_II^{-1} needs schur_prec FP64 (df64 tiles serve the single path only). */
+#define DD_ENSEMBLE_WIDTH 32
+
+/* Recycle state for ensembles: as dd_recycle_create, plus the previous solutions of
+ * DD_ENSEMBLE_WIDTH members (initial guesses, zero at creation). Use it only with
+ * dd_solve_batch. Errors: as dd_recycle_create. */
+dd_status dd_recycle_create_batch(dd_ctx* ctx, int32_t k, int32_t strategy, double freeze_tol, dd_recycle** out);
+
+/* Solves K x_m = f_m for the nrhs (1..DD_ENSEMBLE_WIDTH) members of one time step.
+ * F: [nrhs][n_free] device in (member-major, free nodes lexicographic, x fastest);
+ * X: [nrhs][n_free] device out; stats: [nrhs] host out or NULL (ms is the whole
+ * block's device time). Member m always uses slot m of the state's previous
+ * solutions. Workspace for DD_ENSEMBLE_WIDTH members is allocated on the first call
+ * and kept by the context. Errors: DD_INVALID_ARG (sizes, a state not made by
+ * dd_recycle_create_batch, unsupported options), DD_NOT_CONVERGED (some member hit
+ * maxit; every member's best iterate is written), DD_BREAKDOWN, DD_CUDA_ERROR. */
+dd_status dd_solve_batch(dd_ctx* ctx, int32_t nrhs, const double* F, double* X, double rtol, dd_recycle* st,
+                         dd_stats* stats, void* stream);
+
+/* Ensemble counterparts of dd_schur_apply and dd_precond_apply (eq. Sug; eqs.
+ * averaging_subdomain_solves, coarse_problem, localCorr) on nrhs interface vectors at
+ * once: X, R: [nrhs][n_gamma] device in; Y, Z: [nrhs][n_gamma] device out. Same
+ * arithmetic as dd_solve_batch uses. Errors: DD_INVALID_ARG, DD_CUDA_ERROR. */
+dd_status dd_schur_apply_batch(dd_ctx* ctx, int32_t nrhs, const double* X, double* Y, void* stream);
+dd_status dd_precond_apply_batch(dd_ctx* ctx, int32_t nrhs, const double* R, double* Z, void* stream);
+
 /* Checkpoint of a recycle state: writes at most *bytes bytes to host_buf; with
  * host_buf NULL only sets *bytes to the size needed. */
 dd_status dd_recycle_export(const dd_recycle* st, void* host_buf, size_t* bytes);

@@ -76,7 +76,13 @@ SIGNATURES = {
     "dd_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(KernelProf), ctypes.POINTER(ctypes.c_int64), _P]),
     "dd_recycle_export": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "dd_recycle_import": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "dd_recycle_create_batch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D, ctypes.POINTER(_P)]),
+    "dd_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),
+    "dd_schur_apply_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    "dd_precond_apply_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
 }
+
+ENSEMBLE_WIDTH = 32  # DD_ENSEMBLE_WIDTH
 
 _lib = None
 

@@ -165,6 +165,40 @@ class Solver:
         return x, stats
 
 
+    def ensemble_recycler(self, k=0, strategy="B4", freeze_tol=1e-5) -> "Recycler":
+        """Recycle state for ensemble solves (dd_recycle_create_batch)."""
+        return Recycler(self, k, strategy, freeze_tol, ensemble=True)
+
+    def schur_apply_batch(self, X, out=None):
+        """Y[m] = A X[m] for interface vectors X (device float64 [nrhs][n_gamma])."""
+        Y = out if out is not None else X.new_empty(X.shape)
+        nat.check(self.lib.dd_schur_apply_batch(self.handle, int(X.shape[0]), _dptr(X), _dptr(Y), _stream_ptr()),
+                  "dd_schur_apply_batch")
+        return Y
+
+    def precond_apply_batch(self, R, out=None):
+        """Z[m] = M^{-1} R[m] (BDDC) for interface vectors R (device float64 [nrhs][n_gamma])."""
+        Z = out if out is not None else R.new_empty(R.shape)
+        nat.check(self.lib.dd_precond_apply_batch(self.handle, int(R.shape[0]), _dptr(R), _dptr(Z), _stream_ptr()),
+                  "dd_precond_apply_batch")
+        return Z
+
+    def solve_batch(self, F, rec: "Recycler", rtol=1e-8, out=None, allow_not_converged=False):
+        """X[m] = K^{-1} F[m] for an ensemble F (device float64 [nrhs][n_free], nrhs <= 32);
+        returns (X, list of per-member stats dicts)."""
+        nrhs = int(F.shape[0])
+        X = out if out is not None else F.new_empty(F.shape)
+        st = (nat.Stats * nrhs)()
+        allow = (nat.DD_OK, nat.DD_NOT_CONVERGED) if allow_not_converged else (nat.DD_OK,)
+        code = nat.check(self.lib.dd_solve_batch(self.handle, nrhs, _dptr(F), _dptr(X), ctypes.c_double(rtol),
+                                                 rec.handle, st, _stream_ptr()), "dd_solve_batch", allow)
+        stats = []
+        for m in range(nrhs):
+            d = {f: getattr(st[m], f) for f, _ in nat.Stats._fields_}
+            d["status"] = nat.STATUS_NAMES[code]
+            stats.append(d)
+        return X, stats
+
     def adjoint(self, grad_x, x=None, rec: "Recycler" = None, rtol=1e-10, coef_grad=True):
         """lambda = K^{-1} grad_x (K symmetric); returns (dL/df = lambda, dL/dk per element or None, stats)."""
         import torch
@@ -215,11 +249,12 @@ class PoissonSolve:
 class Recycler:
     """Recycle state of a sequence of solves (dd_recycle_create / dd_recycle_destroy)."""
 
-    def __init__(self, solver: Solver, k=0, strategy="B4", freeze_tol=1e-5):
+    def __init__(self, solver: Solver, k=0, strategy="B4", freeze_tol=1e-5, ensemble=False):
         self.solver = solver
         h = ctypes.c_void_p()
-        nat.check(solver.lib.dd_recycle_create(solver.handle, int(k), nat.STRATEGY[strategy],
-                                               ctypes.c_double(freeze_tol), ctypes.byref(h)), "dd_recycle_create")
+        fn = "dd_recycle_create_batch" if ensemble else "dd_recycle_create"
+        nat.check(getattr(solver.lib, fn)(solver.handle, int(k), nat.STRATEGY[strategy], ctypes.c_double(freeze_tol),
+                                          ctypes.byref(h)), fn)
         self.handle = h
 
     def export(self) -> bytes:

@@ -1,0 +1,101 @@
+// Ensemble (multi-right-hand-side) kernels: every vector of the batched path holds the
+// members of an ensemble interleaved, v[i * BW + m] for row i and member m, so that a
+// warp's lanes are the members of one row (coalesced 128/256-byte rows, one index
+// lookup per row shared by all members). The ensemble is padded to BW members; padded
+// members carry zero right-hand sides and stay inactive.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.h"
+#include "device.h"
+
+namespace dd {
+
+constexpr int BW = 32;  // ensemble block width (members per row, one per lane)
+
+// per-member device scalars, slot-major: sc[slot * BW + m]
+enum {
+  BS_RZ = 0, BS_PQ, BS_ALPHA, BS_RR, BS_BETA, BS_BB, BS_FLAG, BS_ACT, BS_REF, BS_RTOL2, BS_ITS, BS_RR0,
+  BS_COUNT = 16
+};
+enum { BFIN_PQ = 1, BFIN_RR, BFIN_RZ0, BFIN_RZ, BFIN_BB };
+
+// scratch of the batched operators, interleaved [rows][BW]; BDDC vectors in the
+// preconditioner's type (float for FP32, double for FP64)
+struct BatchWork {
+  DeviceArena arena;
+  int kmax = 0;
+  double *tI = nullptr, *sI = nullptr, *yloc = nullptr;
+  void *rloc = nullptr, *uloc = nullptr, *vloc = nullptr, *gloc = nullptr, *gC = nullptr, *uC = nullptr;
+  void *gI2 = nullptr, *u0I2 = nullptr, *rl2 = nullptr, *r2 = nullptr, *rloc2 = nullptr, *uloc2 = nullptr,
+       *vloc2 = nullptr, *gloc2 = nullptr, *g3 = nullptr, *u3 = nullptr, *z2 = nullptr, *uI2 = nullptr;
+  double *xg = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr;
+  double *F = nullptr, *X = nullptr;  // [n_free][BW]
+  double* sc = nullptr;               // [BS_COUNT][BW]
+  double* sc_host = nullptr;          // pinned mirror
+  double* partials = nullptr;         // [NBLK][4][BW]
+  double* wpart = nullptr;            // [NBLK][MAXK][BW]
+  double* mu = nullptr;               // [MAXK][BW]
+};
+
+// ---- layout ----
+// out[i * BW + m] = m < nrhs ? F[m * n + i] : 0   (F member-major, as the caller passes it)
+void launch_pack_in(int64_t n, int nrhs, const double* F, double* out, cudaStream_t s);
+// X[m * n + i] = in[i * BW + m] for m < nrhs
+void launch_pack_out(int64_t n, int nrhs, const double* in, double* X, cudaStream_t s);
+// out[i] = in[i * BW + col]
+void launch_extract_col(int64_t n, const double* in, int col, double* out, cudaStream_t s);
+
+// ---- Schur-complement operator (interleaved counterparts of the single-vector kernels) ----
+void launch_elem_interior_b(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
+                            cudaStream_t s);
+void launch_elem_interface_b(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+                             cudaStream_t s);
+void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStream_t s);
+void launch_gather_b(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
+                     const int64_t* bmap, double* y, cudaStream_t s);
+void launch_scatter_recover_b(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
+
+// ---- BDDC (T = float or double by prec) ----
+// symmetric tiles times a block of BW members: out_m = A_m in_m
+void launch_symm_b(const SymTiles& A, const int64_t* voff, const void* in, void* out, cudaStream_t s);
+void launch_restrict_b(int prec, int64_t nflat, const int* gmap, const double* D, const double* r, void* rloc,
+                       cudaStream_t s);
+// per item m: out[(out_off[m]+i)][.] = alpha * sum_j M_m[i][j] x_j[.] (+ add), x_j = in[in_map?..][.]
+void launch_bmm(const BatchedRows& B, const int64_t* in_off, const int* in_map, const void* in,
+                const int64_t* out_off, void* out, double alpha, const void* add, cudaStream_t s);
+// transposed: out[(out_off[m]+j)][.] = alpha * sum_i M_m[i][j] x_i[.] (+ add)
+void launch_bmm_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const void* in,
+                  const int64_t* out_off, void* out, double alpha, const void* add, cudaStream_t s);
+// y[g][.] = sum over copies of loc[idx[k]][.]  (BDDC coarse / level-2 gathers, type by prec)
+void launch_gather_tb(int prec, int64_t n, const int* ptr, const int* idx, const void* loc, const void* base,
+                      const int64_t* bmap, void* y, cudaStream_t s);
+// typed counterparts for a level whose residual is already in the preconditioner type
+void launch_restrict_tb(int prec, int64_t nflat, const int* gmap, const double* D, const void* r, void* rloc,
+                        cudaStream_t s);
+void launch_wgather_tb(int prec, int64_t n, const int* ptr, const int* idx, const double* D, const void* uloc,
+                       const void* vloc, void* z, cudaStream_t s);
+void launch_wgather_b(int prec, int64_t n, const int* ptr, const int* idx, const double* D, const void* uloc,
+                      const void* vloc, double* z, cudaStream_t s);
+void launch_dense_mm(int prec, int n, const void* A, const void* x, void* y, cudaStream_t s);
+void launch_map_gather_b(int prec, int64_t n, const int* map, const void* in, void* out, cudaStream_t s);
+void launch_map_scatter_b(int prec, int64_t n, const int* map, const void* in, void* out, cudaStream_t s);
+
+// ---- Krylov vectors, per member ----
+void bvec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, double* partials,
+               cudaStream_t s);
+void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s);
+void bvec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q,
+                double* partials, cudaStream_t s);
+void bvec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+void bvec_init(double* sc, int nrhs, double rtol, int stop_rhs_norm, cudaStream_t s);
+// mu[j][m] = sum_l G[j][l] sum_i V[l][i] v[i][m]   (V: k columns of length n, stride ld)
+void bdefl_mu(int64_t n, int k, const double* V, int64_t ld, const double* v, const double* G, double* wpart,
+              double* mu, cudaStream_t s);
+// y[i][m] = z[i][m] + beta_m y[i][m] + sign_w sum_j W[j][i] mu[j][m]  (z NULL: y += sign_w W mu;
+// beta_idx < 0: no beta term)
+void bdefl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
+                  const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+
+}  // namespace dd

@@ -24,15 +24,14 @@ struct SymTiles {
 
 inline size_t tile_bytes(int prec) { return prec == DD_PREC_FP32 ? 4096 : 8192; }
 
-// A batch of row-major matrices addressed through a flat row space (for batched GEMVs):
-// item m owns rows row0[m] .. row0[m] + rows_m - 1; its matrix starts at element moff[m].
+// A batch of row-major matrices (for batched GEMVs): item m has rows row0[m] ..
+// row0[m+1] - 1 of a flat row space and cols[m] columns; its matrix starts at element moff[m].
 struct BatchedRows {
   int prec = DD_PREC_FP64;
   int64_t nrows = 0;
   int count = 0;
   int max_cols = 0;
   int max_rows = 0;
-  const int* item_of_row = nullptr;
   const int64_t* row0 = nullptr;
   const int* cols = nullptr;
   const int64_t* moff = nullptr;

@@ -1,0 +1,350 @@
+// Ensemble solves: BW (= 32) independent right-hand-side sequences that share the
+// matrix, the BDDC preconditioner and one recycled deflation basis W, advanced as
+// one block. Every operator application streams the operator data once for all
+// members; each member runs its own deflated PCG (own alpha, beta and stopping test,
+// decided on the device), and a member that has converged keeps its iterate
+// (alpha = 0) while the others continue. The basis W is shared: it is built from the
+// search vectors of member 0 (V = [W, P of member 0]) with the single-sequence
+// recycling update (Sect. 4.2), and every member is deflated by it (Algorithm 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <string>
+
+#include "batch.h"
+#include "context.h"
+
+namespace dd {
+
+void free_batch_work(BatchWork* bw) {
+  if (!bw) return;
+  if (bw->sc_host) cudaFreeHost(bw->sc_host);
+  delete bw;
+}
+
+namespace {
+
+BatchWork& batch_work(dd_ctx* c) {
+  if (c->bw) return *c->bw;
+  auto B = std::make_unique<BatchWork>();
+  DeviceArena& A = B->arena;
+  const DevMesh& m = c->mesh;
+  const int64_t n = c->n_gamma;
+  auto dvec = [&](int64_t rows) { return A.alloc<double>((size_t)std::max<int64_t>(rows, 1) * BW); };
+  auto tvec = [&](int prec, int64_t rows) -> void* {
+    return prec == DD_PREC_FP32 ? (void*)A.alloc<float>((size_t)std::max<int64_t>(rows, 1) * BW)
+                                : (void*)A.alloc<double>((size_t)std::max<int64_t>(rows, 1) * BW);
+  };
+  B->tI = dvec(m.n_int);
+  B->sI = dvec(m.n_int);
+  B->yloc = dvec(c->b1.n_flat);
+  const int pp = c->b1.prec;
+  B->rloc = tvec(pp, c->b1.n_flat);
+  B->uloc = tvec(pp, c->b1.n_flat);
+  B->vloc = tvec(pp, c->b1.n_flat);
+  B->gloc = tvec(pp, c->b1.n_cflat);
+  B->gC = tvec(pp, c->b1.n_coarse);
+  B->uC = tvec(pp, c->b1.n_coarse);
+  if (c->levels == 3) {
+    const DevLevel2& L = c->l2;
+    const int p2 = L.b.prec;
+    B->gI2 = tvec(p2, L.n_int);
+    B->u0I2 = tvec(p2, L.n_int);
+    B->uI2 = tvec(p2, L.n_int);
+    B->rl2 = tvec(p2, L.b.n_flat);
+    B->rloc2 = tvec(p2, L.b.n_flat);
+    B->uloc2 = tvec(p2, L.b.n_flat);
+    B->vloc2 = tvec(p2, L.b.n_flat);
+    B->r2 = tvec(p2, L.b.n_gamma);
+    B->z2 = tvec(p2, L.b.n_gamma);
+    B->gloc2 = tvec(p2, L.b.n_cflat);
+    B->g3 = tvec(p2, L.n3);
+    B->u3 = tvec(p2, L.n3);
+  }
+  B->xg = dvec(n);
+  B->r = dvec(n);
+  B->z = dvec(n);
+  B->zold = dvec(n);
+  B->p = dvec(n);
+  B->q = dvec(n);
+  B->bvec = dvec(n);
+  B->F = dvec(c->n_free);
+  B->X = dvec(c->n_free);
+  B->sc = A.alloc<double>((size_t)BS_COUNT * BW);
+  B->partials = A.alloc<double>((size_t)NBLK * 4 * BW);
+  B->wpart = A.alloc<double>((size_t)NBLK * MAXK * BW);
+  B->mu = A.alloc<double>((size_t)MAXK * BW);
+  DD_CUDA(cudaMallocHost(&B->sc_host, (size_t)BS_COUNT * BW * sizeof(double)));
+  c->bw = B.release();
+  return *c->bw;
+}
+
+// ---- operators on BW members ----
+void schur_b(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  launch_elem_interior_b(c->mesh, ELEM_SCHUR, x, nullptr, B.tI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_elem_interface_b(c->mesh, ELEM_SCHUR, x, B.sI, B.yloc, s);
+  launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, nullptr, nullptr, y, s);
+}
+
+void condense_b(dd_ctx* c, const double* f, double* b, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  launch_elem_interior_b(c->mesh, ELEM_CONDENSE, nullptr, f, B.tI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_elem_interface_b(c->mesh, ELEM_CONDENSE, nullptr, B.sI, B.yloc, s);
+  launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, f, c->mesh.gamma_free, b, s);
+}
+
+void recover_b(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  launch_elem_interior_b(c->mesh, ELEM_RECOVER, xg, f, B.tI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_scatter_recover_b(c->mesh, xg, B.sI, x, s);
+}
+
+template <class CoarseFn>
+void bddc_b(const DevBDDC& b, const double* r, double* z, void* rloc, void* uloc, void* vloc, void* gloc, void* gC,
+            void* uC, CoarseFn coarse, cudaStream_t s) {
+  launch_restrict_b(b.prec, b.n_flat, b.gmap, b.D, r, rloc, s);
+  launch_symm_b(b.N, b.goff, rloc, uloc, s);                                   // u_i = N_i r_i
+  launch_bmm(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);    // Phi_i^T r_i
+  launch_gather_tb(b.prec, b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
+  coarse(gC, uC);
+  launch_bmm_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);     // Phi_i R_Ci u_C
+  launch_wgather_b(b.prec, b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
+}
+
+// level-2 BDDC on the coarse system of the ensemble (same steps as the single path)
+void level2_b(dd_ctx* c, const void* g, void* u, cudaStream_t s) {
+  DevLevel2& L = c->l2;
+  BatchWork& B = *c->bw;
+  const int p2 = L.b.prec;
+  launch_map_gather_b(p2, L.n_int, L.imap, g, B.gI2, s);
+  launch_symm_b(L.KIIinv, L.ioff, B.gI2, B.u0I2, s);
+  launch_bmm_t(L.E, L.ioff, nullptr, B.gI2, L.b.goff, B.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
+  launch_gather_tb(p2, L.b.n_gamma, L.b.gptr, L.b.gidx, B.rl2, g, L.gam_c64, B.r2, s);
+  {
+    // level-2 interface BDDC on r2 (vectors in the preconditioner type), exact level 3
+    const DevBDDC& b = L.b;
+    launch_restrict_tb(p2, b.n_flat, b.gmap, b.D, B.r2, B.rloc2, s);
+    launch_symm_b(b.N, b.goff, B.rloc2, B.uloc2, s);
+    launch_bmm(b.PhiT, b.goff, nullptr, B.rloc2, b.coff, B.gloc2, 1.0, nullptr, s);
+    launch_gather_tb(p2, b.n_coarse, b.cptr, b.cidx, B.gloc2, nullptr, nullptr, B.g3, s);
+    launch_dense_mm(p2, L.n3, L.KC3inv, B.g3, B.u3, s);
+    launch_bmm_t(b.PhiT, b.coff, b.cmap, B.u3, b.goff, B.vloc2, 1.0, nullptr, s);
+    launch_wgather_tb(p2, b.n_gamma, b.gptr, b.gidx, b.D, B.uloc2, B.vloc2, B.z2, s);
+  }
+  launch_bmm(L.E, L.b.goff, L.b.gmap, B.z2, L.ioff, B.uI2, -1.0, B.u0I2, s);  // u0 - K_II^{-1} K_IG z
+  launch_map_scatter_b(p2, L.n_int, L.imap, B.uI2, u, s);
+  launch_map_scatter_b(p2, L.b.n_gamma, L.gam_c, B.z2, u, s);
+}
+
+void precond_b(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  bddc_b(c->b1, r, z, B.rloc, B.uloc, B.vloc, B.gloc, B.gC, B.uC,
+         [&](const void* g, void* u) {
+           if (c->levels == 2)
+             launch_dense_mm(c->b1.prec, c->b1.n_coarse, c->KCinv, g, u, s);
+           else
+             level2_b(c, g, u, s);
+         },
+         s);
+}
+
+void copy_b(double* dst, const double* src, int64_t rows, cudaStream_t s) {
+  DD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * BW * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+
+// deflated PCG (Algorithm 1) for every member; returns the worst member status
+dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int nrhs, dd_stats* stats,
+                      cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  const int64_t n = c->n_gamma;
+  const dd_options& o = c->opt;
+  const int k = st->k;
+  const double* W = k ? st->W : nullptr;
+  const double* AW = k ? st->AW : nullptr;
+  auto host_sc = [&]() {
+    DD_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, (size_t)BS_COUNT * BW * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+  };
+  auto hs = [&](int slot, int m) { return B.sc_host[slot * BW + m]; };
+  auto any_active = [&]() {
+    for (int m = 0; m < nrhs; ++m)
+      if (hs(BS_ACT, m) != 0.0) return true;
+    return false;
+  };
+  bvec_init(B.sc, nrhs, rtol, o.stop_rhs_norm, s);
+  if (k) {
+    // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})  (shared W, per-member mu)
+    schur_b(c, B.xg, B.q, s);
+    bvec_sub(n, B.bvec, B.q, B.r, s);
+    bdefl_mu(n, k, W, n, B.r, st->Ginv, B.wpart, B.mu, s);
+    bdefl_update(n, k, W, n, B.mu, nullptr, B.xg, B.sc, -1, 1.0, s);
+  }
+  schur_b(c, B.xg, B.q, s);
+  bvec_sub(n, B.bvec, B.q, B.r, s);
+  bvec_dots(n, B.bvec, B.bvec, B.r, B.r, B.partials, s);
+  bvec_finalize(B.partials, B.sc, BFIN_BB, 0, s);
+  host_sc();
+  std::vector<double> rel0(BW);
+  for (int m = 0; m < BW; ++m) rel0[m] = std::sqrt(hs(BS_RR0, m)) / hs(BS_REF, m);
+  if (st) st->alphas.clear();
+  dd_status status = DD_OK;
+  int its = 0;
+  bool rec0 = record && st->hmax > 0 && hs(BS_ACT, 0) != 0.0;  // member 0 feeds the recycling
+  if (any_active()) {
+    precond_b(c, B.r, B.z, s);
+    if (rec0) launch_extract_col(n, B.z, 0, st->Z, s);
+    bvec_dots(n, B.r, B.z, nullptr, nullptr, B.partials, s);
+    bvec_finalize(B.partials, B.sc, BFIN_RZ0, 0, s);
+    if (k) {
+      bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
+    } else {
+      copy_b(B.p, B.z, n, s);
+    }
+    while (true) {
+      schur_b(c, B.p, B.q, s);
+      bvec_dots(n, B.p, B.q, nullptr, nullptr, B.partials, s);
+      bvec_finalize(B.partials, B.sc, BFIN_PQ, 0, s);
+      const bool rec_now = rec0 && its < st->hmax;
+      if (rec_now) {
+        launch_extract_col(n, B.p, 0, st->P + (size_t)its * n, s);
+        launch_extract_col(n, B.q, 0, st->AP + (size_t)its * n, s);
+      }
+      bvec_axpy2(n, B.sc, B.xg, B.p, B.r, B.q, B.partials, s);
+      bvec_finalize(B.partials, B.sc, BFIN_RR, 0, s);
+      its++;
+      host_sc();
+      if (rec0) st->alphas.push_back(hs(BS_ALPHA, 0));
+      rec0 = rec0 && hs(BS_ACT, 0) != 0.0;
+      if (!any_active()) break;
+      if (its >= o.maxit) {
+        status = DD_NOT_CONVERGED;
+        break;
+      }
+      std::swap(B.z, B.zold);
+      precond_b(c, B.r, B.z, s);
+      if (rec0 && its <= st->hmax) launch_extract_col(n, B.z, 0, st->Z + (size_t)its * n, s);
+      bvec_dots(n, B.r, B.z, o.flexible ? B.r : nullptr, o.flexible ? B.zold : nullptr, B.partials, s);
+      bvec_finalize(B.partials, B.sc, BFIN_RZ, o.flexible, s);
+      if (k) bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
+    }
+  }
+  for (int m = 0; m < nrhs; ++m) {
+    if (hs(BS_FLAG, m) != 0.0) status = DD_BREAKDOWN;
+    if (stats) {
+      stats[m].iters = (int)hs(BS_ITS, m);
+      stats[m].rel_res0 = rel0[m];
+      stats[m].rel_res = std::sqrt(hs(BS_RR, m)) / hs(BS_REF, m);
+      stats[m].recycled_k = k;
+      stats[m].frozen = (int)st->frozen;
+    }
+  }
+  return status;
+}
+
+}  // namespace
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_recycle_create_batch(dd_ctx* c, int32_t k, int32_t strategy, double freeze_tol, dd_recycle** out) {
+  dd_status rc = dd_recycle_create(c, k, strategy, freeze_tol, out);
+  if (rc != DD_OK) return rc;
+  rc = guard_call([&] {
+    dd_recycle* st = *out;
+    st->nrhs = BW;
+    st->xg_prev_b = st->arena.alloc<double>((size_t)c->n_gamma * BW);
+    DD_CUDA(cudaMemset(st->xg_prev_b, 0, (size_t)c->n_gamma * BW * sizeof(double)));
+  });
+  if (rc != DD_OK) {
+    dd_recycle_destroy(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+// operator-level ensemble calls (interface vectors, member-major [nrhs][n_gamma])
+static dd_status batch_op(dd_ctx* c, int32_t nrhs, const double* X, double* Y, void* stream, bool precond,
+                          const char* what) {
+  if (!c || !X || !Y || nrhs < 1 || nrhs > BW) {
+    set_last_error(std::string(what) + ": invalid argument");
+    return DD_INVALID_ARG;
+  }
+  if (!precond && c->mesh.local_solver != DD_LOCAL_FDM && c->mesh.schur_prec == DD_PREC_DF64) {
+    set_last_error(std::string(what) + ": dense K_II^{-1} needs schur_prec FP64 for ensembles");
+    return DD_INVALID_ARG;
+  }
+  return guard_call([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchWork& B = batch_work(c);
+    launch_pack_in(c->n_gamma, nrhs, X, B.p, s);
+    if (precond)
+      precond_b(c, B.p, B.q, s);
+    else
+      schur_b(c, B.p, B.q, s);
+    launch_pack_out(c->n_gamma, nrhs, B.q, Y, s);
+    check_err(c, s);
+  });
+}
+
+dd_status dd_schur_apply_batch(dd_ctx* c, int32_t nrhs, const double* X, double* Y, void* stream) {
+  return batch_op(c, nrhs, X, Y, stream, false, "dd_schur_apply_batch");
+}
+
+dd_status dd_precond_apply_batch(dd_ctx* c, int32_t nrhs, const double* R, double* Z, void* stream) {
+  return batch_op(c, nrhs, R, Z, stream, true, "dd_precond_apply_batch");
+}
+
+dd_status dd_solve_batch(dd_ctx* c, int32_t nrhs, const double* F, double* X, double rtol, dd_recycle* st,
+                         dd_stats* stats, void* stream) {
+  if (!c || !F || !X || !st || st->ctx != c || st->nrhs != BW || nrhs < 1 || nrhs > BW || !(rtol > 0.0)) {
+    set_last_error("dd_solve_batch: invalid argument");
+    return DD_INVALID_ARG;
+  }
+  if (c->mesh.local_solver != DD_LOCAL_FDM && c->mesh.schur_prec == DD_PREC_DF64) {
+    set_last_error("dd_solve_batch: dense K_II^{-1} needs schur_prec FP64 for ensembles");
+    return DD_INVALID_ARG;
+  }
+  dd_status result = DD_OK;
+  dd_status gs = guard_call([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchWork& B = batch_work(c);
+    DD_CUDA(cudaEventRecord(c->ev0, s));
+    launch_pack_in(c->n_free, nrhs, F, B.F, s);
+    condense_b(c, B.F, B.bvec, s);
+    copy_b(B.xg, st->xg_prev_b, c->n_gamma, s);
+    const bool record = st->kmax > 0 && !st->frozen;
+    result = pcg_solve_b(c, st, rtol, record, nrhs, stats, s);
+    recover_b(c, B.F, B.xg, B.X, s);
+    copy_b(st->xg_prev_b, B.xg, c->n_gamma, s);
+    if (record && (result == DD_OK || result == DD_NOT_CONVERGED))
+      recycle_update(c, st, (int)st->alphas.size(), s);
+    else
+      st->step++;
+    launch_pack_out(c->n_free, nrhs, B.X, X, s);
+    DD_CUDA(cudaEventRecord(c->ev1, s));
+    check_err(c, s);
+    if (stats) {
+      float ms = 0.f;
+      DD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      for (int m = 0; m < nrhs; ++m) {
+        stats[m].ms = ms;
+        stats[m].frozen = (int)st->frozen;
+      }
+    }
+  });
+  if (gs != DD_OK) return gs;
+  if (result != DD_OK) set_last_error(result == DD_NOT_CONVERGED ? "maxit reached" : "PCG breakdown");
+  return result;
+}
+
+}  // extern "C"

@@ -18,138 +18,10 @@
 #include <climits>
 
 #include "device.h"
+#include "policy.cuh"
+#include "ptx.cuh"
 
 namespace dd {
-
-// ---------------------------------------------------------------------------
-// arithmetic policies
-// ---------------------------------------------------------------------------
-struct PolF64 {
-  using V = double;
-  using Acc = double;
-  __device__ static V from_d(double d) { return d; }
-  __device__ static double to_d(V v) { return v; }
-  __device__ static V zero() { return 0.0; }
-  __device__ static V neg(V v) { return -v; }
-  __device__ static void init(Acc& a) { a = 0.0; }
-  __device__ static void fma(Acc& a, V k, V x) { a = ::fma(k, x, a); }
-  __device__ static V get(const Acc& a) { return a; }
-  __device__ static V add(V a, V b) { return a + b; }
-  // element entry for corner pair differing on axes d (bit0 x, bit1 y, bit2 z)
-  __device__ static V entry(const V* c, int d) {
-    double sx = (d & 1) ? -1.0 : 1.0, mx = (d & 1) ? 1.0 : 2.0;
-    double sy = (d & 2) ? -1.0 : 1.0, my = (d & 2) ? 1.0 : 2.0;
-    double sz = (d & 4) ? -1.0 : 1.0, mz = (d & 4) ? 1.0 : 2.0;
-    return c[0] * (sx * my * mz) + c[1] * (mx * sy * mz) + c[2] * (mx * my * sz);
-  }
-};
-
-struct PolDF {
-  using V = df64;
-  using Acc = df64_acc;
-  __device__ static V from_d(double d) { return df64_from_double(d); }
-  __device__ static double to_d(V v) { return df64_to_double(v); }
-  __device__ static V zero() { return {0.f, 0.f}; }
-  __device__ static V neg(V v) { return df64_neg(v); }
-  __device__ static void init(Acc& a) { a = df64_acc(); }
-  __device__ static void fma(Acc& a, V k, V x) { a.fma(k, x); }
-  __device__ static V get(const Acc& a) { return a.get(); }
-  __device__ static V add(V a, V b) { return df64_add(a, b); }
-  __device__ static V entry(const V* c, int d) {
-    // the scalings are +-1, +-2, +-4: exact on both halves
-    float sx = (d & 1) ? -1.f : 1.f, mx = (d & 1) ? 1.f : 2.f;
-    float sy = (d & 2) ? -1.f : 1.f, my = (d & 2) ? 1.f : 2.f;
-    float sz = (d & 4) ? -1.f : 1.f, mz = (d & 4) ? 1.f : 2.f;
-    V a = df64_scale_pow2(c[0], sx * my * mz);
-    V b = df64_scale_pow2(c[1], mx * sy * mz);
-    V e = df64_scale_pow2(c[2], mx * my * sz);
-    return df64_add(df64_add(a, b), e);
-  }
-};
-
-struct PolF32 {
-  using V = float;
-  using Acc = float;
-  __device__ static V from_d(double d) { return (float)d; }
-  __device__ static double to_d(V v) { return (double)v; }
-  __device__ static V zero() { return 0.f; }
-  __device__ static void init(Acc& a) { a = 0.f; }
-  __device__ static void fma(Acc& a, V k, V x) { a = fmaf(k, x, a); }
-  __device__ static V get(const Acc& a) { return a; }
-  __device__ static V add(V a, V b) { return a + b; }
-};
-
-template <class P>
-__device__ __forceinline__ void load_factors(const DevMesh& m, int64_t e, typename P::V* c);
-template <>
-__device__ __forceinline__ void load_factors<PolF64>(const DevMesh& m, int64_t e, double* c) {
-  c[0] = m.ec[3 * e]; c[1] = m.ec[3 * e + 1]; c[2] = m.ec[3 * e + 2];
-}
-template <>
-__device__ __forceinline__ void load_factors<PolDF>(const DevMesh& m, int64_t e, df64* c) {
-  c[0] = m.ec_df[3 * e]; c[1] = m.ec_df[3 * e + 1]; c[2] = m.ec_df[3 * e + 2];
-}
-
-__device__ __forceinline__ int64_t free_index(const DevMesh& m, int s, int l) {
-  int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
-  int a = l % m.NLx, b = (l / m.NLx) % m.NLy, c = l / (m.NLx * m.NLy);
-  int64_t x = I * m.sx + a - m.fx0, y = J * m.sy + b - m.fy0, z = K * m.sz + c - m.fz0;
-  int64_t Nfx = m.fx1 - m.fx0, Nfy = m.fy1 - m.fy0;
-  return x + Nfx * (y + Nfy * z);
-}
-
-// ---------------------------------------------------------------------------
-// Element passes driven by per-subdomain-type work lists. Subdomains with the same
-// pattern of interior / interface / absent nodes share lists built on the host:
-//   * the boundary-layer elements (those with an interface corner): only they contribute
-//     when the input vanishes in the interior (first pass) or the output is taken on the
-//     interface (second pass);
-//   * output items: node l and up to 8 slots (element * 8 + corner of l in it), sorted by
-//     slot count so that the lanes of a warp do the same amount of work.
-// S is the subdomain edge in elements (0: taken from the mesh at run time).
-// ---------------------------------------------------------------------------
-template <class P, int S>
-__device__ __forceinline__ void build_kd_list(const DevMesh& m, int s, const int16_t* bll, int nbl,
-                                              typename P::V* kd) {
-  const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
-  const int NE = sx * sy * sz;
-  const int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
-  for (int t = threadIdx.x; t < nbl; t += blockDim.x) {
-    const int el = bll[t];
-    const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
-    const int64_t e = (int64_t)(I * sx + ea) + (int64_t)m.nx * ((J * sy + eb) + (int64_t)m.ny * (K * sz + ec));
-    typename P::V c[3];
-    load_factors<P>(m, e, c);
-#pragma unroll
-    for (int d = 0; d < 8; ++d) kd[d * NE + el] = P::entry(c, d);
-  }
-}
-
-template <class P, int S>
-__device__ __forceinline__ typename P::V apply_item(const DevMesh& m, const int16_t* it, const typename P::V* xl,
-                                                    const typename P::V* kd) {
-  const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
-  const int NE = sx * sy * sz;
-  const int NLx = sx + 1, NLy = sy + 1;
-  typename P::Acc acc[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) P::init(acc[t]);
-#pragma unroll 1
-  for (int k = 0; k < 8; ++k) {
-    const int v = it[1 + k];
-    if (v < 0) break;
-    const int el = v >> 3, p = v & 7;
-    const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
-    const int base = ea + NLx * (eb + NLy * ec);
-    const typename P::V* kp = kd + el;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int lq = base + (q & 1) + NLx * (((q >> 1) & 1) + NLy * (q >> 2));
-      P::fma(acc[q & 3], kp[(p ^ q) * NE], xl[lq]);
-    }
-  }
-  return P::add(P::add(P::get(acc[0]), P::get(acc[1])), P::add(P::get(acc[2]), P::get(acc[3])));
-}
 
 // t_I = f_I - ck * (K [0; x_G])_I   (SCHUR: t = (K x)_I; CONDENSE: t = f_I; RECOVER: t = f_I - (K x)_I)
 template <class P, int S>
@@ -255,48 +127,6 @@ void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const d
   else
     elem_interface_dispatch<PolF64>(m, mode, xg, sI, yloc, smem, s);
   DD_CHECK_LAUNCH();
-}
-
-// ---------------------------------------------------------------------------
-// TMA bulk copies and mbarriers (PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-constexpr long long WAIT_LIMIT = 1ll << 24;  // try_wait attempts before giving up (seconds)
-
-// bounded wait on an mbarrier phase; returns false (and raises *err) on timeout
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicExch(err, (int)DD_TIMEOUT);
-  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -558,17 +388,6 @@ void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, doubl
 // six contractions along one axis each in shared memory (about 14k multiply-adds per
 // 8^3 subdomain instead of a 343^2 matrix).
 // ---------------------------------------------------------------------------
-template <class P>
-__device__ __forceinline__ typename P::V ld_fdm(const void* base, int64_t i);
-template <>
-__device__ __forceinline__ double ld_fdm<PolF64>(const void* base, int64_t i) {
-  return static_cast<const double*>(base)[i];
-}
-template <>
-__device__ __forceinline__ df64 ld_fdm<PolDF>(const void* base, int64_t i) {
-  return static_cast<const df64*>(base)[i];
-}
-
 // out[..j..] = sum_i A(i, j) in[..i..] (transposed) or sum_i A(j, i) in[..i..] along axis `ax`
 template <class P>
 __device__ __forceinline__ void fdm_contract(const typename P::V* A, int ax, bool trans, const int* n,
@@ -740,119 +559,123 @@ void launch_restrict(int64_t nflat, const int* gmap, const double* D, const doub
   DD_CHECK_LAUNCH();
 }
 
-// Batched row-major GEMV over a flat row space: row r of the batch belongs to item
-// item_of_row[r] (local row r - row0[item]); out[out_off[m] + i] = alpha * sum_j M_m[i][j] * x_j
-// (+ add[out_off[m] + i]), x_j = in[in_map ? in_map[in_off[m] + j] : in_off[m] + j].
-// Wide rows: a warp per row with lanes along the row (coalesced); narrow rows: a thread per row.
-template <class T, bool WIDE>
-__global__ void __launch_bounds__(256) k_bgemv(int64_t nrows, const int* __restrict__ item_of_row,
-                                               const int64_t* __restrict__ row0, const int* __restrict__ cols,
+// x_j of item m is in[in_map ? in_map[in_off[m] + j] : in_off[m] + j]; the outputs of item m
+// start at out_off[m].
+// Batched GEMVs over row-major matrices A_m (R_m x C_m). The input slice of item m is
+// staged once per block in shared memory, converted to the matrix type T, so FP32
+// operators also do FP32 arithmetic (the BDDC preconditioner in FP32 mode).
+//   k_bgemv:   y_m = alpha A_m x_m (+ add), warp per row, lanes along the row (coalesced)
+//   k_bgemv_t: y_m = alpha A_m^T x_m (+ add), thread per column, rows streamed in order
+constexpr int BGEMV_ROWS = 32;    // rows per block of k_bgemv (8 warps x 4 rows)
+constexpr int BGEMV_T_COLS = 128; // columns per block of k_bgemv_t
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bgemv(const int64_t* __restrict__ row0, const int* __restrict__ cols,
                                                const int64_t* __restrict__ moff, const T* __restrict__ M,
                                                const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
                                                const double* __restrict__ in, const int64_t* __restrict__ out_off,
                                                double* __restrict__ out, double alpha,
                                                const double* __restrict__ add) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = WIDE ? ((int64_t)gridDim.x * blockDim.x) >> 5 : (int64_t)gridDim.x * blockDim.x;
-  int64_t r = WIDE ? (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5 : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; r < nrows; r += stride) {
-    const int m = item_of_row[r];
-    const int i = (int)(r - row0[m]);
-    const int C = cols[m];
+  extern __shared__ __align__(16) unsigned char bg_smem[];
+  T* xs = reinterpret_cast<T*>(bg_smem);
+  const int m = blockIdx.x;
+  const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
+  const int r0 = blockIdx.y * BGEMV_ROWS;
+  if (r0 >= R) return;
+  const int64_t io = in_off[m];
+  for (int j = threadIdx.x; j < C; j += blockDim.x) xs[j] = (T)in[in_map ? in_map[io + j] : io + j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r1 = min(R, r0 + BGEMV_ROWS);
+  const int64_t oo = out_off[m];
+  for (int i = r0 + warp; i < r1; i += blockDim.x >> 5) {
     const T* a = M + moff[m] + (int64_t)i * C;
-    const int64_t io = in_off[m];
-    double acc = 0.0;
-    if (WIDE) {
-      for (int j = lane; j < C; j += 32) acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane != 0) continue;
-    } else {
-      double a2 = 0.0;
-      int j = 0;
-      for (; j + 1 < C; j += 2) {
-        acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
-        a2 = fma((double)a[j + 1], in[in_map ? in_map[io + j + 1] : io + j + 1], a2);
-      }
-      if (j < C) acc = fma((double)a[j], in[in_map ? in_map[io + j] : io + j], acc);
-      acc += a2;
+    T acc0 = 0, acc1 = 0;
+    int j = lane;
+    for (; j + 32 < C; j += 64) {
+      acc0 = fma(a[j], xs[j], acc0);
+      acc1 = fma(a[j + 32], xs[j + 32], acc1);
     }
-    const int64_t oi = out_off[m] + i;
-    out[oi] = alpha * acc + (add ? add[oi] : 0.0);
+    if (j < C) acc0 = fma(a[j], xs[j], acc0);
+    T acc = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[oo + i] = alpha * (double)acc + (add ? add[oo + i] : 0.0);
   }
+}
+
+template <class T>
+static void bgemv_go(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                     const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
+  size_t smem = (size_t)std::max(B.max_cols, 1) * sizeof(T);
+  if (smem > 48 * 1024) DD_CUDA(cudaFuncSetAttribute(k_bgemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(B.count, (B.max_rows + BGEMV_ROWS - 1) / BGEMV_ROWS);
+  k_bgemv<T><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off, in_map, in,
+                                      out_off, out, alpha, add);
 }
 
 void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                   const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
   if (B.nrows == 0) return;
-  const bool wide = B.max_cols >= 64;
-  int64_t threads = wide ? B.nrows * 32 : B.nrows;
-  int grid = (int)std::min<int64_t>((threads + 255) / 256, 152 * 16);
-  if (grid < 1) grid = 1;
-  if (B.prec == DD_PREC_FP32) {
-    const float* M = static_cast<const float*>(B.data);
-    if (wide)
-      k_bgemv<float, true><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map, in,
-                                                out_off, out, alpha, add);
-    else
-      k_bgemv<float, false><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
-                                                 in, out_off, out, alpha, add);
-  } else {
-    const double* M = static_cast<const double*>(B.data);
-    if (wide)
-      k_bgemv<double, true><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
-                                                 in, out_off, out, alpha, add);
-    else
-      k_bgemv<double, false><<<grid, 256, 0, s>>>(B.nrows, B.item_of_row, B.row0, B.cols, B.moff, M, in_off, in_map,
-                                                  in, out_off, out, alpha, add);
-  }
+  if (B.prec == DD_PREC_FP32)
+    bgemv_go<float>(B, in_off, in_map, in, out_off, out, alpha, add, s);
+  else
+    bgemv_go<double>(B, in_off, in_map, in, out_off, out, alpha, add, s);
   DD_CHECK_LAUNCH();
 }
 
-// Batched transposed GEMV: one block per item, x staged in shared memory, thread per output
-// column j reading row i of M at consecutive addresses across the block (coalesced).
 template <class T>
-__global__ void __launch_bounds__(256) k_bgemv_t(const int64_t* __restrict__ row0, const int* __restrict__ cols,
-                                                 const int64_t* __restrict__ moff, const T* __restrict__ M,
-                                                 const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
-                                                 const double* __restrict__ in, const int64_t* __restrict__ out_off,
-                                                 double* __restrict__ out, double alpha,
-                                                 const double* __restrict__ add) {
-  extern __shared__ double xs[];
+__global__ void __launch_bounds__(BGEMV_T_COLS) k_bgemv_t(const int64_t* __restrict__ row0,
+                                                          const int* __restrict__ cols,
+                                                          const int64_t* __restrict__ moff, const T* __restrict__ M,
+                                                          const int64_t* __restrict__ in_off,
+                                                          const int* __restrict__ in_map,
+                                                          const double* __restrict__ in,
+                                                          const int64_t* __restrict__ out_off,
+                                                          double* __restrict__ out, double alpha,
+                                                          const double* __restrict__ add) {
+  extern __shared__ __align__(16) unsigned char bg_smem[];
+  T* xs = reinterpret_cast<T*>(bg_smem);
   const int m = blockIdx.x;
   const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
+  const int j = blockIdx.y * BGEMV_T_COLS + threadIdx.x;
+  if (blockIdx.y * BGEMV_T_COLS >= C) return;
   const int64_t io = in_off[m];
-  for (int i = threadIdx.x; i < R; i += blockDim.x) xs[i] = in[in_map ? in_map[io + i] : io + i];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) xs[i] = (T)in[in_map ? in_map[io + i] : io + i];
   __syncthreads();
-  const T* A = M + moff[m];
-  const int64_t oo = out_off[m];
-  for (int j = threadIdx.x; j < C; j += blockDim.x) {
-    double a0 = 0.0, a1 = 0.0;
-    int i = 0;
-    for (; i + 1 < R; i += 2) {
-      a0 = fma((double)A[(int64_t)i * C + j], xs[i], a0);
-      a1 = fma((double)A[(int64_t)(i + 1) * C + j], xs[i + 1], a1);
-    }
-    if (i < R) a0 = fma((double)A[(int64_t)i * C + j], xs[i], a0);
-    out[oo + j] = alpha * (a0 + a1) + (add ? add[oo + j] : 0.0);
+  if (j >= C) return;
+  const T* A = M + moff[m] + j;
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int i = 0;
+  for (; i + 3 < R; i += 4) {
+    a0 = fma(A[(int64_t)i * C], xs[i], a0);
+    a1 = fma(A[(int64_t)(i + 1) * C], xs[i + 1], a1);
+    a2 = fma(A[(int64_t)(i + 2) * C], xs[i + 2], a2);
+    a3 = fma(A[(int64_t)(i + 3) * C], xs[i + 3], a3);
   }
+  for (; i < R; ++i) a0 = fma(A[(int64_t)i * C], xs[i], a0);
+  const int64_t oo = out_off[m];
+  out[oo + j] = alpha * (double)((a0 + a1) + (a2 + a3)) + (add ? add[oo + j] : 0.0);
+}
+
+template <class T>
+static void bgemv_t_go(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                       const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
+  size_t smem = (size_t)std::max(B.max_rows, 1) * sizeof(T);
+  if (smem > 48 * 1024)
+    DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(B.count, (B.max_cols + BGEMV_T_COLS - 1) / BGEMV_T_COLS);
+  k_bgemv_t<T><<<grid, BGEMV_T_COLS, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off,
+                                                 in_map, in, out_off, out, alpha, add);
 }
 
 void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                     const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
   if (B.count == 0) return;
-  size_t smem = (size_t)std::max(B.max_rows, 1) * sizeof(double);
-  int threads = B.max_cols >= 256 ? 256 : 128;
-  if (B.prec == DD_PREC_FP32) {
-    if (smem > 48 * 1024)
-      DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bgemv_t<float><<<B.count, threads, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const float*>(B.data), in_off,
-                                                    in_map, in, out_off, out, alpha, add);
-  } else {
-    if (smem > 48 * 1024)
-      DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bgemv_t<double><<<B.count, threads, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const double*>(B.data),
-                                                     in_off, in_map, in, out_off, out, alpha, add);
-  }
+  if (B.prec == DD_PREC_FP32)
+    bgemv_t_go<float>(B, in_off, in_map, in, out_off, out, alpha, add, s);
+  else
+    bgemv_t_go<double>(B, in_off, in_map, in, out_off, out, alpha, add, s);
   DD_CHECK_LAUNCH();
 }
 

@@ -18,6 +18,7 @@
 #include "hostla.h"
 #include "setup.h"
 #include "vecops.h"
+#include "context.h"
 
 using namespace dd;
 
@@ -27,123 +28,10 @@ namespace dd {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace dd
 
-struct dd_ctx {
-  dd_options opt{};
-  dd_info_t info{};
-  DeviceArena arena;
-  std::vector<int64_t> gamma_free_host;
-  int64_t n_free = 0, n_gamma = 0;
-  int levels = 2;
-  DevMesh mesh{};
-  DevBDDC b1{};
-  DevLevel2 l2{};
-  const void* KCinv = nullptr;
-  Work w{};
-  // Krylov buffers
-  double *xg = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr;
-  double* tmp = nullptr;
-  double* sc = nullptr;        // device scalars [SC_COUNT]
-  double* sc_host = nullptr;   // pinned mirror
-  double* partials = nullptr;  // [NBLK*MAXDOT]
-  double* wpart = nullptr;     // [NBLK*MAXK]
-  double* mu = nullptr;        // [MAXK]
-  double* gram_part = nullptr; // [NBLK*4096]
-  double* gram_out = nullptr;  // [4096]
-  double* ybuf = nullptr;      // [128*128] combination coefficients
-  const double** ptrs = nullptr;  // device pointer table for gram / lincomb
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  // profiling: events around timed launches, harvested after a synchronization
-  bool prof_on = false;
-  struct Pending {
-    int cls;
-    cudaEvent_t a, b;
-  };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> pool;
-  double prof_ms[DD_PROF_COUNT] = {0};
-  int64_t prof_n[DD_PROF_COUNT] = {0};
-  double prof_bytes[DD_PROF_COUNT] = {0};
-  cudaEvent_t get_event() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    DD_CUDA(cudaEventCreate(&e));
-    return e;
-  }
-  void harvest() {  // caller has synchronized the stream
-    for (auto& p : pending) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-        prof_ms[p.cls] += ms;
-        prof_n[p.cls] += 1;
-      }
-      pool.push_back(p.a);
-      pool.push_back(p.b);
-    }
-    pending.clear();
-  }
-  ~dd_ctx() {
-    if (sc_host) cudaFreeHost(sc_host);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (auto& p : pending) {
-      cudaEventDestroy(p.a);
-      cudaEventDestroy(p.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
-
-namespace {
-// times the launches issued on `s` during its lifetime when profiling is on
-struct ProfScope {
-  dd_ctx* c;
-  int cls;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(dd_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
-    if (c->prof_on && cls >= 0 && cls < DD_PROF_COUNT) {
-      a = c->get_event();
-      b = c->get_event();
-      DD_CUDA(cudaEventRecord(a, s));
-    }
-  }
-  ~ProfScope() {
-    if (a) {
-      cudaEventRecord(b, s);
-      c->pending.push_back({cls, a, b});
-    }
-  }
-};
-}  // namespace
-
-struct dd_recycle {
-  dd_ctx* ctx = nullptr;
-  int kmax = 0, strategy = DD_B4;
-  double freeze_tol = 1e-5;
-  int k = 0;
-  bool frozen = false;
-  int step = 0;
-  DeviceArena arena;
-  double *W = nullptr, *AW = nullptr, *MAW = nullptr;       // [kmax][n_gamma]
-  double *W2 = nullptr, *AW2 = nullptr, *MAW2 = nullptr;    // next basis
-  double* Ginv = nullptr;                                   // [kmax*kmax] (W^T A W)^{-1}
-  double* WWinv = nullptr;                                  // [kmax*kmax] (W^T W)^{-1}
-  std::vector<double> theta;
-  double* xg_prev = nullptr;                                // [n_gamma]
-  bool have_prev = false;
-  int hmax = 0;
-  double *P = nullptr, *AP = nullptr, *Z = nullptr, *MAP = nullptr;  // histories [hmax][n_gamma]
-  std::vector<double> alphas;
-};
-
 // ---------------------------------------------------------------------------
 // uploads
 // ---------------------------------------------------------------------------
-namespace {
+namespace dd {
 
 SymTiles upload_sym(DeviceArena& A, const std::vector<const double*>& mats, const std::vector<int>& dims, int prec,
                     cudaStream_t s) {
@@ -214,9 +102,6 @@ BatchedRows upload_rows(DeviceArena& A, const std::vector<const double*>& mats, 
   }
   B.nrows = row0[cnt];
   B.count = (int)cnt;
-  std::vector<int> item((size_t)B.nrows);
-  for (size_t m = 0; m < cnt; ++m)
-    for (int64_t r = row0[m]; r < row0[m + 1]; ++r) item[r] = (int)m;
   std::vector<double> buf(tot);
   for (size_t m = 0; m < cnt; ++m) {
     int R0 = rows[m], C0 = cols[m];
@@ -239,7 +124,6 @@ BatchedRows upload_rows(DeviceArena& A, const std::vector<const double*>& mats, 
     DD_CUDA(cudaMemcpy(d, buf.data(), buf.size() * 8, cudaMemcpyHostToDevice));
     B.data = d;
   }
-  B.item_of_row = A.upload(item, s);
   B.row0 = A.upload(row0, s);
   B.cols = A.upload(ncol, s);
   B.moff = A.upload(moff, s);
@@ -472,7 +356,7 @@ WorkLists build_work_lists(const Mesh1& M) {
   return W;
 }
 
-}  // namespace
+}  // namespace dd
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -800,7 +684,7 @@ void dd_recycle_destroy(dd_recycle* st) { delete st; }
 // ---------------------------------------------------------------------------
 // deflated PCG (Algorithm 1) and the recycling update
 // ---------------------------------------------------------------------------
-namespace {
+namespace dd {
 
 void set_ptrs(dd_ctx* c, const std::vector<const double*>& v, int at, cudaStream_t s) {
   DD_CUDA(cudaMemcpyAsync(c->ptrs + at, v.data(), v.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
@@ -1092,7 +976,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   return status;
 }
 
-}  // namespace
+}  // namespace dd
 
 extern "C" {
 
