@@ -268,6 +268,134 @@ def rank_seed(wl, rank: int) -> int:
     return wl["seed"] + 1000 * rank
 
 
+ENS_METRIC = "member solves/s to rtol 1e-8, 32 graded-mesh sequences as one block (ensemble path); %HBM peak"
+
+
+def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, seed, rtol):
+    """Ensemble workload: R sequences (seeds seed .. seed+R-1) advanced as one block by
+    dd_solve_batch with one shared recycled basis; the single-sequence path solves some of
+    the same sequences one at a time on the same GPU for the batching ratio."""
+    R = wl["nrhs"]
+    k = wl["k"]
+    nsteps = args.warmup + args.steps
+    t0 = time.perf_counter()
+    seqs = [load_sequence(mesh, seed + j, nsteps) for j in range(R)]
+    F_host = torch.from_numpy(np.ascontiguousarray(np.stack(seqs, axis=1)))  # [steps][R][n]
+    del seqs
+    t_rhs = time.perf_counter() - t0
+    F_dev = F_host.to(dev)
+    t0 = time.perf_counter()
+    S = pkg.Solver(mesh, **solver_options(wl, True))
+    setup_s = time.perf_counter() - t0
+    hbm, peak_kind = peaks()
+    rec = S.ensemble_recycler(k, "B4")
+    X = torch.empty_like(F_dev[0])
+    for t in range(args.warmup):
+        S.solve_batch(F_dev[t], rec, rtol, out=X)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    S.profile(True, read=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for t in range(args.warmup, nsteps):
+            _, st = S.solve_batch(F_dev[t], rec, rtol, out=X)
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    sec = max_over_ranks(torch, e0.elapsed_time(e1) / 1e3, dist, dev)
+    prof, launches = S.profile(False, read=True)
+    value = args.steps * R * world / sec
+    its = [m["iters"] for st in stats for m in st]
+    rec.close()
+
+    # single-sequence path on the same GPU: the first few members, each with its own state
+    n_single = min(4, R)
+    tot = 0.0
+    for j in range(n_single):
+        r1 = S.recycler(k, "B4")
+        x1 = torch.empty_like(F_dev[0, 0])
+        for t in range(args.warmup):
+            S.solve(F_dev[t, j].contiguous(), r1, rtol, out=x1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fs = [F_dev[t, j].contiguous() for t in range(args.warmup, nsteps)]
+        a.record(stream)
+        for f in fs:
+            S.solve(f, r1, rtol, out=x1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+        r1.close()
+    single = {"value": n_single * args.steps / tot, "unit": "solves/s", "members_timed": n_single,
+              "options": "same solver and options, dd_solve per sequence with its own recycle state"}
+
+    e2e = None
+    if not args.no_e2e:
+        Fp = F_host.pin_memory()
+        rec2 = S.ensemble_recycler(k, "B4")
+        f_dev = torch.empty_like(F_dev[0])
+        x_host = torch.empty_like(Fp[0]).pin_memory()
+        for t in range(args.warmup):
+            f_dev.copy_(Fp[t], non_blocking=True)
+            S.solve_batch(f_dev, rec2, rtol, out=X)
+            x_host.copy_(X, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for t in range(args.warmup, nsteps):
+            f_dev.copy_(Fp[t], non_blocking=True)
+            S.solve_batch(f_dev, rec2, rtol, out=X)
+            x_host.copy_(X, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        esec = max_over_ranks(torch, a.elapsed_time(b) / 1e3, dist, dev)
+        nb = int(F_host[0].numel()) * 8
+        e2e = {"value": args.steps * R * world / esec, "unit": "solves/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+        rec2.close()
+
+    nn = prof["ens_N"]
+    nn_ms = nn[0] / max(nn[1], 1)
+    achieved = nn[2] / (nn_ms / 1e3) / 1e9 if nn[1] else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "kernel": "k_symm_b<float> (ensemble constrained-Neumann products N_i R_i, eq. localCorr)",
+            "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
+            "avg_launch_ms": nn_ms, "launches": nn[1]}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, wl)
+    if rank == 0:
+        per_kernel = {name: {"ms_total": v[0], "launches": v[1], "avg_ms": (v[0] / v[1]) if v[1] else None}
+                      for name, v in prof.items()}
+        line = {"metric": ENS_METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64 (df64 Schur, f32 BDDC)", "data": "synthetic",
+                "config": {"workload": args.workload, "n": wl["n"], "subdomains": (wl["n"] // wl["sub"]) ** 3,
+                           "members": R, "levels": wl["levels"], "k": k, "strategy": "B4 (shared W from member 0)",
+                           "rtol": rtol, "n_free": S.n_free, "n_gamma": S.n_gamma,
+                           "l2": "members' vectors and operators exceed L2 (inputs larger than L2)",
+                           "rhs_seeds": [seed, seed + R - 1]},
+                "iters_min_max_avg": [min(its), max(its), sum(its) / len(its)],
+                "setup_s": setup_s, "rhs_gen_s": t_rhs, "single_sequence": single,
+                "ens_nmm": {"kernel": {1: "simt", 2: "tcgen05 3xTF32"}.get(S.info["ens_nmm"], "none"),
+                            "tuning_ms": S.info["ens_nmm_ms"]},
+                "batching_speedup": value / single["value"],
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": launches, "kernels": per_kernel}
+        print(json.dumps(line), flush=True)
+    S.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +407,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="elements per axis of a smaller member of the workload's mesh family (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world, rank, local = dist_env()
@@ -297,8 +427,12 @@ def main():
     dev = torch.device("cuda", local)
     rtol = args.rtol if args.rtol is not None else wl["rtol"]
     k = wl["k"]
-    mesh = workload_mesh(args.workload)
+    mesh = workload_mesh(args.workload, n=args.n)
+    if args.n is not None:
+        wl = dict(wl, n=args.n)
     seed = rank_seed(wl, rank)
+    if wl.get("nrhs"):
+        return ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, seed, rtol)
     nsteps = args.warmup + args.steps
     t0 = time.perf_counter()
     F_host = torch.from_numpy(load_sequence(mesh, seed, nsteps))

@@ -72,6 +72,7 @@ enum { DD_WEIGHTS_CARD = 0, DD_WEIGHTS_DIAG = 1 };                 /* Sect. 3.2 
 enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_DF64 = 2 };     /* arithmetic of an operator */
 enum { DD_B1 = 1, DD_B2 = 2, DD_B3 = 3, DD_B4 = 4 };                /* Sect. 4.2 recycling strategies */
 enum { DD_LOCAL_AUTO = 0, DD_LOCAL_DENSE = 1, DD_LOCAL_FDM = 2 };   /* K_II^{-1} representation */
+enum { DD_ENS_AUTO = 0, DD_ENS_SIMT = 1, DD_ENS_TC = 2 };            /* ensemble N_i products */
 
 typedef struct {
   int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
@@ -90,6 +91,9 @@ typedef struct {
   int32_t maxit;            /* iteration limit per solve */
   int32_t local_solver;     /* K_II^{-1} representation: DD_LOCAL_AUTO (fast diagonalization when every
                                subdomain has a constant coefficient, else dense), DD_LOCAL_DENSE, DD_LOCAL_FDM */
+  int32_t ens_nmm;          /* ensemble products N_i R_i of an FP32 preconditioner: DD_ENS_AUTO (both
+                               kernels timed on the first ensemble call, the faster kept), DD_ENS_SIMT
+                               (CUDA-core tiles), DD_ENS_TC (tensor cores, 3xTF32) */
 } dd_options;
 
 typedef struct {
@@ -103,6 +107,9 @@ typedef struct {
   int32_t local_solver;     /* DD_LOCAL_DENSE or DD_LOCAL_FDM: the representation in use */
   int64_t device_bytes;     /* device memory held by the context */
   double setup_seconds;     /* wall time of dd_setup */
+  int32_t ens_nmm;          /* ensemble N_i kernel in use: DD_ENS_SIMT or DD_ENS_TC (0 before the first
+                               ensemble call) */
+  float ens_nmm_ms[2];      /* its selection timings (SIMT, tensor cores; 0 when not timed), ms */
 } dd_info_t;
 
 typedef struct {
@@ -206,7 +213,10 @@ enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} application of the Schur ope
        DD_PROF_SCHUR = 2,      /* whole Schur-complement applications */
        DD_PROF_PRECOND = 3,    /* whole BDDC applications */
        DD_PROF_RECYCLE = 4,    /* recycling updates between solves (Sect. 4.2) */
-       DD_PROF_COUNT = 5 };
+       DD_PROF_ENS_SCHUR = 5,  /* ensemble Schur-complement applications (dd_solve_batch) */
+       DD_PROF_ENS_PRECOND = 6,/* ensemble BDDC applications */
+       DD_PROF_ENS_N = 7,      /* ensemble constrained-Neumann products N_i [r_i of every member] */
+       DD_PROF_COUNT = 8 };
 typedef struct {
   double ms;                /* summed device time of the timed launches/regions */
   int64_t launches;         /* number of timed launches/regions */

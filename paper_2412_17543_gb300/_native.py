@@ -14,6 +14,7 @@ WEIGHTS = {"card": 0, "diag": 1}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 STRATEGY = {"B1": 1, "B2": 2, "B3": 3, "B4": 4}
 LOCAL = {"auto": 0, "dense": 1, "fdm": 2}
+ENS_NMM = {"auto": 0, "simt": 1, "tc": 2}
 
 
 class MeshDesc(ctypes.Structure):
@@ -30,21 +31,23 @@ class Options(ctypes.Structure):
                 ("adaptive", ctypes.c_int32), ("tau", ctypes.c_double), ("max_eig_per_face", ctypes.c_int32),
                 ("weights", ctypes.c_int32), ("precond_prec", ctypes.c_int32), ("schur_prec", ctypes.c_int32),
                 ("flexible", ctypes.c_int32), ("reorth", ctypes.c_int32), ("stop_rhs_norm", ctypes.c_int32),
-                ("maxit", ctypes.c_int32), ("local_solver", ctypes.c_int32)]
+                ("maxit", ctypes.c_int32), ("local_solver", ctypes.c_int32),
+                ("ens_nmm", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n_free", ctypes.c_int64), ("n_gamma", ctypes.c_int64), ("n_sub", ctypes.c_int32),
                 ("n_coarse", ctypes.c_int32), ("n_adaptive", ctypes.c_int32), ("n_sub2", ctypes.c_int32),
                 ("n_coarse3", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("setup_seconds", ctypes.c_double)]
+                ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 2)]
 
 
 class KernelProf(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("alg_bytes", ctypes.c_double)]
 
 
-PROF_CLASSES = ["KIIinv_apply", "symv_N", "schur_apply", "precond_apply", "recycle_update"]
+PROF_CLASSES = ["KIIinv_apply", "symv_N", "schur_apply", "precond_apply", "recycle_update", "ens_schur_apply",
+                "ens_precond_apply", "ens_N"]
 
 
 class Stats(ctypes.Structure):

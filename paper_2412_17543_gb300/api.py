@@ -39,6 +39,8 @@ def make_options(**kw) -> nat.Options:
             v = nat.PREC[v]
         if k == "local_solver" and isinstance(v, str):
             v = nat.LOCAL[v]
+        if k == "ens_nmm" and isinstance(v, str):
+            v = nat.ENS_NMM[v]
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)
@@ -91,12 +93,19 @@ class Solver:
         nat.check(self.lib.dd_setup(ctypes.byref(d), ctypes.byref(self.options), _stream_ptr(), ctypes.byref(h)),
                   "dd_setup")
         self.handle = h
+        info = self.info
+        self.n_free = int(info["n_free"])
+        self.n_gamma = int(info["n_gamma"])
+        self.n_elem = int(mesh.nx) * int(mesh.ny) * int(mesh.nz)
+
+    @property
+    def info(self) -> dict:
+        """dd_get_info of the context (current: includes the ensemble kernel once selected)."""
         info = nat.Info()
         nat.check(self.lib.dd_get_info(self.handle, ctypes.byref(info)), "dd_get_info")
-        self.info = _info_dict(info)
-        self.n_free = int(info.n_free)
-        self.n_gamma = int(info.n_gamma)
-        self.n_elem = int(mesh.nx) * int(mesh.ny) * int(mesh.nz)
+        d = _info_dict(info)
+        d["ens_nmm_ms"] = list(info.ens_nmm_ms)
+        return d
 
     def close(self):
         if getattr(self, "handle", None):

@@ -102,97 +102,106 @@ __device__ __forceinline__ void apply_item_b(const DevMesh& m, const int16_t* it
   out = P::add(P::get(acc[0]), P::get(acc[1]));
 }
 
+// A block takes one subdomain: the element entries are formed once, then the members
+// pass through in chunks of RC (their local values staged in shared memory).
 template <class P, int S, int RC>
-__global__ void __launch_bounds__(256) k_elem_interior_b(DevMesh m, int mode, const double* __restrict__ xg,
+__global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, const double* __restrict__ xg,
                                                          const double* __restrict__ f, double* __restrict__ tI) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_b[];
   V* xl = reinterpret_cast<V*>(smem_b);  // [NL][RC]
   V* kd = xl + (size_t)m.NL * RC;
-  const int s = blockIdx.x, m0 = blockIdx.y * RC;
+  const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
   const int* to = m.type_off + 6 * m.sub_type[s];
   const int64_t io = m.ioff[s];
-  for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
-    const int l = t / RC, mm = t % RC;
+  // every interior output first gets its base value (0 or f_I), all members
+  for (int t = threadIdx.x; t < m.NL * BW; t += blockDim.x) {
+    const int l = t / BW, mm = t % BW;
     const int cd = code[l];
-    if (cd >= 0) tI[(io + cd) * BW + m0 + mm] = (mode == ELEM_SCHUR) ? 0.0 : f[free_index(m, s, l) * BW + m0 + mm];
+    if (cd >= 0) tI[(io + cd) * BW + mm] = (mode == ELEM_SCHUR) ? 0.0 : f[free_index(m, s, l) * BW + mm];
   }
   if (mode == ELEM_CONDENSE) return;
-  for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
-    const int l = t / RC, mm = t % RC;
-    const int cd = code[l];
-    xl[t] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + mm])
-                                        : P::zero();
-  }
   build_kd_list<P, S>(m, s, m.type_bl + to[4], to[5] - to[4], kd);
-  __syncthreads();
   constexpr int IPW = 32 / RC;  // items per warp pass
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int mm = lane % RC;
-  for (int i = to[0] + warp * IPW + lane / RC; i < to[1]; i += nw * IPW) {
-    const int16_t* it = m.type_items + 9 * (size_t)i;
-    const int l = it[0];
-    V v;
-    apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
-    const int64_t o = (io + code[l]) * BW + m0 + mm;
-    if (mode == ELEM_SCHUR)
-      tI[o] = P::to_d(v);
-    else
-      tI[o] = f[free_index(m, s, l) * BW + m0 + mm] - P::to_d(v);
+  for (int m0 = 0; m0 < BW; m0 += RC) {
+    for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
+      const int l = t / RC, c = t % RC;
+      const int cd = code[l];
+      xl[t] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c])
+                                          : P::zero();
+    }
+    __syncthreads();
+    for (int i = to[0] + warp * IPW + lane / RC; i < to[1]; i += nw * IPW) {
+      const int16_t* it = m.type_items + 9 * (size_t)i;
+      const int l = it[0];
+      V v;
+      apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
+      const int64_t o = (io + code[l]) * BW + m0 + mm;
+      if (mode == ELEM_SCHUR)
+        tI[o] = P::to_d(v);
+      else
+        tI[o] = f[free_index(m, s, l) * BW + m0 + mm] - P::to_d(v);
+    }
+    __syncthreads();
   }
 }
 
 template <class P, int S, int RC>
-__global__ void __launch_bounds__(256) k_elem_interface_b(DevMesh m, int mode, const double* __restrict__ xg,
+__global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, const double* __restrict__ xg,
                                                           const double* __restrict__ sI,
                                                           double* __restrict__ yloc) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_b[];
   V* xl = reinterpret_cast<V*>(smem_b);
   V* kd = xl + (size_t)m.NL * RC;
-  const int s = blockIdx.x, m0 = blockIdx.y * RC;
+  const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
   const int* to = m.type_off + 6 * m.sub_type[s];
-  for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
-    const int l = t / RC, mm = t % RC;
-    const int cd = code[l];
-    V v = P::zero();
-    if (cd >= 0)
-      v = P::from_d(-sI[(m.ioff[s] + cd) * BW + m0 + mm]);
-    else if (cd != INT16_MIN && mode == ELEM_SCHUR)
-      v = P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + mm]);
-    xl[t] = v;
-  }
   build_kd_list<P, S>(m, s, m.type_bl + to[4], to[5] - to[4], kd);
-  __syncthreads();
   constexpr int IPW = 32 / RC;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int mm = lane % RC;
-  for (int i = to[2] + warp * IPW + lane / RC; i < to[3]; i += nw * IPW) {
-    const int16_t* it = m.type_items + 9 * (size_t)i;
-    V v;
-    apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
-    yloc[(m.goff[s] + (-1 - code[it[0]])) * BW + m0 + mm] = P::to_d(v);
+  for (int m0 = 0; m0 < BW; m0 += RC) {
+    for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
+      const int l = t / RC, c = t % RC;
+      const int cd = code[l];
+      V v = P::zero();
+      if (cd >= 0)
+        v = P::from_d(-sI[(m.ioff[s] + cd) * BW + m0 + c]);
+      else if (cd != INT16_MIN && mode == ELEM_SCHUR)
+        v = P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c]);
+      xl[t] = v;
+    }
+    __syncthreads();
+    for (int i = to[2] + warp * IPW + lane / RC; i < to[3]; i += nw * IPW) {
+      const int16_t* it = m.type_items + 9 * (size_t)i;
+      V v;
+      apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
+      yloc[(m.goff[s] + (-1 - code[it[0]])) * BW + m0 + mm] = P::to_d(v);
+    }
+    __syncthreads();
   }
 }
 
-constexpr int ELEM_RC = 16;  // members per block of the batched element passes
+constexpr int ELEM_RC = 8;        // members per pass of the batched element kernels
+constexpr int ELEM_THREADS = 512;
 
 template <class P, int S>
 static void elem_b_go(const DevMesh& m, bool interior, int mode, const double* xg, const double* in, double* out,
                       cudaStream_t s) {
   const int NE = m.sx * m.sy * m.sz;
   const size_t smem = ((size_t)m.NL * ELEM_RC + (size_t)NE * 8) * sizeof(typename P::V);
-  dim3 grid(m.S, BW / ELEM_RC);
   if (interior) {
     DD_CUDA(cudaFuncSetAttribute(k_elem_interior_b<P, S, ELEM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    k_elem_interior_b<P, S, ELEM_RC><<<grid, 256, smem, s>>>(m, mode, xg, in, out);
+    k_elem_interior_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   } else {
     DD_CUDA(cudaFuncSetAttribute(k_elem_interface_b<P, S, ELEM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    k_elem_interface_b<P, S, ELEM_RC><<<grid, 256, smem, s>>>(m, mode, xg, in, out);
+    k_elem_interface_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   }
 }
 
@@ -228,29 +237,48 @@ void launch_elem_interface_b(const DevMesh& m, int mode, const double* xg, const
 // ---------------------------------------------------------------------------
 // K_II^{-1} of the ensemble: fast diagonalization with RC members per block
 // ---------------------------------------------------------------------------
+// contraction along axis ax, one thread per line (the other two indices and a member):
+// the line's values sit in registers and all its outputs are formed at once
+// (out_j = sum_i A(i, j) in_i when trans, else sum_i A(j, i) in_i)
 template <class P, int RC>
 __device__ __forceinline__ void fdm_contract_b(const typename P::V* A, int ax, bool trans, const int* n,
                                                const typename P::V* in, typename P::V* out) {
-  const int N = n[0] * n[1] * n[2];
+  using V = typename P::V;
   const int na = n[ax];
   const int stride = ax == 0 ? 1 : (ax == 1 ? n[0] : n[0] * n[1]);
-  for (int t = threadIdx.x; t < N * RC; t += blockDim.x) {
-    const int idx = t / RC, mm = t % RC;
-    const int j = (idx / stride) % na;
-    const int base = idx - j * stride;
-    typename P::Acc acc[2];
-    P::init(acc[0]);
-    P::init(acc[1]);
-    for (int i = 0; i < na; ++i) {
-      typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
-      P::fma(acc[i & 1], a, in[(base + i * stride) * RC + mm]);
+  const int o1 = ax == 0 ? n[1] : n[0];
+  const int o2 = ax == 2 ? n[1] : n[2];
+  const int nl = o1 * o2 * RC;
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    const int mm = t % RC, lw = t / RC;
+    const int u = lw % o1, w = lw / o1;
+    const int base = ax == 0 ? n[0] * (u + n[1] * w) : (ax == 1 ? u + n[0] * n[1] * w : u + n[0] * w);
+    V x[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = i < na ? in[(base + i * stride) * RC + mm] : P::zero();
+    // two outputs of the line at a time: independent accumulation chains overlap
+    const int ajs = trans ? 1 : 9, ais = trans ? 9 : 1;  // A(j, i) at A[j * ajs + i * ais]
+    for (int j = 0; j < na; j += 2) {
+      const bool two = j + 1 < na;
+      typename P::Acc a0, a1;
+      P::init(a0);
+      P::init(a1);
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        if (i < na) {
+          P::fma(a0, A[j * ajs + i * ais], x[i]);
+          if (two) P::fma(a1, A[(j + 1) * ajs + i * ais], x[i]);
+        }
+      out[(base + j * stride) * RC + mm] = P::get(a0);
+      if (two) out[(base + (j + 1) * stride) * RC + mm] = P::get(a1);
     }
-    out[t] = P::add(P::get(acc[0]), P::get(acc[1]));
   }
 }
 
+constexpr int FDM_THREADS = 448;  // 7 x 7 lines of 8 members (interior subdomains) in one pass
+
 template <class P, int RC>
-__global__ void __launch_bounds__(256) k_fdm_apply_b(DevMesh m, const double* __restrict__ tI,
+__global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const double* __restrict__ tI,
                                                      double* __restrict__ sI) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_f[];
@@ -295,7 +323,7 @@ template <class P>
 static void fdm_b_go(const DevMesh& m, const double* tI, double* sI, cudaStream_t s) {
   const size_t smem = (size_t)2 * 729 * FDM_RC * sizeof(typename P::V);
   DD_CUDA(cudaFuncSetAttribute(k_fdm_apply_b<P, FDM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_fdm_apply_b<P, FDM_RC><<<dim3(m.S, BW / FDM_RC), 256, smem, s>>>(m, tI, sI);
+  k_fdm_apply_b<P, FDM_RC><<<dim3(m.S, BW / FDM_RC), FDM_THREADS, smem, s>>>(m, tI, sI);
 }
 
 void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStream_t s) {
@@ -584,16 +612,31 @@ void launch_symm_b(const SymTiles& A, const int64_t* voff, const void* in, void*
 //            of them per load (lane = row * 8 + column)
 // ---------------------------------------------------------------------------
 template <class T>
+__device__ __forceinline__ T ld_x(const T* in, const int* in_map, int64_t io, int j, int lane) {
+  const int64_t src = in_map ? (int64_t)in_map[io + j] : io + j;
+  return in[src * BW + lane];
+}
+
+// STAGE: the item's input rows are first copied to shared memory ([rows][BW]) so the
+// inner loop runs on shared-memory loads and register shuffles only
+template <class T, bool STAGE>
 __global__ void __launch_bounds__(256) k_bmm(const int64_t* __restrict__ row0, const int* __restrict__ cols,
                                              const int64_t* __restrict__ moff, const T* __restrict__ M,
                                              const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
                                              const T* __restrict__ in, const int64_t* __restrict__ out_off,
                                              T* __restrict__ out, T alpha, const T* __restrict__ add) {
+  extern __shared__ __align__(16) unsigned char bm_smem[];
+  T* xs = reinterpret_cast<T*>(bm_smem);
   const int mi = blockIdx.x;
   const int R = (int)(row0[mi + 1] - row0[mi]), C = cols[mi];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t io = in_off[mi], oo = out_off[mi];
   const T* A = M + moff[mi];
+  if (blockIdx.y * nw * 4 >= R) return;
+  if (STAGE) {
+    for (int t = threadIdx.x; t < C * BW; t += blockDim.x) xs[t] = ld_x(in, in_map, io, t / BW, t % BW);
+    __syncthreads();
+  }
   for (int i0 = (blockIdx.y * nw + warp) * 4; i0 < R; i0 += gridDim.y * nw * 4) {
     T acc[4] = {0, 0, 0, 0};
     for (int j0 = 0; j0 < C; j0 += 32) {
@@ -602,10 +645,9 @@ __global__ void __launch_bounds__(256) k_bmm(const int64_t* __restrict__ row0, c
 #pragma unroll
       for (int k = 0; k < 4; ++k) a[k] = (i0 + k < R && j < C) ? A[(int64_t)(i0 + k) * C + j] : (T)0;
       const int jn = min(32, C - j0);
+#pragma unroll 4
       for (int jj = 0; jj < jn; ++jj) {
-        const int jx = j0 + jj;
-        const int64_t src = in_map ? (int64_t)in_map[io + jx] : io + jx;
-        const T x = in[src * BW + lane];
+        const T x = STAGE ? xs[(j0 + jj) * BW + lane] : ld_x(in, in_map, io, j0 + jj, lane);
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[k] = fma(__shfl_sync(0xffffffffu, a[k], jj), x, acc[k]);
       }
@@ -619,17 +661,24 @@ __global__ void __launch_bounds__(256) k_bmm(const int64_t* __restrict__ row0, c
   }
 }
 
-template <class T>
+template <class T, bool STAGE>
 __global__ void __launch_bounds__(256) k_bmm_t(const int64_t* __restrict__ row0, const int* __restrict__ cols,
                                                const int64_t* __restrict__ moff, const T* __restrict__ M,
                                                const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
                                                const T* __restrict__ in, const int64_t* __restrict__ out_off,
                                                T* __restrict__ out, T alpha, const T* __restrict__ add) {
+  extern __shared__ __align__(16) unsigned char bm_smem[];
+  T* xs = reinterpret_cast<T*>(bm_smem);
   const int mi = blockIdx.x;
   const int R = (int)(row0[mi + 1] - row0[mi]), C = cols[mi];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t io = in_off[mi], oo = out_off[mi];
   const T* A = M + moff[mi];
+  if (blockIdx.y * nw * 8 >= C) return;
+  if (STAGE) {
+    for (int t = threadIdx.x; t < R * BW; t += blockDim.x) xs[t] = ld_x(in, in_map, io, t / BW, t % BW);
+    __syncthreads();
+  }
   const int lr = lane >> 3, lc = lane & 7;
   for (int j0 = (blockIdx.y * nw + warp) * 8; j0 < C; j0 += gridDim.y * nw * 8) {
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -639,11 +688,7 @@ __global__ void __launch_bounds__(256) k_bmm_t(const int64_t* __restrict__ row0,
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int i = i0 + rr;
-        T x = 0;
-        if (i < R) {
-          const int64_t src = in_map ? (int64_t)in_map[io + i] : io + i;
-          x = in[src * BW + lane];
-        }
+        const T x = i < R ? (STAGE ? xs[i * BW + lane] : ld_x(in, in_map, io, i, lane)) : (T)0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = fma(__shfl_sync(0xffffffffu, a, rr * 8 + k), x, acc[k]);
       }
@@ -657,18 +702,37 @@ __global__ void __launch_bounds__(256) k_bmm_t(const int64_t* __restrict__ row0,
   }
 }
 
+constexpr size_t BMM_STAGE_MAX = 96 * 1024;  // largest staged input slice (bytes)
+
 template <class T>
 static void bmm_go(const BatchedRows& B, bool trans, const int64_t* in_off, const int* in_map, const void* in,
                    const int64_t* out_off, void* out, double alpha, const void* add, cudaStream_t s) {
   const int per_block = trans ? 8 * 8 : 8 * 4;  // columns / rows per block pass
   const int extent = trans ? B.max_cols : B.max_rows;
+  const int inrows = trans ? B.max_rows : B.max_cols;
   dim3 grid(B.count, std::max(1, std::min(16, (extent + per_block - 1) / per_block)));
-  if (trans)
-    k_bmm_t<T><<<grid, 256, 0, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off, in_map,
-                                    (const T*)in, out_off, (T*)out, (T)alpha, (const T*)add);
-  else
-    k_bmm<T><<<grid, 256, 0, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off, in_map,
-                                  (const T*)in, out_off, (T*)out, (T)alpha, (const T*)add);
+  const size_t smem = (size_t)inrows * BW * sizeof(T);
+  const bool stage = smem <= BMM_STAGE_MAX;
+  const T* Md = static_cast<const T*>(B.data);
+  if (trans) {
+    if (stage) {
+      DD_CUDA(cudaFuncSetAttribute(k_bmm_t<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_bmm_t<T, true><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
+                                               (T*)out, (T)alpha, (const T*)add);
+    } else {
+      k_bmm_t<T, false><<<grid, 256, 0, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
+                                             (T*)out, (T)alpha, (const T*)add);
+    }
+  } else {
+    if (stage) {
+      DD_CUDA(cudaFuncSetAttribute(k_bmm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_bmm<T, true><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
+                                             (T*)out, (T)alpha, (const T*)add);
+    } else {
+      k_bmm<T, false><<<grid, 256, 0, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
+                                           (T*)out, (T)alpha, (const T*)add);
+    }
+  }
 }
 
 void launch_bmm(const BatchedRows& B, const int64_t* in_off, const int* in_map, const void* in,
@@ -773,13 +837,30 @@ __global__ void __launch_bounds__(BRB) k_baxpy2(int64_t n, const double* __restr
 
 // one warp, lane = member: sums the block partials in a fixed order and updates the
 // member's scalars. Inactive members keep alpha = beta = 0, so their iterates stay fixed.
-__global__ void k_bfinalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible) {
+constexpr int BFIN_WARPS = 32;
+__global__ void __launch_bounds__(BFIN_WARPS * 32) k_bfinalize(int nblk, const double* __restrict__ partials,
+                                                               double* sc, int op, int flexible) {
+  // warp w sums the blocks w, w + 32, ... (lane = member); warp 0 then adds the 32
+  // warp sums in order: a fixed reduction tree
+  __shared__ double part[BFIN_WARPS][2][BW];
+  {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+    for (int b = w; b < nblk; b += BFIN_WARPS) {
+      a0 += partials[((int64_t)b * BND + 0) * BW + l];
+      a1 += partials[((int64_t)b * BND + 1) * BW + l];
+    }
+    part[w][0][l] = a0;
+    part[w][1][l] = a1;
+  }
+  __syncthreads();
   const int m = threadIdx.x;
   if (m >= BW) return;
   double t0 = 0.0, t1 = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    t0 += partials[((int64_t)b * BND + 0) * BW + m];
-    t1 += partials[((int64_t)b * BND + 1) * BW + m];
+  for (int w = 0; w < BFIN_WARPS; ++w) {
+    t0 += part[w][0][m];
+    t1 += part[w][1][m];
   }
   double* S = sc;
   auto at = [&](int slot) -> double& { return S[slot * BW + m]; };
@@ -848,16 +929,16 @@ __global__ void k_bfinalize(int nblk, const double* __restrict__ partials, doubl
 
 void bvec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, double* partials,
                cudaStream_t s) {
-  k_bdots<<<NBLK, BRB, 0, s>>>(n, a0, b0, a1, b1, partials);
+  k_bdots<<<NBLKB, BRB, 0, s>>>(n, a0, b0, a1, b1, partials);
   DD_CHECK_LAUNCH();
 }
 void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s) {
-  k_bfinalize<<<1, BW, 0, s>>>(NBLK, partials, sc, op, flexible);
+  k_bfinalize<<<1, BFIN_WARPS * 32, 0, s>>>(NBLKB, partials, sc, op, flexible);
   DD_CHECK_LAUNCH();
 }
 void bvec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q,
                 double* partials, cudaStream_t s) {
-  k_baxpy2<<<NBLK, BRB, 0, s>>>(n, sc, x, p, r, q, partials);
+  k_baxpy2<<<NBLKB, BRB, 0, s>>>(n, sc, x, p, r, q, partials);
   DD_CHECK_LAUNCH();
 }
 
@@ -910,31 +991,53 @@ __global__ void __launch_bounds__(BRB) k_bwdots(int64_t n, int k, const double* 
   }
 }
 
-// mu[j][m] = sum_l G[j][l] d[l][m], d = fixed-order sum of the partials
-__global__ void k_bwfinal(int nblk, int k, const double* __restrict__ wpart, const double* __restrict__ G,
-                          double* mu) {
-  __shared__ double d[MAXK][BW];
-  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) {
-    const int c = q / BW, m = q % BW;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += wpart[((int64_t)b * MAXK + c) * BW + m];
-    d[c][m] = s;
+// d[c][m] = fixed-order sum of the block partials (one block per column c: warp w takes
+// the blocks w, w + 8, ..., warp 0 adds the warp sums in order); written into mu
+__global__ void __launch_bounds__(1024) k_bwsum(int nblk, const double* __restrict__ wpart, double* d) {
+  __shared__ double part[32][BW];
+  const int c = blockIdx.x, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  double a0 = 0.0, a1 = 0.0;
+  int b = w;
+  for (; b + 32 < nblk; b += 64) {
+    a0 += wpart[((int64_t)b * MAXK + c) * BW + l];
+    a1 += wpart[((int64_t)(b + 32) * MAXK + c) * BW + l];
   }
+  if (b < nblk) a0 += wpart[((int64_t)b * MAXK + c) * BW + l];
+  part[w][l] = a0 + a1;
   __syncthreads();
-  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) {
-    const int a = q / BW, m = q % BW;
-    double s = 0.0;
-    for (int c = 0; c < k; ++c) s += G[a * k + c] * d[c][m];
-    mu[a * BW + m] = s;
+  if (w == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < 32; ++q) sum += part[q][l];
+    d[c * BW + l] = sum;
+  }
+}
+
+// mu[a][m] = sum_c G[a][c] d[c][m] (d read from mu into shared memory first)
+__global__ void __launch_bounds__(256) k_bwfinal(int k, const double* __restrict__ G, double* mu) {
+  __shared__ double d[MAXK][BW];
+  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) d[q / BW][q % BW] = mu[q];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = w; a < k; a += nw) {
+    double s0 = 0.0, s1 = 0.0;
+    int c = 0;
+    for (; c + 1 < k; c += 2) {
+      s0 = fma(G[a * k + c], d[c][l], s0);
+      s1 = fma(G[a * k + c + 1], d[c + 1][l], s1);
+    }
+    if (c < k) s0 = fma(G[a * k + c], d[c][l], s0);
+    mu[a * BW + l] = s0 + s1;
   }
 }
 
 void bdefl_mu(int64_t n, int k, const double* V, int64_t ld, const double* v, const double* G, double* wpart,
               double* mu, cudaStream_t s) {
   if (k == 0) return;
-  k_bwdots<<<NBLK, BRB, 0, s>>>(n, k, V, ld, v, wpart);
+  k_bwdots<<<NBLKB, BRB, 0, s>>>(n, k, V, ld, v, wpart);
   DD_CHECK_LAUNCH();
-  k_bwfinal<<<1, 256, 0, s>>>(NBLK, k, wpart, G, mu);
+  k_bwsum<<<k, 1024, 0, s>>>(NBLKB, wpart, mu);
+  DD_CHECK_LAUNCH();
+  k_bwfinal<<<1, 256, 0, s>>>(k, G, mu);
   DD_CHECK_LAUNCH();
 }
 
@@ -963,7 +1066,79 @@ __global__ void __launch_bounds__(BRB) k_bpupdate(int64_t n, int k, const double
 
 void bdefl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
                   const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
-  k_bpupdate<<<NBLK, BRB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  k_bpupdate<<<NBLKB, BRB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  DD_CHECK_LAUNCH();
+}
+
+// deflation with the df64-stored shared basis (float pairs, error-free FP32 arithmetic)
+__device__ __forceinline__ df64 dbl_to_df_b(double d) {
+  const float hi = (float)d;
+  return {hi, (float)(d - (double)hi)};
+}
+
+__global__ void __launch_bounds__(BRB) k_bwdots_df(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
+                                                   const double* __restrict__ v, double* wpart) {
+  __shared__ double sh[8][BRB / 32][BW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int nc = min(8, k - c0);
+    df64_acc acc[8];
+    for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
+      const df64 vi = dbl_to_df_b(v[i * BW + lane]);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < nc) acc[t].fma(V[(int64_t)(c0 + t) * ld + i], vi);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) sh[t][warp][lane] = df64_to_double(acc[t].get());
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * BW; q += blockDim.x) {
+      const int t = q / BW, m = q % BW;
+      double sum = 0.0;
+      for (int w = 0; w < BRB / 32; ++w) sum += sh[t][w][m];
+      wpart[((int64_t)blockIdx.x * MAXK + c0 + t) * BW + m] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+void bdefl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* G, double* wpart,
+                 double* mu, cudaStream_t s) {
+  if (k == 0) return;
+  k_bwdots_df<<<NBLKB, BRB, 0, s>>>(n, k, V, ld, v, wpart);
+  DD_CHECK_LAUNCH();
+  k_bwsum<<<k, 1024, 0, s>>>(NBLKB, wpart, mu);
+  DD_CHECK_LAUNCH();
+  k_bwfinal<<<1, 256, 0, s>>>(k, G, mu);
+  DD_CHECK_LAUNCH();
+}
+
+__global__ void __launch_bounds__(BRB) k_bpupdate_df(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
+                                                     const double* __restrict__ mu, const double* __restrict__ z,
+                                                     double* __restrict__ y, const double* __restrict__ sc,
+                                                     int beta_idx, double sign_w) {
+  __shared__ df64 mus[MAXK][BW];
+  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) mus[q / BW][q % BW] = dbl_to_df_b(sign_w * mu[q]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const double beta = beta_idx >= 0 ? sc[beta_idx * BW + lane] : 0.0;
+  for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
+    const int64_t o = i * BW + lane;
+    const double v = (z ? z[o] : 0.0) + (beta_idx >= 0 ? beta * y[o] : (z ? 0.0 : y[o]));
+    df64_acc a0, a1;
+    int c = 0;
+    for (; c + 1 < k; c += 2) {
+      a0.fma(W[(int64_t)c * ld + i], mus[c][lane]);
+      a1.fma(W[(int64_t)(c + 1) * ld + i], mus[c + 1][lane]);
+    }
+    if (c < k) a0.fma(W[(int64_t)c * ld + i], mus[c][lane]);
+    y[o] = v + df64_to_double(df64_add(a0.get(), a1.get()));
+  }
+}
+
+void bdefl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
+                     const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
+  k_bpupdate_df<<<NBLKB, BRB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
   DD_CHECK_LAUNCH();
 }
 

@@ -9,10 +9,12 @@
 
 #include "common.h"
 #include "device.h"
+#include "tc_nmm.h"
 
 namespace dd {
 
 constexpr int BW = 32;  // ensemble block width (members per row, one per lane)
+constexpr int NBLKB = 152 * 8;  // fixed reduction grid of the ensemble kernels (deterministic partials)
 
 // per-member device scalars, slot-major: sc[slot * BW + m]
 enum {
@@ -34,10 +36,18 @@ struct BatchWork {
   double *F = nullptr, *X = nullptr;  // [n_free][BW]
   double* sc = nullptr;               // [BS_COUNT][BW]
   double* sc_host = nullptr;          // pinned mirror
-  double* partials = nullptr;         // [NBLK][4][BW]
-  double* wpart = nullptr;            // [NBLK][MAXK][BW]
+  double* partials = nullptr;         // [NBLKB][4][BW]
+  double* wpart = nullptr;            // [NBLKB][MAXK][BW]
   double* mu = nullptr;               // [MAXK][BW]
+  // symmetric products of the ensemble (level-1 N_i; level-2 K_II^{-1} and N): tensor-core
+  // operand copy, whether it is used, and the selection timings (SIMT, tensor cores)
+  struct SymOp {
+    TcMats tc;
+    bool use_tc = false;
+    float ms[2] = {0.f, 0.f};
+  } op[3];
 };
+enum { BOP_N1 = 0, BOP_KII2 = 1, BOP_N2 = 2 };
 
 // ---- layout ----
 // out[i * BW + m] = m < nrhs ? F[m * n + i] : 0   (F member-major, as the caller passes it)
@@ -97,5 +107,10 @@ void bdefl_mu(int64_t n, int k, const double* V, int64_t ld, const double* v, co
 // beta_idx < 0: no beta term)
 void bdefl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
                   const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+// the same with the shared basis stored as df64 (float pairs)
+void bdefl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* G, double* wpart,
+                 double* mu, cudaStream_t s);
+void bdefl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
+                     const double* sc, int beta_idx, double sign_w, cudaStream_t s);
 
 }  // namespace dd

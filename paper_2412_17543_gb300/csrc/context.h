@@ -126,6 +126,7 @@ struct dd_recycle {
   DeviceArena arena;
   double *W = nullptr, *AW = nullptr, *MAW = nullptr;       // [kmax][n_gamma]
   double *W2 = nullptr, *AW2 = nullptr, *MAW2 = nullptr;    // next basis
+  dd::df64 *Wd = nullptr, *AWd = nullptr;                   // df64 copies of W, AW (deflation kernels)
   double* Ginv = nullptr;                                   // [kmax*kmax] (W^T A W)^{-1}
   double* WWinv = nullptr;                                  // [kmax*kmax] (W^T W)^{-1}
   std::vector<double> theta;

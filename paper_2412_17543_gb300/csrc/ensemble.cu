@@ -12,6 +12,7 @@
 #include <cmath>
 #include <memory>
 #include <string>
+#include <vector>
 
 #include "batch.h"
 #include "context.h"
@@ -26,7 +27,66 @@ void free_batch_work(BatchWork* bw) {
 
 namespace {
 
-BatchWork& batch_work(dd_ctx* c) {
+// The symmetric products of the ensemble (level-1 N_i, level-2 K_II^{-1} and N) run on
+// the tensor cores (3xTF32) or on CUDA-core tiles. With DD_ENS_AUTO both kernels run on
+// the context's own operators (three timed launches each after a warm-up) and the faster
+// one is kept: the autotuning step of the ensemble path.
+void apply_sym_b(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, const void* in, void* out,
+                 cudaStream_t s) {
+  const BatchWork::SymOp& o = c->bw->op[which];
+  if (o.use_tc)
+    launch_nmm_tc(o.tc, voff, (const float*)in, (float*)out, c->w.err, s);
+  else
+    launch_symm_b(S, voff, in, out, s);
+}
+
+void select_op(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, void* in, void* out, int64_t rows,
+               cudaStream_t s) {
+  BatchWork::SymOp& o = c->bw->op[which];
+  const int mode = c->opt.ens_nmm;
+  o.use_tc = false;
+  if (S.prec != DD_PREC_FP32 || mode == DD_ENS_SIMT || S.count == 0) return;
+  std::vector<int> nh(S.count);
+  DD_CUDA(cudaMemcpyAsync(nh.data(), S.n, nh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  o.tc = build_tc_mats(c->bw->arena, S, nh, s);
+  const int npad = ((S.max_n + 31) / 32) * 32;
+  if (mode == DD_ENS_TC || (size_t)npad * BW * sizeof(float) > 227 * 1024) {  // CUDA-core tiles do not fit
+    o.use_tc = true;
+    return;
+  }
+  DD_CUDA(cudaMemsetAsync(in, 0, (size_t)rows * BW * sizeof(float), s));
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  for (int v = 0; v < 2; ++v) {
+    o.use_tc = v == 1;
+    apply_sym_b(c, which, S, voff, in, out, s);
+    DD_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) apply_sym_b(c, which, S, voff, in, out, s);
+    DD_CUDA(cudaEventRecord(e1, s));
+    DD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    o.ms[v] = ms / 3.f;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_err(c, s);
+  o.use_tc = o.ms[1] < o.ms[0];
+}
+
+void select_ops(dd_ctx* c, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  select_op(c, BOP_N1, c->b1.N, c->b1.goff, B.rloc, B.uloc, c->b1.n_flat, s);
+  if (c->levels == 3) {
+    const DevLevel2& L = c->l2;
+    select_op(c, BOP_KII2, L.KIIinv, L.ioff, B.gI2, B.u0I2, L.n_int, s);
+    select_op(c, BOP_N2, L.b.N, L.b.goff, B.rloc2, B.uloc2, L.b.n_flat, s);
+  }
+}
+
+BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   if (c->bw) return *c->bw;
   auto B = std::make_unique<BatchWork>();
   DeviceArena& A = B->arena;
@@ -73,16 +133,18 @@ BatchWork& batch_work(dd_ctx* c) {
   B->F = dvec(c->n_free);
   B->X = dvec(c->n_free);
   B->sc = A.alloc<double>((size_t)BS_COUNT * BW);
-  B->partials = A.alloc<double>((size_t)NBLK * 4 * BW);
-  B->wpart = A.alloc<double>((size_t)NBLK * MAXK * BW);
+  B->partials = A.alloc<double>((size_t)NBLKB * 4 * BW);
+  B->wpart = A.alloc<double>((size_t)NBLKB * MAXK * BW);
   B->mu = A.alloc<double>((size_t)MAXK * BW);
   DD_CUDA(cudaMallocHost(&B->sc_host, (size_t)BS_COUNT * BW * sizeof(double)));
   c->bw = B.release();
+  select_ops(c, s);
   return *c->bw;
 }
 
 // ---- operators on BW members ----
 void schur_b(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
+  ProfScope ps(c, DD_PROF_ENS_SCHUR, s);
   BatchWork& B = *c->bw;
   launch_elem_interior_b(c->mesh, ELEM_SCHUR, x, nullptr, B.tI, s);
   launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
@@ -106,10 +168,13 @@ void recover_b(dd_ctx* c, const double* f, const double* xg, double* x, cudaStre
 }
 
 template <class CoarseFn>
-void bddc_b(const DevBDDC& b, const double* r, double* z, void* rloc, void* uloc, void* vloc, void* gloc, void* gC,
+void bddc_b(dd_ctx* c, const DevBDDC& b, const double* r, double* z, void* rloc, void* uloc, void* vloc, void* gloc, void* gC,
             void* uC, CoarseFn coarse, cudaStream_t s) {
   launch_restrict_b(b.prec, b.n_flat, b.gmap, b.D, r, rloc, s);
-  launch_symm_b(b.N, b.goff, rloc, uloc, s);                                   // u_i = N_i r_i
+  {
+    ProfScope pk(c, DD_PROF_ENS_N, s);
+    apply_sym_b(c, BOP_N1, b.N, b.goff, rloc, uloc, s);                        // u_i = N_i r_i
+  }
   launch_bmm(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);    // Phi_i^T r_i
   launch_gather_tb(b.prec, b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
   coarse(gC, uC);
@@ -123,14 +188,14 @@ void level2_b(dd_ctx* c, const void* g, void* u, cudaStream_t s) {
   BatchWork& B = *c->bw;
   const int p2 = L.b.prec;
   launch_map_gather_b(p2, L.n_int, L.imap, g, B.gI2, s);
-  launch_symm_b(L.KIIinv, L.ioff, B.gI2, B.u0I2, s);
+  apply_sym_b(c, BOP_KII2, L.KIIinv, L.ioff, B.gI2, B.u0I2, s);
   launch_bmm_t(L.E, L.ioff, nullptr, B.gI2, L.b.goff, B.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather_tb(p2, L.b.n_gamma, L.b.gptr, L.b.gidx, B.rl2, g, L.gam_c64, B.r2, s);
   {
     // level-2 interface BDDC on r2 (vectors in the preconditioner type), exact level 3
     const DevBDDC& b = L.b;
     launch_restrict_tb(p2, b.n_flat, b.gmap, b.D, B.r2, B.rloc2, s);
-    launch_symm_b(b.N, b.goff, B.rloc2, B.uloc2, s);
+    apply_sym_b(c, BOP_N2, b.N, b.goff, B.rloc2, B.uloc2, s);
     launch_bmm(b.PhiT, b.goff, nullptr, B.rloc2, b.coff, B.gloc2, 1.0, nullptr, s);
     launch_gather_tb(p2, b.n_coarse, b.cptr, b.cidx, B.gloc2, nullptr, nullptr, B.g3, s);
     launch_dense_mm(p2, L.n3, L.KC3inv, B.g3, B.u3, s);
@@ -143,8 +208,9 @@ void level2_b(dd_ctx* c, const void* g, void* u, cudaStream_t s) {
 }
 
 void precond_b(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+  ProfScope ps(c, DD_PROF_ENS_PRECOND, s);
   BatchWork& B = *c->bw;
-  bddc_b(c->b1, r, z, B.rloc, B.uloc, B.vloc, B.gloc, B.gC, B.uC,
+  bddc_b(c, c->b1, r, z, B.rloc, B.uloc, B.vloc, B.gloc, B.gC, B.uC,
          [&](const void* g, void* u) {
            if (c->levels == 2)
              launch_dense_mm(c->b1.prec, c->b1.n_coarse, c->KCinv, g, u, s);
@@ -165,8 +231,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
   const int64_t n = c->n_gamma;
   const dd_options& o = c->opt;
   const int k = st->k;
-  const double* W = k ? st->W : nullptr;
-  const double* AW = k ? st->AW : nullptr;
+  const df64* W = k ? st->Wd : nullptr;
+  const df64* AW = k ? st->AWd : nullptr;
   auto host_sc = [&]() {
     DD_CUDA(cudaMemcpyAsync(B.sc_host, B.sc, (size_t)BS_COUNT * BW * sizeof(double), cudaMemcpyDeviceToHost, s));
     DD_CUDA(cudaStreamSynchronize(s));
@@ -182,8 +248,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})  (shared W, per-member mu)
     schur_b(c, B.xg, B.q, s);
     bvec_sub(n, B.bvec, B.q, B.r, s);
-    bdefl_mu(n, k, W, n, B.r, st->Ginv, B.wpart, B.mu, s);
-    bdefl_update(n, k, W, n, B.mu, nullptr, B.xg, B.sc, -1, 1.0, s);
+    bdefl_mu_df(n, k, W, n, B.r, st->Ginv, B.wpart, B.mu, s);
+    bdefl_update_df(n, k, W, n, B.mu, nullptr, B.xg, B.sc, -1, 1.0, s);
   }
   schur_b(c, B.xg, B.q, s);
   bvec_sub(n, B.bvec, B.q, B.r, s);
@@ -202,8 +268,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
     bvec_dots(n, B.r, B.z, nullptr, nullptr, B.partials, s);
     bvec_finalize(B.partials, B.sc, BFIN_RZ0, 0, s);
     if (k) {
-      bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
+      bdefl_mu_df(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update_df(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
     } else {
       copy_b(B.p, B.z, n, s);
     }
@@ -232,8 +298,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
       if (rec0 && its <= st->hmax) launch_extract_col(n, B.z, 0, st->Z + (size_t)its * n, s);
       bvec_dots(n, B.r, B.z, o.flexible ? B.r : nullptr, o.flexible ? B.zold : nullptr, B.partials, s);
       bvec_finalize(B.partials, B.sc, BFIN_RZ, o.flexible, s);
-      if (k) bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
+      if (k) bdefl_mu_df(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update_df(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
     }
   }
   for (int m = 0; m < nrhs; ++m) {
@@ -285,7 +351,7 @@ static dd_status batch_op(dd_ctx* c, int32_t nrhs, const double* X, double* Y, v
   }
   return guard_call([&] {
     cudaStream_t s = (cudaStream_t)stream;
-    BatchWork& B = batch_work(c);
+    BatchWork& B = batch_work(c, s);
     launch_pack_in(c->n_gamma, nrhs, X, B.p, s);
     if (precond)
       precond_b(c, B.p, B.q, s);
@@ -317,7 +383,7 @@ dd_status dd_solve_batch(dd_ctx* c, int32_t nrhs, const double* F, double* X, do
   dd_status result = DD_OK;
   dd_status gs = guard_call([&] {
     cudaStream_t s = (cudaStream_t)stream;
-    BatchWork& B = batch_work(c);
+    BatchWork& B = batch_work(c, s);
     DD_CUDA(cudaEventRecord(c->ev0, s));
     launch_pack_in(c->n_free, nrhs, F, B.F, s);
     condense_b(c, B.F, B.bvec, s);
@@ -326,13 +392,15 @@ dd_status dd_solve_batch(dd_ctx* c, int32_t nrhs, const double* F, double* X, do
     result = pcg_solve_b(c, st, rtol, record, nrhs, stats, s);
     recover_b(c, B.F, B.xg, B.X, s);
     copy_b(st->xg_prev_b, B.xg, c->n_gamma, s);
-    if (record && (result == DD_OK || result == DD_NOT_CONVERGED))
+    if (record && (result == DD_OK || result == DD_NOT_CONVERGED)) {
+      ProfScope pr(c, DD_PROF_RECYCLE, s);
       recycle_update(c, st, (int)st->alphas.size(), s);
-    else
+    } else
       st->step++;
     launch_pack_out(c->n_free, nrhs, B.X, X, s);
     DD_CUDA(cudaEventRecord(c->ev1, s));
     check_err(c, s);
+    if (c->prof_on) c->harvest();
     if (stats) {
       float ms = 0.f;
       DD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));

@@ -19,6 +19,7 @@
 #include "setup.h"
 #include "vecops.h"
 #include "context.h"
+#include "batch.h"
 
 using namespace dd;
 
@@ -382,6 +383,7 @@ dd_status dd_default_options(dd_options* o) {
   o->stop_rhs_norm = 1;
   o->maxit = 500;
   o->local_solver = DD_LOCAL_AUTO;
+  o->ens_nmm = DD_ENS_AUTO;
   return DD_OK;
 }
 
@@ -398,6 +400,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
                "precond_prec must be FP64 or FP32");
     DD_REQUIRE(opt->schur_prec == DD_PREC_FP64 || opt->schur_prec == DD_PREC_DF64, "schur_prec must be FP64 or DF64");
     DD_REQUIRE(opt->maxit >= 1, "maxit must be positive");
+    DD_REQUIRE(opt->ens_nmm >= DD_ENS_AUTO && opt->ens_nmm <= DD_ENS_TC, "ens_nmm must be AUTO, SIMT or TC");
     auto H = std::make_unique<HostSetup>();
     build_host_setup(*md, *opt, *H);
     auto c = std::make_unique<dd_ctx>();
@@ -556,7 +559,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     {
       // algorithmic bytes of one K_II^{-1} application: the operator data read once and the
       // vectors in and out (dense: packed triangles; FDM: 1D eigenbases and D^{-1})
-      double kii = 0, nn = 0;
+      double kii = 0, nn = 0, nne = 0;
       for (int i = 0; i < M.S; ++i) {
         double a = H->l1.sub[i].nI, g = H->l1.sub[i].nG;
         if (H->local_solver == DD_LOCAL_FDM) {
@@ -566,9 +569,12 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
           kii += a * (a + 1) / 2 * 8.0 + 2 * a * 8.0;
         }
         nn += g * (g + 1) / 2 * (pp == DD_PREC_FP32 ? 4.0 : 8.0) + 2 * g * 8.0;
+        // ensemble: the same matrix once, the members' vectors in the preconditioner type
+        nne += g * (g + 1) / 2 * (pp == DD_PREC_FP32 ? 4.0 : 8.0) + 2 * g * BW * (pp == DD_PREC_FP32 ? 4.0 : 8.0);
       }
       c->prof_bytes[DD_PROF_SYMV_KII] = kii;
       c->prof_bytes[DD_PROF_SYMV_N] = nn;
+      c->prof_bytes[DD_PROF_ENS_N] = nne;
     }
     c->info.n_free = c->n_free;
     c->info.n_gamma = c->n_gamma;
@@ -615,6 +621,11 @@ dd_status dd_plan(const dd_mesh_desc* md, const dd_options* opt, dd_info_t* info
 dd_status dd_get_info(const dd_ctx* c, dd_info_t* info) {
   if (!c || !info) return DD_INVALID_ARG;
   *info = c->info;
+  if (c->bw) {
+    info->ens_nmm = c->bw->op[BOP_N1].use_tc ? DD_ENS_TC : DD_ENS_SIMT;
+    info->ens_nmm_ms[0] = c->bw->op[BOP_N1].ms[0];
+    info->ens_nmm_ms[1] = c->bw->op[BOP_N1].ms[1];
+  }
   return DD_OK;
 }
 
@@ -665,6 +676,8 @@ dd_status dd_recycle_create(dd_ctx* c, int32_t k, int32_t strategy, double freez
       st->W2 = st->arena.alloc<double>((size_t)k * n);
       st->AW2 = st->arena.alloc<double>((size_t)k * n);
       st->MAW2 = st->arena.alloc<double>((size_t)k * n);
+      st->Wd = st->arena.alloc<df64>((size_t)k * n);
+      st->AWd = st->arena.alloc<df64>((size_t)k * n);
       st->Ginv = st->arena.alloc<double>((size_t)k * k);
       st->WWinv = st->arena.alloc<double>((size_t)k * k);
       st->hmax = std::min(c->opt.maxit + 1, std::max(16, 128 - k));
@@ -725,6 +738,14 @@ void lincomb_dev(dd_ctx* c, const std::vector<const double*>& V, const std::vect
 }
 
 // G = W^T A W and its inverse (k x k, FP64, on the host)
+// df64 copies of the basis used by the deflation kernels
+void refresh_df(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
+  if (st->k == 0) return;
+  const int64_t kn = (int64_t)st->k * c->n_gamma;
+  to_df64(kn, st->W, st->Wd, s);
+  to_df64(kn, st->AW, st->AWd, s);
+}
+
 void refresh_gram(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
   int k = st->k;
   if (k == 0) return;
@@ -755,6 +776,7 @@ void refresh_gram(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
     }
     DD_CUDA(cudaMemcpyAsync(st->WWinv, WWi.data(), WWi.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
+  refresh_df(c, st, s);
   DD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -889,13 +911,14 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   const int k = st ? st->k : 0;
   const double* W = k ? st->W : nullptr;
   const double* AW = k ? st->AW : nullptr;
+  const df64* Wd = k ? st->Wd : nullptr;
   DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
     vec_sub(n, c->bvec, c->q, c->r, s);
     defl_mu(n, k, W, n, c->r, st->Ginv, c->wpart, c->mu, s);
-    defl_update(n, k, W, n, c->mu, nullptr, c->xg, c->sc, -1, 1.0, s);
+    defl_update_df(n, k, Wd, n, c->mu, nullptr, c->xg, c->sc, -1, 1.0, s);
   }
   schur_apply(c, c->xg, c->q, s);
   vec_sub(n, c->bvec, c->q, c->r, s);
@@ -920,7 +943,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     vec_finalize(c->partials, c->sc, FIN_RZ0, 0, s);
     if (k) {
       defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
-      defl_update(n, k, W, n, c->mu, c->z, c->p, c->sc, -1, -1.0, s);
+      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, -1, -1.0, s);
     } else {
       DD_CUDA(cudaMemcpyAsync(c->p, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
     }
@@ -938,7 +961,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
       if (k && o.reorth) {
         // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
         defl_mu(n, k, W, n, c->r, st->WWinv, c->wpart, c->mu, s);
-        defl_update(n, k, W, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, s);
+        defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, s);
         vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, s);
         vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
       }
@@ -964,7 +987,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
                c->partials, s);
       vec_finalize(c->partials, c->sc, FIN_RZ, o.flexible, s);
       if (k) defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
-      defl_update(n, k, W, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, s);
+      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, s);
     }
   }
   if (stats) {
@@ -1161,6 +1184,8 @@ dd_status dd_recycle_import(dd_ctx* c, const void* host_buf, size_t bytes, dd_re
       DD_CUDA(cudaMemcpy(st->Ginv, p, k * k * 8, cudaMemcpyHostToDevice));
       p += k * k * 8;
       DD_CUDA(cudaMemcpy(st->WWinv, p, k * k * 8, cudaMemcpyHostToDevice));
+      refresh_df(c, st, nullptr);
+      DD_CUDA(cudaStreamSynchronize(nullptr));
     }
   });
   if (rc != DD_OK) {

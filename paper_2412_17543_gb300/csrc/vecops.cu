@@ -3,6 +3,8 @@
 // deflation projection (Algorithm 1: mu = (W^T A W)^{-1} (AW)^T z, p = z + beta p - W mu),
 // and tall-skinny Gram / combination kernels for the recycling update
 // (eq. harmonicRitz).
+#include <algorithm>
+
 #include "vecops.h"
 
 namespace dd {
@@ -135,60 +137,65 @@ void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_
 // ---------------------------------------------------------------------------
 // deflation
 // ---------------------------------------------------------------------------
-// partial dots of the k columns of W (column-major, leading dimension ld) with v; eight
-// columns per sweep so that v is read k/8 times and every W element once
-__global__ void __launch_bounds__(RB) k_wdots(int64_t n, int k, const double* __restrict__ W, int64_t ld,
-                                              const double* __restrict__ v, double* wpart) {
-  __shared__ double sh[8][RB / 32];
+// wpart[b][c] = sum over the rows of chunk b of V_c[i] v[i]: one block per (row chunk,
+// column), so every block streams one contiguous piece of one column (long DRAM bursts)
+// instead of every thread touching all k columns of its row
+__global__ void __launch_bounds__(RB) k_wdots2(int64_t n, int64_t per, const double* __restrict__ V, int64_t ld,
+                                               const double* __restrict__ v, double* wpart) {
+  const int b = blockIdx.x, c = blockIdx.y;
+  const int64_t i0 = (int64_t)b * per, i1 = min(n, i0 + per);
+  const double* col = V + (int64_t)c * ld;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int64_t i = i0 + threadIdx.x;
+  for (; i + 3 * RB < i1; i += 4 * RB) {
+    a0 = fma(col[i], v[i], a0);
+    a1 = fma(col[i + RB], v[i + RB], a1);
+    a2 = fma(col[i + 2 * RB], v[i + 2 * RB], a2);
+    a3 = fma(col[i + 3 * RB], v[i + 3 * RB], a3);
+  }
+  for (; i < i1; i += RB) a0 = fma(col[i], v[i], a0);
+  double x = (a0 + a1) + (a2 + a3);
+  __shared__ double sh[RB / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < k; c0 += 8) {
-    const int nc = min(8, k - c0);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
-      const double vi = v[i];
-#pragma unroll
-      for (int t = 0; t < 8; ++t)
-        if (t < nc) acc[t] = fma(W[(int64_t)(c0 + t) * ld + i], vi, acc[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      double x = acc[t];
-      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) sh[t][warp] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < nc) {
-      double s = 0.0;
-      for (int w2 = 0; w2 < RB / 32; ++w2) s += sh[threadIdx.x][w2];
-      wpart[(int64_t)blockIdx.x * MAXK + c0 + threadIdx.x] = s;
-    }
-    __syncthreads();
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) sh[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < RB / 32; ++w) sum += sh[w];
+    wpart[(int64_t)b * MAXK + c] = sum;
   }
 }
 
-// mu = Ginv * (sum of partials)   (k x k, one block)
-__global__ void k_wfinal(int nblk, int k, const double* __restrict__ wpart, const double* __restrict__ Ginv,
-                         double* mu) {
+// mu = Ginv * (sum of partials)   (k x k, one block of 256 threads): a warp per column
+// sums the block partials (lanes stride over the blocks, fixed shuffle tree), then a warp
+// per output row forms Ginv d the same way
+__global__ void __launch_bounds__(256) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
+                                                const double* __restrict__ Ginv, double* mu) {
   __shared__ double d[MAXK];
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += wpart[(int64_t)b * MAXK + c];
-    d[c] = s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < k; c += nw) {
+    double sum = 0.0;
+    for (int b = lane; b < nblk; b += 32) sum += wpart[(int64_t)b * MAXK + c];
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) d[c] = sum;
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < k; ++c) s += Ginv[a * k + c] * d[c];
-    mu[a] = s;
+  for (int a = warp; a < k; a += nw) {
+    double sum = 0.0;
+    for (int c = lane; c < k; c += 32) sum = fma(Ginv[a * k + c], d[c], sum);
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) mu[a] = sum;
   }
 }
 
 void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, const double* Ginv, double* wpart,
              double* mu, cudaStream_t s) {
   if (k == 0) return;
-  k_wdots<<<NBLK, RB, 0, s>>>(n, k, W, ld, v, wpart);
+  const int64_t per = (n + NBLK - 1) / NBLK;
+  k_wdots2<<<dim3(NBLK, k), RB, 0, s>>>(n, per, W, ld, v, wpart);
   DD_CHECK_LAUNCH();
-  k_wfinal<<<1, 64, 0, s>>>(NBLK, k, wpart, Ginv, mu);
+  k_wfinal<<<1, 256, 0, s>>>(NBLK, k, wpart, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 
@@ -215,29 +222,108 @@ void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu
 }
 
 // ---------------------------------------------------------------------------
+// deflation with the basis stored as df64 (float pairs): the k-column products run on
+// the FP32 pipes with error-free transformations (about 2^-44 relative), FP64 only
+// converts the vector entries and forms the final update
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df64 dbl_to_df(double d) {
+  const float hi = (float)d;
+  return {hi, (float)(d - (double)hi)};
+}
+
+__global__ void k_to_df64(int64_t n, const double* __restrict__ in, df64* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = dbl_to_df(in[i]);
+}
+void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_to_df64<<<NBLK * 2, RB, 0, s>>>(n, in, out);
+  DD_CHECK_LAUNCH();
+}
+
+// y = z + beta y + sign_w W mu over row chunks of PT * RB rows: a block walks the k
+// columns, each a contiguous 16-KiB piece per chunk, and keeps its rows' sums in df64
+constexpr int PT = 4;  // rows per thread
+__global__ void __launch_bounds__(RB) k_pupdate2(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
+                                                 const double* __restrict__ mu, const double* __restrict__ z,
+                                                 double* __restrict__ y, const double* __restrict__ sc, int beta_idx,
+                                                 double sign_w) {
+  __shared__ df64 m[MAXK];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) m[c] = dbl_to_df(sign_w * mu[c]);
+  __syncthreads();
+  const double beta = beta_idx >= 0 ? sc[beta_idx] : 0.0;
+  const int64_t i0 = (int64_t)blockIdx.x * PT * RB + threadIdx.x;
+  df64_acc acc[PT];
+  int c = 0;
+  for (; c + 1 < k; c += 2) {
+    // both columns' entries are loaded before any product (more loads in flight)
+    const df64* c0 = W + (int64_t)c * ld;
+    const df64* c1 = c0 + ld;
+    df64 v0[PT], v1[PT];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      const int64_t i = i0 + (int64_t)r * RB;
+      v0[r] = i < n ? c0[i] : df64{0.f, 0.f};
+      v1[r] = i < n ? c1[i] : df64{0.f, 0.f};
+    }
+    const df64 m0 = m[c], m1 = m[c + 1];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      acc[r].fma(v0[r], m0);
+      acc[r].fma(v1[r], m1);
+    }
+  }
+  if (c < k) {
+    const df64* c0 = W + (int64_t)c * ld;
+    const df64 m0 = m[c];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      const int64_t i = i0 + (int64_t)r * RB;
+      if (i < n) acc[r].fma(c0[i], m0);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PT; ++r) {
+    const int64_t i = i0 + (int64_t)r * RB;
+    if (i < n) {
+      const double v = (z ? z[i] : 0.0) + (beta_idx >= 0 ? beta * y[i] : (z ? 0.0 : y[i]));
+      y[i] = v + df64_to_double(acc[r].get());
+    }
+  }
+}
+
+void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
+                    const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
+  const int64_t blocks = (n + (int64_t)PT * RB - 1) / ((int64_t)PT * RB);
+  k_pupdate2<<<(unsigned)std::max<int64_t>(blocks, 1), RB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  DD_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
 // tall-skinny products for the recycling update
 // ---------------------------------------------------------------------------
-// partial C[a][b] = sum_i X_a[i] Y_b[i] over this block's rows (na, nb <= 128)
-constexpr int GR = 16;  // rows per smem stage (2 x 16 x 129 doubles of static shared memory)
+// partial C[a][b] = sum_i X_a[i] Y_b[i] over this block's rows (na, nb <= 128). The
+// staged rows are converted once to df64 and the products accumulate with error-free
+// FP32 transformations (about 2^-44 relative per product): each staged value feeds up
+// to 128 products, so the FP64 pipe only converts.
+constexpr int GR = 16;  // rows per smem stage (2 x 16 x 129 float pairs of static shared memory)
 __global__ void __launch_bounds__(256) k_gram(int64_t n, int na, const double* const* __restrict__ X, int nb,
                                               const double* const* __restrict__ Y, double* part) {
-  __shared__ double xs[GR][129];
-  __shared__ double ys[GR][129];
+  __shared__ df64 xs[GR][129];
+  __shared__ df64 ys[GR][129];
   const int npair = na * nb;
-  double acc[16];
-#pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  df64_acc acc[16];
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
   for (int64_t base = i0; base < i1; base += GR) {
     int rows = (int)min((int64_t)GR, i1 - base);
     for (int t = threadIdx.x; t < GR * na; t += blockDim.x) {
       int r = t % GR, a = t / GR;
-      xs[r][a] = r < rows ? X[a][base + r] : 0.0;
+      xs[r][a] = dbl_to_df(r < rows ? X[a][base + r] : 0.0);
     }
     for (int t = threadIdx.x; t < GR * nb; t += blockDim.x) {
       int r = t % GR, b = t / GR;
-      ys[r][b] = r < rows ? Y[b][base + r] : 0.0;
+      ys[r][b] = dbl_to_df(r < rows ? Y[b][base + r] : 0.0);
     }
     __syncthreads();
 #pragma unroll
@@ -245,9 +331,7 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int na, const double* c
       int pr = threadIdx.x + t * 256;
       if (pr < npair) {
         int a = pr / nb, b = pr % nb;
-        double s = acc[t];
-        for (int r = 0; r < GR; ++r) s = fma(xs[r][a], ys[r][b], s);
-        acc[t] = s;
+        for (int r = 0; r < GR; ++r) acc[t].fma(xs[r][a], ys[r][b]);
       }
     }
     __syncthreads();
@@ -255,15 +339,19 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int na, const double* c
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     int pr = threadIdx.x + t * 256;
-    if (pr < npair) part[(int64_t)blockIdx.x * npair + pr] = acc[t];
+    if (pr < npair) part[(int64_t)blockIdx.x * npair + pr] = df64_to_double(acc[t].get());
   }
 }
 
-__global__ void k_gram_reduce(int nblk, int npair, const double* __restrict__ part, double* C) {
-  for (int pr = blockIdx.x * blockDim.x + threadIdx.x; pr < npair; pr += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * npair + pr];
-    C[pr] = s;
+// C[pr] = fixed-order sum of the block partials: a warp per pair, lanes over the blocks
+__global__ void __launch_bounds__(256) k_gram_reduce(int nblk, int npair, const double* __restrict__ part,
+                                                     double* C) {
+  const int lane = threadIdx.x & 31;
+  for (int pr = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pr < npair; pr += (gridDim.x * blockDim.x) >> 5) {
+    double sum = 0.0;
+    for (int b = lane; b < nblk; b += 32) sum += part[(int64_t)b * npair + pr];
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) C[pr] = sum;
   }
 }
 
@@ -273,35 +361,36 @@ void gram(int64_t n, int na, const double* const* X, int nb, const double* const
   if (na > 128 || nb > 128 || na * nb > 16 * 256) throw Error(DD_INVALID_ARG, "gram: too many columns");
   k_gram<<<NBLK, 256, 0, s>>>(n, na, X, nb, Y, part);
   DD_CHECK_LAUNCH();
-  k_gram_reduce<<<(na * nb + 255) / 256, 256, 0, s>>>(NBLK, na * nb, part, C);
+  k_gram_reduce<<<std::min(152 * 8, (na * nb + 7) / 8), 256, 0, s>>>(NBLK, na * nb, part, C);
   DD_CHECK_LAUNCH();
 }
 
-// out_c[i] = sum_a V_a[i] Y[a][c]   (Y row-major m x kc)
+// out_c[i] = sum_a V_a[i] Y[a][c]   (Y row-major m x kc); V entries converted once per
+// row to df64, sums with error-free FP32 transformations
 __global__ void k_lincomb(int64_t n, int m, const double* const* __restrict__ V, const double* __restrict__ Yc, int kc,
                           double* const* __restrict__ out) {
-  extern __shared__ double ysm[];
-  for (int t = threadIdx.x; t < m * kc; t += blockDim.x) ysm[t] = Yc[t];
+  extern __shared__ df64 ysm[];
+  for (int t = threadIdx.x; t < m * kc; t += blockDim.x) ysm[t] = dbl_to_df(Yc[t]);
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     for (int c0 = 0; c0 < kc; c0 += 8) {
-      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      df64_acc acc[8];
       for (int a = 0; a < m; ++a) {
-        double v = V[a][i];
+        const df64 v = dbl_to_df(V[a][i]);
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-          if (c0 + t < kc) acc[t] = fma(v, ysm[a * kc + c0 + t], acc[t]);
+          if (c0 + t < kc) acc[t].fma(v, ysm[a * kc + c0 + t]);
       }
 #pragma unroll
       for (int t = 0; t < 8; ++t)
-        if (c0 + t < kc) out[c0 + t][i] = acc[t];
+        if (c0 + t < kc) out[c0 + t][i] = df64_to_double(acc[t].get());
     }
   }
 }
 
 void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s) {
   if (kc == 0) return;
-  size_t smem = (size_t)m * kc * sizeof(double);
+  size_t smem = (size_t)m * kc * sizeof(df64);
   if (smem > 48 * 1024) DD_CUDA(cudaFuncSetAttribute(k_lincomb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_lincomb<<<NBLK, RB, smem, s>>>(n, m, V, Yc, kc, out);
   DD_CHECK_LAUNCH();

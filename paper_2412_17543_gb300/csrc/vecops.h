@@ -28,6 +28,10 @@ void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, con
 // y = z + beta*y + sign_w * W mu  (beta from sc[beta_idx] if beta_idx >= 0; with z == NULL and beta_idx < 0: y += sign_w W mu)
 void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
                  const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+// df64-stored basis (float pairs) variant of defl_update, and the conversion
+void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s);
+void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
+                    const double* sc, int beta_idx, double sign_w, cudaStream_t s);
 void gram(int64_t n, int na, const double* const* X, int nb, const double* const* Y, double* part, double* C,
           cudaStream_t s);
 void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s);

@@ -82,16 +82,29 @@ def test_schur_apply_batch_rejects_df64_dense():
 
 @pytest.mark.parametrize("name", ["cube16_cf", "graded24_s8", "graded16_s2_3l"])
 @pytest.mark.parametrize("weights", ["card", "diag"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
-def test_precond_apply_batch(name, weights, prec, tol):
+@pytest.mark.parametrize("prec,nmm,tol", [("fp64", "auto", 1e-10), ("fp32", "simt", 1e-4), ("fp32", "tc", 1e-4)])
+def test_precond_apply_batch(name, weights, prec, nmm, tol):
+    """BDDC of the ensemble; with FP32 both N_i kernels (CUDA-core tiles and tensor-core
+    3xTF32, including the partial 128-row block of 386-row operators) are checked."""
     m, subs, kinds, levels = case(name)
-    S = P.Solver(m, **_opts(levels, kinds, weights=weights, precond_prec=prec))
+    S = P.Solver(m, **_opts(levels, kinds, weights=weights, precond_prec=prec, ens_nmm=nmm))
     Po = dd.Preconditioner(subs, levels, kinds, weights, group=4)
     R = np.random.default_rng(5).standard_normal((7, len(subs.gamma)))
     Z = N(S.precond_apply_batch(T(R)))
     for j in range(R.shape[0]):
         zo = Po.apply(R[j])
         assert np.abs(Z[j] - zo).max() <= tol * np.abs(zo).max()
+    if prec == "fp32":
+        assert S.info["ens_nmm"] == (2 if nmm == "tc" else 1)
+    S.close()
+
+
+def test_nmm_autotune_picks_a_kernel():
+    m, subs, kinds, levels = case("graded24_s8")
+    S = P.Solver(m, **_opts(2, kinds, precond_prec="fp32", ens_nmm="auto"))
+    S.precond_apply_batch(T(np.ones((2, len(subs.gamma)))))
+    info = S.info
+    assert info["ens_nmm"] in (1, 2) and min(info["ens_nmm_ms"]) > 0.0
     S.close()
 
 
@@ -99,15 +112,16 @@ def _member_sequences(m, nrhs, steps, seed0):
     return [load_sequence(m, seed0 + j, steps) for j in range(nrhs)]
 
 
-@pytest.mark.parametrize("name", ["cube16_cf", "graded16_s2_3l"])
-@pytest.mark.parametrize("schur,pre,flex", [("fp64", "fp64", 0), ("df64", "fp32", 1)])
+@pytest.mark.parametrize("name", ["cube16_cf", "graded16_s2_3l", "graded24_s8"])
+@pytest.mark.parametrize("schur,pre,flex,nmm", [("fp64", "fp64", 0, "auto"), ("df64", "fp32", 1, "simt"),
+                                                ("df64", "fp32", 1, "tc")])
 @pytest.mark.parametrize("k", [0, 6])
-def test_solve_batch_matches_direct(name, schur, pre, flex, k):
+def test_solve_batch_matches_direct(name, schur, pre, flex, nmm, k):
     m, subs, kinds, levels = case(name)
     nrhs, steps = 5, 4
     seqs = _member_sequences(m, nrhs, steps, 30)
     ch = cholesky.factor_mesh(m)
-    S = P.Solver(m, **_opts(levels, kinds, schur_prec=schur, precond_prec=pre, flexible=flex))
+    S = P.Solver(m, **_opts(levels, kinds, schur_prec=schur, precond_prec=pre, flexible=flex, ens_nmm=nmm))
     rec = S.ensemble_recycler(k, "B4")
     iters = []
     for t in range(steps):

@@ -154,6 +154,19 @@ class BumpSequence:
             out += self.a[m] * np.exp(-d2 / (2.0 * self.w[m] ** 2))
         return out
 
+    def f_grid(self, xs: np.ndarray, ys: np.ndarray, zs: np.ndarray, t: int) -> np.ndarray:
+        """f_t on the tensor grid zs x ys x xs (x fastest), using that each bump is a
+        product of one-dimensional Gaussians."""
+        c = self.centres(t)
+        out = np.zeros((len(zs), len(ys), len(xs)))
+        for m in range(self.nbumps):
+            s2 = 2.0 * self.w[m] ** 2
+            gx = np.exp(-((xs - c[m, 0]) ** 2) / s2)
+            gy = np.exp(-((ys - c[m, 1]) ** 2) / s2)
+            gz = self.a[m] * np.exp(-((zs - c[m, 2]) ** 2) / s2)
+            out += gz[:, None, None] * (gy[:, None] * gx[None, :])[None, :, :]
+        return out.ravel()
+
 
 def lumped_nodal_volumes(mesh: Mesh) -> np.ndarray:
     """Volume share of each free node: product over axes of half the adjacent element sizes."""
@@ -179,13 +192,14 @@ def load_vector(mesh: Mesh, seq: BumpSequence, t: int, _cache: dict | None = Non
 def load_sequence(mesh: Mesh, seed: int, steps: int, start: int = 0) -> np.ndarray:
     """[steps, n_free] float64 load vectors for t = start .. start+steps-1."""
     seq = BumpSequence(seed)
-    pts = mesh.free_node_coords()
+    x0, x1, y0, y1, z0, z1 = mesh.free_box
+    xs, ys, zs = mesh.xc[x0:x1], mesh.yc[y0:y1], mesh.zc[z0:z1]
     vol = lumped_nodal_volumes(mesh)
-    out = np.empty((steps, pts.shape[0]))
+    out = np.empty((steps, vol.shape[0]))
     for i in range(steps):
         t = start + i
-        xi = np.random.default_rng([seq.seed, t, 7]).standard_normal(pts.shape[0])
-        out[i] = vol * (seq.f(pts, t) + seq.noise * xi)
+        xi = np.random.default_rng([seq.seed, t, 7]).standard_normal(vol.shape[0])
+        out[i] = vol * (seq.f_grid(xs, ys, zs, t) + seq.noise * xi)
     return out
 
 
