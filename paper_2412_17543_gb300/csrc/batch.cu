@@ -23,7 +23,7 @@ static int grid_for_b(int64_t rows, int rows_per_block) {
 // ---------------------------------------------------------------------------
 // layout conversion (32 x 32 tiles through shared memory, both sides coalesced)
 // ---------------------------------------------------------------------------
-__global__ void k_pack_in(int64_t n, int nrhs, const double* __restrict__ F, double* __restrict__ out) {
+__global__ void k_pack_in(int64_t n, int nrhs, const double* __restrict__ F, df64* __restrict__ out) {
   __shared__ double t[BW][BW + 1];
   const int64_t i0 = (int64_t)blockIdx.x * BW;
   for (int m = threadIdx.y; m < BW; m += blockDim.y) {
@@ -33,16 +33,16 @@ __global__ void k_pack_in(int64_t n, int nrhs, const double* __restrict__ F, dou
   __syncthreads();
   for (int r = threadIdx.y; r < BW; r += blockDim.y) {
     const int64_t i = i0 + r;
-    if (i < n) out[i * BW + threadIdx.x] = t[threadIdx.x][r];
+    if (i < n) out[i * BW + threadIdx.x] = df64_from_double_bits(t[threadIdx.x][r]);
   }
 }
 
-__global__ void k_pack_out(int64_t n, int nrhs, const double* __restrict__ in, double* __restrict__ X) {
+__global__ void k_pack_out(int64_t n, int nrhs, const df64* __restrict__ in, double* __restrict__ X) {
   __shared__ double t[BW][BW + 1];
   const int64_t i0 = (int64_t)blockIdx.x * BW;
   for (int r = threadIdx.y; r < BW; r += blockDim.y) {
     const int64_t i = i0 + r;
-    t[r][threadIdx.x] = (i < n) ? in[i * BW + threadIdx.x] : 0.0;
+    t[r][threadIdx.x] = (i < n) ? df64_to_double_bits(in[i * BW + threadIdx.x]) : 0.0;
   }
   __syncthreads();
   for (int m = threadIdx.y; m < nrhs; m += blockDim.y) {
@@ -51,22 +51,32 @@ __global__ void k_pack_out(int64_t n, int nrhs, const double* __restrict__ in, d
   }
 }
 
-void launch_pack_in(int64_t n, int nrhs, const double* F, double* out, cudaStream_t s) {
+void launch_pack_in(int64_t n, int nrhs, const double* F, df64* out, cudaStream_t s) {
   if (n == 0) return;
   k_pack_in<<<(unsigned)((n + BW - 1) / BW), dim3(BW, 8), 0, s>>>(n, nrhs, F, out);
   DD_CHECK_LAUNCH();
 }
-void launch_pack_out(int64_t n, int nrhs, const double* in, double* X, cudaStream_t s) {
+void launch_pack_out(int64_t n, int nrhs, const df64* in, double* X, cudaStream_t s) {
   if (n == 0) return;
   k_pack_out<<<(unsigned)((n + BW - 1) / BW), dim3(BW, 8), 0, s>>>(n, nrhs, in, X);
   DD_CHECK_LAUNCH();
 }
 
-__global__ void k_extract_col(int64_t n, const double* __restrict__ in, int col, double* __restrict__ out) {
+__global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = in[i * BW + col];
+    out[i] = (float)in[i];
 }
-void launch_extract_col(int64_t n, const double* in, int col, double* out, cudaStream_t s) {
+void launch_to_float(int64_t n, const double* in, float* out, cudaStream_t s) {
+  if (n == 0) return;
+  k_to_float<<<grid_for_b(n, 256), 256, 0, s>>>(n, in, out);
+  DD_CHECK_LAUNCH();
+}
+
+__global__ void k_extract_col(int64_t n, const df64* __restrict__ in, int col, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df64_to_double_bits(in[i * BW + col]);
+}
+void launch_extract_col(int64_t n, const df64* in, int col, double* out, cudaStream_t s) {
   if (n == 0) return;
   k_extract_col<<<grid_for_b(n, 256), 256, 0, s>>>(n, in, col, out);
   DD_CHECK_LAUNCH();
@@ -105,8 +115,8 @@ __device__ __forceinline__ void apply_item_b(const DevMesh& m, const int16_t* it
 // A block takes one subdomain: the element entries are formed once, then the members
 // pass through in chunks of RC (their local values staged in shared memory).
 template <class P, int S, int RC>
-__global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, const double* __restrict__ xg,
-                                                         const double* __restrict__ f, double* __restrict__ tI) {
+__global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, const df64* __restrict__ xg,
+                                                         const df64* __restrict__ f, df64* __restrict__ tI) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_b[];
   V* xl = reinterpret_cast<V*>(smem_b);  // [NL][RC]
@@ -119,7 +129,7 @@ __global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, co
   for (int t = threadIdx.x; t < m.NL * BW; t += blockDim.x) {
     const int l = t / BW, mm = t % BW;
     const int cd = code[l];
-    if (cd >= 0) tI[(io + cd) * BW + mm] = (mode == ELEM_SCHUR) ? 0.0 : f[free_index(m, s, l) * BW + mm];
+    if (cd >= 0) tI[(io + cd) * BW + mm] = (mode == ELEM_SCHUR) ? df64{0.f, 0.f} : f[free_index(m, s, l) * BW + mm];
   }
   if (mode == ELEM_CONDENSE) return;
   build_kd_list<P, S>(m, s, m.type_bl + to[4], to[5] - to[4], kd);
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, co
     for (int t = threadIdx.x; t < m.NL * RC; t += blockDim.x) {
       const int l = t / RC, c = t % RC;
       const int cd = code[l];
-      xl[t] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c])
+      xl[t] = (cd < 0 && cd != INT16_MIN) ? P::from_v(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c])
                                           : P::zero();
     }
     __syncthreads();
@@ -141,18 +151,18 @@ __global__ void __launch_bounds__(512) k_elem_interior_b(DevMesh m, int mode, co
       apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
       const int64_t o = (io + code[l]) * BW + m0 + mm;
       if (mode == ELEM_SCHUR)
-        tI[o] = P::to_d(v);
+        tI[o] = P::to_v(v);
       else
-        tI[o] = f[free_index(m, s, l) * BW + m0 + mm] - P::to_d(v);
+        tI[o] = df64_add(f[free_index(m, s, l) * BW + m0 + mm], df64_neg(P::to_v(v)));
     }
     __syncthreads();
   }
 }
 
 template <class P, int S, int RC>
-__global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, const double* __restrict__ xg,
-                                                          const double* __restrict__ sI,
-                                                          double* __restrict__ yloc) {
+__global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, const df64* __restrict__ xg,
+                                                          const df64* __restrict__ sI,
+                                                          df64* __restrict__ yloc) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_b[];
   V* xl = reinterpret_cast<V*>(smem_b);
@@ -170,9 +180,9 @@ __global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, c
       const int cd = code[l];
       V v = P::zero();
       if (cd >= 0)
-        v = P::from_d(-sI[(m.ioff[s] + cd) * BW + m0 + c]);
+        v = P::from_v(df64_neg(sI[(m.ioff[s] + cd) * BW + m0 + c]));
       else if (cd != INT16_MIN && mode == ELEM_SCHUR)
-        v = P::from_d(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c]);
+        v = P::from_v(xg[(int64_t)m.gmap[m.goff[s] + (-1 - cd)] * BW + m0 + c]);
       xl[t] = v;
     }
     __syncthreads();
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, c
       const int16_t* it = m.type_items + 9 * (size_t)i;
       V v;
       apply_item_b<P, S, RC>(m, it, xl, kd, mm, v);
-      yloc[(m.goff[s] + (-1 - code[it[0]])) * BW + m0 + mm] = P::to_d(v);
+      yloc[(m.goff[s] + (-1 - code[it[0]])) * BW + m0 + mm] = P::to_v(v);
     }
     __syncthreads();
   }
@@ -190,24 +200,22 @@ constexpr int ELEM_RC = 8;        // members per pass of the batched element ker
 constexpr int ELEM_THREADS = 512;
 
 template <class P, int S>
-static void elem_b_go(const DevMesh& m, bool interior, int mode, const double* xg, const double* in, double* out,
+static void elem_b_go(const DevMesh& m, bool interior, int mode, const df64* xg, const df64* in, df64* out,
                       cudaStream_t s) {
   const int NE = m.sx * m.sy * m.sz;
   const size_t smem = ((size_t)m.NL * ELEM_RC + (size_t)NE * 8) * sizeof(typename P::V);
   if (interior) {
-    DD_CUDA(cudaFuncSetAttribute(k_elem_interior_b<P, S, ELEM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    max_smem(k_elem_interior_b<P, S, ELEM_RC>, smem);
     k_elem_interior_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   } else {
-    DD_CUDA(cudaFuncSetAttribute(k_elem_interface_b<P, S, ELEM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    max_smem(k_elem_interface_b<P, S, ELEM_RC>, smem);
     k_elem_interface_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   }
 }
 
 template <class P>
-static void elem_b_dispatch(const DevMesh& m, bool interior, int mode, const double* xg, const double* in,
-                            double* out, cudaStream_t s) {
+static void elem_b_dispatch(const DevMesh& m, bool interior, int mode, const df64* xg, const df64* in,
+                            df64* out, cudaStream_t s) {
   if (m.sx == 8 && m.sy == 8 && m.sz == 8)
     elem_b_go<P, 8>(m, interior, mode, xg, in, out, s);
   else if (m.sx == 4 && m.sy == 4 && m.sz == 4)
@@ -216,7 +224,7 @@ static void elem_b_dispatch(const DevMesh& m, bool interior, int mode, const dou
     elem_b_go<P, 0>(m, interior, mode, xg, in, out, s);
 }
 
-void launch_elem_interior_b(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
+void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI,
                             cudaStream_t s) {
   if (m.schur_prec == DD_PREC_DF64)
     elem_b_dispatch<PolDF>(m, true, mode, xg, f, tI, s);
@@ -225,7 +233,7 @@ void launch_elem_interior_b(const DevMesh& m, int mode, const double* xg, const 
   DD_CHECK_LAUNCH();
 }
 
-void launch_elem_interface_b(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc,
                              cudaStream_t s) {
   if (m.schur_prec == DD_PREC_DF64)
     elem_b_dispatch<PolDF>(m, false, mode, xg, sI, yloc, s);
@@ -278,8 +286,8 @@ __device__ __forceinline__ void fdm_contract_b(const typename P::V* A, int ax, b
 constexpr int FDM_THREADS = 448;  // 7 x 7 lines of 8 members (interior subdomains) in one pass
 
 template <class P, int RC>
-__global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const double* __restrict__ tI,
-                                                     double* __restrict__ sI) {
+__global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const df64* __restrict__ tI,
+                                                              df64* __restrict__ sI) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_f[];
   V* b0 = reinterpret_cast<V*>(smem_f);  // [729][RC]
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const do
   const int N = n[0] * n[1] * n[2];
   const int64_t off = m.ioff[s];
   for (int t = threadIdx.x; t < N * RC; t += blockDim.x)
-    b0[t] = P::from_d(tI[(off + t / RC) * BW + m0 + t % RC]);
+    b0[t] = P::from_v(tI[(off + t / RC) * BW + m0 + t % RC]);
   __syncthreads();
   fdm_contract_b<P, RC>(Vs[0], 0, true, n, b0, b1);
   __syncthreads();
@@ -314,19 +322,28 @@ __global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const do
   __syncthreads();
   fdm_contract_b<P, RC>(Vs[2], 2, false, n, b1, b0);
   __syncthreads();
-  for (int t = threadIdx.x; t < N * RC; t += blockDim.x) sI[(off + t / RC) * BW + m0 + t % RC] = P::to_d(b0[t]);
+  for (int t = threadIdx.x; t < N * RC; t += blockDim.x) sI[(off + t / RC) * BW + m0 + t % RC] = P::to_v(b0[t]);
 }
 
 constexpr int FDM_RC = 8;
 
 template <class P>
-static void fdm_b_go(const DevMesh& m, const double* tI, double* sI, cudaStream_t s) {
+static void fdm_b_go(const DevMesh& m, const df64* tI, df64* sI, cudaStream_t s) {
   const size_t smem = (size_t)2 * 729 * FDM_RC * sizeof(typename P::V);
-  DD_CUDA(cudaFuncSetAttribute(k_fdm_apply_b<P, FDM_RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  max_smem(k_fdm_apply_b<P, FDM_RC>, smem);
   k_fdm_apply_b<P, FDM_RC><<<dim3(m.S, BW / FDM_RC), FDM_THREADS, smem, s>>>(m, tI, sI);
 }
 
-void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStream_t s) {
+__global__ void k_df_to_dbl(int64_t n, const df64* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df64_to_double_bits(in[i]);
+}
+__global__ void k_dbl_to_df(int64_t n, const double* __restrict__ in, df64* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df64_from_double_bits(in[i]);
+}
+
+void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, cudaStream_t s) {
   if (m.local_solver == DD_LOCAL_FDM) {
     if (m.schur_prec == DD_PREC_DF64)
       fdm_b_go<PolDF>(m, tI, sI, s);
@@ -334,8 +351,14 @@ void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStre
       fdm_b_go<PolF64>(m, tI, sI, s);
     DD_CHECK_LAUNCH();
   } else {
-    // dense K_II^{-1}: FP64 tiles only (the caller rejects df64 dense ensembles)
-    launch_symm_b(m.KIIinv, m.ioff, tI, sI, s);
+    // dense K_II^{-1} (FP64 tiles; the caller rejects df64 dense ensembles): the tiles work
+    // on doubles, so the block passes through tmp ([n_int][BW] doubles) both ways
+    const int64_t nn = m.n_int * BW;
+    k_df_to_dbl<<<grid_for_b(nn, 256), 256, 0, s>>>(nn, tI, tmp);
+    DD_CHECK_LAUNCH();
+    launch_symm_b(m.KIIinv, m.ioff, tmp, tmp, s);
+    k_dbl_to_df<<<grid_for_b(nn, 256), 256, 0, s>>>(nn, tmp, sI);
+    DD_CHECK_LAUNCH();
   }
 }
 
@@ -343,25 +366,27 @@ void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStre
 // gathers and scatters (warp = one row, lane = member)
 // ---------------------------------------------------------------------------
 __global__ void k_gather_b(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
-                           const double* __restrict__ loc, const double* __restrict__ base,
-                           const int64_t* __restrict__ bmap, double* __restrict__ y) {
+                           const df64* __restrict__ loc, const df64* __restrict__ base,
+                           const int64_t* __restrict__ bmap, df64* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < n;
        g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double s = base ? base[(bmap ? bmap[g] : g) * BW + lane] : 0.0;
-    for (int k = ptr[g]; k < ptr[g + 1]; ++k) s += loc[(int64_t)idx[k] * BW + lane];
-    y[g * BW + lane] = s;
+    // copies summed in df64 in the fixed copy order
+    df64_acc sum;
+    if (base) sum.add(base[(bmap ? bmap[g] : g) * BW + lane]);
+    for (int k = ptr[g]; k < ptr[g + 1]; ++k) sum.add(loc[(int64_t)idx[k] * BW + lane]);
+    y[g * BW + lane] = sum.get();
   }
 }
-void launch_gather_b(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
-                     const int64_t* bmap, double* y, cudaStream_t s) {
+void launch_gather_b(int64_t n, const int* ptr, const int* idx, const df64* loc, const df64* base,
+                     const int64_t* bmap, df64* y, cudaStream_t s) {
   if (n == 0) return;
   k_gather_b<<<grid_for_b(n, 8), 256, 0, s>>>(n, ptr, idx, loc, base, bmap, y);
   DD_CHECK_LAUNCH();
 }
 
-__global__ void k_scatter_recover_b(DevMesh m, const double* __restrict__ xg, const double* __restrict__ sI,
-                                    double* __restrict__ x) {
+__global__ void k_scatter_recover_b(DevMesh m, const df64* __restrict__ xg, const df64* __restrict__ sI,
+                                    df64* __restrict__ x) {
   const int s = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
@@ -375,26 +400,33 @@ __global__ void k_scatter_recover_b(DevMesh m, const double* __restrict__ xg, co
     if (m.gidx[m.gptr[g]] == (int)k) x[m.gamma_free[g] * BW + lane] = xg[(int64_t)g * BW + lane];
   }
 }
-void launch_scatter_recover_b(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s) {
+void launch_scatter_recover_b(const DevMesh& m, const df64* xg, const df64* sI, df64* x, cudaStream_t s) {
   k_scatter_recover_b<<<m.S, 256, 0, s>>>(m, xg, sI, x);
   DD_CHECK_LAUNCH();
 }
 
+// rloc = D_k r with r in df64: the FP32 preconditioner takes the float weight times the
+// float sum of the pair; the FP64 one widens both
 template <class T>
-__global__ void k_restrict_b(int64_t nflat, const int* __restrict__ gmap, const double* __restrict__ D,
-                             const double* __restrict__ r, T* __restrict__ rloc) {
+__global__ void k_restrict_b(int64_t nflat, const int* __restrict__ gmap, const float* __restrict__ Df,
+                             const double* __restrict__ D, const df64* __restrict__ r, T* __restrict__ rloc) {
   const int lane = threadIdx.x & 31;
   for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; k < nflat;
-       k += ((int64_t)gridDim.x * blockDim.x) >> 5)
-    rloc[k * BW + lane] = (T)(D[k] * r[(int64_t)gmap[k] * BW + lane]);
+       k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const df64 rv = r[(int64_t)gmap[k] * BW + lane];
+    if (sizeof(T) == 4)
+      rloc[k * BW + lane] = (T)(Df[k] * (rv.hi + rv.lo));
+    else
+      rloc[k * BW + lane] = (T)(D[k] * df64_to_double_bits(rv));
+  }
 }
-void launch_restrict_b(int prec, int64_t nflat, const int* gmap, const double* D, const double* r, void* rloc,
-                       cudaStream_t s) {
+void launch_restrict_b(int prec, int64_t nflat, const int* gmap, const float* Df, const double* D, const df64* r,
+                       void* rloc, cudaStream_t s) {
   if (nflat == 0) return;
   if (prec == DD_PREC_FP32)
-    k_restrict_b<float><<<grid_for_b(nflat, 8), 256, 0, s>>>(nflat, gmap, D, r, (float*)rloc);
+    k_restrict_b<float><<<grid_for_b(nflat, 8), 256, 0, s>>>(nflat, gmap, Df, D, r, (float*)rloc);
   else
-    k_restrict_b<double><<<grid_for_b(nflat, 8), 256, 0, s>>>(nflat, gmap, D, r, (double*)rloc);
+    k_restrict_b<double><<<grid_for_b(nflat, 8), 256, 0, s>>>(nflat, gmap, Df, D, r, (double*)rloc);
   DD_CHECK_LAUNCH();
 }
 
@@ -469,27 +501,38 @@ void launch_gather_tb(int prec, int64_t n, const int* ptr, const int* idx, const
 
 template <class T>
 __global__ void k_wgather_b(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
-                            const double* __restrict__ D, const T* __restrict__ uloc, const T* __restrict__ vloc,
-                            double* __restrict__ z) {
+                            const float* __restrict__ Df, const double* __restrict__ D, const T* __restrict__ uloc,
+                            const T* __restrict__ vloc, df64* __restrict__ z) {
   const int lane = threadIdx.x & 31;
   for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < n;
        g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    double acc = 0.0;
-    for (int t = ptr[g]; t < ptr[g + 1]; ++t) {
-      const int64_t k = idx[t];
-      acc = fma(D[k], (double)(uloc[k * BW + lane] + vloc[k * BW + lane]), acc);
+    if (sizeof(T) == 4) {
+      // D_k (u + v): exact float products summed in df64
+      df64_acc acc;
+      for (int t = ptr[g]; t < ptr[g + 1]; ++t) {
+        const int64_t k = idx[t];
+        acc.fma(df64{Df[k], 0.f}, df64{(float)(uloc[k * BW + lane] + vloc[k * BW + lane]), 0.f});
+      }
+      z[g * BW + lane] = acc.get();
+    } else {
+      double acc = 0.0;
+      for (int t = ptr[g]; t < ptr[g + 1]; ++t) {
+        const int64_t k = idx[t];
+        acc = fma(D[k], (double)(uloc[k * BW + lane] + vloc[k * BW + lane]), acc);
+      }
+      z[g * BW + lane] = df64_from_double_bits(acc);
     }
-    z[g * BW + lane] = acc;
   }
 }
-void launch_wgather_b(int prec, int64_t n, const int* ptr, const int* idx, const double* D, const void* uloc,
-                      const void* vloc, double* z, cudaStream_t s) {
+void launch_wgather_b(int prec, int64_t n, const int* ptr, const int* idx, const float* Df, const double* D,
+                      const void* uloc, const void* vloc, df64* z, cudaStream_t s) {
   if (n == 0) return;
   if (prec == DD_PREC_FP32)
-    k_wgather_b<float><<<grid_for_b(n, 8), 256, 0, s>>>(n, ptr, idx, D, (const float*)uloc, (const float*)vloc, z);
+    k_wgather_b<float><<<grid_for_b(n, 8), 256, 0, s>>>(n, ptr, idx, Df, D, (const float*)uloc,
+                                                        (const float*)vloc, z);
   else
-    k_wgather_b<double><<<grid_for_b(n, 8), 256, 0, s>>>(n, ptr, idx, D, (const double*)uloc, (const double*)vloc,
-                                                         z);
+    k_wgather_b<double><<<grid_for_b(n, 8), 256, 0, s>>>(n, ptr, idx, Df, D, (const double*)uloc,
+                                                         (const double*)vloc, z);
   DD_CHECK_LAUNCH();
 }
 
@@ -591,12 +634,12 @@ void launch_symm_b(const SymTiles& A, const int64_t* voff, const void* in, void*
   const int npad = ((A.max_n + 31) / 32) * 32;
   if (A.prec == DD_PREC_FP32) {
     const size_t smem = (size_t)npad * BW * 4;
-    DD_CUDA(cudaFuncSetAttribute(k_symm_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    max_smem(k_symm_b<float>, smem);
     k_symm_b<float><<<A.count, SYMM_WARPS * 32, smem, s>>>(A, voff, (const float*)in, (float*)out);
   } else if (A.prec == DD_PREC_FP64) {
     const size_t smem = (size_t)npad * BW * 8;
     DD_REQUIRE(smem <= 227 * 1024, "ensemble: local matrix too large for the batched tile kernel");
-    DD_CUDA(cudaFuncSetAttribute(k_symm_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    max_smem(k_symm_b<double>, smem);
     k_symm_b<double><<<A.count, SYMM_WARPS * 32, smem, s>>>(A, voff, (const double*)in, (double*)out);
   } else {
     throw Error(DD_INVALID_ARG, "ensemble: df64 dense tiles are not supported by the batched path");
@@ -716,7 +759,7 @@ static void bmm_go(const BatchedRows& B, bool trans, const int64_t* in_off, cons
   const T* Md = static_cast<const T*>(B.data);
   if (trans) {
     if (stage) {
-      DD_CUDA(cudaFuncSetAttribute(k_bmm_t<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      max_smem(k_bmm_t<T, true>, smem);
       k_bmm_t<T, true><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
                                                (T*)out, (T)alpha, (const T*)add);
     } else {
@@ -725,7 +768,7 @@ static void bmm_go(const BatchedRows& B, bool trans, const int64_t* in_off, cons
     }
   } else {
     if (stage) {
-      DD_CUDA(cudaFuncSetAttribute(k_bmm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      max_smem(k_bmm<T, true>, smem);
       k_bmm<T, true><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, Md, in_off, in_map, (const T*)in, out_off,
                                              (T*)out, (T)alpha, (const T*)add);
     } else {
@@ -807,31 +850,41 @@ __device__ __forceinline__ void bblock_store(const double* v, int nd, double* pa
   }
 }
 
-__global__ void __launch_bounds__(BRB) k_bdots(int64_t n, const double* __restrict__ a0,
-                                               const double* __restrict__ b0, const double* __restrict__ a1,
-                                               const double* __restrict__ b1, double* partials) {
+// member dots of df64 vectors, accumulated in df64 on the FP32 pipes
+__global__ void __launch_bounds__(BRB) k_bdots(int64_t n, const df64* __restrict__ a0, const df64* __restrict__ b0,
+                                               const df64* __restrict__ a1, const df64* __restrict__ b1,
+                                               double* partials) {
   const int lane = threadIdx.x & 31;
-  double v[2] = {0.0, 0.0};
+  df64_acc s0, s1;
   for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
-    v[0] = fma(a0[i * BW + lane], b0[i * BW + lane], v[0]);
-    if (a1) v[1] = fma(a1[i * BW + lane], b1[i * BW + lane], v[1]);
+    s0.fma(a0[i * BW + lane], b0[i * BW + lane]);
+    if (a1) s1.fma(a1[i * BW + lane], b1[i * BW + lane]);
   }
+  double v[2] = {df64_to_double_bits(s0.get()), df64_to_double_bits(s1.get())};
   bblock_store(v, 2, partials);
 }
 
-__global__ void __launch_bounds__(BRB) k_baxpy2(int64_t n, const double* __restrict__ sc, double* __restrict__ x,
-                                                const double* __restrict__ p, double* __restrict__ r,
-                                                const double* __restrict__ q, double* partials) {
+// x += alpha p ; r -= alpha q ; partial ||r||^2   (per member alpha, df64 arithmetic)
+__global__ void __launch_bounds__(BRB) k_baxpy2(int64_t n, const double* __restrict__ sc, df64* __restrict__ x,
+                                                const df64* __restrict__ p, df64* __restrict__ r,
+                                                const df64* __restrict__ q, double* partials) {
   const int lane = threadIdx.x & 31;
-  const double alpha = sc[BS_ALPHA * BW + lane];
-  double v[1] = {0.0};
+  const df64 alpha = df64_from_double_bits(sc[BS_ALPHA * BW + lane]);
+  const df64 malpha = df64_neg(alpha);
+  df64_acc rr;
   for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
     const int64_t o = i * BW + lane;
-    x[o] = fma(alpha, p[o], x[o]);
-    const double ri = fma(-alpha, q[o], r[o]);
+    df64_acc xa, ra;
+    xa.add(x[o]);
+    xa.fma(alpha, p[o]);
+    x[o] = xa.get();
+    ra.add(r[o]);
+    ra.fma(malpha, q[o]);
+    const df64 ri = ra.get();
     r[o] = ri;
-    v[0] = fma(ri, ri, v[0]);
+    rr.fma(ri, ri);
   }
+  double v[1] = {df64_to_double_bits(rr.get())};
   bblock_store(v, 1, partials);
 }
 
@@ -927,7 +980,7 @@ __global__ void __launch_bounds__(BFIN_WARPS * 32) k_bfinalize(int nblk, const d
   }
 }
 
-void bvec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, double* partials,
+void bvec_dots(int64_t n, const df64* a0, const df64* b0, const df64* a1, const df64* b1, double* partials,
                cudaStream_t s) {
   k_bdots<<<NBLKB, BRB, 0, s>>>(n, a0, b0, a1, b1, partials);
   DD_CHECK_LAUNCH();
@@ -936,17 +989,17 @@ void bvec_finalize(const double* partials, double* sc, int op, int flexible, cud
   k_bfinalize<<<1, BFIN_WARPS * 32, 0, s>>>(NBLKB, partials, sc, op, flexible);
   DD_CHECK_LAUNCH();
 }
-void bvec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q,
-                double* partials, cudaStream_t s) {
+void bvec_axpy2(int64_t n, const double* sc, df64* x, const df64* p, df64* r, const df64* q, double* partials,
+                cudaStream_t s) {
   k_baxpy2<<<NBLKB, BRB, 0, s>>>(n, sc, x, p, r, q, partials);
   DD_CHECK_LAUNCH();
 }
 
-__global__ void k_bsub(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y) {
+__global__ void k_bsub(int64_t n, const df64* __restrict__ a, const df64* __restrict__ b, df64* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a[i] - b[i];
+    y[i] = df64_add(a[i], df64_neg(b[i]));
 }
-void bvec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s) {
+void bvec_sub(int64_t n, const df64* a, const df64* b, df64* y, cudaStream_t s) {
   k_bsub<<<NBLK, BRB, 0, s>>>(n * BW, a, b, y);
   DD_CHECK_LAUNCH();
 }
@@ -964,51 +1017,63 @@ void bvec_init(double* sc, int nrhs, double rtol, int stop_rhs_norm, cudaStream_
   DD_CHECK_LAUNCH();
 }
 
-// deflation with a basis shared by the ensemble: wpart[blk][j][m] = partial sum_i V[j][i] v[i][m]
-__global__ void __launch_bounds__(BRB) k_bwdots(int64_t n, int k, const double* __restrict__ V, int64_t ld,
-                                                const double* __restrict__ v, double* wpart) {
-  __shared__ double sh[8][BRB / 32][BW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < k; c0 += 8) {
-    const int nc = min(8, k - c0);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
-      const double vi = v[i * BW + lane];
-#pragma unroll
-      for (int t = 0; t < 8; ++t)
-        if (t < nc) acc[t] = fma(V[(int64_t)(c0 + t) * ld + i], vi, acc[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) sh[t][warp][lane] = acc[t];
+// ---------------------------------------------------------------------------
+// deflation with the basis W shared by the ensemble, as blocked GEMMs in df64:
+//   mu = G (W^T Z)             Z: [n][BW]   W: k columns of length n (stride ld)
+//   Y = Z + beta Y + s W mu    (per member beta)
+// A block takes DROWS rows: the slice of W (16 columns at a time) and of Z is staged in
+// shared memory with coalesced loads, so every element of W and Z is read once from HBM.
+// ---------------------------------------------------------------------------
+constexpr int DROWS = 128;  // rows per block
+constexpr int DCOLS = 16;   // basis columns per stage
+
+int defl_blocks(int64_t n) { return (int)((n + DROWS - 1) / DROWS); }
+
+// wpart[b][c][m] = sum over the rows of block b of W[c][i] Z[i][m]  (df64 partials)
+__global__ void __launch_bounds__(256) k_bwdots3(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
+                                                 const df64* __restrict__ Z, df64* __restrict__ wpart) {
+  __shared__ df64 zs[DROWS][BW];      // 32 KiB
+  __shared__ df64 ws[DCOLS][DROWS];   // 16 KiB
+  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
+  const int rows = (int)min((int64_t)DROWS, n - r0);
+  for (int t = threadIdx.x; t < DROWS * BW; t += blockDim.x) {
+    const int r = t / BW, m = t % BW;
+    zs[r][m] = r < rows ? Z[(r0 + r) * BW + m] : df64{0.f, 0.f};
+  }
+  const int m = threadIdx.x & 31, cw = threadIdx.x >> 5;  // 8 warps: columns cw and cw + 8 of a stage
+  for (int c0 = 0; c0 < k; c0 += DCOLS) {
+    const int nc = min(DCOLS, k - c0);
     __syncthreads();
-    for (int q = threadIdx.x; q < nc * BW; q += blockDim.x) {
-      const int t = q / BW, m = q % BW;
-      double s = 0.0;
-      for (int w = 0; w < BRB / 32; ++w) s += sh[t][w][m];
-      wpart[((int64_t)blockIdx.x * MAXK + c0 + t) * BW + m] = s;
+    for (int t = threadIdx.x; t < DCOLS * DROWS; t += blockDim.x) {
+      const int c = t / DROWS, r = t % DROWS;
+      ws[c][r] = (c < nc && r < rows) ? W[(int64_t)(c0 + c) * ld + r0 + r] : df64{0.f, 0.f};
     }
     __syncthreads();
+    df64_acc a0, a1;
+#pragma unroll 4
+    for (int r = 0; r < DROWS; ++r) {
+      const df64 z = zs[r][m];
+      a0.fma(ws[cw][r], z);
+      a1.fma(ws[cw + 8][r], z);
+    }
+    if (cw < nc) wpart[((int64_t)blockIdx.x * k + c0 + cw) * BW + m] = a0.get();
+    if (cw + 8 < nc) wpart[((int64_t)blockIdx.x * k + c0 + cw + 8) * BW + m] = a1.get();
   }
 }
 
-// d[c][m] = fixed-order sum of the block partials (one block per column c: warp w takes
-// the blocks w, w + 8, ..., warp 0 adds the warp sums in order); written into mu
-__global__ void __launch_bounds__(1024) k_bwsum(int nblk, const double* __restrict__ wpart, double* d) {
-  __shared__ double part[32][BW];
+// d[c][m] = fixed-order sum of the block partials (one block per column c; warp w takes
+// the blocks w, w + 32, ...; warp 0 adds the warp sums in order), written into mu
+__global__ void __launch_bounds__(1024) k_bwsum(int nblk, int k, const df64* __restrict__ wpart, double* d) {
+  __shared__ df64 part[32][BW];
   const int c = blockIdx.x, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  double a0 = 0.0, a1 = 0.0;
-  int b = w;
-  for (; b + 32 < nblk; b += 64) {
-    a0 += wpart[((int64_t)b * MAXK + c) * BW + l];
-    a1 += wpart[((int64_t)(b + 32) * MAXK + c) * BW + l];
-  }
-  if (b < nblk) a0 += wpart[((int64_t)b * MAXK + c) * BW + l];
-  part[w][l] = a0 + a1;
+  df64_acc a;
+  for (int b = w; b < nblk; b += 32) a.add(wpart[((int64_t)b * k + c) * BW + l]);
+  part[w][l] = a.get();
   __syncthreads();
   if (w == 0) {
-    double sum = 0.0;
-    for (int q = 0; q < 32; ++q) sum += part[q][l];
-    d[c * BW + l] = sum;
+    df64_acc sum;
+    for (int q = 0; q < 32; ++q) sum.add(part[q][l]);
+    d[c * BW + l] = df64_to_double_bits(sum.get());
   }
 }
 
@@ -1030,115 +1095,70 @@ __global__ void __launch_bounds__(256) k_bwfinal(int k, const double* __restrict
   }
 }
 
-void bdefl_mu(int64_t n, int k, const double* V, int64_t ld, const double* v, const double* G, double* wpart,
-              double* mu, cudaStream_t s) {
+void bdefl_mu(int64_t n, int k, const df64* W, int64_t ld, const df64* Z, const double* G, df64* wpart, double* mu,
+              cudaStream_t s) {
   if (k == 0) return;
-  k_bwdots<<<NBLKB, BRB, 0, s>>>(n, k, V, ld, v, wpart);
+  const int nb = defl_blocks(n);
+  k_bwdots3<<<nb, 256, 0, s>>>(n, k, W, ld, Z, wpart);
   DD_CHECK_LAUNCH();
-  k_bwsum<<<k, 1024, 0, s>>>(NBLKB, wpart, mu);
+  k_bwsum<<<k, 1024, 0, s>>>(nb, k, wpart, mu);
   DD_CHECK_LAUNCH();
   k_bwfinal<<<1, 256, 0, s>>>(k, G, mu);
   DD_CHECK_LAUNCH();
 }
 
-__global__ void __launch_bounds__(BRB) k_bpupdate(int64_t n, int k, const double* __restrict__ W, int64_t ld,
-                                                  const double* __restrict__ mu, const double* __restrict__ z,
-                                                  double* __restrict__ y, const double* __restrict__ sc,
-                                                  int beta_idx, double sign_w) {
-  __shared__ double mus[MAXK][BW];
-  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) mus[q / BW][q % BW] = mu[q];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const double beta = beta_idx >= 0 ? sc[beta_idx * BW + lane] : 0.0;
-  for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
-    const int64_t o = i * BW + lane;
-    double v = (z ? z[o] : 0.0) + (beta_idx >= 0 ? beta * y[o] : (z ? 0.0 : y[o]));
-    double w0 = 0.0, w1 = 0.0;
-    int c = 0;
-    for (; c + 1 < k; c += 2) {
-      w0 = fma(W[(int64_t)c * ld + i], mus[c][lane], w0);
-      w1 = fma(W[(int64_t)(c + 1) * ld + i], mus[c + 1][lane], w1);
+// Y = Z + beta Y + sign W mu; warp = 16 rows, lane = member, the sums kept in registers
+// while the basis columns pass through shared memory
+__global__ void __launch_bounds__(256) k_bpupdate3(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
+                                                   const double* __restrict__ mu, const df64* __restrict__ Z,
+                                                   df64* __restrict__ Y, const double* __restrict__ sc, int beta_idx,
+                                                   double sign_w) {
+  __shared__ df64 mus[MAXK][BW];      // 32 KiB
+  __shared__ df64 ws[DCOLS][DROWS];   // 16 KiB
+  constexpr int RPW = DROWS / 8;      // rows per warp
+  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) mus[q / BW][q % BW] = df64_from_double_bits(sign_w * mu[q]);
+  const int64_t r0 = (int64_t)blockIdx.x * DROWS;
+  const int rows = (int)min((int64_t)DROWS, n - r0);
+  const int m = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const df64 beta = df64_from_double_bits(beta_idx >= 0 ? sc[beta_idx * BW + m] : 0.0);
+  df64_acc acc[RPW];
+#pragma unroll
+  for (int j = 0; j < RPW; ++j) {
+    const int r = w * RPW + j;
+    if (r < rows) {
+      const int64_t o = (r0 + r) * BW + m;
+      if (Z) acc[j].add(Z[o]);
+      if (beta_idx >= 0)
+        acc[j].fma(beta, Y[o]);
+      else if (!Z)
+        acc[j].add(Y[o]);
     }
-    if (c < k) w0 = fma(W[(int64_t)c * ld + i], mus[c][lane], w0);
-    y[o] = v + sign_w * (w0 + w1);
+  }
+  for (int c0 = 0; c0 < k; c0 += DCOLS) {
+    const int nc = min(DCOLS, k - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < DCOLS * DROWS; t += blockDim.x) {
+      const int c = t / DROWS, r = t % DROWS;
+      ws[c][r] = (c < nc && r < rows) ? W[(int64_t)(c0 + c) * ld + r0 + r] : df64{0.f, 0.f};
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      const df64 mc = mus[c0 + c][m];
+#pragma unroll
+      for (int j = 0; j < RPW; ++j) acc[j].fma(ws[c][w * RPW + j], mc);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RPW; ++j) {
+    const int r = w * RPW + j;
+    if (r < rows) Y[(r0 + r) * BW + m] = acc[j].get();
   }
 }
 
-void bdefl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
+void bdefl_update(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const df64* Z, df64* Y,
                   const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
-  k_bpupdate<<<NBLKB, BRB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
-  DD_CHECK_LAUNCH();
-}
-
-// deflation with the df64-stored shared basis (float pairs, error-free FP32 arithmetic)
-__device__ __forceinline__ df64 dbl_to_df_b(double d) {
-  const float hi = (float)d;
-  return {hi, (float)(d - (double)hi)};
-}
-
-__global__ void __launch_bounds__(BRB) k_bwdots_df(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
-                                                   const double* __restrict__ v, double* wpart) {
-  __shared__ double sh[8][BRB / 32][BW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < k; c0 += 8) {
-    const int nc = min(8, k - c0);
-    df64_acc acc[8];
-    for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
-      const df64 vi = dbl_to_df_b(v[i * BW + lane]);
-#pragma unroll
-      for (int t = 0; t < 8; ++t)
-        if (t < nc) acc[t].fma(V[(int64_t)(c0 + t) * ld + i], vi);
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) sh[t][warp][lane] = df64_to_double(acc[t].get());
-    __syncthreads();
-    for (int q = threadIdx.x; q < nc * BW; q += blockDim.x) {
-      const int t = q / BW, m = q % BW;
-      double sum = 0.0;
-      for (int w = 0; w < BRB / 32; ++w) sum += sh[t][w][m];
-      wpart[((int64_t)blockIdx.x * MAXK + c0 + t) * BW + m] = sum;
-    }
-    __syncthreads();
-  }
-}
-
-void bdefl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* G, double* wpart,
-                 double* mu, cudaStream_t s) {
-  if (k == 0) return;
-  k_bwdots_df<<<NBLKB, BRB, 0, s>>>(n, k, V, ld, v, wpart);
-  DD_CHECK_LAUNCH();
-  k_bwsum<<<k, 1024, 0, s>>>(NBLKB, wpart, mu);
-  DD_CHECK_LAUNCH();
-  k_bwfinal<<<1, 256, 0, s>>>(k, G, mu);
-  DD_CHECK_LAUNCH();
-}
-
-__global__ void __launch_bounds__(BRB) k_bpupdate_df(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
-                                                     const double* __restrict__ mu, const double* __restrict__ z,
-                                                     double* __restrict__ y, const double* __restrict__ sc,
-                                                     int beta_idx, double sign_w) {
-  __shared__ df64 mus[MAXK][BW];
-  for (int q = threadIdx.x; q < k * BW; q += blockDim.x) mus[q / BW][q % BW] = dbl_to_df_b(sign_w * mu[q]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const double beta = beta_idx >= 0 ? sc[beta_idx * BW + lane] : 0.0;
-  for (int64_t i = (blockIdx.x * (int64_t)BRB + threadIdx.x) >> 5; i < n; i += ((int64_t)gridDim.x * BRB) >> 5) {
-    const int64_t o = i * BW + lane;
-    const double v = (z ? z[o] : 0.0) + (beta_idx >= 0 ? beta * y[o] : (z ? 0.0 : y[o]));
-    df64_acc a0, a1;
-    int c = 0;
-    for (; c + 1 < k; c += 2) {
-      a0.fma(W[(int64_t)c * ld + i], mus[c][lane]);
-      a1.fma(W[(int64_t)(c + 1) * ld + i], mus[c + 1][lane]);
-    }
-    if (c < k) a0.fma(W[(int64_t)c * ld + i], mus[c][lane]);
-    y[o] = v + df64_to_double(df64_add(a0.get(), a1.get()));
-  }
-}
-
-void bdefl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
-                     const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
-  k_bpupdate_df<<<NBLKB, BRB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  if (n == 0) return;
+  k_bpupdate3<<<defl_blocks(n), 256, 0, s>>>(n, k, W, ld, mu, Z, Y, sc, beta_idx, sign_w);
   DD_CHECK_LAUNCH();
 }
 

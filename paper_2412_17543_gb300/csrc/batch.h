@@ -23,21 +23,24 @@ enum {
 };
 enum { BFIN_PQ = 1, BFIN_RR, BFIN_RZ0, BFIN_RZ, BFIN_BB };
 
-// scratch of the batched operators, interleaved [rows][BW]; BDDC vectors in the
-// preconditioner's type (float for FP32, double for FP64)
+// scratch of the batched operators, interleaved [rows][BW]: the Krylov and local vectors
+// of the Schur operator in df64 (float pairs: the ensemble's steps run on the FP32 pipes,
+// FP64 only at the boundary), the BDDC vectors in the preconditioner's type (float for
+// FP32, double for FP64)
 struct BatchWork {
   DeviceArena arena;
-  int kmax = 0;
-  double *tI = nullptr, *sI = nullptr, *yloc = nullptr;
+  df64 *tI = nullptr, *sI = nullptr, *yloc = nullptr;
+  double* kii_tmp = nullptr;          // [n_int][BW] doubles (dense K_II^{-1} only)
+  float* D1f = nullptr;               // level-1 BDDC weights as floats
   void *rloc = nullptr, *uloc = nullptr, *vloc = nullptr, *gloc = nullptr, *gC = nullptr, *uC = nullptr;
   void *gI2 = nullptr, *u0I2 = nullptr, *rl2 = nullptr, *r2 = nullptr, *rloc2 = nullptr, *uloc2 = nullptr,
        *vloc2 = nullptr, *gloc2 = nullptr, *g3 = nullptr, *u3 = nullptr, *z2 = nullptr, *uI2 = nullptr;
-  double *xg = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr;
-  double *F = nullptr, *X = nullptr;  // [n_free][BW]
+  df64 *xg = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr;
+  df64 *F = nullptr, *X = nullptr;    // [n_free][BW]
   double* sc = nullptr;               // [BS_COUNT][BW]
   double* sc_host = nullptr;          // pinned mirror
   double* partials = nullptr;         // [NBLKB][4][BW]
-  double* wpart = nullptr;            // [NBLKB][MAXK][BW]
+  df64* wpart = nullptr;              // [deflation blocks][MAXK][BW]
   double* mu = nullptr;               // [MAXK][BW]
   // symmetric products of the ensemble (level-1 N_i; level-2 K_II^{-1} and N): tensor-core
   // operand copy, whether it is used, and the selection timings (SIMT, tensor cores)
@@ -51,27 +54,29 @@ enum { BOP_N1 = 0, BOP_KII2 = 1, BOP_N2 = 2 };
 
 // ---- layout ----
 // out[i * BW + m] = m < nrhs ? F[m * n + i] : 0   (F member-major, as the caller passes it)
-void launch_pack_in(int64_t n, int nrhs, const double* F, double* out, cudaStream_t s);
+void launch_pack_in(int64_t n, int nrhs, const double* F, df64* out, cudaStream_t s);
 // X[m * n + i] = in[i * BW + m] for m < nrhs
-void launch_pack_out(int64_t n, int nrhs, const double* in, double* X, cudaStream_t s);
+void launch_pack_out(int64_t n, int nrhs, const df64* in, double* X, cudaStream_t s);
 // out[i] = in[i * BW + col]
-void launch_extract_col(int64_t n, const double* in, int col, double* out, cudaStream_t s);
+void launch_extract_col(int64_t n, const df64* in, int col, double* out, cudaStream_t s);
+void launch_to_float(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // ---- Schur-complement operator (interleaved counterparts of the single-vector kernels) ----
-void launch_elem_interior_b(const DevMesh& m, int mode, const double* xg, const double* f, double* tI,
-                            cudaStream_t s);
-void launch_elem_interface_b(const DevMesh& m, int mode, const double* xg, const double* sI, double* yloc,
+void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI, cudaStream_t s);
+void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc,
                              cudaStream_t s);
-void launch_kii_apply_b(const DevMesh& m, const double* tI, double* sI, cudaStream_t s);
-void launch_gather_b(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
-                     const int64_t* bmap, double* y, cudaStream_t s);
-void launch_scatter_recover_b(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
+// tmp: [n_int][BW] doubles, used by the dense local solver only
+void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, cudaStream_t s);
+void launch_gather_b(int64_t n, const int* ptr, const int* idx, const df64* loc, const df64* base,
+                     const int64_t* bmap, df64* y, cudaStream_t s);
+void launch_scatter_recover_b(const DevMesh& m, const df64* xg, const df64* sI, df64* x, cudaStream_t s);
 
 // ---- BDDC (T = float or double by prec) ----
 // symmetric tiles times a block of BW members: out_m = A_m in_m
 void launch_symm_b(const SymTiles& A, const int64_t* voff, const void* in, void* out, cudaStream_t s);
-void launch_restrict_b(int prec, int64_t nflat, const int* gmap, const double* D, const double* r, void* rloc,
-                       cudaStream_t s);
+// rloc[k][.] = D_k r[gmap[k]][.]  (Df: the weights as floats, used by the FP32 preconditioner)
+void launch_restrict_b(int prec, int64_t nflat, const int* gmap, const float* Df, const double* D, const df64* r,
+                       void* rloc, cudaStream_t s);
 // per item m: out[(out_off[m]+i)][.] = alpha * sum_j M_m[i][j] x_j[.] (+ add), x_j = in[in_map?..][.]
 void launch_bmm(const BatchedRows& B, const int64_t* in_off, const int* in_map, const void* in,
                 const int64_t* out_off, void* out, double alpha, const void* add, cudaStream_t s);
@@ -86,31 +91,29 @@ void launch_restrict_tb(int prec, int64_t nflat, const int* gmap, const double* 
                         cudaStream_t s);
 void launch_wgather_tb(int prec, int64_t n, const int* ptr, const int* idx, const double* D, const void* uloc,
                        const void* vloc, void* z, cudaStream_t s);
-void launch_wgather_b(int prec, int64_t n, const int* ptr, const int* idx, const double* D, const void* uloc,
-                      const void* vloc, double* z, cudaStream_t s);
+// z[g][.] = sum over copies k of D_k (u_k + v_k)   (level-1 combine into the df64 Krylov vector)
+void launch_wgather_b(int prec, int64_t n, const int* ptr, const int* idx, const float* Df, const double* D,
+                      const void* uloc, const void* vloc, df64* z, cudaStream_t s);
 void launch_dense_mm(int prec, int n, const void* A, const void* x, void* y, cudaStream_t s);
 void launch_map_gather_b(int prec, int64_t n, const int* map, const void* in, void* out, cudaStream_t s);
 void launch_map_scatter_b(int prec, int64_t n, const int* map, const void* in, void* out, cudaStream_t s);
 
-// ---- Krylov vectors, per member ----
-void bvec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, double* partials,
+// ---- Krylov vectors, per member (df64 storage and arithmetic) ----
+void bvec_dots(int64_t n, const df64* a0, const df64* b0, const df64* a1, const df64* b1, double* partials,
                cudaStream_t s);
 void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s);
-void bvec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q,
-                double* partials, cudaStream_t s);
-void bvec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+void bvec_axpy2(int64_t n, const double* sc, df64* x, const df64* p, df64* r, const df64* q, double* partials,
+                cudaStream_t s);
+void bvec_sub(int64_t n, const df64* a, const df64* b, df64* y, cudaStream_t s);
 void bvec_init(double* sc, int nrhs, double rtol, int stop_rhs_norm, cudaStream_t s);
-// mu[j][m] = sum_l G[j][l] sum_i V[l][i] v[i][m]   (V: k columns of length n, stride ld)
-void bdefl_mu(int64_t n, int k, const double* V, int64_t ld, const double* v, const double* G, double* wpart,
-              double* mu, cudaStream_t s);
-// y[i][m] = z[i][m] + beta_m y[i][m] + sign_w sum_j W[j][i] mu[j][m]  (z NULL: y += sign_w W mu;
+// deflation with the shared basis (df64 copy W, k columns of length n, stride ld):
+// mu[j][m] = sum_l G[j][l] sum_i W[l][i] Z[i][m]; wpart: [defl_blocks(n)][MAXK][BW] scratch
+int defl_blocks(int64_t n);
+void bdefl_mu(int64_t n, int k, const df64* W, int64_t ld, const df64* Z, const double* G, df64* wpart, double* mu,
+              cudaStream_t s);
+// Y[i][m] = Z[i][m] + beta_m Y[i][m] + sign_w sum_j W[j][i] mu[j][m]  (Z NULL: Y += sign_w W mu;
 // beta_idx < 0: no beta term)
-void bdefl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
+void bdefl_update(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const df64* Z, df64* Y,
                   const double* sc, int beta_idx, double sign_w, cudaStream_t s);
-// the same with the shared basis stored as df64 (float pairs)
-void bdefl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* G, double* wpart,
-                 double* mu, cudaStream_t s);
-void bdefl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
-                     const double* sc, int beta_idx, double sign_w, cudaStream_t s);
 
 }  // namespace dd

@@ -28,6 +28,13 @@ struct Error : std::runtime_error {
   } while (0)
 
 void count_launch();  // process-wide counter of kernel launches (profiling)
+// raises a kernel's dynamic shared-memory limit once per (kernel, device) and size
+// (cudaFuncSetAttribute is a host-side call that costs far more than a launch)
+void set_max_smem(const void* func, int bytes);
+template <class F>
+inline void max_smem(F* func, size_t bytes) {
+  set_max_smem(reinterpret_cast<const void*>(func), (int)bytes);
+}
 #define DD_CHECK_LAUNCH() \
   do {                    \
     ::dd::count_launch(); \
@@ -106,6 +113,38 @@ __device__ __forceinline__ df64 df64_add(df64 a, df64 b) {
   return df64_fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df64 df64_neg(df64 a) { return {-a.hi, -a.lo}; }
+
+// Conversions between double and df64 by bit manipulation, so that the FP64 pipe (1/64 of
+// the FP32 rate on this part) is not used for them: hi keeps the top 24 significand bits
+// of d (truncated), lo the next 29 bits rounded to a float (I2F and a power-of-two scale).
+// Values outside the float exponent range of both parts take the FP64 route.
+__device__ __forceinline__ df64 df64_from_double_bits(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned int h = (unsigned int)(u >> 32), l = (unsigned int)u;
+  const unsigned int sgn = h & 0x80000000u;
+  const int e = (int)((h >> 20) & 0x7FF);
+  if (e == 0 && ((h & 0xFFFFFu) | l) == 0u) return {__uint_as_float(sgn), 0.f};
+  const int ef = e - 1023 + 127;  // float exponent of hi
+  const int es = e - 1075 + 127;  // float exponent of one unit of lo's 29-bit integer
+  if (ef <= 0 || ef >= 255 || es <= 0) return df64_from_double(d);
+  const float hi = __uint_as_float(sgn | ((unsigned int)ef << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+  const float lo = __uint2float_rn(l & 0x1FFFFFFFu) * __uint_as_float((unsigned int)es << 23);
+  return {hi, sgn ? -lo : lo};
+}
+// exact widening of a float to double without the FP64 pipe (denormal floats become 0)
+__device__ __forceinline__ double double_from_float_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sgn = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u) return __hiloint2double((int)sgn, 0);
+  if (e == 255u) return (double)f;
+  const unsigned int m = u & 0x7FFFFFu;
+  return __hiloint2double((int)(sgn | ((e - 127u + 1023u) << 20) | (m >> 3)), (int)(m << 29));
+}
+// hi + lo in FP64 with one add on the FP64 pipe
+__device__ __forceinline__ double df64_to_double_bits(df64 a) {
+  return double_from_float_bits(a.hi) + double_from_float_bits(a.lo);
+}
 __device__ __forceinline__ df64 df64_mul(df64 a, df64 b) {
   float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);

@@ -132,7 +132,7 @@ struct dd_recycle {
   std::vector<double> theta;
   double* xg_prev = nullptr;                                // [n_gamma]
   int nrhs = 0;                                             // ensemble width (0: single sequence)
-  double* xg_prev_b = nullptr;                              // [n_gamma][BW] previous ensemble solutions
+  dd::df64* xg_prev_b = nullptr;                            // [n_gamma][BW] previous ensemble solutions (df64)
   bool have_prev = false;
   int hmax = 0;
   double *P = nullptr, *AP = nullptr, *Z = nullptr, *MAP = nullptr;  // histories [hmax][n_gamma]

@@ -92,7 +92,7 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   DeviceArena& A = B->arena;
   const DevMesh& m = c->mesh;
   const int64_t n = c->n_gamma;
-  auto dvec = [&](int64_t rows) { return A.alloc<double>((size_t)std::max<int64_t>(rows, 1) * BW); };
+  auto dvec = [&](int64_t rows) { return A.alloc<df64>((size_t)std::max<int64_t>(rows, 1) * BW); };
   auto tvec = [&](int prec, int64_t rows) -> void* {
     return prec == DD_PREC_FP32 ? (void*)A.alloc<float>((size_t)std::max<int64_t>(rows, 1) * BW)
                                 : (void*)A.alloc<double>((size_t)std::max<int64_t>(rows, 1) * BW);
@@ -100,6 +100,9 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   B->tI = dvec(m.n_int);
   B->sI = dvec(m.n_int);
   B->yloc = dvec(c->b1.n_flat);
+  if (m.local_solver != DD_LOCAL_FDM) B->kii_tmp = A.alloc<double>((size_t)std::max<int64_t>(m.n_int, 1) * BW);
+  B->D1f = A.alloc<float>((size_t)std::max<int64_t>(c->b1.n_flat, 1));
+  launch_to_float(c->b1.n_flat, c->b1.D, B->D1f, s);
   const int pp = c->b1.prec;
   B->rloc = tvec(pp, c->b1.n_flat);
   B->uloc = tvec(pp, c->b1.n_flat);
@@ -134,7 +137,7 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   B->X = dvec(c->n_free);
   B->sc = A.alloc<double>((size_t)BS_COUNT * BW);
   B->partials = A.alloc<double>((size_t)NBLKB * 4 * BW);
-  B->wpart = A.alloc<double>((size_t)NBLKB * MAXK * BW);
+  B->wpart = A.alloc<df64>((size_t)defl_blocks(std::max<int64_t>(n, 1)) * MAXK * BW);
   B->mu = A.alloc<double>((size_t)MAXK * BW);
   DD_CUDA(cudaMallocHost(&B->sc_host, (size_t)BS_COUNT * BW * sizeof(double)));
   c->bw = B.release();
@@ -143,34 +146,34 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
 }
 
 // ---- operators on BW members ----
-void schur_b(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
+void schur_b(dd_ctx* c, const df64* x, df64* y, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_ENS_SCHUR, s);
   BatchWork& B = *c->bw;
   launch_elem_interior_b(c->mesh, ELEM_SCHUR, x, nullptr, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
   launch_elem_interface_b(c->mesh, ELEM_SCHUR, x, B.sI, B.yloc, s);
   launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, nullptr, nullptr, y, s);
 }
 
-void condense_b(dd_ctx* c, const double* f, double* b, cudaStream_t s) {
+void condense_b(dd_ctx* c, const df64* f, df64* b, cudaStream_t s) {
   BatchWork& B = *c->bw;
   launch_elem_interior_b(c->mesh, ELEM_CONDENSE, nullptr, f, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
   launch_elem_interface_b(c->mesh, ELEM_CONDENSE, nullptr, B.sI, B.yloc, s);
   launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, f, c->mesh.gamma_free, b, s);
 }
 
-void recover_b(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream_t s) {
+void recover_b(dd_ctx* c, const df64* f, const df64* xg, df64* x, cudaStream_t s) {
   BatchWork& B = *c->bw;
   launch_elem_interior_b(c->mesh, ELEM_RECOVER, xg, f, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
   launch_scatter_recover_b(c->mesh, xg, B.sI, x, s);
 }
 
 template <class CoarseFn>
-void bddc_b(dd_ctx* c, const DevBDDC& b, const double* r, double* z, void* rloc, void* uloc, void* vloc, void* gloc, void* gC,
-            void* uC, CoarseFn coarse, cudaStream_t s) {
-  launch_restrict_b(b.prec, b.n_flat, b.gmap, b.D, r, rloc, s);
+void bddc_b(dd_ctx* c, const DevBDDC& b, const df64* r, df64* z, void* rloc, void* uloc, void* vloc, void* gloc,
+            void* gC, void* uC, CoarseFn coarse, cudaStream_t s) {
+  launch_restrict_b(b.prec, b.n_flat, b.gmap, c->bw->D1f, b.D, r, rloc, s);
   {
     ProfScope pk(c, DD_PROF_ENS_N, s);
     apply_sym_b(c, BOP_N1, b.N, b.goff, rloc, uloc, s);                        // u_i = N_i r_i
@@ -179,7 +182,7 @@ void bddc_b(dd_ctx* c, const DevBDDC& b, const double* r, double* z, void* rloc,
   launch_gather_tb(b.prec, b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
   coarse(gC, uC);
   launch_bmm_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);     // Phi_i R_Ci u_C
-  launch_wgather_b(b.prec, b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
+  launch_wgather_b(b.prec, b.n_gamma, b.gptr, b.gidx, c->bw->D1f, b.D, uloc, vloc, z, s);
 }
 
 // level-2 BDDC on the coarse system of the ensemble (same steps as the single path)
@@ -207,7 +210,7 @@ void level2_b(dd_ctx* c, const void* g, void* u, cudaStream_t s) {
   launch_map_scatter_b(p2, L.b.n_gamma, L.gam_c, B.z2, u, s);
 }
 
-void precond_b(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+void precond_b(dd_ctx* c, const df64* r, df64* z, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_ENS_PRECOND, s);
   BatchWork& B = *c->bw;
   bddc_b(c, c->b1, r, z, B.rloc, B.uloc, B.vloc, B.gloc, B.gC, B.uC,
@@ -220,8 +223,8 @@ void precond_b(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
          s);
 }
 
-void copy_b(double* dst, const double* src, int64_t rows, cudaStream_t s) {
-  DD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * BW * sizeof(double), cudaMemcpyDeviceToDevice, s));
+void copy_b(df64* dst, const df64* src, int64_t rows, cudaStream_t s) {
+  DD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * BW * sizeof(df64), cudaMemcpyDeviceToDevice, s));
 }
 
 // deflated PCG (Algorithm 1) for every member; returns the worst member status
@@ -248,8 +251,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})  (shared W, per-member mu)
     schur_b(c, B.xg, B.q, s);
     bvec_sub(n, B.bvec, B.q, B.r, s);
-    bdefl_mu_df(n, k, W, n, B.r, st->Ginv, B.wpart, B.mu, s);
-    bdefl_update_df(n, k, W, n, B.mu, nullptr, B.xg, B.sc, -1, 1.0, s);
+    bdefl_mu(n, k, W, n, B.r, st->Ginv, B.wpart, B.mu, s);
+    bdefl_update(n, k, W, n, B.mu, nullptr, B.xg, B.sc, -1, 1.0, s);
   }
   schur_b(c, B.xg, B.q, s);
   bvec_sub(n, B.bvec, B.q, B.r, s);
@@ -268,8 +271,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
     bvec_dots(n, B.r, B.z, nullptr, nullptr, B.partials, s);
     bvec_finalize(B.partials, B.sc, BFIN_RZ0, 0, s);
     if (k) {
-      bdefl_mu_df(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update_df(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
+      bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
     } else {
       copy_b(B.p, B.z, n, s);
     }
@@ -298,8 +301,8 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
       if (rec0 && its <= st->hmax) launch_extract_col(n, B.z, 0, st->Z + (size_t)its * n, s);
       bvec_dots(n, B.r, B.z, o.flexible ? B.r : nullptr, o.flexible ? B.zold : nullptr, B.partials, s);
       bvec_finalize(B.partials, B.sc, BFIN_RZ, o.flexible, s);
-      if (k) bdefl_mu_df(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update_df(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
+      if (k) bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
+      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
     }
   }
   for (int m = 0; m < nrhs; ++m) {
@@ -328,8 +331,8 @@ dd_status dd_recycle_create_batch(dd_ctx* c, int32_t k, int32_t strategy, double
   rc = guard_call([&] {
     dd_recycle* st = *out;
     st->nrhs = BW;
-    st->xg_prev_b = st->arena.alloc<double>((size_t)c->n_gamma * BW);
-    DD_CUDA(cudaMemset(st->xg_prev_b, 0, (size_t)c->n_gamma * BW * sizeof(double)));
+    st->xg_prev_b = st->arena.alloc<df64>((size_t)c->n_gamma * BW);
+    DD_CUDA(cudaMemset(st->xg_prev_b, 0, (size_t)c->n_gamma * BW * sizeof(df64)));
   });
   if (rc != DD_OK) {
     dd_recycle_destroy(*out);

@@ -369,15 +369,15 @@ void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, doubl
   dim3 grid(A.count), block(SYMV_WARPS * 32);
   switch (A.prec) {
     case DD_PREC_FP64:
-      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      max_smem(k_symv<DD_PREC_FP64>, smem);
       k_symv<DD_PREC_FP64><<<grid, block, smem, s>>>(A, voff, in, out, err);
       break;
     case DD_PREC_FP32:
-      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      max_smem(k_symv<DD_PREC_FP32>, smem);
       k_symv<DD_PREC_FP32><<<grid, block, smem, s>>>(A, voff, in, out, err);
       break;
     default:
-      DD_CUDA(cudaFuncSetAttribute(k_symv<DD_PREC_DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      max_smem(k_symv<DD_PREC_DF64>, smem);
       k_symv<DD_PREC_DF64><<<grid, block, smem, s>>>(A, voff, in, out, err);
   }
   DD_CHECK_LAUNCH();
@@ -608,7 +608,7 @@ template <class T>
 static void bgemv_go(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                      const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
   size_t smem = (size_t)std::max(B.max_cols, 1) * sizeof(T);
-  if (smem > 48 * 1024) DD_CUDA(cudaFuncSetAttribute(k_bgemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) max_smem(k_bgemv<T>, smem);
   dim3 grid(B.count, (B.max_rows + BGEMV_ROWS - 1) / BGEMV_ROWS);
   k_bgemv<T><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off, in_map, in,
                                       out_off, out, alpha, add);
@@ -663,7 +663,7 @@ static void bgemv_t_go(const BatchedRows& B, const int64_t* in_off, const int* i
                        const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
   size_t smem = (size_t)std::max(B.max_rows, 1) * sizeof(T);
   if (smem > 48 * 1024)
-    DD_CUDA(cudaFuncSetAttribute(k_bgemv_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    max_smem(k_bgemv_t<T>, smem);
   dim3 grid(B.count, (B.max_cols + BGEMV_T_COLS - 1) / BGEMV_T_COLS);
   k_bgemv_t<T><<<grid, BGEMV_T_COLS, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off,
                                                  in_map, in, out_off, out, alpha, add);

@@ -17,6 +17,9 @@ struct PolF64 {
   using Acc = double;
   __device__ static V from_d(double d) { return d; }
   __device__ static double to_d(V v) { return v; }
+  // ensemble vectors are stored as df64
+  __device__ static V from_v(df64 x) { return df64_to_double_bits(x); }
+  __device__ static df64 to_v(V v) { return df64_from_double_bits(v); }
   __device__ static V zero() { return 0.0; }
   __device__ static V neg(V v) { return -v; }
   __device__ static void init(Acc& a) { a = 0.0; }
@@ -37,6 +40,8 @@ struct PolDF {
   using Acc = df64_acc;
   __device__ static V from_d(double d) { return df64_from_double(d); }
   __device__ static double to_d(V v) { return df64_to_double(v); }
+  __device__ static V from_v(df64 x) { return x; }
+  __device__ static df64 to_v(V v) { return v; }
   __device__ static V zero() { return {0.f, 0.f}; }
   __device__ static V neg(V v) { return df64_neg(v); }
   __device__ static void init(Acc& a) { a = df64_acc(); }

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "common.h"
@@ -27,6 +28,18 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
 namespace dd {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_max_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;
+  int dev = 0;
+  DD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& have = done[{func, dev}];
+  if (have >= bytes) return;
+  DD_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  have = bytes;
+}
 }  // namespace dd
 
 // ---------------------------------------------------------------------------

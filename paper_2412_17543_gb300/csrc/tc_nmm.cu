@@ -292,7 +292,7 @@ TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<in
 void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, cudaStream_t s) {
   if (A.count == 0) return;
   const size_t smem = tc_smem_bytes();
-  DD_CUDA(cudaFuncSetAttribute(k_nmm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  max_smem(k_nmm_tc, smem);
   k_nmm_tc<<<dim3(A.count, A.max_nmb), TC_THREADS, smem, s>>>(A, goff, rloc, uloc, err);
   DD_CHECK_LAUNCH();
 }

@@ -391,7 +391,7 @@ __global__ void k_lincomb(int64_t n, int m, const double* const* __restrict__ V,
 void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s) {
   if (kc == 0) return;
   size_t smem = (size_t)m * kc * sizeof(df64);
-  if (smem > 48 * 1024) DD_CUDA(cudaFuncSetAttribute(k_lincomb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) max_smem(k_lincomb, smem);
   k_lincomb<<<NBLK, RB, smem, s>>>(n, m, V, Yc, kc, out);
   DD_CHECK_LAUNCH();
 }
