@@ -559,7 +559,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->tmp = A.alloc<double>(nG);
     c->sc = A.alloc<double>(SC_COUNT);
     c->partials = A.alloc<double>(NBLK * MAXDOT);
-    c->wpart = A.alloc<double>((size_t)NBLK * MAXK);
+    c->wpart = A.alloc<double>((size_t)std::max<int64_t>(NBLK, defl_df_blocks(c->n_gamma)) * MAXK);
     c->mu = A.alloc<double>(MAXK);
     c->gram_part = A.alloc<double>((size_t)NBLK * 4096);
     c->gram_out = A.alloc<double>(4096);
@@ -922,15 +922,14 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   const int64_t n = c->n_gamma;
   const dd_options& o = c->opt;
   const int k = st ? st->k : 0;
-  const double* W = k ? st->W : nullptr;
-  const double* AW = k ? st->AW : nullptr;
   const df64* Wd = k ? st->Wd : nullptr;
+  const df64* AWd = k ? st->AWd : nullptr;
   DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
     vec_sub(n, c->bvec, c->q, c->r, s);
-    defl_mu(n, k, W, n, c->r, st->Ginv, c->wpart, c->mu, s);
+    defl_mu_df(n, k, Wd, n, c->r, st->Ginv, c->wpart, c->mu, s);
     defl_update_df(n, k, Wd, n, c->mu, nullptr, c->xg, c->sc, -1, 1.0, s);
   }
   schur_apply(c, c->xg, c->q, s);
@@ -955,7 +954,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     vec_dots(n, c->r, c->z, nullptr, nullptr, nullptr, nullptr, c->partials, s);
     vec_finalize(c->partials, c->sc, FIN_RZ0, 0, s);
     if (k) {
-      defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
+      defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, s);
       defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, -1, -1.0, s);
     } else {
       DD_CUDA(cudaMemcpyAsync(c->p, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
@@ -973,7 +972,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
       vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
       if (k && o.reorth) {
         // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
-        defl_mu(n, k, W, n, c->r, st->WWinv, c->wpart, c->mu, s);
+        defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, s);
         defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, s);
         vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, s);
         vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
@@ -999,7 +998,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
       vec_dots(n, c->r, c->z, o.flexible ? c->r : nullptr, o.flexible ? c->zold : nullptr, nullptr, nullptr,
                c->partials, s);
       vec_finalize(c->partials, c->sc, FIN_RZ, o.flexible, s);
-      if (k) defl_mu(n, k, AW, n, c->z, st->Ginv, c->wpart, c->mu, s);
+      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, s);
       defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, s);
     }
   }

@@ -226,10 +226,7 @@ void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu
 // the FP32 pipes with error-free transformations (about 2^-44 relative), FP64 only
 // converts the vector entries and forms the final update
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ df64 dbl_to_df(double d) {
-  const float hi = (float)d;
-  return {hi, (float)(d - (double)hi)};
-}
+__device__ __forceinline__ df64 dbl_to_df(double d) { return df64_from_double_bits(d); }
 
 __global__ void k_to_df64(int64_t n, const double* __restrict__ in, df64* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -241,9 +238,87 @@ void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s) {
   DD_CHECK_LAUNCH();
 }
 
+constexpr int PT = 4;  // rows per thread of the row-blocked deflation kernels
+
+// wpart[b][c] = sum over the rows of block b of V_c[i] v[i] with the basis as df64: a block
+// takes RB * PT consecutive rows, each thread holds its PT entries of v (converted once) and
+// walks the columns (each a contiguous piece per block, two columns' loads in flight);
+// warp sums by shuffles in df64, then a fixed-order sum over the warps
+__global__ void __launch_bounds__(RB) k_wdots4(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
+                                               const double* __restrict__ v, double* wpart) {
+  __shared__ df64 sh[RB / 32][MAXK];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * PT * RB + threadIdx.x;
+  df64 z[PT];
+#pragma unroll
+  for (int r = 0; r < PT; ++r) {
+    const int64_t i = i0 + (int64_t)r * RB;
+    z[r] = i < n ? dbl_to_df(v[i]) : df64{0.f, 0.f};
+  }
+  auto warp_sum = [&](df64 x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const df64 y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+      x = df64_add(x, y);
+    }
+    return x;
+  };
+  int c = 0;
+  for (; c + 1 < k; c += 2) {
+    const df64* c0 = V + (int64_t)c * ld;
+    const df64* c1 = c0 + ld;
+    df64 v0[PT], v1[PT];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      const int64_t i = i0 + (int64_t)r * RB;
+      v0[r] = i < n ? c0[i] : df64{0.f, 0.f};
+      v1[r] = i < n ? c1[i] : df64{0.f, 0.f};
+    }
+    df64_acc a0, a1;
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      a0.fma(v0[r], z[r]);
+      a1.fma(v1[r], z[r]);
+    }
+    const df64 s0 = warp_sum(a0.get()), s1 = warp_sum(a1.get());
+    if (lane == 0) {
+      sh[warp][c] = s0;
+      sh[warp][c + 1] = s1;
+    }
+  }
+  if (c < k) {
+    const df64* c0 = V + (int64_t)c * ld;
+    df64_acc a0;
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      const int64_t i = i0 + (int64_t)r * RB;
+      if (i < n) a0.fma(c0[i], z[r]);
+    }
+    const df64 s0 = warp_sum(a0.get());
+    if (lane == 0) sh[warp][c] = s0;
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < k; cc += blockDim.x) {
+    df64_acc sum;
+    for (int w = 0; w < RB / 32; ++w) sum.add(sh[w][cc]);
+    wpart[(int64_t)blockIdx.x * MAXK + cc] = df64_to_double_bits(sum.get());
+  }
+}
+
+int defl_df_blocks(int64_t n) { return (int)((n + (int64_t)PT * RB - 1) / ((int64_t)PT * RB)); }
+
+void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
+                double* mu, cudaStream_t s) {
+  if (k == 0) return;
+  const int nb = defl_df_blocks(n);
+  k_wdots4<<<nb, RB, 0, s>>>(n, k, V, ld, v, wpart);
+  DD_CHECK_LAUNCH();
+  k_wfinal<<<1, 256, 0, s>>>(nb, k, wpart, Ginv, mu);
+  DD_CHECK_LAUNCH();
+}
+
 // y = z + beta y + sign_w W mu over row chunks of PT * RB rows: a block walks the k
 // columns, each a contiguous 16-KiB piece per chunk, and keeps its rows' sums in df64
-constexpr int PT = 4;  // rows per thread
 __global__ void __launch_bounds__(RB) k_pupdate2(int64_t n, int k, const df64* __restrict__ W, int64_t ld,
                                                  const double* __restrict__ mu, const double* __restrict__ z,
                                                  double* __restrict__ y, const double* __restrict__ sc, int beta_idx,
