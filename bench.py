@@ -386,6 +386,8 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
                 "setup_s": setup_s, "rhs_gen_s": t_rhs, "single_sequence": single,
                 "ens_nmm": {"kernel": {1: "simt", 2: "tcgen05 3xTF32"}.get(S.info["ens_nmm"], "none"),
                             "tuning_ms": S.info["ens_nmm_ms"]},
+                "ens_shapes": {"element_members_per_pass": S.info["ens_elem_rc"],
+                               "fdm_members_per_block": S.info["ens_fdm_rc"]},
                 "batching_speedup": value / single["value"],
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": launches, "kernels": per_kernel}

@@ -94,6 +94,10 @@ typedef struct {
   int32_t ens_nmm;          /* ensemble products N_i R_i of an FP32 preconditioner: DD_ENS_AUTO (both
                                kernels timed on the first ensemble call, the faster kept), DD_ENS_SIMT
                                (CUDA-core tiles), DD_ENS_TC (tensor cores, 3xTF32) */
+  int32_t ens_elem_rc;      /* members per pass of the ensemble element kernels of a DF64 operator on
+                               8^3-element subdomains: 0 (timed on the first ensemble call), 4, 8 or 16;
+                               any other shape of subdomain uses 8 */
+  int32_t ens_fdm_rc;       /* members per block of its ensemble fast diagonalization: 0 (timed), 4 or 8 */
 } dd_options;
 
 typedef struct {
@@ -110,6 +114,8 @@ typedef struct {
   int32_t ens_nmm;          /* ensemble N_i kernel in use: DD_ENS_SIMT or DD_ENS_TC (0 before the first
                                ensemble call) */
   float ens_nmm_ms[2];      /* its selection timings (SIMT, tensor cores; 0 when not timed), ms */
+  int32_t ens_elem_rc;      /* members per pass of the ensemble element kernels (0 before the first call) */
+  int32_t ens_fdm_rc;       /* members per block of the ensemble fast diagonalization (0 before) */
 } dd_info_t;
 
 typedef struct {

@@ -32,14 +32,15 @@ class Options(ctypes.Structure):
                 ("weights", ctypes.c_int32), ("precond_prec", ctypes.c_int32), ("schur_prec", ctypes.c_int32),
                 ("flexible", ctypes.c_int32), ("reorth", ctypes.c_int32), ("stop_rhs_norm", ctypes.c_int32),
                 ("maxit", ctypes.c_int32), ("local_solver", ctypes.c_int32),
-                ("ens_nmm", ctypes.c_int32)]
+                ("ens_nmm", ctypes.c_int32), ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n_free", ctypes.c_int64), ("n_gamma", ctypes.c_int64), ("n_sub", ctypes.c_int32),
                 ("n_coarse", ctypes.c_int32), ("n_adaptive", ctypes.c_int32), ("n_sub2", ctypes.c_int32),
                 ("n_coarse3", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 2)]
+                ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 2),
+                ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32)]
 
 
 class KernelProf(ctypes.Structure):

@@ -196,49 +196,56 @@ __global__ void __launch_bounds__(512) k_elem_interface_b(DevMesh m, int mode, c
   }
 }
 
-constexpr int ELEM_RC = 8;        // members per pass of the batched element kernels
 constexpr int ELEM_THREADS = 512;
 
-template <class P, int S>
+// members per pass (RC) of the element kernels: 4, 8 or 16 for the 8^3 subdomains of the
+// production meshes (chosen by timing at the first ensemble call), 8 otherwise
+template <class P, int S, int RC>
 static void elem_b_go(const DevMesh& m, bool interior, int mode, const df64* xg, const df64* in, df64* out,
                       cudaStream_t s) {
   const int NE = m.sx * m.sy * m.sz;
-  const size_t smem = ((size_t)m.NL * ELEM_RC + (size_t)NE * 8) * sizeof(typename P::V);
+  const size_t smem = ((size_t)m.NL * RC + (size_t)NE * 8) * sizeof(typename P::V);
   if (interior) {
-    max_smem(k_elem_interior_b<P, S, ELEM_RC>, smem);
-    k_elem_interior_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
+    max_smem(k_elem_interior_b<P, S, RC>, smem);
+    k_elem_interior_b<P, S, RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   } else {
-    max_smem(k_elem_interface_b<P, S, ELEM_RC>, smem);
-    k_elem_interface_b<P, S, ELEM_RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
+    max_smem(k_elem_interface_b<P, S, RC>, smem);
+    k_elem_interface_b<P, S, RC><<<m.S, ELEM_THREADS, smem, s>>>(m, mode, xg, in, out);
   }
 }
 
 template <class P>
 static void elem_b_dispatch(const DevMesh& m, bool interior, int mode, const df64* xg, const df64* in,
-                            df64* out, cudaStream_t s) {
-  if (m.sx == 8 && m.sy == 8 && m.sz == 8)
-    elem_b_go<P, 8>(m, interior, mode, xg, in, out, s);
-  else if (m.sx == 4 && m.sy == 4 && m.sz == 4)
-    elem_b_go<P, 4>(m, interior, mode, xg, in, out, s);
-  else
-    elem_b_go<P, 0>(m, interior, mode, xg, in, out, s);
+                            df64* out, int rc, cudaStream_t s) {
+  if (m.sx == 8 && m.sy == 8 && m.sz == 8) {
+    if (rc == 4)
+      elem_b_go<P, 8, 4>(m, interior, mode, xg, in, out, s);
+    else if (rc == 16)
+      elem_b_go<P, 8, 16>(m, interior, mode, xg, in, out, s);
+    else
+      elem_b_go<P, 8, 8>(m, interior, mode, xg, in, out, s);
+  } else if (m.sx == 4 && m.sy == 4 && m.sz == 4) {
+    elem_b_go<P, 4, 8>(m, interior, mode, xg, in, out, s);
+  } else {
+    elem_b_go<P, 0, 8>(m, interior, mode, xg, in, out, s);
+  }
 }
 
-void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI,
+void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI, int rc,
                             cudaStream_t s) {
   if (m.schur_prec == DD_PREC_DF64)
-    elem_b_dispatch<PolDF>(m, true, mode, xg, f, tI, s);
+    elem_b_dispatch<PolDF>(m, true, mode, xg, f, tI, rc, s);
   else
-    elem_b_dispatch<PolF64>(m, true, mode, xg, f, tI, s);
+    elem_b_dispatch<PolF64>(m, true, mode, xg, f, tI, 8, s);
   DD_CHECK_LAUNCH();
 }
 
-void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc,
+void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc, int rc,
                              cudaStream_t s) {
   if (m.schur_prec == DD_PREC_DF64)
-    elem_b_dispatch<PolDF>(m, false, mode, xg, sI, yloc, s);
+    elem_b_dispatch<PolDF>(m, false, mode, xg, sI, yloc, rc, s);
   else
-    elem_b_dispatch<PolF64>(m, false, mode, xg, sI, yloc, s);
+    elem_b_dispatch<PolF64>(m, false, mode, xg, sI, yloc, 8, s);
   DD_CHECK_LAUNCH();
 }
 
@@ -283,10 +290,15 @@ __device__ __forceinline__ void fdm_contract_b(const typename P::V* A, int ax, b
   }
 }
 
-constexpr int FDM_THREADS = 448;  // 7 x 7 lines of 8 members (interior subdomains) in one pass
+// 56 lines (7 x 8: the largest two-axis face of an 8^3 subdomain's interior block) of RC
+// members per thread pass
+template <int RC>
+constexpr int fdm_threads() {
+  return 56 * RC;
+}
 
 template <class P, int RC>
-__global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const df64* __restrict__ tI,
+__global__ void __launch_bounds__(fdm_threads<RC>()) k_fdm_apply_b(DevMesh m, const df64* __restrict__ tI,
                                                               df64* __restrict__ sI) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_f[];
@@ -325,13 +337,11 @@ __global__ void __launch_bounds__(FDM_THREADS) k_fdm_apply_b(DevMesh m, const df
   for (int t = threadIdx.x; t < N * RC; t += blockDim.x) sI[(off + t / RC) * BW + m0 + t % RC] = P::to_v(b0[t]);
 }
 
-constexpr int FDM_RC = 8;
-
-template <class P>
+template <class P, int RC>
 static void fdm_b_go(const DevMesh& m, const df64* tI, df64* sI, cudaStream_t s) {
-  const size_t smem = (size_t)2 * 729 * FDM_RC * sizeof(typename P::V);
-  max_smem(k_fdm_apply_b<P, FDM_RC>, smem);
-  k_fdm_apply_b<P, FDM_RC><<<dim3(m.S, BW / FDM_RC), FDM_THREADS, smem, s>>>(m, tI, sI);
+  const size_t smem = (size_t)2 * 729 * RC * sizeof(typename P::V);
+  max_smem(k_fdm_apply_b<P, RC>, smem);
+  k_fdm_apply_b<P, RC><<<dim3(m.S, BW / RC), fdm_threads<RC>(), smem, s>>>(m, tI, sI);
 }
 
 __global__ void k_df_to_dbl(int64_t n, const df64* __restrict__ in, double* __restrict__ out) {
@@ -343,12 +353,16 @@ __global__ void k_dbl_to_df(int64_t n, const double* __restrict__ in, df64* __re
     out[i] = df64_from_double_bits(in[i]);
 }
 
-void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, cudaStream_t s) {
+void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, int rc, cudaStream_t s) {
   if (m.local_solver == DD_LOCAL_FDM) {
-    if (m.schur_prec == DD_PREC_DF64)
-      fdm_b_go<PolDF>(m, tI, sI, s);
-    else
-      fdm_b_go<PolF64>(m, tI, sI, s);
+    if (m.schur_prec == DD_PREC_DF64) {
+      if (rc == 4)
+        fdm_b_go<PolDF, 4>(m, tI, sI, s);
+      else
+        fdm_b_go<PolDF, 8>(m, tI, sI, s);
+    } else {
+      fdm_b_go<PolF64, 8>(m, tI, sI, s);
+    }
     DD_CHECK_LAUNCH();
   } else {
     // dense K_II^{-1} (FP64 tiles; the caller rejects df64 dense ensembles): the tiles work

@@ -42,6 +42,10 @@ struct BatchWork {
   double* partials = nullptr;         // [NBLKB][4][BW]
   df64* wpart = nullptr;              // [deflation blocks][MAXK][BW]
   double* mu = nullptr;               // [MAXK][BW]
+  // members per pass of the element kernels and per block of the fast diagonalization
+  // (launch shapes chosen by timing at the first ensemble call), and their timings (ms)
+  int elem_rc = 8, fdm_rc = 8;
+  float elem_ms[3] = {0.f, 0.f, 0.f}, fdm_ms[2] = {0.f, 0.f};
   // symmetric products of the ensemble (level-1 N_i; level-2 K_II^{-1} and N): tensor-core
   // operand copy, whether it is used, and the selection timings (SIMT, tensor cores)
   struct SymOp {
@@ -62,11 +66,14 @@ void launch_extract_col(int64_t n, const df64* in, int col, double* out, cudaStr
 void launch_to_float(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // ---- Schur-complement operator (interleaved counterparts of the single-vector kernels) ----
-void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI, cudaStream_t s);
-void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc,
+// rc: members per pass of the element kernels (4, 8 or 16; used for 8^3 subdomains, df64)
+void launch_elem_interior_b(const DevMesh& m, int mode, const df64* xg, const df64* f, df64* tI, int rc,
+                            cudaStream_t s);
+void launch_elem_interface_b(const DevMesh& m, int mode, const df64* xg, const df64* sI, df64* yloc, int rc,
                              cudaStream_t s);
-// tmp: [n_int][BW] doubles, used by the dense local solver only
-void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, cudaStream_t s);
+// tmp: [n_int][BW] doubles, used by the dense local solver only; rc: members per block of
+// the fast diagonalization (4 or 8, df64)
+void launch_kii_apply_b(const DevMesh& m, const df64* tI, df64* sI, double* tmp, int rc, cudaStream_t s);
 void launch_gather_b(int64_t n, const int* ptr, const int* idx, const df64* loc, const df64* base,
                      const int64_t* bmap, df64* y, cudaStream_t s);
 void launch_scatter_recover_b(const DevMesh& m, const df64* xg, const df64* sI, df64* x, cudaStream_t s);

@@ -76,8 +76,61 @@ void select_op(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, voi
   o.use_tc = o.ms[1] < o.ms[0];
 }
 
+// mean time of three launches of f after one warm-up (ms)
+template <class F>
+float time_ms(F&& f, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  f();
+  DD_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < 3; ++r) f();
+  DD_CUDA(cudaEventRecord(e1, s));
+  DD_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / 3.f;
+}
+
+// launch shapes of the Schur operator of the ensemble: members per pass of the element
+// kernels (4, 8, 16) and per block of the fast diagonalization (4, 8), taken from the
+// options or else each timed on the context's own mesh (df64 operator on 8^3 subdomains;
+// other meshes keep 8)
+void select_shapes(dd_ctx* c, cudaStream_t s) {
+  BatchWork& B = *c->bw;
+  const DevMesh& m = c->mesh;
+  if (m.schur_prec != DD_PREC_DF64 || !(m.sx == 8 && m.sy == 8 && m.sz == 8)) return;
+  const int64_t n = c->n_gamma;
+  DD_CUDA(cudaMemsetAsync(B.p, 0, (size_t)n * BW * sizeof(df64), s));
+  DD_CUDA(cudaMemsetAsync(B.sI, 0, (size_t)std::max<int64_t>(m.n_int, 1) * BW * sizeof(df64), s));
+  if (c->opt.ens_elem_rc) {
+    B.elem_rc = c->opt.ens_elem_rc;
+  } else {
+    const int rcs[3] = {4, 8, 16};
+    int best = 1;
+    for (int v = 0; v < 3; ++v) {
+      B.elem_ms[v] = time_ms([&] { launch_elem_interface_b(m, ELEM_SCHUR, B.p, B.sI, B.yloc, rcs[v], s); }, s);
+      if (B.elem_ms[v] < B.elem_ms[best]) best = v;
+    }
+    B.elem_rc = rcs[best];
+  }
+  if (m.local_solver == DD_LOCAL_FDM) {
+    if (c->opt.ens_fdm_rc) {
+      B.fdm_rc = c->opt.ens_fdm_rc;
+    } else {
+      for (int v = 0; v < 2; ++v)
+        B.fdm_ms[v] = time_ms([&] { launch_kii_apply_b(m, B.sI, B.tI, B.kii_tmp, v == 0 ? 4 : 8, s); }, s);
+      B.fdm_rc = B.fdm_ms[0] < B.fdm_ms[1] ? 4 : 8;
+    }
+  }
+  check_err(c, s);
+}
+
 void select_ops(dd_ctx* c, cudaStream_t s) {
   BatchWork& B = *c->bw;
+  select_shapes(c, s);
   select_op(c, BOP_N1, c->b1.N, c->b1.goff, B.rloc, B.uloc, c->b1.n_flat, s);
   if (c->levels == 3) {
     const DevLevel2& L = c->l2;
@@ -149,24 +202,24 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
 void schur_b(dd_ctx* c, const df64* x, df64* y, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_ENS_SCHUR, s);
   BatchWork& B = *c->bw;
-  launch_elem_interior_b(c->mesh, ELEM_SCHUR, x, nullptr, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
-  launch_elem_interface_b(c->mesh, ELEM_SCHUR, x, B.sI, B.yloc, s);
+  launch_elem_interior_b(c->mesh, ELEM_SCHUR, x, nullptr, B.tI, B.elem_rc, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, B.fdm_rc, s);
+  launch_elem_interface_b(c->mesh, ELEM_SCHUR, x, B.sI, B.yloc, B.elem_rc, s);
   launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, nullptr, nullptr, y, s);
 }
 
 void condense_b(dd_ctx* c, const df64* f, df64* b, cudaStream_t s) {
   BatchWork& B = *c->bw;
-  launch_elem_interior_b(c->mesh, ELEM_CONDENSE, nullptr, f, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
-  launch_elem_interface_b(c->mesh, ELEM_CONDENSE, nullptr, B.sI, B.yloc, s);
+  launch_elem_interior_b(c->mesh, ELEM_CONDENSE, nullptr, f, B.tI, B.elem_rc, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, B.fdm_rc, s);
+  launch_elem_interface_b(c->mesh, ELEM_CONDENSE, nullptr, B.sI, B.yloc, B.elem_rc, s);
   launch_gather_b(c->n_gamma, c->mesh.gptr, c->mesh.gidx, B.yloc, f, c->mesh.gamma_free, b, s);
 }
 
 void recover_b(dd_ctx* c, const df64* f, const df64* xg, df64* x, cudaStream_t s) {
   BatchWork& B = *c->bw;
-  launch_elem_interior_b(c->mesh, ELEM_RECOVER, xg, f, B.tI, s);
-  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, s);
+  launch_elem_interior_b(c->mesh, ELEM_RECOVER, xg, f, B.tI, B.elem_rc, s);
+  launch_kii_apply_b(c->mesh, B.tI, B.sI, B.kii_tmp, B.fdm_rc, s);
   launch_scatter_recover_b(c->mesh, xg, B.sI, x, s);
 }
 

@@ -397,6 +397,8 @@ dd_status dd_default_options(dd_options* o) {
   o->maxit = 500;
   o->local_solver = DD_LOCAL_AUTO;
   o->ens_nmm = DD_ENS_AUTO;
+  o->ens_elem_rc = 0;
+  o->ens_fdm_rc = 0;
   return DD_OK;
 }
 
@@ -414,6 +416,9 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     DD_REQUIRE(opt->schur_prec == DD_PREC_FP64 || opt->schur_prec == DD_PREC_DF64, "schur_prec must be FP64 or DF64");
     DD_REQUIRE(opt->maxit >= 1, "maxit must be positive");
     DD_REQUIRE(opt->ens_nmm >= DD_ENS_AUTO && opt->ens_nmm <= DD_ENS_TC, "ens_nmm must be AUTO, SIMT or TC");
+    DD_REQUIRE(opt->ens_elem_rc == 0 || opt->ens_elem_rc == 4 || opt->ens_elem_rc == 8 || opt->ens_elem_rc == 16,
+               "ens_elem_rc must be 0, 4, 8 or 16");
+    DD_REQUIRE(opt->ens_fdm_rc == 0 || opt->ens_fdm_rc == 4 || opt->ens_fdm_rc == 8, "ens_fdm_rc must be 0, 4 or 8");
     auto H = std::make_unique<HostSetup>();
     build_host_setup(*md, *opt, *H);
     auto c = std::make_unique<dd_ctx>();
@@ -638,6 +643,8 @@ dd_status dd_get_info(const dd_ctx* c, dd_info_t* info) {
     info->ens_nmm = c->bw->op[BOP_N1].use_tc ? DD_ENS_TC : DD_ENS_SIMT;
     info->ens_nmm_ms[0] = c->bw->op[BOP_N1].ms[0];
     info->ens_nmm_ms[1] = c->bw->op[BOP_N1].ms[1];
+    info->ens_elem_rc = c->bw->elem_rc;
+    info->ens_fdm_rc = c->bw->fdm_rc;
   }
   return DD_OK;
 }

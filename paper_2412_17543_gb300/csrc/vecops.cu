@@ -167,10 +167,10 @@ __global__ void __launch_bounds__(RB) k_wdots2(int64_t n, int64_t per, const dou
   }
 }
 
-// mu = Ginv * (sum of partials)   (k x k, one block of 256 threads): a warp per column
+// mu = Ginv * (sum of partials)   (k x k, one block of 1024 threads): a warp per column
 // sums the block partials (lanes stride over the blocks, fixed shuffle tree), then a warp
 // per output row forms Ginv d the same way
-__global__ void __launch_bounds__(256) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
+__global__ void __launch_bounds__(1024) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
                                                 const double* __restrict__ Ginv, double* mu) {
   __shared__ double d[MAXK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -195,7 +195,7 @@ void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, con
   const int64_t per = (n + NBLK - 1) / NBLK;
   k_wdots2<<<dim3(NBLK, k), RB, 0, s>>>(n, per, W, ld, v, wpart);
   DD_CHECK_LAUNCH();
-  k_wfinal<<<1, 256, 0, s>>>(NBLK, k, wpart, Ginv, mu);
+  k_wfinal<<<1, 1024, 0, s>>>(NBLK, k, wpart, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 
@@ -313,7 +313,7 @@ void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, co
   const int nb = defl_df_blocks(n);
   k_wdots4<<<nb, RB, 0, s>>>(n, k, V, ld, v, wpart);
   DD_CHECK_LAUNCH();
-  k_wfinal<<<1, 256, 0, s>>>(nb, k, wpart, Ginv, mu);
+  k_wfinal<<<1, 1024, 0, s>>>(nb, k, wpart, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 

@@ -72,6 +72,23 @@ def test_schur_apply_batch(name, prec, local, tol, nrhs):
     S.close()
 
 
+@pytest.mark.parametrize("elem_rc,fdm_rc", [(4, 4), (8, 8), (16, 4), (16, 8)])
+def test_schur_apply_batch_launch_shapes(elem_rc, fdm_rc):
+    """Every members-per-pass choice of the df64 element kernels and per-block choice of
+    the ensemble fast diagonalization gives the same operator (8^3 subdomains, all 32
+    members, tolerance of the df64 operator)."""
+    m, subs, kinds, _ = case("graded24_s8")
+    S = P.Solver(m, **_opts(2, kinds, schur_prec="df64", local_solver="fdm", ens_elem_rc=elem_rc,
+                            ens_fdm_rc=fdm_rc))
+    X = np.random.default_rng(elem_rc + fdm_rc).standard_normal((W, len(subs.gamma)))
+    Y = N(S.schur_apply_batch(T(X)))
+    for j in range(W):
+        yo = subs.schur_apply(X[j])
+        assert np.abs(Y[j] - yo).max() <= 1e-11 * np.abs(yo).max()
+    assert (S.info["ens_elem_rc"], S.info["ens_fdm_rc"]) == (elem_rc, fdm_rc)
+    S.close()
+
+
 def test_schur_apply_batch_rejects_df64_dense():
     m, subs, kinds, _ = case("cube16_cf")
     S = P.Solver(m, **_opts(2, kinds, schur_prec="df64", local_solver="dense"))
@@ -105,6 +122,19 @@ def test_nmm_autotune_picks_a_kernel():
     S.precond_apply_batch(T(np.ones((2, len(subs.gamma)))))
     info = S.info
     assert info["ens_nmm"] in (1, 2) and min(info["ens_nmm_ms"]) > 0.0
+    S.close()
+
+
+def test_launch_shapes_are_tuned_on_first_call():
+    """Members per pass of the df64 element kernels and per block of the ensemble
+    fast diagonalization are chosen by timing on the context's own mesh; every choice
+    gives the same operator (checked in test_schur_apply_batch)."""
+    m, subs, kinds, levels = case("graded24_s8")
+    S = P.Solver(m, **_opts(2, kinds, schur_prec="df64", local_solver="fdm", precond_prec="fp32"))
+    assert S.info["ens_elem_rc"] == 0
+    S.schur_apply_batch(T(np.ones((2, len(subs.gamma)))))
+    info = S.info
+    assert info["ens_elem_rc"] in (4, 8, 16) and info["ens_fdm_rc"] in (4, 8)
     S.close()
 
 
