@@ -98,6 +98,11 @@ typedef struct {
                                8^3-element subdomains: 0 (timed on the first ensemble call), 4, 8 or 16;
                                any other shape of subdomain uses 8 */
   int32_t ens_fdm_rc;       /* members per block of its ensemble fast diagonalization: 0 (timed), 4 or 8 */
+  int32_t loop_graph;       /* 1 (default): the PCG iterations of a solve run on the device as one launch
+                               of a CUDA graph (conditional WHILE node; the stopping test is a kernel);
+                               0: the host issues each iteration and reads the stopping test back.
+                               Both run the same kernels in the same order (identical results); while
+                               profiling (dd_profile) the host-issued form is used */
 } dd_options;
 
 typedef struct {

@@ -906,7 +906,8 @@ __global__ void __launch_bounds__(BRB) k_baxpy2(int64_t n, const double* __restr
 // member's scalars. Inactive members keep alpha = beta = 0, so their iterates stay fixed.
 constexpr int BFIN_WARPS = 32;
 __global__ void __launch_bounds__(BFIN_WARPS * 32) k_bfinalize(int nblk, const double* __restrict__ partials,
-                                                               double* sc, int op, int flexible) {
+                                                               double* sc, int op, int flexible,
+                                                               const int* __restrict__ its) {
   // warp w sums the blocks w, w + 32, ... (lane = member); warp 0 then adds the 32
   // warp sums in order: a fixed reduction tree
   __shared__ double part[BFIN_WARPS][2][BW];
@@ -932,6 +933,7 @@ __global__ void __launch_bounds__(BFIN_WARPS * 32) k_bfinalize(int nblk, const d
   double* S = sc;
   auto at = [&](int slot) -> double& { return S[slot * BW + m]; };
   const bool act = at(BS_ACT) != 0.0;
+  if (op == BFIN_RZL) op = *its == 0 ? BFIN_RZ0 : BFIN_RZ;  // device-resident loop: first iteration or not
   switch (op) {
     case BFIN_PQ:
       at(BS_PQ) = t0;
@@ -999,8 +1001,8 @@ void bvec_dots(int64_t n, const df64* a0, const df64* b0, const df64* a1, const 
   k_bdots<<<NBLKB, BRB, 0, s>>>(n, a0, b0, a1, b1, partials);
   DD_CHECK_LAUNCH();
 }
-void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s) {
-  k_bfinalize<<<1, BFIN_WARPS * 32, 0, s>>>(NBLKB, partials, sc, op, flexible);
+void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s, const int* its) {
+  k_bfinalize<<<1, BFIN_WARPS * 32, 0, s>>>(NBLKB, partials, sc, op, flexible, its);
   DD_CHECK_LAUNCH();
 }
 void bvec_axpy2(int64_t n, const double* sc, df64* x, const df64* p, df64* r, const df64* q, double* partials,

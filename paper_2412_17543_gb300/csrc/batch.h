@@ -9,6 +9,7 @@
 
 #include "common.h"
 #include "device.h"
+#include "loop.h"
 #include "tc_nmm.h"
 
 namespace dd {
@@ -21,7 +22,8 @@ enum {
   BS_RZ = 0, BS_PQ, BS_ALPHA, BS_RR, BS_BETA, BS_BB, BS_FLAG, BS_ACT, BS_REF, BS_RTOL2, BS_ITS, BS_RR0,
   BS_COUNT = 16
 };
-enum { BFIN_PQ = 1, BFIN_RR, BFIN_RZ0, BFIN_RZ, BFIN_BB };
+// BFIN_RZL: BFIN_RZ0 when the device iteration count *its is 0, else BFIN_RZ
+enum { BFIN_PQ = 1, BFIN_RR, BFIN_RZ0, BFIN_RZ, BFIN_BB, BFIN_RZL };
 
 // scratch of the batched operators, interleaved [rows][BW]: the Krylov and local vectors
 // of the Schur operator in df64 (float pairs: the ensemble's steps run on the FP32 pipes,
@@ -42,6 +44,9 @@ struct BatchWork {
   double* partials = nullptr;         // [NBLKB][4][BW]
   df64* wpart = nullptr;              // [deflation blocks][MAXK][BW]
   double* mu = nullptr;               // [MAXK][BW]
+  LoopCtl* ctl = nullptr;             // device-resident loop control
+  LoopCtl* ctl_host = nullptr;        // pinned mirror
+  double* alphas = nullptr;           // [maxit] member 0's step lengths
   // members per pass of the element kernels and per block of the fast diagonalization
   // (launch shapes chosen by timing at the first ensemble call), and their timings (ms)
   int elem_rc = 8, fdm_rc = 8;
@@ -108,7 +113,8 @@ void launch_map_scatter_b(int prec, int64_t n, const int* map, const void* in, v
 // ---- Krylov vectors, per member (df64 storage and arithmetic) ----
 void bvec_dots(int64_t n, const df64* a0, const df64* b0, const df64* a1, const df64* b1, double* partials,
                cudaStream_t s);
-void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s);
+void bvec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s,
+                   const int* its = nullptr);
 void bvec_axpy2(int64_t n, const double* sc, df64* x, const df64* p, df64* r, const df64* q, double* partials,
                 cudaStream_t s);
 void bvec_sub(int64_t n, const df64* a, const df64* b, df64* y, cudaStream_t s);

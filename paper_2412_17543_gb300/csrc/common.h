@@ -28,6 +28,8 @@ struct Error : std::runtime_error {
   } while (0)
 
 void count_launch();  // process-wide counter of kernel launches (profiling)
+int64_t launch_counter();
+void add_launches(int64_t n);  // launches made by the device (graph replays)
 // raises a kernel's dynamic shared-memory limit once per (kernel, device) and size
 // (cudaFuncSetAttribute is a host-side call that costs far more than a launch)
 void set_max_smem(const void* func, int bytes);

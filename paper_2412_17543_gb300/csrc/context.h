@@ -8,6 +8,7 @@
 
 #include "common.h"
 #include "device.h"
+#include "loop.h"
 #include "vecops.h"
 
 namespace dd {
@@ -39,6 +40,10 @@ struct dd_ctx {
   double* tmp = nullptr;
   double* sc = nullptr;        // device scalars [SC_COUNT]
   double* sc_host = nullptr;   // pinned mirror
+  dd::LoopCtl* ctl = nullptr;       // device-resident loop control
+  dd::LoopCtl* ctl_host = nullptr;  // pinned mirror
+  double* alphas = nullptr;         // [maxit] step lengths of the last solve
+  dd::LoopGraph loop;               // captured PCG loop of solves without a recycle state
   double* partials = nullptr;  // [NBLK*MAXDOT]
   double* wpart = nullptr;     // [NBLK*MAXK]
   double* mu = nullptr;        // [MAXK]
@@ -83,6 +88,7 @@ struct dd_ctx {
   ~dd_ctx() {
     if (bw) dd::free_batch_work(bw);
     if (sc_host) cudaFreeHost(sc_host);
+    if (ctl_host) cudaFreeHost(ctl_host);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (auto& p : pending) {
@@ -137,6 +143,7 @@ struct dd_recycle {
   int hmax = 0;
   double *P = nullptr, *AP = nullptr, *Z = nullptr, *MAP = nullptr;  // histories [hmax][n_gamma]
   std::vector<double> alphas;
+  dd::LoopGraph loop;                                       // captured PCG loop of this sequence
 };
 
 

@@ -22,6 +22,7 @@ namespace dd {
 void free_batch_work(BatchWork* bw) {
   if (!bw) return;
   if (bw->sc_host) cudaFreeHost(bw->sc_host);
+  if (bw->ctl_host) cudaFreeHost(bw->ctl_host);
   delete bw;
 }
 
@@ -193,6 +194,9 @@ BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   B->wpart = A.alloc<df64>((size_t)defl_blocks(std::max<int64_t>(n, 1)) * MAXK * BW);
   B->mu = A.alloc<double>((size_t)MAXK * BW);
   DD_CUDA(cudaMallocHost(&B->sc_host, (size_t)BS_COUNT * BW * sizeof(double)));
+  B->ctl = A.alloc<LoopCtl>(1);
+  B->alphas = A.alloc<double>((size_t)c->opt.maxit);
+  DD_CUDA(cudaMallocHost(&B->ctl_host, sizeof(LoopCtl)));
   c->bw = B.release();
   select_ops(c, s);
   return *c->bw;
@@ -294,11 +298,6 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
     DD_CUDA(cudaStreamSynchronize(s));
   };
   auto hs = [&](int slot, int m) { return B.sc_host[slot * BW + m]; };
-  auto any_active = [&]() {
-    for (int m = 0; m < nrhs; ++m)
-      if (hs(BS_ACT, m) != 0.0) return true;
-    return false;
-  };
   bvec_init(B.sc, nrhs, rtol, o.stop_rhs_norm, s);
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})  (shared W, per-member mu)
@@ -311,58 +310,55 @@ dd_status pcg_solve_b(dd_ctx* c, dd_recycle* st, double rtol, bool record, int n
   bvec_sub(n, B.bvec, B.q, B.r, s);
   bvec_dots(n, B.bvec, B.bvec, B.r, B.r, B.partials, s);
   bvec_finalize(B.partials, B.sc, BFIN_BB, 0, s);
+  // member 0 feeds the recycling histories while it is active
+  launch_loop_begin_b(B.ctl, B.sc, o.maxit, record && st->hmax > 0 ? 1 : 0, s);
+  // p enters the first update p = z + beta p - W mu with beta = 0
+  DD_CUDA(cudaMemsetAsync(B.p, 0, (size_t)n * BW * sizeof(df64), s));
+  const bool rec = record && st->hmax > 0;
+  const int flex = o.flexible;
+  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool in_graph) {
+    if (flex) copy_b(B.zold, B.z, n, bs);
+    precond_b(c, B.r, B.z, bs);
+    if (rec) launch_record_col0(B.ctl, B.z, st->Z, n, st->hmax, 1, bs);
+    bvec_dots(n, B.r, B.z, flex ? B.r : nullptr, flex ? B.zold : nullptr, B.partials, bs);
+    bvec_finalize(B.partials, B.sc, BFIN_RZL, flex, bs, &B.ctl->its);
+    if (k) bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, bs);
+    bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, bs);
+    schur_b(c, B.p, B.q, bs);
+    bvec_dots(n, B.p, B.q, nullptr, nullptr, B.partials, bs);
+    bvec_finalize(B.partials, B.sc, BFIN_PQ, 0, bs);
+    if (rec) {
+      launch_record_col0(B.ctl, B.p, st->P, n, st->hmax, 0, bs);
+      launch_record_col0(B.ctl, B.q, st->AP, n, st->hmax, 0, bs);
+    }
+    bvec_axpy2(n, B.sc, B.xg, B.p, B.r, B.q, B.partials, bs);
+    bvec_finalize(B.partials, B.sc, BFIN_RR, 0, bs);
+    launch_loop_check_b(B.ctl, B.sc, B.alphas, h, in_graph, bs);
+  };
+  const std::vector<uint64_t> key = {2,
+                                     (uint64_t)k,
+                                     (uint64_t)rec,
+                                     (uint64_t)st->hmax,
+                                     (uint64_t)flex,
+                                     (uint64_t)(uintptr_t)W,
+                                     (uint64_t)(uintptr_t)AW,
+                                     (uint64_t)(uintptr_t)st->Ginv,
+                                     (uint64_t)(uintptr_t)st->P,
+                                     (uint64_t)(uintptr_t)st->AP,
+                                     (uint64_t)(uintptr_t)st->Z};
+  st->loop.run(key, body, B.ctl, B.ctl_host, o.loop_graph && !c->prof_on, s);
+  const LoopCtl L = *B.ctl_host;
+  st->alphas.assign(rec ? (size_t)L.nalpha : 0, 0.0);
+  if (rec && L.nalpha > 0)
+    DD_CUDA(cudaMemcpyAsync(st->alphas.data(), B.alphas, (size_t)L.nalpha * sizeof(double), cudaMemcpyDeviceToHost,
+                            s));
   host_sc();
-  std::vector<double> rel0(BW);
-  for (int m = 0; m < BW; ++m) rel0[m] = std::sqrt(hs(BS_RR0, m)) / hs(BS_REF, m);
-  if (st) st->alphas.clear();
-  dd_status status = DD_OK;
-  int its = 0;
-  bool rec0 = record && st->hmax > 0 && hs(BS_ACT, 0) != 0.0;  // member 0 feeds the recycling
-  if (any_active()) {
-    precond_b(c, B.r, B.z, s);
-    if (rec0) launch_extract_col(n, B.z, 0, st->Z, s);
-    bvec_dots(n, B.r, B.z, nullptr, nullptr, B.partials, s);
-    bvec_finalize(B.partials, B.sc, BFIN_RZ0, 0, s);
-    if (k) {
-      bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, -1, -1.0, s);
-    } else {
-      copy_b(B.p, B.z, n, s);
-    }
-    while (true) {
-      schur_b(c, B.p, B.q, s);
-      bvec_dots(n, B.p, B.q, nullptr, nullptr, B.partials, s);
-      bvec_finalize(B.partials, B.sc, BFIN_PQ, 0, s);
-      const bool rec_now = rec0 && its < st->hmax;
-      if (rec_now) {
-        launch_extract_col(n, B.p, 0, st->P + (size_t)its * n, s);
-        launch_extract_col(n, B.q, 0, st->AP + (size_t)its * n, s);
-      }
-      bvec_axpy2(n, B.sc, B.xg, B.p, B.r, B.q, B.partials, s);
-      bvec_finalize(B.partials, B.sc, BFIN_RR, 0, s);
-      its++;
-      host_sc();
-      if (rec0) st->alphas.push_back(hs(BS_ALPHA, 0));
-      rec0 = rec0 && hs(BS_ACT, 0) != 0.0;
-      if (!any_active()) break;
-      if (its >= o.maxit) {
-        status = DD_NOT_CONVERGED;
-        break;
-      }
-      std::swap(B.z, B.zold);
-      precond_b(c, B.r, B.z, s);
-      if (rec0 && its <= st->hmax) launch_extract_col(n, B.z, 0, st->Z + (size_t)its * n, s);
-      bvec_dots(n, B.r, B.z, o.flexible ? B.r : nullptr, o.flexible ? B.zold : nullptr, B.partials, s);
-      bvec_finalize(B.partials, B.sc, BFIN_RZ, o.flexible, s);
-      if (k) bdefl_mu(n, k, AW, n, B.z, st->Ginv, B.wpart, B.mu, s);
-      bdefl_update(n, k, W, n, B.mu, B.z, B.p, B.sc, BS_BETA, -1.0, s);
-    }
-  }
+  dd_status status = L.status == LOOP_NOT_CONVERGED ? DD_NOT_CONVERGED : DD_OK;
   for (int m = 0; m < nrhs; ++m) {
     if (hs(BS_FLAG, m) != 0.0) status = DD_BREAKDOWN;
     if (stats) {
       stats[m].iters = (int)hs(BS_ITS, m);
-      stats[m].rel_res0 = rel0[m];
+      stats[m].rel_res0 = std::sqrt(hs(BS_RR0, m)) / hs(BS_REF, m);
       stats[m].rel_res = std::sqrt(hs(BS_RR, m)) / hs(BS_REF, m);
       stats[m].recycled_k = k;
       stats[m].frozen = (int)st->frozen;

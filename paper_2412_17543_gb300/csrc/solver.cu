@@ -28,6 +28,8 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
 namespace dd {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_max_smem(const void* func, int bytes) {
   static std::mutex mu;
@@ -399,6 +401,7 @@ dd_status dd_default_options(dd_options* o) {
   o->ens_nmm = DD_ENS_AUTO;
   o->ens_elem_rc = 0;
   o->ens_fdm_rc = 0;
+  o->loop_graph = 1;
   return DD_OK;
 }
 
@@ -419,6 +422,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     DD_REQUIRE(opt->ens_elem_rc == 0 || opt->ens_elem_rc == 4 || opt->ens_elem_rc == 8 || opt->ens_elem_rc == 16,
                "ens_elem_rc must be 0, 4, 8 or 16");
     DD_REQUIRE(opt->ens_fdm_rc == 0 || opt->ens_fdm_rc == 4 || opt->ens_fdm_rc == 8, "ens_fdm_rc must be 0, 4 or 8");
+    DD_REQUIRE(opt->loop_graph == 0 || opt->loop_graph == 1, "loop_graph must be 0 or 1");
     auto H = std::make_unique<HostSetup>();
     build_host_setup(*md, *opt, *H);
     auto c = std::make_unique<dd_ctx>();
@@ -563,6 +567,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->bvec = A.alloc<double>(nG);
     c->tmp = A.alloc<double>(nG);
     c->sc = A.alloc<double>(SC_COUNT);
+    c->ctl = A.alloc<LoopCtl>(1);
+    c->alphas = A.alloc<double>((size_t)opt->maxit);
     c->partials = A.alloc<double>(NBLK * MAXDOT);
     c->wpart = A.alloc<double>((size_t)std::max<int64_t>(NBLK, defl_df_blocks(c->n_gamma)) * MAXK);
     c->mu = A.alloc<double>(MAXK);
@@ -571,6 +577,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->ybuf = A.alloc<double>(128 * 128);
     c->ptrs = A.alloc<const double*>(512);
     DD_CUDA(cudaMallocHost(&c->sc_host, SC_COUNT * sizeof(double)));
+    DD_CUDA(cudaMallocHost(&c->ctl_host, sizeof(LoopCtl)));
     DD_CUDA(cudaEventCreate(&c->ev0));
     DD_CUDA(cudaEventCreate(&c->ev1));
     DD_CUDA(cudaStreamSynchronize(s));
@@ -943,71 +950,67 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   vec_sub(n, c->bvec, c->q, c->r, s);
   vec_dots(n, c->bvec, c->bvec, c->r, c->r, nullptr, nullptr, c->partials, s);
   vec_finalize(c->partials, c->sc, FIN_BB, 0, s);
-  DD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-  DD_CUDA(cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(c->sc_host[SC_BB]);
-  const double r0 = std::sqrt(c->sc_host[SC_RR]);
-  double ref = o.stop_rhs_norm ? bnorm : r0;
-  if (ref == 0.0) ref = 1.0;
-  double rel = r0 / ref;
-  int its = 0;
-  dd_status status = DD_OK;
-  if (stats) stats->rel_res0 = rel;
-  if (st) st->alphas.clear();
-  if (rel >= rtol) {
-    precond_apply(c, c->r, c->z, s);
-    if (record && st && st->hmax > 0)
-      DD_CUDA(cudaMemcpyAsync(st->Z, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
-    vec_dots(n, c->r, c->z, nullptr, nullptr, nullptr, nullptr, c->partials, s);
-    vec_finalize(c->partials, c->sc, FIN_RZ0, 0, s);
-    if (k) {
-      defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, s);
-      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, -1, -1.0, s);
-    } else {
-      DD_CUDA(cudaMemcpyAsync(c->p, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
+  launch_loop_begin(c->ctl, c->sc, rtol, o.maxit, o.stop_rhs_norm, s);
+  // p enters the first update p = z + beta p - W mu with beta = 0
+  DD_CUDA(cudaMemsetAsync(c->p, 0, n * sizeof(double), s));
+  const bool rec = record && st && st->hmax > 0;
+  const bool reo = k && o.reorth;
+  const int flex = o.flexible;
+  // one iteration of Algorithm 1 in the order z = M^{-1} r, beta, p = z + beta p - W mu,
+  // q = A p, alpha, x += alpha p, r -= alpha q, stopping test (first pass: beta = 0)
+  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool in_graph) {
+    if (flex) DD_CUDA(cudaMemcpyAsync(c->zold, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, bs));
+    precond_apply(c, c->r, c->z, bs);
+    if (rec) launch_record(c->ctl, c->z, st->Z, n, st->hmax, 1, bs);
+    vec_dots(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, nullptr, nullptr, c->partials, bs);
+    vec_finalize(c->partials, c->sc, FIN_RZL, flex, bs, &c->ctl->its);
+    if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, bs);
+    defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
+    schur_apply(c, c->p, c->q, bs);
+    vec_dots(n, c->p, c->q, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
+    vec_finalize(c->partials, c->sc, FIN_PQ, 0, bs);
+    if (rec) {
+      launch_record(c->ctl, c->p, st->P, n, st->hmax, 0, bs);
+      launch_record(c->ctl, c->q, st->AP, n, st->hmax, 0, bs);
     }
-    while (true) {
-      schur_apply(c, c->p, c->q, s);
-      vec_dots(n, c->p, c->q, nullptr, nullptr, nullptr, nullptr, c->partials, s);
-      vec_finalize(c->partials, c->sc, FIN_PQ, 0, s);
-      bool rec = record && st && its < st->hmax;
-      if (rec) {
-        DD_CUDA(cudaMemcpyAsync(st->P + (size_t)its * n, c->p, n * 8, cudaMemcpyDeviceToDevice, s));
-        DD_CUDA(cudaMemcpyAsync(st->AP + (size_t)its * n, c->q, n * 8, cudaMemcpyDeviceToDevice, s));
-      }
-      vec_axpy2(n, c->sc, c->xg, c->p, c->r, c->q, c->partials, s);
-      vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
-      if (k && o.reorth) {
-        // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
-        defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, s);
-        defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, s);
-        vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, s);
-        vec_finalize(c->partials, c->sc, FIN_RR, 0, s);
-      }
-      its++;
-      DD_CUDA(cudaMemcpyAsync(c->sc_host, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-      DD_CUDA(cudaStreamSynchronize(s));
-      if (st) st->alphas.push_back(c->sc_host[SC_ALPHA]);
-      if (c->sc_host[SC_FLAG] != 0.0) {
-        status = DD_BREAKDOWN;
-        break;
-      }
-      rel = std::sqrt(c->sc_host[SC_RR]) / ref;
-      if (rel < rtol) break;
-      if (its >= o.maxit) {
-        status = DD_NOT_CONVERGED;
-        break;
-      }
-      std::swap(c->z, c->zold);
-      precond_apply(c, c->r, c->z, s);
-      if (record && st && its <= st->hmax)
-        DD_CUDA(cudaMemcpyAsync(st->Z + (size_t)its * n, c->z, n * 8, cudaMemcpyDeviceToDevice, s));
-      vec_dots(n, c->r, c->z, o.flexible ? c->r : nullptr, o.flexible ? c->zold : nullptr, nullptr, nullptr,
-               c->partials, s);
-      vec_finalize(c->partials, c->sc, FIN_RZ, o.flexible, s);
-      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, s);
-      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, s);
+    vec_axpy2(n, c->sc, c->xg, c->p, c->r, c->q, c->partials, bs);
+    vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);
+    if (reo) {
+      // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
+      defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, bs);
+      defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, bs);
+      vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
+      vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);
     }
+    launch_loop_check(c->ctl, c->sc, c->alphas, h, in_graph, bs);
+  };
+  // everything the captured body bakes into its launches
+  const std::vector<uint64_t> key = {1,
+                                     (uint64_t)k,
+                                     (uint64_t)rec,
+                                     (uint64_t)(st ? st->hmax : 0),
+                                     (uint64_t)reo,
+                                     (uint64_t)flex,
+                                     (uint64_t)(uintptr_t)Wd,
+                                     (uint64_t)(uintptr_t)AWd,
+                                     (uint64_t)(uintptr_t)(st ? st->Ginv : nullptr),
+                                     (uint64_t)(uintptr_t)(st ? st->WWinv : nullptr),
+                                     (uint64_t)(uintptr_t)(st ? st->P : nullptr),
+                                     (uint64_t)(uintptr_t)(st ? st->AP : nullptr),
+                                     (uint64_t)(uintptr_t)(st ? st->Z : nullptr)};
+  (st ? st->loop : c->loop).run(key, body, c->ctl, c->ctl_host, o.loop_graph && !c->prof_on, s);
+  const LoopCtl L = *c->ctl_host;
+  const int its = L.its;
+  const double rel = L.rel;
+  const dd_status status =
+      L.status == LOOP_BREAKDOWN ? DD_BREAKDOWN : (L.status == LOOP_NOT_CONVERGED ? DD_NOT_CONVERGED : DD_OK);
+  if (stats) stats->rel_res0 = L.rel0;
+  // the step lengths feed the recycling update (M^{-1} A p_j from consecutive z)
+  if (st) st->alphas.assign(record ? (size_t)L.nalpha : 0, 0.0);
+  if (st && record && L.nalpha > 0) {
+    DD_CUDA(cudaMemcpyAsync(st->alphas.data(), c->alphas, (size_t)L.nalpha * sizeof(double), cudaMemcpyDeviceToHost,
+                            s));
+    DD_CUDA(cudaStreamSynchronize(s));
   }
   if (stats) {
     stats->iters = its;

@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(RB) k_axpy2(int64_t n, const double* __restric
 
 // single-block finalization: sums the partials in a fixed order (a warp per dot product,
 // fixed lane assignment and shuffle tree) and updates the scalars
-__global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible) {
+__global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible,
+                           const int* __restrict__ its) {
   __shared__ double tot[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 3) {
@@ -71,6 +72,7 @@ __global__ void k_finalize(int nblk, const double* __restrict__ partials, double
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  if (op == FIN_RZL) op = *its == 0 ? FIN_RZ0 : FIN_RZ;  // device-resident loop: first iteration or not
   switch (op) {
     case FIN_PQ: {
       double pq = tot[0];
@@ -114,8 +116,8 @@ void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, c
   k_dots<<<NBLK, RB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, partials);
   DD_CHECK_LAUNCH();
 }
-void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s) {
-  k_finalize<<<1, 96, 0, s>>>(NBLK, partials, sc, op, flexible);
+void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s, const int* its) {
+  k_finalize<<<1, 96, 0, s>>>(NBLK, partials, sc, op, flexible, its);
   DD_CHECK_LAUNCH();
 }
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,

@@ -15,11 +15,13 @@ constexpr int MAXK = 128;   // maximum deflation basis size
 enum {
   SC_RZ = 0, SC_PQ, SC_ALPHA, SC_RR, SC_BETA, SC_BB, SC_FLAG, SC_COUNT = 16
 };
-enum { FIN_PQ = 1, FIN_RR, FIN_RZ0, FIN_RZ, FIN_BB };
+// FIN_RZL: FIN_RZ0 when the device iteration count *its is 0, else FIN_RZ
+enum { FIN_PQ = 1, FIN_RR, FIN_RZ0, FIN_RZ, FIN_BB, FIN_RZL };
 
 void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, const double* a2,
               const double* b2, double* partials, cudaStream_t s);
-void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s);
+void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s,
+                  const int* its = nullptr);
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
                cudaStream_t s);
 void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
