@@ -115,7 +115,11 @@ def solver_options(wl, mixed: bool) -> dict:
 
 
 def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist, prof=False):
-    """W untimed solves then K timed solves; returns (seconds, stats list, profile)."""
+    """W untimed solves then K timed solves; returns (seconds, stats list, (profile, kernel launches)).
+
+    Without prof the solves run as the library runs them by default: each PCG loop is one
+    CUDA-graph launch. With prof, CUDA events bracket every operator application, which
+    needs the host-issued form of the same loop (same kernels, identical results)."""
     rec = solver.recycler(k, strategy)
     x = torch.empty(solver.n_free, dtype=torch.float64, device=F_dev.device)
     for t in range(warmup):
@@ -123,8 +127,7 @@ def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist,
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    if prof:
-        solver.profile(True, read=True)  # reset counters, start timing
+    solver.profile(prof, read=True)  # resets the counters; prof: starts event timing
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
@@ -136,7 +139,7 @@ def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist,
     e1.record(stream)
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
-    pr = solver.profile(False, read=True) if prof else None
+    pr = solver.profile(False, read=True)
     sec = max_over_ranks(torch, sec, dist, F_dev.device)
     rec.close()
     return sec, stats, pr
@@ -268,6 +271,10 @@ def rank_seed(wl, rank: int) -> int:
     return wl["seed"] + 1000 * rank
 
 
+PROF_TIMING = ("CUDA events around every launch of the kernel on its stream, in a replay of the same warm-up and "
+               "timed steps (fresh recycle state, identical iterates) with the PCG loop issued from the host; "
+               "the timed steps themselves run each loop as one CUDA-graph launch")
+
 ENS_METRIC = "member solves/s to rtol 1e-8, 32 graded-mesh sequences as one block (ensemble path); %HBM peak"
 
 
@@ -288,18 +295,19 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
     S = pkg.Solver(mesh, **solver_options(wl, True))
     setup_s = time.perf_counter() - t0
     hbm, peak_kind = peaks()
-    rec = S.ensemble_recycler(k, "B4")
     X = torch.empty_like(F_dev[0])
-    for t in range(args.warmup):
-        S.solve_batch(F_dev[t], rec, rtol, out=X)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    S.profile(True, read=True)
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
-    with ClockSampler(local) as clk:
+
+    def ens_run(prof):
+        rec = S.ensemble_recycler(k, "B4")
+        for t in range(args.warmup):
+            S.solve_batch(F_dev[t], rec, rtol, out=X)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        S.profile(prof, read=True)  # resets the counters; prof: event timing (host-issued loop)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
         torch.cuda.synchronize()
         e0.record(stream)
         for t in range(args.warmup, nsteps):
@@ -307,12 +315,18 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
             stats.append(st)
         e1.record(stream)
         torch.cuda.synchronize()
+        sec = max_over_ranks(torch, e0.elapsed_time(e1) / 1e3, dist, dev)
+        pr = S.profile(False, read=True)
+        rec.close()
+        return sec, stats, pr
+
+    with ClockSampler(local) as clk:
+        sec, stats, (_, launches) = ens_run(False)
     clocks = clk.summary()
-    sec = max_over_ranks(torch, e0.elapsed_time(e1) / 1e3, dist, dev)
-    prof, launches = S.profile(False, read=True)
+    prof_sec, prof_stats, (prof, _) = ens_run(True)
+    assert [[m["iters"] for m in st] for st in prof_stats] == [[m["iters"] for m in st] for st in stats]
     value = args.steps * R * world / sec
     its = [m["iters"] for st in stats for m in st]
-    rec.close()
 
     # single-sequence path on the same GPU: the first few members, each with its own state
     n_single = min(4, R)
@@ -363,11 +377,14 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
     nn = prof["ens_N"]
     nn_ms = nn[0] / max(nn[1], 1)
     achieved = nn[2] / (nn_ms / 1e3) / 1e9 if nn[1] else None
+    nmm_kernel = {1: "k_symm_b<float> (CUDA cores)", 2: "k_nmm_tc (tcgen05 kind::tf32, 3xTF32)"}.get(
+        S.info["ens_nmm"], "none")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": None,
-            "kernel": "k_symm_b<float> (ensemble constrained-Neumann products N_i R_i, eq. localCorr)",
+            "kernel": f"{nmm_kernel}: ensemble constrained-Neumann products N_i R_i, eq. localCorr",
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
-            "avg_launch_ms": nn_ms, "launches": nn[1]}
+            "avg_launch_ms": nn_ms, "launches": nn[1], "timing": PROF_TIMING,
+            "replay_ms_per_step": 1e3 * prof_sec / args.steps}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl)
@@ -446,9 +463,13 @@ def main():
     setup_mixed = time.perf_counter() - t0
     hbm, peak_kind = peaks()
     with ClockSampler(local) as clk:
-        sec, stats, (prof, launches) = run_arm(torch, mixed, F_dev, args.warmup, args.steps, k, "B4", rtol, world,
-                                               dist, prof=True)
+        sec, stats, (_, launches) = run_arm(torch, mixed, F_dev, args.warmup, args.steps, k, "B4", rtol, world, dist)
     clocks = clk.summary()
+    # per-kernel device times: a replay of the same warm-up and timed steps with CUDA
+    # events around every operator application (host-issued loop, identical iterates)
+    prof_sec, prof_stats, (prof, _) = run_arm(torch, mixed, F_dev, args.warmup, args.steps, k, "B4", rtol, world,
+                                              dist, prof=True)
+    assert [s["iters"] for s in prof_stats] == [s["iters"] for s in stats]
     total_solves = args.steps * world
     value = total_solves / sec
     its = [s["iters"] for s in stats]
@@ -486,7 +507,8 @@ def main():
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
             "kernel": "k_symv<FP32> (batched constrained-Neumann N_i GEMV, eq. localCorr)",
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
-            "avg_launch_ms": nn_ms, "launches": nn[1]}
+            "avg_launch_ms": nn_ms, "launches": nn[1], "timing": PROF_TIMING,
+            "replay_ms_per_step": 1e3 * prof_sec / args.steps}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl)

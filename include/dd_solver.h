@@ -234,7 +234,8 @@ typedef struct {
   double alg_bytes;         /* algorithmic bytes of one launch (matrix entries once, vectors in and out) */
 } dd_kernel_prof;
 /* enable != 0 starts event timing of the classes above (adds two event records
- * per timed launch); enable == 0 stops it. If prof is not NULL, writes the totals
+ * per timed launch; while it is on, solves issue their PCG iterations from the host,
+ * since a CUDA graph's conditional body cannot hold event records); enable == 0 stops it. If prof is not NULL, writes the totals
  * accumulated since the last read ([DD_PROF_COUNT], host) and resets them
  * (synchronizes `stream`). *kernel_launches (nullable) receives the number of
  * kernels this context launched since the last read. */
