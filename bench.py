@@ -292,7 +292,7 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
     t_rhs = time.perf_counter() - t0
     F_dev = F_host.to(dev)
     t0 = time.perf_counter()
-    S = pkg.Solver(mesh, **solver_options(wl, True))
+    S = pkg.Solver(mesh, **solver_options(wl, True), ens_nmm=args.ens_nmm)
     setup_s = time.perf_counter() - t0
     hbm, peak_kind = peaks()
     X = torch.empty_like(F_dev[0])
@@ -377,8 +377,8 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
     nn = prof["ens_N"]
     nn_ms = nn[0] / max(nn[1], 1)
     achieved = nn[2] / (nn_ms / 1e3) / 1e9 if nn[1] else None
-    nmm_kernel = {1: "k_symm_b<float> (CUDA cores)", 2: "k_nmm_tc (tcgen05 kind::tf32, 3xTF32)"}.get(
-        S.info["ens_nmm"], "none")
+    nmm_kernel = {1: "k_symm_b<float> (CUDA cores)", 2: "k_nmm_tc<TF32X3> (persistent, tcgen05 kind::tf32)",
+                  3: "k_nmm_tc<BF16X3> (persistent, tcgen05 kind::f16, bf16 slices)"}.get(S.info["ens_nmm"], "none")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": None,
             "kernel": f"{nmm_kernel}: ensemble constrained-Neumann products N_i R_i, eq. localCorr",
@@ -401,7 +401,8 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
                            "rhs_seeds": [seed, seed + R - 1]},
                 "iters_min_max_avg": [min(its), max(its), sum(its) / len(its)],
                 "setup_s": setup_s, "rhs_gen_s": t_rhs, "single_sequence": single,
-                "ens_nmm": {"kernel": {1: "simt", 2: "tcgen05 3xTF32"}.get(S.info["ens_nmm"], "none"),
+                "ens_nmm": {"kernel": {1: "simt", 2: "tcgen05 3xTF32", 3: "tcgen05 BF16x3"}.get(S.info["ens_nmm"],
+                                                                                                "none"),
                             "tuning_ms": S.info["ens_nmm_ms"]},
                 "ens_shapes": {"element_members_per_pass": S.info["ens_elem_rc"],
                                "fdm_members_per_block": S.info["ens_fdm_rc"]},
@@ -426,6 +427,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--ens-nmm", default="auto", choices=["auto", "simt", "tc", "bf16x3"],
+                    help="ensemble N_i product kernel (default: timed on the first call)")
     ap.add_argument("--n", type=int, default=None,
                     help="elements per axis of a smaller member of the workload's mesh family (profiling runs)")
     args = ap.parse_args()

@@ -72,7 +72,7 @@ enum { DD_WEIGHTS_CARD = 0, DD_WEIGHTS_DIAG = 1 };                 /* Sect. 3.2 
 enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_DF64 = 2 };     /* arithmetic of an operator */
 enum { DD_B1 = 1, DD_B2 = 2, DD_B3 = 3, DD_B4 = 4 };                /* Sect. 4.2 recycling strategies */
 enum { DD_LOCAL_AUTO = 0, DD_LOCAL_DENSE = 1, DD_LOCAL_FDM = 2 };   /* K_II^{-1} representation */
-enum { DD_ENS_AUTO = 0, DD_ENS_SIMT = 1, DD_ENS_TC = 2 };            /* ensemble N_i products */
+enum { DD_ENS_AUTO = 0, DD_ENS_SIMT = 1, DD_ENS_TC = 2, DD_ENS_BF16X3 = 3 };  /* ensemble N_i products */
 
 typedef struct {
   int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
@@ -91,9 +91,10 @@ typedef struct {
   int32_t maxit;            /* iteration limit per solve */
   int32_t local_solver;     /* K_II^{-1} representation: DD_LOCAL_AUTO (fast diagonalization when every
                                subdomain has a constant coefficient, else dense), DD_LOCAL_DENSE, DD_LOCAL_FDM */
-  int32_t ens_nmm;          /* ensemble products N_i R_i of an FP32 preconditioner: DD_ENS_AUTO (both
-                               kernels timed on the first ensemble call, the faster kept), DD_ENS_SIMT
-                               (CUDA-core tiles), DD_ENS_TC (tensor cores, 3xTF32) */
+  int32_t ens_nmm;          /* ensemble products N_i R_i of an FP32 preconditioner: DD_ENS_AUTO (the
+                               kernels timed on the first ensemble call, the fastest kept), DD_ENS_SIMT
+                               (CUDA-core tiles), DD_ENS_TC (tensor cores, 3xTF32), DD_ENS_BF16X3
+                               (tensor cores, bf16 operands in three slices, six products) */
   int32_t ens_elem_rc;      /* members per pass of the ensemble element kernels of a DF64 operator on
                                8^3-element subdomains: 0 (timed on the first ensemble call), 4, 8 or 16;
                                any other shape of subdomain uses 8 */
@@ -116,9 +117,9 @@ typedef struct {
   int32_t local_solver;     /* DD_LOCAL_DENSE or DD_LOCAL_FDM: the representation in use */
   int64_t device_bytes;     /* device memory held by the context */
   double setup_seconds;     /* wall time of dd_setup */
-  int32_t ens_nmm;          /* ensemble N_i kernel in use: DD_ENS_SIMT or DD_ENS_TC (0 before the first
-                               ensemble call) */
-  float ens_nmm_ms[2];      /* its selection timings (SIMT, tensor cores; 0 when not timed), ms */
+  int32_t ens_nmm;          /* ensemble N_i kernel in use: DD_ENS_SIMT, DD_ENS_TC or DD_ENS_BF16X3 (0
+                               before the first ensemble call) */
+  float ens_nmm_ms[3];      /* its selection timings (SIMT, 3xTF32, BF16x3; 0 when not timed), ms */
   int32_t ens_elem_rc;      /* members per pass of the ensemble element kernels (0 before the first call) */
   int32_t ens_fdm_rc;       /* members per block of the ensemble fast diagonalization (0 before) */
 } dd_info_t;

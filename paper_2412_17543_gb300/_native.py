@@ -14,7 +14,7 @@ WEIGHTS = {"card": 0, "diag": 1}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 STRATEGY = {"B1": 1, "B2": 2, "B3": 3, "B4": 4}
 LOCAL = {"auto": 0, "dense": 1, "fdm": 2}
-ENS_NMM = {"auto": 0, "simt": 1, "tc": 2}
+ENS_NMM = {"auto": 0, "simt": 1, "tc": 2, "bf16x3": 3}
 
 
 class MeshDesc(ctypes.Structure):
@@ -40,7 +40,7 @@ class Info(ctypes.Structure):
     _fields_ = [("n_free", ctypes.c_int64), ("n_gamma", ctypes.c_int64), ("n_sub", ctypes.c_int32),
                 ("n_coarse", ctypes.c_int32), ("n_adaptive", ctypes.c_int32), ("n_sub2", ctypes.c_int32),
                 ("n_coarse3", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 2),
+                ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 3),
                 ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32)]
 
 

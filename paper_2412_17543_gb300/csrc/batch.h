@@ -52,11 +52,11 @@ struct BatchWork {
   int elem_rc = 8, fdm_rc = 8;
   float elem_ms[3] = {0.f, 0.f, 0.f}, fdm_ms[2] = {0.f, 0.f};
   // symmetric products of the ensemble (level-1 N_i; level-2 K_II^{-1} and N): tensor-core
-  // operand copy, whether it is used, and the selection timings (SIMT, tensor cores)
+  // operand copy, the kernel in use, and the selection timings (SIMT, 3xTF32, BF16x3)
   struct SymOp {
     TcMats tc;
-    bool use_tc = false;
-    float ms[2] = {0.f, 0.f};
+    int kind = DD_ENS_SIMT;  // DD_ENS_SIMT, DD_ENS_TC (3xTF32) or DD_ENS_BF16X3
+    float ms[3] = {0.f, 0.f, 0.f};
   } op[3];
 };
 enum { BOP_N1 = 0, BOP_KII2 = 1, BOP_N2 = 2 };

@@ -29,52 +29,17 @@ void free_batch_work(BatchWork* bw) {
 namespace {
 
 // The symmetric products of the ensemble (level-1 N_i, level-2 K_II^{-1} and N) run on
-// the tensor cores (3xTF32) or on CUDA-core tiles. With DD_ENS_AUTO both kernels run on
-// the context's own operators (three timed launches each after a warm-up) and the faster
-// one is kept: the autotuning step of the ensemble path.
+// the tensor cores (3xTF32 or BF16x3 splits) or on CUDA-core tiles. With DD_ENS_AUTO the
+// kernels run on the context's own operators (three timed launches each after a warm-up)
+// and the fastest is kept: the autotuning step of the ensemble path.
 void apply_sym_b(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, const void* in, void* out,
                  cudaStream_t s) {
   const BatchWork::SymOp& o = c->bw->op[which];
-  if (o.use_tc)
-    launch_nmm_tc(o.tc, voff, (const float*)in, (float*)out, c->w.err, s);
-  else
+  if (o.kind == DD_ENS_SIMT)
     launch_symm_b(S, voff, in, out, s);
-}
-
-void select_op(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, void* in, void* out, int64_t rows,
-               cudaStream_t s) {
-  BatchWork::SymOp& o = c->bw->op[which];
-  const int mode = c->opt.ens_nmm;
-  o.use_tc = false;
-  if (S.prec != DD_PREC_FP32 || mode == DD_ENS_SIMT || S.count == 0) return;
-  std::vector<int> nh(S.count);
-  DD_CUDA(cudaMemcpyAsync(nh.data(), S.n, nh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-  DD_CUDA(cudaStreamSynchronize(s));
-  o.tc = build_tc_mats(c->bw->arena, S, nh, s);
-  const int npad = ((S.max_n + 31) / 32) * 32;
-  if (mode == DD_ENS_TC || (size_t)npad * BW * sizeof(float) > 227 * 1024) {  // CUDA-core tiles do not fit
-    o.use_tc = true;
-    return;
-  }
-  DD_CUDA(cudaMemsetAsync(in, 0, (size_t)rows * BW * sizeof(float), s));
-  cudaEvent_t e0, e1;
-  DD_CUDA(cudaEventCreate(&e0));
-  DD_CUDA(cudaEventCreate(&e1));
-  for (int v = 0; v < 2; ++v) {
-    o.use_tc = v == 1;
-    apply_sym_b(c, which, S, voff, in, out, s);
-    DD_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) apply_sym_b(c, which, S, voff, in, out, s);
-    DD_CUDA(cudaEventRecord(e1, s));
-    DD_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    o.ms[v] = ms / 3.f;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  check_err(c, s);
-  o.use_tc = o.ms[1] < o.ms[0];
+  else
+    launch_nmm_tc(o.tc, voff, (const float*)in, (float*)out, c->w.err,
+                  o.kind == DD_ENS_BF16X3 ? TC_BF16X3 : TC_TF32X3, s);
 }
 
 // mean time of three launches of f after one warm-up (ms)
@@ -94,6 +59,37 @@ float time_ms(F&& f, cudaStream_t s) {
   cudaEventDestroy(e1);
   return ms / 3.f;
 }
+
+void select_op(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, void* in, void* out, int64_t rows,
+               cudaStream_t s) {
+  BatchWork::SymOp& o = c->bw->op[which];
+  const int mode = c->opt.ens_nmm;
+  o.kind = DD_ENS_SIMT;
+  if (S.prec != DD_PREC_FP32 || mode == DD_ENS_SIMT || S.count == 0) return;
+  std::vector<int> nh(S.count);
+  DD_CUDA(cudaMemcpyAsync(nh.data(), S.n, nh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  o.tc = build_tc_mats(c->bw->arena, S, nh, s);
+  if (mode == DD_ENS_TC || mode == DD_ENS_BF16X3) {
+    o.kind = mode;
+    return;
+  }
+  const int npad = ((S.max_n + 31) / 32) * 32;
+  const bool simt_fits = (size_t)npad * BW * sizeof(float) <= 227 * 1024;  // CUDA-core tiles hold the vector
+  DD_CUDA(cudaMemsetAsync(in, 0, (size_t)rows * BW * sizeof(float), s));
+  const int kinds[3] = {DD_ENS_SIMT, DD_ENS_TC, DD_ENS_BF16X3};
+  int best = -1;
+  for (int v = 0; v < 3; ++v) {
+    o.ms[v] = 0.f;
+    if (v == 0 && !simt_fits) continue;
+    o.kind = kinds[v];
+    o.ms[v] = time_ms([&] { apply_sym_b(c, which, S, voff, in, out, s); }, s);
+    if (best < 0 || o.ms[v] < o.ms[best]) best = v;
+  }
+  check_err(c, s);
+  o.kind = kinds[best];
+}
+
 
 // launch shapes of the Schur operator of the ensemble: members per pass of the element
 // kernels (4, 8, 16) and per block of the fast diagonalization (4, 8), taken from the

@@ -418,7 +418,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
                "precond_prec must be FP64 or FP32");
     DD_REQUIRE(opt->schur_prec == DD_PREC_FP64 || opt->schur_prec == DD_PREC_DF64, "schur_prec must be FP64 or DF64");
     DD_REQUIRE(opt->maxit >= 1, "maxit must be positive");
-    DD_REQUIRE(opt->ens_nmm >= DD_ENS_AUTO && opt->ens_nmm <= DD_ENS_TC, "ens_nmm must be AUTO, SIMT or TC");
+    DD_REQUIRE(opt->ens_nmm >= DD_ENS_AUTO && opt->ens_nmm <= DD_ENS_BF16X3,
+               "ens_nmm must be AUTO, SIMT, TC or BF16X3");
     DD_REQUIRE(opt->ens_elem_rc == 0 || opt->ens_elem_rc == 4 || opt->ens_elem_rc == 8 || opt->ens_elem_rc == 16,
                "ens_elem_rc must be 0, 4, 8 or 16");
     DD_REQUIRE(opt->ens_fdm_rc == 0 || opt->ens_fdm_rc == 4 || opt->ens_fdm_rc == 8, "ens_fdm_rc must be 0, 4 or 8");
@@ -647,9 +648,8 @@ dd_status dd_get_info(const dd_ctx* c, dd_info_t* info) {
   if (!c || !info) return DD_INVALID_ARG;
   *info = c->info;
   if (c->bw) {
-    info->ens_nmm = c->bw->op[BOP_N1].use_tc ? DD_ENS_TC : DD_ENS_SIMT;
-    info->ens_nmm_ms[0] = c->bw->op[BOP_N1].ms[0];
-    info->ens_nmm_ms[1] = c->bw->op[BOP_N1].ms[1];
+    info->ens_nmm = c->bw->op[BOP_N1].kind;
+    for (int v = 0; v < 3; ++v) info->ens_nmm_ms[v] = c->bw->op[BOP_N1].ms[v];
     info->ens_elem_rc = c->bw->elem_rc;
     info->ens_fdm_rc = c->bw->fdm_rc;
   }

@@ -1,20 +1,36 @@
 // Ensemble constrained-Neumann products U_i = N_i R_i (eq. localCorr) on the 5th-generation
-// tensor cores: one CTA per subdomain, D = N_i [rows of a 128-row block] x R_i [32 members]
-// accumulated in tensor memory (tcgen05.mma kind::tf32, M = 128, N = 32, K = 8) with the
-// 3xTF32 split (a = a_hi + a_lo, a_hi = a with the 13 low mantissa bits cleared; products
-// a_hi b_hi + a_hi b_lo + a_lo b_hi), which keeps the FP32 accuracy of the preconditioner.
+// tensor cores, in a persistent kernel: one CTA per SM walks a list of work items (a
+// subdomain and a 128-row block of its N_i, full blocks first), streaming the items'
+// 32-wide k chunks through one ring of bulk copies that runs on across item boundaries.
+// For each chunk the CTA splits the FP32 tile and the members' chunk into low-precision
+// slices, and one thread issues the tcgen05.mma that accumulate D (128 rows x 32 members,
+// FP32) in tensor memory; two accumulator slots let the epilogue of an item overlap the
+// first products of the next.
 //
-// Operands in shared memory use the canonical K-major layout without swizzle: 8 x 16-byte
-// core matrices (8 rows, 4 consecutive k), core matrices adjacent in K at the leading byte
-// offset, adjacent in M (or N) at the stride byte offset.
-//   A tile (128 rows x 32 k):  [kg 8][mg 16][8][4] floats, LBO 2048 B, SBO 128 B
-//   B chunk (32 members x 32 k): [kg 8][ng 4][8][4] floats, LBO 512 B, SBO 128 B
-// N_i is kept in HBM once per subdomain as full FP32 rows in the tile order [kc][kg][mg][8][4]
-// (expanded on the device from the packed symmetric tiles), so each (k chunk, row block) tile
-// is eight contiguous slabs that cp.async.bulk copies straight into the A layout.
+// Two splits keep the FP32 accuracy of the preconditioner:
+//  * 3xTF32 (kind::tf32, K = 8): a = a_hi + a_lo with a_hi = a with the 13 low mantissa
+//    bits cleared; products a_hi b_hi + a_hi b_lo + a_lo b_hi. The first two are one
+//    MMA with N = 64 (B rows: b_hi then b_lo), the third one with N = 32.
+//  * BF16x3 (kind::f16 with bf16 operands, K = 16): a = a0 + a1 + a2, each slice the
+//    bf16 rounding of what the previous ones leave; the six products a_i b_j with
+//    i + j <= 2 are three MMAs: a0 [b0 b1 b2] (N = 96), a1 [b0 b1] (N = 64), a2 b0 (N = 32).
+// The column groups of D are summed in the epilogue.
+//
+// Operands in shared memory use the canonical K-major layout without swizzle: core
+// matrices of 8 rows x 16 bytes, adjacent in K at the leading byte offset (LBO), adjacent
+// in M (or N) at the stride byte offset (SBO).
+//   TF32 A slice (128 x 32):  [kg 8][mg 16][8][4] floats,  LBO 2048 B, SBO 128 B
+//   TF32 B (64 x 32):         [kg 8][ng 8][8][4] floats,   LBO 1024 B, SBO 128 B
+//   BF16 A slice (128 x 32):  [kb 4][mg 16][8][8] bf16,    LBO 2048 B, SBO 128 B
+//   BF16 B (96 x 32):         [kb 4][ng 12][8][8] bf16,    LBO 1536 B, SBO 128 B
+// N_i is kept in HBM once per subdomain as full FP32 rows in the TF32 tile order
+// [kc][kg][mg][8][4] (expanded on the device from the packed symmetric tiles), so each
+// (k chunk, row block) tile is eight contiguous slabs that cp.async.bulk copies as they are.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "batch.h"
 #include "ptx.cuh"
@@ -24,22 +40,63 @@ namespace dd {
 
 namespace {
 
-constexpr int TC_THREADS = 128;  // 4 warps: each owns 32 TMEM lanes (rows of a block)
-constexpr int NST = 2;           // raw A stages in flight
+constexpr int TC_THREADS = 256;  // 8 warps split the tiles; thread 0 also issues copies and MMAs
+constexpr int NST = 5;           // raw A tiles in flight per CTA
+constexpr int RAW_BYTES = 16384; // one raw tile: 128 rows x 32 k FP32
+
+template <int SCHEME>
+struct Tc;
+template <>
+struct Tc<TC_TF32X3> {
+  static constexpr int NA = 2;                // A slices
+  static constexpr int A_SLICE = 16384;       // bytes
+  static constexpr int B_BYTES = 8192;
+  static constexpr int ACC_COLS = 64;         // TMEM columns of one accumulator slot
+  static constexpr uint32_t TMEM_COLS = 128;  // two slots
+  static constexpr int NPART = 2;             // column groups summed in the epilogue
+};
+template <>
+struct Tc<TC_BF16X3> {
+  static constexpr int NA = 3;
+  static constexpr int A_SLICE = 8192;
+  static constexpr int B_BYTES = 6144;
+  static constexpr int ACC_COLS = 128;
+  static constexpr uint32_t TMEM_COLS = 256;
+  static constexpr int NPART = 3;
+};
+
+template <int SCHEME>
+constexpr size_t smem_bytes() {
+  return (size_t)NST * RAW_BYTES + 2 * (size_t)Tc<SCHEME>::NA * Tc<SCHEME>::A_SLICE + 2 * (size_t)Tc<SCHEME>::B_BYTES +
+         (NST + 4) * 8 + 16;
+}
 
 __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
   const uint64_t a = smem_u32(p);
   return ((a & 0x3FFFFull) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = 32, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptors, M = 128, D = F32, A and B K-major: kind::tf32 (A = B = TF32)
+// and kind::f16 (A = B = BF16)
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -49,70 +106,178 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive FP32 columns of the warp's 32 TMEM lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// split 32 floats per thread of a tile: hi in place is not allowed (the raw stage is reused
-// by the copy engine), so hi and lo go to the operand buffers
-__device__ __forceinline__ void split_tile(const float* raw, float* hi, float* lo, int nfl) {
-  for (int i = threadIdx.x * 4; i < nfl; i += TC_THREADS * 4) {
-    const float4 v = *reinterpret_cast<const float4*>(raw + i);
-    float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-    float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-    *reinterpret_cast<float4*>(hi + i) = h;
-    *reinterpret_cast<float4*>(lo + i) = l;
+// three bf16 slices of x: each the round-to-nearest bf16 of what the previous ones leave
+__device__ __forceinline__ void bf16_slices(float x, __nv_bfloat16& s0, __nv_bfloat16& s1, __nv_bfloat16& s2) {
+  s0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(s0);
+  s1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(s1);
+  s2 = __float2bfloat16_rn(r2);
+}
+
+struct ItemInfo {
+  int n, mg, mb, nmg, T;
+  int64_t base;
+  const float* gA;
+};
+
+__device__ __forceinline__ ItemInfo item_info(const TcMats& A, const int64_t* goff, int item) {
+  const int2 it = A.items[item];
+  ItemInfo I;
+  I.n = A.n[it.x];
+  I.mg = (I.n + 7) / 8;
+  I.mb = it.y;
+  I.nmg = min(16, I.mg - 16 * I.mb);
+  I.T = (I.n + 31) / 32;
+  I.base = goff[it.x];
+  I.gA = A.data + A.off[it.x];
+  return I;
+}
+
+// ---- operand splits (one 32-wide k chunk) ----
+// A tile: float4 index i of the raw tile holds rows (mg = (i >> 3) & 15, rr = i & 7) and
+// k = kg * 4 .. kg * 4 + 3 with kg = i >> 7; groups past the block's valid rows are skipped
+// (their products only reach accumulator rows that are never stored)
+template <int SCHEME>
+__device__ __forceinline__ void split_a(const float* rt, unsigned char* a_op, int nmg);
+template <>
+__device__ __forceinline__ void split_a<TC_TF32X3>(const float* rt, unsigned char* a_op, int nmg) {
+  float4* hi = reinterpret_cast<float4*>(a_op);
+  float4* lo = reinterpret_cast<float4*>(a_op + Tc<TC_TF32X3>::A_SLICE);
+#pragma unroll
+  for (int t = 0; t < 1024 / TC_THREADS; ++t) {
+    const int i = threadIdx.x + t * TC_THREADS;
+    if (((i >> 3) & 15) >= nmg) continue;
+    const float4 v = reinterpret_cast<const float4*>(rt)[i];
+    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+    hi[i] = h;
+    lo[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  }
+}
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+template <>
+__device__ __forceinline__ void split_a<TC_BF16X3>(const float* rt, unsigned char* a_op, int nmg) {
+#pragma unroll
+  for (int t = 0; t < 1024 / TC_THREADS; ++t) {
+    const int i = threadIdx.x + t * TC_THREADS;
+    const int kg = i >> 7, mg = (i >> 3) & 15, rr = i & 7;
+    if (mg >= nmg) continue;
+    const float4 v = reinterpret_cast<const float4*>(rt)[i];
+    __nv_bfloat16 s[3][4];
+    bf16_slices(v.x, s[0][0], s[1][0], s[2][0]);
+    bf16_slices(v.y, s[0][1], s[1][1], s[2][1]);
+    bf16_slices(v.z, s[0][2], s[1][2], s[2][2]);
+    bf16_slices(v.w, s[0][3], s[1][3], s[2][3]);
+    const int e = (((kg >> 1) * 16 + mg) * 64 + rr * 8 + (kg & 1) * 4) * 2;  // byte offset in a slice
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl)
+      *reinterpret_cast<uint2*>(a_op + sl * Tc<TC_BF16X3>::A_SLICE + e) =
+          make_uint2(pack_bf16(s[sl][0], s[sl][1]), pack_bf16(s[sl][2], s[sl][3]));
   }
 }
 
-// One CTA per (matrix, 128-row block): it streams the block's k chunks through a
-// two-stage ring of bulk copies, splits each tile and the matching member chunk into
-// hi/lo operands, and accumulates D (128 x 32 FP32) in tensor memory. 112 KiB of shared
-// memory per CTA, so two CTAs share an SM.
-__global__ void __launch_bounds__(TC_THREADS) k_nmm_tc(TcMats A, const int64_t* __restrict__ goff,
-                                                      const float* __restrict__ rloc, float* __restrict__ uloc,
-                                                      int* err) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  float* araw = reinterpret_cast<float*>(sm);                                   // [NST][4096]
-  float* ahi = araw + NST * 4096;                                               // [2][4096]
-  float* alo = ahi + 2 * 4096;                                                  // [2][4096]
-  float* bhi = alo + 2 * 4096;                                                  // [2][1024]
-  float* blo = bhi + 2 * 1024;                                                  // [2][1024]
-  uint64_t* full = reinterpret_cast<uint64_t*>(blo + 2 * 1024);                 // [NST]
-  uint64_t* done = full + NST;                                                  // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 2);
-  const int s = blockIdx.x, mb = blockIdx.y;
-  const int n = A.n[s];
-  const int mg = (n + 7) / 8;          // 8-row groups
-  const int nmb = (mg + 15) / 16;      // 128-row blocks
-  if (mb >= nmb) return;               // uniform over the block, before any allocation
-  const int T = (n + 31) / 32;         // 32-wide k chunks
-  const int nmg = min(16, mg - 16 * mb);
-  const float* gA = A.data + A.off[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t base = goff[s];
+// B chunk: this thread holds rows kq * 4 .. kq * 4 + 3 of the chunk for member j
+template <int SCHEME>
+__device__ __forceinline__ void split_b(const float (&bv)[4], unsigned char* b_op, int kq, int j);
+template <>
+__device__ __forceinline__ void split_b<TC_TF32X3>(const float (&bv)[4], unsigned char* b_op, int kq, int j) {
+  float4 h = make_float4(tf32_hi(bv[0]), tf32_hi(bv[1]), tf32_hi(bv[2]), tf32_hi(bv[3]));
+  float4 l = make_float4(bv[0] - h.x, bv[1] - h.y, bv[2] - h.z, bv[3] - h.w);
+  float* B = reinterpret_cast<float*>(b_op);
+  *reinterpret_cast<float4*>(B + ((kq * 8 + (j >> 3)) * 8 + (j & 7)) * 4) = h;
+  *reinterpret_cast<float4*>(B + ((kq * 8 + 4 + (j >> 3)) * 8 + (j & 7)) * 4) = l;
+}
+template <>
+__device__ __forceinline__ void split_b<TC_BF16X3>(const float (&bv)[4], unsigned char* b_op, int kq, int j) {
+  __nv_bfloat16 s[3][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) bf16_slices(bv[r], s[0][r], s[1][r], s[2][r]);
+  const int kb = kq >> 1, koff = (kq & 1) * 4;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    const int e = (((kb * 12 + sl * 4 + (j >> 3)) * 8 + (j & 7)) * 8 + koff) * 2;
+    *reinterpret_cast<uint2*>(b_op + e) = make_uint2(pack_bf16(s[sl][0], s[sl][1]), pack_bf16(s[sl][2], s[sl][3]));
+  }
+}
 
-  if (threadIdx.x == 0) {
+// the products of one k chunk into the accumulator at TMEM address dt
+template <int SCHEME>
+__device__ __forceinline__ void issue_mma(uint32_t dt, const unsigned char* a_op, const unsigned char* b_op, int kc);
+template <>
+__device__ __forceinline__ void issue_mma<TC_TF32X3>(uint32_t dt, const unsigned char* a_op,
+                                                     const unsigned char* b_op, int kc) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // K = 8 per instruction
+    const uint64_t ah = smem_desc(a_op + j * 4096, 2048, 128);
+    const uint64_t al = smem_desc(a_op + Tc<TC_TF32X3>::A_SLICE + j * 4096, 2048, 128);
+    const uint64_t b = smem_desc(b_op + j * 2048, 1024, 128);
+    mma_tf32(dt, ah, b, idesc_tf32(64), (kc > 0 || j > 0) ? 1u : 0u);  // a_hi [b_hi b_lo]
+    mma_tf32(dt, al, b, idesc_tf32(32), 1u);                           // a_lo b_hi
+  }
+}
+template <>
+__device__ __forceinline__ void issue_mma<TC_BF16X3>(uint32_t dt, const unsigned char* a_op,
+                                                     const unsigned char* b_op, int kc) {
+  constexpr int AS = Tc<TC_BF16X3>::A_SLICE;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {  // K = 16 per instruction
+    const uint64_t b = smem_desc(b_op + j * 3072, 1536, 128);
+    mma_f16(dt, smem_desc(a_op + j * 4096, 2048, 128), b, idesc_bf16(96), (kc > 0 || j > 0) ? 1u : 0u);
+    mma_f16(dt, smem_desc(a_op + AS + j * 4096, 2048, 128), b, idesc_bf16(64), 1u);
+    mma_f16(dt, smem_desc(a_op + 2 * AS + j * 4096, 2048, 128), b, idesc_bf16(32), 1u);
+  }
+}
+
+// Persistent kernel: CTA b takes the items b, b + gridDim.x, ...; tile g of its sequence
+// (item q, chunk kc) goes through raw stage g % NST, operand slot g % 2 and accumulator
+// slot q % 2. Every wait is bounded: on a timeout the CTA records DD_TIMEOUT, waits
+// (bounded) for its copies and products in flight, frees its tensor memory and returns.
+template <int SCHEME>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_nmm_tc(TcMats A, const int64_t* __restrict__ goff,
+                                                         const float* __restrict__ rloc, float* __restrict__ uloc,
+                                                         int* err) {
+  using P = Tc<SCHEME>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float* raw = reinterpret_cast<float*>(sm);                                   // [NST][4096]
+  unsigned char* opA = sm + (size_t)NST * RAW_BYTES;                           // [2][NA][A_SLICE]
+  unsigned char* opB = opA + 2 * (size_t)P::NA * P::A_SLICE;                   // [2][B_BYTES]
+  uint64_t* full = reinterpret_cast<uint64_t*>(opB + 2 * (size_t)P::B_BYTES);  // [NST] raw tile landed
+  uint64_t* done = full + NST;                                                 // [2] operand slot read
+  uint64_t* accf = done + 2;                                                   // [2] accumulator complete
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nq = (A.n_items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (nq <= 0) return;  // uniform over the block, before any barrier or allocation
+  auto item_of = [&](int q) { return (int)blockIdx.x + q * (int)gridDim.x; };
+
+  if (tid == 0) {
     for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
-    for (int i = 0; i < 2; ++i) mbar_init(&done[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&done[i], 1);
+      mbar_init(&accf[i], 1);
+    }
   }
   fence_mbar_init();
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(32u)
+                 "r"(P::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -121,114 +286,121 @@ __global__ void __launch_bounds__(TC_THREADS) k_nmm_tc(TcMats A, const int64_t* 
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // raw tile of k chunk kc: eight slabs of nmg 128-byte core-matrix rows
-  const uint32_t slab = (uint32_t)nmg * 128u;
-  auto issue = [&](int kc) {
-    float* dst = araw + (size_t)(kc % NST) * 4096;
-    mbar_arrive_expect_tx(&full[kc % NST], 8u * slab);
-    for (int kg = 0; kg < 8; ++kg)
-      bulk_g2s(dst + kg * 512, gA + ((size_t)(kc * 8 + kg) * mg + 16 * mb) * 32, slab, &full[kc % NST]);
-  };
-  if (threadIdx.x == 0)
-    for (int t = 0; t < NST && t < T; ++t) issue(t);
-
-  // member chunk of k chunk kc, 8 values per thread: element (member j, row k) of the B
-  // operand goes to ((kg * 4 + j / 8) * 8 + j % 8) * 4 + k % 4
-  float bv[8];
-  auto load_b = [&](int kc) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = threadIdx.x + q * TC_THREADS, k = i >> 5, j = i & 31;
-      const int row = kc * 32 + k;
-      bv[q] = (kc < T && row < n) ? rloc[(base + row) * BW + j] : 0.f;
+  // producer cursor, advanced identically by every thread (thread 0 issues the copies)
+  int pq = 0, pkc = 0, issued = 0;
+  ItemInfo PI = item_info(A, goff, item_of(0));
+  auto issue_next = [&]() {
+    if (pq >= nq) return;
+    if (tid == 0) {
+      const int st = issued % NST;
+      float* dst = raw + (size_t)st * 4096;
+      const uint32_t slab = (uint32_t)PI.nmg * 128u;
+      mbar_arrive_expect_tx(&full[st], 8u * slab);
+      for (int kg = 0; kg < 8; ++kg)
+        bulk_g2s(dst + kg * 512, PI.gA + ((size_t)(pkc * 8 + kg) * PI.mg + 16 * PI.mb) * 32, slab, &full[st]);
+    }
+    ++issued;
+    if (++pkc == PI.T) {
+      pkc = 0;
+      if (++pq < nq) PI = item_info(A, goff, item_of(pq));
     }
   };
-  load_b(0);
+  for (int i = 0; i < NST; ++i) issue_next();
 
-  bool ok = T > 0;
-  int t = 0;
-  for (; ok && t < T; ++t) {
-    const int sl = t & 1;
-    // every thread waits (bounded) for the raw tile and for the MMAs that last read the
-    // operand slot; the block leaves together if any wait gave up
-    bool mine = mbar_wait_bounded(&full[t % NST], (uint32_t)((t / NST) & 1), err);
-    if (mine && t >= 2) mine = mbar_wait_bounded(&done[sl], (uint32_t)(((t - 2) >> 1) & 1), err);
+  // the members' chunk of the next tile, in registers: rows kq * 4 + r, member lane
+  const int kq = warp;
+  float bv[4];
+  auto load_b = [&](const ItemInfo& J, int kc) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = kc * 32 + kq * 4 + r;
+      bv[r] = row < J.n ? rloc[(J.base + row) * BW + lane] : 0.f;
+    }
+  };
+  // epilogue of item qj: the column groups of its accumulator summed, rows stored
+  auto drain = [&](const ItemInfo& J, int qj) -> bool {
+    const bool w = mbar_wait_bounded(&accf[qj & 1], (uint32_t)((qj >> 1) & 1), err);
+    if (!__syncthreads_and(w)) return false;
+    tc_fence_after();
+    const int lb = (warp & 3) * 32, half = warp >> 2;
+    float acc[16], v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+#pragma unroll
+    for (int p = P::NPART - 1; p >= 0; --p) {  // smallest terms first
+      tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((qj & 1) * P::ACC_COLS + p * 32 + half * 16), v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] += v[i];
+    }
+    tc_fence_before();
+    const int row = J.mb * 128 + lb + lane;
+    if (row < J.n) {
+      float4* o = reinterpret_cast<float4*>(uloc + (J.base + row) * BW + half * 16);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) o[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+    }
+    return true;
+  };
+
+  int q = 0, kc = 0;
+  ItemInfo I = item_info(A, goff, item_of(0));
+  ItemInfo Iprev = I;
+  load_b(I, 0);
+  bool ok = true;
+  int g = 0, consumed = 0, committed = -1;
+  while (true) {
+    const int slot = g & 1;
+    bool mine = mbar_wait_bounded(&full[g % NST], (uint32_t)((g / NST) & 1), err);
+    if (mine && g >= 2) mine = mbar_wait_bounded(&done[slot], (uint32_t)(((g - 2) >> 1) & 1), err);
     if (!__syncthreads_and(mine)) {
       ok = false;
       break;
     }
-    float* hi = ahi + sl * 4096;
-    float* lo = alo + sl * 4096;
-    const float* raw = araw + (size_t)(t % NST) * 4096;
-    if (nmg == 16) {
-      split_tile(raw, hi, lo, 4096);
-    } else {
-      // partial row block: the slab rows past nmg are zero in both operands
-      for (int i = threadIdx.x; i < 4096; i += TC_THREADS) {
-        const int g = (i >> 5) & 15;
-        const float v = g < nmg ? raw[i] : 0.f;
-        const float h = tf32_hi(v);
-        hi[i] = h;
-        lo[i] = v - h;
-      }
+    unsigned char* a_op = opA + (size_t)slot * P::NA * P::A_SLICE;
+    unsigned char* b_op = opB + (size_t)slot * P::B_BYTES;
+    split_a<SCHEME>(raw + (size_t)(g % NST) * 4096, a_op, I.nmg);
+    split_b<SCHEME>(bv, b_op, kq, lane);
+    if (kc + 1 < I.T) {
+      load_b(I, kc + 1);
+    } else if (q + 1 < nq) {
+      const ItemInfo J = item_info(A, goff, item_of(q + 1));
+      load_b(J, 0);
     }
-    {
-      float* bh = bhi + sl * 1024;
-      float* bl = blo + sl * 1024;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = threadIdx.x + q * TC_THREADS, k = i >> 5, j = i & 31;
-        const int o = (((k >> 2) * 4 + (j >> 3)) * 8 + (j & 7)) * 4 + (k & 3);
-        const float h = tf32_hi(bv[q]);
-        bh[o] = h;
-        bl[o] = bv[q] - h;
-      }
-    }
-    load_b(t + 1);  // next member chunk, in flight during this tile's MMAs
     fence_proxy_async();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      if (t + NST < T) issue(t + NST);  // the raw stage of tile t has been consumed
+    consumed = g + 1;
+    issue_next();  // into the raw stage this tile has left
+    if (tid == 0) {
       tc_fence_after();
-      const float* bh = bhi + sl * 1024;
-      const float* bl = blo + sl * 1024;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint64_t ah = smem_desc(hi + j * 1024, 2048, 128), al = smem_desc(lo + j * 1024, 2048, 128);
-        const uint64_t bh_d = smem_desc(bh + j * 256, 512, 128), bl_d = smem_desc(bl + j * 256, 512, 128);
-        mma_tf32(tmem, ah, bh_d, (t > 0 || j > 0) ? 1u : 0u);
-        mma_tf32(tmem, ah, bl_d, 1u);
-        mma_tf32(tmem, al, bh_d, 1u);
-      }
-      mma_commit(&done[sl]);
+      issue_mma<SCHEME>(tmem + (uint32_t)((q & 1) * P::ACC_COLS), a_op, b_op, kc);
+      mma_commit(&done[slot]);
+      if (kc == I.T - 1) mma_commit(&accf[q & 1]);
+    }
+    committed = g;
+    if (kc == 0 && q > 0 && !drain(Iprev, q - 1)) {
+      ok = false;
+      break;
+    }
+    ++g;
+    if (++kc == I.T) {
+      kc = 0;
+      Iprev = I;
+      if (++q == nq) break;
+      I = item_info(A, goff, item_of(q));
     }
   }
-  if (ok) {
-    // the last commit covers every MMA issued before it (T > 0 here)
-    const int tl = T - 1;
-    if (!mbar_wait_bounded(&done[tl & 1], (uint32_t)((tl >> 1) & 1), err)) ok = false;
-  } else if (T > 0) {
-    // leave after the copies and MMAs in flight have landed (bounded waits)
-    for (int tt = t; tt < T && tt < t + NST; ++tt)
-      mbar_wait_bounded(&full[tt % NST], (uint32_t)((tt / NST) & 1), nullptr);
-    if (t >= 1) mbar_wait_bounded(&done[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1), nullptr);
-  }
-  tc_fence_after();
-  if (ok) {
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-    const int row = mb * 128 + warp * 32 + lane;
-    if (row < n) {
-      float4* o = reinterpret_cast<float4*>(uloc + (base + row) * BW);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    }
+  if (ok) ok = drain(Iprev, nq - 1);
+  if (!ok) {
+    // leave after the copies and products in flight have landed (bounded waits)
+    for (int t = consumed; t < issued; ++t) mbar_wait_bounded(&full[t % NST], (uint32_t)((t / NST) & 1), nullptr);
+    if (committed >= 0) mbar_wait_bounded(&done[committed & 1], (uint32_t)((committed >> 1) & 1), nullptr);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS) : "memory");
 }
+
 
 // full rows of N_i in the tile order [kc][kg][mg][8][4] from the packed upper tiles
 __global__ void k_expand_tc(SymTiles S, TcMats A) {
@@ -261,8 +433,8 @@ __global__ void k_expand_tc(SymTiles S, TcMats A) {
 
 }  // namespace
 
-size_t tc_smem_bytes() {
-  return (size_t)(NST * 4096 + 4 * 4096 + 4 * 1024) * sizeof(float) + (NST + 2) * 8 + 16;
+size_t tc_smem_bytes(int scheme) {
+  return scheme == TC_BF16X3 ? smem_bytes<TC_BF16X3>() : smem_bytes<TC_TF32X3>();
 }
 
 TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<int>& n_host, cudaStream_t s) {
@@ -271,16 +443,27 @@ TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<in
   std::vector<int64_t> off(S.count);
   int64_t tot = 0;
   int max_nmb = 1;
+  // work items (matrix, 128-row block), full blocks first so that a static round-robin
+  // over the CTAs spreads them evenly
+  std::vector<std::pair<int, int2>> items;
   for (int i = 0; i < S.count; ++i) {
     const int n = n_host[i];
     const int mg = (n + 7) / 8, nkc = (n + 31) / 32;
     off[i] = tot;
     tot += (int64_t)nkc * 8 * mg * 32;
-    max_nmb = std::max(max_nmb, (mg + 15) / 16);
+    const int nmb = (mg + 15) / 16;
+    max_nmb = std::max(max_nmb, nmb);
+    if (n > 0)
+      for (int mb = 0; mb < nmb; ++mb) items.push_back({std::min(16, mg - 16 * mb), make_int2(i, mb)});
   }
+  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<int2> it(items.size());
+  for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
   A.max_nmb = max_nmb;
   A.n = S.n;
   A.off = arena.upload(off, s);
+  A.n_items = (int)it.size();
+  A.items = arena.upload(it, s);
   A.data = arena.alloc<float>((size_t)std::max<int64_t>(tot, 1));
   DD_CUDA(cudaMemsetAsync(A.data, 0, (size_t)std::max<int64_t>(tot, 1) * sizeof(float), s));
   A.bytes = (double)tot * 4.0;
@@ -289,11 +472,30 @@ TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<in
   return A;
 }
 
-void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, cudaStream_t s) {
-  if (A.count == 0) return;
-  const size_t smem = tc_smem_bytes();
-  max_smem(k_nmm_tc, smem);
-  k_nmm_tc<<<dim3(A.count, A.max_nmb), TC_THREADS, smem, s>>>(A, goff, rloc, uloc, err);
+static int sm_count() {
+  static std::mutex mu;
+  static int dev_cached = -1, count = 0;
+  int dev = 0;
+  DD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev != dev_cached) {
+    DD_CUDA(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    dev_cached = dev;
+  }
+  return count;
+}
+
+void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, int scheme,
+                   cudaStream_t s) {
+  if (A.n_items == 0) return;
+  const int grid = std::min(A.n_items, sm_count());  // one persistent CTA per SM
+  if (scheme == TC_BF16X3) {
+    max_smem(k_nmm_tc<TC_BF16X3>, smem_bytes<TC_BF16X3>());
+    k_nmm_tc<TC_BF16X3><<<grid, TC_THREADS, smem_bytes<TC_BF16X3>(), s>>>(A, goff, rloc, uloc, err);
+  } else {
+    max_smem(k_nmm_tc<TC_TF32X3>, smem_bytes<TC_TF32X3>());
+    k_nmm_tc<TC_TF32X3><<<grid, TC_THREADS, smem_bytes<TC_TF32X3>(), s>>>(A, goff, rloc, uloc, err);
+  }
   DD_CHECK_LAUNCH();
 }
 

@@ -11,10 +11,15 @@
 
 namespace dd {
 
-// full FP32 rows of every N_i in the tcgen05 operand tile order
+// operand splits of the tensor-core products (FP32 accuracy from low-precision slices)
+enum { TC_TF32X3 = 0, TC_BF16X3 = 1 };
+
+// full FP32 rows of every N_i in the tcgen05 operand tile order, and the work items
 struct TcMats {
   int count = 0;
-  int max_nmb = 1;              // most 128-row blocks of a matrix (grid height)
+  int max_nmb = 1;              // most 128-row blocks of a matrix
+  int n_items = 0;              // (matrix, 128-row block) items, full blocks first
+  const int2* items = nullptr;  // [n_items] (matrix, block) (device)
   const int* n = nullptr;       // [count] local interface sizes (device)
   const int64_t* off = nullptr; // [count] first float of each matrix (device)
   float* data = nullptr;
@@ -23,8 +28,10 @@ struct TcMats {
 
 // expands the packed FP32 symmetric tiles S (device) into TcMats; n_host = S's sizes
 TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<int>& n_host, cudaStream_t s);
-// uloc[(goff[i] + r) * BW + m] = sum_c N_i[r][c] rloc[(goff[i] + c) * BW + m]  (3xTF32 on tcgen05)
-void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, cudaStream_t s);
-size_t tc_smem_bytes();
+// uloc[(goff[i] + r) * BW + m] = sum_c N_i[r][c] rloc[(goff[i] + c) * BW + m] on tcgen05
+// with the split `scheme` (TC_TF32X3 or TC_BF16X3); a persistent CTA per SM
+void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, int scheme,
+                   cudaStream_t s);
+size_t tc_smem_bytes(int scheme);
 
 }  // namespace dd

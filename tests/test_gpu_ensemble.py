@@ -99,10 +99,11 @@ def test_schur_apply_batch_rejects_df64_dense():
 
 @pytest.mark.parametrize("name", ["cube16_cf", "graded24_s8", "graded16_s2_3l"])
 @pytest.mark.parametrize("weights", ["card", "diag"])
-@pytest.mark.parametrize("prec,nmm,tol", [("fp64", "auto", 1e-10), ("fp32", "simt", 1e-4), ("fp32", "tc", 1e-4)])
+@pytest.mark.parametrize("prec,nmm,tol", [("fp64", "auto", 1e-10), ("fp32", "simt", 1e-4), ("fp32", "tc", 1e-4),
+                                          ("fp32", "bf16x3", 1e-4)])
 def test_precond_apply_batch(name, weights, prec, nmm, tol):
-    """BDDC of the ensemble; with FP32 both N_i kernels (CUDA-core tiles and tensor-core
-    3xTF32, including the partial 128-row block of 386-row operators) are checked."""
+    """BDDC of the ensemble; with FP32 every N_i kernel (CUDA-core tiles, tensor-core
+    3xTF32 and BF16x3, including the partial 128-row block of 386-row operators) is checked."""
     m, subs, kinds, levels = case(name)
     S = P.Solver(m, **_opts(levels, kinds, weights=weights, precond_prec=prec, ens_nmm=nmm))
     Po = dd.Preconditioner(subs, levels, kinds, weights, group=4)
@@ -112,7 +113,7 @@ def test_precond_apply_batch(name, weights, prec, nmm, tol):
         zo = Po.apply(R[j])
         assert np.abs(Z[j] - zo).max() <= tol * np.abs(zo).max()
     if prec == "fp32":
-        assert S.info["ens_nmm"] == (2 if nmm == "tc" else 1)
+        assert S.info["ens_nmm"] == {"simt": 1, "tc": 2, "bf16x3": 3}[nmm]
     S.close()
 
 
@@ -121,7 +122,7 @@ def test_nmm_autotune_picks_a_kernel():
     S = P.Solver(m, **_opts(2, kinds, precond_prec="fp32", ens_nmm="auto"))
     S.precond_apply_batch(T(np.ones((2, len(subs.gamma)))))
     info = S.info
-    assert info["ens_nmm"] in (1, 2) and min(info["ens_nmm_ms"]) > 0.0
+    assert info["ens_nmm"] in (1, 2, 3) and min(info["ens_nmm_ms"]) > 0.0
     S.close()
 
 
@@ -144,7 +145,7 @@ def _member_sequences(m, nrhs, steps, seed0):
 
 @pytest.mark.parametrize("name", ["cube16_cf", "graded16_s2_3l", "graded24_s8"])
 @pytest.mark.parametrize("schur,pre,flex,nmm", [("fp64", "fp64", 0, "auto"), ("df64", "fp32", 1, "simt"),
-                                                ("df64", "fp32", 1, "tc")])
+                                                ("df64", "fp32", 1, "tc"), ("df64", "fp32", 1, "bf16x3")])
 @pytest.mark.parametrize("k", [0, 6])
 def test_solve_batch_matches_direct(name, schur, pre, flex, nmm, k):
     m, subs, kinds, levels = case(name)
@@ -218,4 +219,22 @@ def test_solve_batch_invalid_arguments():
         S.solve_batch(F[:0], rec_b)                   # no member
     with pytest.raises(DDError):
         S.solve_batch(F[:2], rec_1)                   # single-sequence state
+    S.close()
+
+
+@pytest.mark.parametrize("nmm", ["tc", "bf16x3"])
+def test_precond_apply_batch_persistent_items(nmm):
+    """125 subdomains give 500 (subdomain, 128-row block) items, more than the GPU has
+    SMs: each persistent CTA walks several items, so the copy ring runs across item
+    boundaries and both accumulator slots are used. All 32 members against the oracle."""
+    m = make_mesh(40, 8, 1.2, 20.0)
+    subs = dd.q1_substructures(m)
+    kinds = (dd.CORNER, dd.EDGE, dd.FACE)
+    S = P.Solver(m, **_opts(2, kinds, precond_prec="fp32", ens_nmm=nmm))
+    Po = dd.Preconditioner(subs, 2, kinds, "diag", group=4)
+    R = np.random.default_rng(9).standard_normal((W, len(subs.gamma)))
+    Z = N(S.precond_apply_batch(T(R)))
+    for j in range(W):
+        zo = Po.apply(R[j])
+        assert np.abs(Z[j] - zo).max() <= 1e-4 * np.abs(zo).max(), j
     S.close()

@@ -145,7 +145,7 @@ def test_profiling_uses_host_loop_with_same_results():
     Sref.close()
 
 
-@pytest.mark.parametrize("mixed,nmm", [(False, "auto"), (True, "tc")])
+@pytest.mark.parametrize("mixed,nmm", [(False, "auto"), (True, "tc"), (True, "bf16x3")])
 def test_graph_loop_equals_host_loop_ensemble(mixed, nmm):
     m, levels = mesh("graded24_s8")
     prec = dict(schur_prec="df64", precond_prec="fp32", flexible=1, local_solver="fdm") if mixed else {}
