@@ -40,9 +40,23 @@ namespace dd {
 
 namespace {
 
-constexpr int TC_THREADS = 256;  // 8 warps split the tiles; thread 0 also issues copies and MMAs
-constexpr int NST = 5;           // raw A tiles in flight per CTA
-constexpr int RAW_BYTES = 16384; // one raw tile: 128 rows x 32 k FP32
+// warp roles of a CTA: 8 consumer warps (operand splits, epilogue), one thread that issues
+// the tensor-core products, one thread that issues the bulk copies
+constexpr int NCONS = 256;
+constexpr int MMA_WARP = NCONS / 32;
+constexpr int PROD_WARP = MMA_WARP + 1;
+constexpr int TC_THREADS = NCONS + 64;
+constexpr int NST = 5;                   // raw tiles in flight per CTA
+constexpr int RAW_A = 16384;             // A tile: 128 rows x 32 k FP32
+constexpr int RAW_BYTES = RAW_A + 4096;  // + the members' chunk: 32 rows x 32 members FP32
+constexpr int MAXQ = 128;                // work items of one CTA (table in shared memory)
+
+// a work item as the CTA keeps it in shared memory
+struct ItemS {
+  int64_t base;  // first row of the matrix in the members' local vectors
+  int64_t aoff;  // first float of the matrix in TcMats::data
+  int n, mg, mb, nmg, T, pad;
+};
 
 template <int SCHEME>
 struct Tc;
@@ -68,7 +82,7 @@ struct Tc<TC_BF16X3> {
 template <int SCHEME>
 constexpr size_t smem_bytes() {
   return (size_t)NST * RAW_BYTES + 2 * (size_t)Tc<SCHEME>::NA * Tc<SCHEME>::A_SLICE + 2 * (size_t)Tc<SCHEME>::B_BYTES +
-         (NST + 4) * 8 + 16;
+         MAXQ * sizeof(ItemS) + (2 * NST + 8) * 8 + 16;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
@@ -130,25 +144,6 @@ __device__ __forceinline__ void bf16_slices(float x, __nv_bfloat16& s0, __nv_bfl
   s2 = __float2bfloat16_rn(r2);
 }
 
-struct ItemInfo {
-  int n, mg, mb, nmg, T;
-  int64_t base;
-  const float* gA;
-};
-
-__device__ __forceinline__ ItemInfo item_info(const TcMats& A, const int64_t* goff, int item) {
-  const int2 it = A.items[item];
-  ItemInfo I;
-  I.n = A.n[it.x];
-  I.mg = (I.n + 7) / 8;
-  I.mb = it.y;
-  I.nmg = min(16, I.mg - 16 * I.mb);
-  I.T = (I.n + 31) / 32;
-  I.base = goff[it.x];
-  I.gA = A.data + A.off[it.x];
-  return I;
-}
-
 // ---- operand splits (one 32-wide k chunk) ----
 // A tile: float4 index i of the raw tile holds rows (mg = (i >> 3) & 15, rr = i & 7) and
 // k = kg * 4 .. kg * 4 + 3 with kg = i >> 7; groups past the block's valid rows are skipped
@@ -160,8 +155,8 @@ __device__ __forceinline__ void split_a<TC_TF32X3>(const float* rt, unsigned cha
   float4* hi = reinterpret_cast<float4*>(a_op);
   float4* lo = reinterpret_cast<float4*>(a_op + Tc<TC_TF32X3>::A_SLICE);
 #pragma unroll
-  for (int t = 0; t < 1024 / TC_THREADS; ++t) {
-    const int i = threadIdx.x + t * TC_THREADS;
+  for (int t = 0; t < 1024 / NCONS; ++t) {
+    const int i = threadIdx.x + t * NCONS;
     if (((i >> 3) & 15) >= nmg) continue;
     const float4 v = reinterpret_cast<const float4*>(rt)[i];
     const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
@@ -175,8 +170,8 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
 template <>
 __device__ __forceinline__ void split_a<TC_BF16X3>(const float* rt, unsigned char* a_op, int nmg) {
 #pragma unroll
-  for (int t = 0; t < 1024 / TC_THREADS; ++t) {
-    const int i = threadIdx.x + t * TC_THREADS;
+  for (int t = 0; t < 1024 / NCONS; ++t) {
+    const int i = threadIdx.x + t * NCONS;
     const int kg = i >> 7, mg = (i >> 3) & 15, rr = i & 7;
     if (mg >= nmg) continue;
     const float4 v = reinterpret_cast<const float4*>(rt)[i];
@@ -245,38 +240,89 @@ __device__ __forceinline__ void issue_mma<TC_BF16X3>(uint32_t dt, const unsigned
   }
 }
 
-// Persistent kernel: CTA b takes the items b, b + gridDim.x, ...; tile g of its sequence
-// (item q, chunk kc) goes through raw stage g % NST, operand slot g % 2 and accumulator
-// slot q % 2. Every wait is bounded: on a timeout the CTA records DD_TIMEOUT, waits
-// (bounded) for its copies and products in flight, frees its tensor memory and returns.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded mbarrier wait that also gives up once another role of the CTA has given up
+__device__ __forceinline__ bool wait_tc(uint64_t* bar, uint32_t parity, int* err, volatile int* abort) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  if (err) atomicExch(err, (int)DD_TIMEOUT);
+  *abort = 1;
+  return false;
+}
+
+// Persistent, warp-specialized kernel. CTA b takes the items b, b + gridDim.x, ... (at
+// most MAXQ); its tiles g = 0, 1, ... (item q, k chunk kc) pass through raw stage g % NST,
+// operand slot g % 2 and accumulator slot q % 2:
+//   producer thread: waits until the consumers have split the stage's previous tile
+//     (empty), then bulk-copies the A tile and the members' chunk (full);
+//   consumer warps: wait for the tile (full) and for the products that last read the
+//     operand slot (done), split into the slot, release the stage (empty) and hand the
+//     slot to the tensor cores (opready); after the first tile of an item they drain the
+//     previous item's accumulator (accf), free it (acce) and store its rows;
+//   MMA thread: waits for the operands (opready) and, at an item's first tile, for its
+//     accumulator slot to be drained (acce); issues the products and commits them to
+//     done, and at the item's last tile to accf.
+// Every wait is bounded: on a timeout the CTA records DD_TIMEOUT, the other roles stop at
+// their next wait, and the CTA waits (bounded) for its copies and products in flight,
+// frees its tensor memory and returns.
 template <int SCHEME>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_nmm_tc(TcMats A, const int64_t* __restrict__ goff,
                                                          const float* __restrict__ rloc, float* __restrict__ uloc,
                                                          int* err) {
   using P = Tc<SCHEME>;
   extern __shared__ __align__(1024) unsigned char sm[];
-  float* raw = reinterpret_cast<float*>(sm);                                   // [NST][4096]
-  unsigned char* opA = sm + (size_t)NST * RAW_BYTES;                           // [2][NA][A_SLICE]
-  unsigned char* opB = opA + 2 * (size_t)P::NA * P::A_SLICE;                   // [2][B_BYTES]
-  uint64_t* full = reinterpret_cast<uint64_t*>(opB + 2 * (size_t)P::B_BYTES);  // [NST] raw tile landed
-  uint64_t* done = full + NST;                                                 // [2] operand slot read
-  uint64_t* accf = done + 2;                                                   // [2] accumulator complete
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+  unsigned char* raw = sm;                                                // [NST][RAW_BYTES]
+  unsigned char* opA = raw + (size_t)NST * RAW_BYTES;                     // [2][NA][A_SLICE]
+  unsigned char* opB = opA + 2 * (size_t)P::NA * P::A_SLICE;              // [2][B_BYTES]
+  ItemS* items = reinterpret_cast<ItemS*>(opB + 2 * (size_t)P::B_BYTES);  // [MAXQ]
+  uint64_t* full = reinterpret_cast<uint64_t*>(items + MAXQ);             // [NST] tile landed
+  uint64_t* empty = full + NST;                                           // [NST] tile split
+  uint64_t* opready = empty + NST;                                        // [2] operands written
+  uint64_t* done = opready + 2;                                           // [2] the slot's products complete
+  uint64_t* accf = done + 2;                                              // [2] an item's accumulator complete
+  uint64_t* acce = accf + 2;                                              // [2] accumulator drained
+  int* ctl = reinterpret_cast<int*>(acce + 2);  // TMEM address, abort flag, tiles issued, last committed tile
+  volatile int* abort = ctl + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nq = (A.n_items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int nq = min(MAXQ, (A.n_items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
   if (nq <= 0) return;  // uniform over the block, before any barrier or allocation
-  auto item_of = [&](int q) { return (int)blockIdx.x + q * (int)gridDim.x; };
 
+  for (int q = tid; q < nq; q += TC_THREADS) {
+    const int2 it = A.items[(int)blockIdx.x + q * (int)gridDim.x];
+    ItemS I;
+    I.n = A.n[it.x];
+    I.mg = (I.n + 7) / 8;
+    I.mb = it.y;
+    I.nmg = min(16, I.mg - 16 * I.mb);
+    I.T = (I.n + 31) / 32;
+    I.base = goff[it.x];
+    I.aoff = A.off[it.x];
+    I.pad = 0;
+    items[q] = I;
+  }
   if (tid == 0) {
-    for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCONS);
+    }
     for (int i = 0; i < 2; ++i) {
+      mbar_init(&opready[i], NCONS);
       mbar_init(&done[i], 1);
       mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], NCONS);
     }
+    ctl[1] = 0;
+    ctl[2] = 0;
+    ctl[3] = -1;
   }
   fence_mbar_init();
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(ctl)),
                  "r"(P::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -284,123 +330,132 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nmm_tc(TcMats A, const int64_
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
+  const uint32_t tmem = (uint32_t)ctl[0];
 
-  // producer cursor, advanced identically by every thread (thread 0 issues the copies)
-  int pq = 0, pkc = 0, issued = 0;
-  ItemInfo PI = item_info(A, goff, item_of(0));
-  auto issue_next = [&]() {
-    if (pq >= nq) return;
-    if (tid == 0) {
-      const int st = issued % NST;
-      float* dst = raw + (size_t)st * 4096;
-      const uint32_t slab = (uint32_t)PI.nmg * 128u;
-      mbar_arrive_expect_tx(&full[st], 8u * slab);
-      for (int kg = 0; kg < 8; ++kg)
-        bulk_g2s(dst + kg * 512, PI.gA + ((size_t)(pkc * 8 + kg) * PI.mg + 16 * PI.mb) * 32, slab, &full[st]);
+  if (warp == PROD_WARP) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const ItemS I = items[q];
+        const float* gA = A.data + I.aoff;
+        const uint32_t slab = (uint32_t)I.nmg * 128u;
+        for (int kc = 0; kc < I.T; ++kc, ++g) {
+          const int st = g % NST;
+          if (g >= NST && !wait_tc(&empty[st], (uint32_t)(((g / NST) - 1) & 1), err, abort)) {
+            ok = false;
+            break;
+          }
+          unsigned char* dst = raw + (size_t)st * RAW_BYTES;
+          const int vb = min(32, I.n - kc * 32);  // members' rows of this chunk inside the matrix
+          mbar_arrive_expect_tx(&full[st], 8u * slab + (uint32_t)vb * 128u);
+          for (int kg = 0; kg < 8; ++kg)
+            bulk_g2s(dst + kg * 2048, gA + ((size_t)(kc * 8 + kg) * I.mg + 16 * I.mb) * 32, slab, &full[st]);
+          bulk_g2s(dst + RAW_A, rloc + (I.base + kc * 32) * BW, (uint32_t)vb * 128u, &full[st]);
+          ctl[2] = g + 1;
+        }
+      }
     }
-    ++issued;
-    if (++pkc == PI.T) {
-      pkc = 0;
-      if (++pq < nq) PI = item_info(A, goff, item_of(pq));
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const int T = items[q].T;
+        if (q >= 2 && !wait_tc(&acce[q & 1], (uint32_t)(((q - 2) >> 1) & 1), err, abort)) break;
+        const uint32_t dt = tmem + (uint32_t)((q & 1) * P::ACC_COLS);
+        for (int kc = 0; kc < T; ++kc, ++g) {
+          const int slot = g & 1;
+          if (!wait_tc(&opready[slot], (uint32_t)((g >> 1) & 1), err, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          issue_mma<SCHEME>(dt, opA + (size_t)slot * P::NA * P::A_SLICE, opB + (size_t)slot * P::B_BYTES, kc);
+          mma_commit(&done[slot]);
+          if (kc == T - 1) mma_commit(&accf[q & 1]);
+          ctl[3] = g;
+        }
+      }
     }
-  };
-  for (int i = 0; i < NST; ++i) issue_next();
-
-  // the members' chunk of the next tile, in registers: rows kq * 4 + r, member lane
-  const int kq = warp;
-  float bv[4];
-  auto load_b = [&](const ItemInfo& J, int kc) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = kc * 32 + kq * 4 + r;
-      bv[r] = row < J.n ? rloc[(J.base + row) * BW + lane] : 0.f;
-    }
-  };
-  // epilogue of item qj: the column groups of its accumulator summed, rows stored
-  auto drain = [&](const ItemInfo& J, int qj) -> bool {
-    const bool w = mbar_wait_bounded(&accf[qj & 1], (uint32_t)((qj >> 1) & 1), err);
-    if (!__syncthreads_and(w)) return false;
-    tc_fence_after();
-    const int lb = (warp & 3) * 32, half = warp >> 2;
-    float acc[16], v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-#pragma unroll
-    for (int p = P::NPART - 1; p >= 0; --p) {  // smallest terms first
-      tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((qj & 1) * P::ACC_COLS + p * 32 + half * 16), v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] += v[i];
-    }
-    tc_fence_before();
-    const int row = J.mb * 128 + lb + lane;
-    if (row < J.n) {
-      float4* o = reinterpret_cast<float4*>(uloc + (J.base + row) * BW + half * 16);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) o[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-    }
-    return true;
-  };
-
-  int q = 0, kc = 0;
-  ItemInfo I = item_info(A, goff, item_of(0));
-  ItemInfo Iprev = I;
-  load_b(I, 0);
-  bool ok = true;
-  int g = 0, consumed = 0, committed = -1;
-  while (true) {
-    const int slot = g & 1;
-    bool mine = mbar_wait_bounded(&full[g % NST], (uint32_t)((g / NST) & 1), err);
-    if (mine && g >= 2) mine = mbar_wait_bounded(&done[slot], (uint32_t)(((g - 2) >> 1) & 1), err);
-    if (!__syncthreads_and(mine)) {
-      ok = false;
-      break;
-    }
-    unsigned char* a_op = opA + (size_t)slot * P::NA * P::A_SLICE;
-    unsigned char* b_op = opB + (size_t)slot * P::B_BYTES;
-    split_a<SCHEME>(raw + (size_t)(g % NST) * 4096, a_op, I.nmg);
-    split_b<SCHEME>(bv, b_op, kq, lane);
-    if (kc + 1 < I.T) {
-      load_b(I, kc + 1);
-    } else if (q + 1 < nq) {
-      const ItemInfo J = item_info(A, goff, item_of(q + 1));
-      load_b(J, 0);
-    }
-    fence_proxy_async();
-    __syncthreads();
-    consumed = g + 1;
-    issue_next();  // into the raw stage this tile has left
-    if (tid == 0) {
+  } else {
+    // consumers: warp kq holds rows kq * 4 .. kq * 4 + 3 of each members' chunk
+    const int kq = warp;
+    auto drain = [&](const ItemS& J, int qj) -> bool {
+      const bool w = __all_sync(0xffffffffu, wait_tc(&accf[qj & 1], (uint32_t)((qj >> 1) & 1), err, abort));
+      if (!w) return false;
       tc_fence_after();
-      issue_mma<SCHEME>(tmem + (uint32_t)((q & 1) * P::ACC_COLS), a_op, b_op, kc);
-      mma_commit(&done[slot]);
-      if (kc == I.T - 1) mma_commit(&accf[q & 1]);
+      const int lb = (warp & 3) * 32, half = warp >> 2;
+      float acc[16], v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+#pragma unroll
+      for (int p = P::NPART - 1; p >= 0; --p) {  // smallest terms first
+        tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)((qj & 1) * P::ACC_COLS + p * 32 + half * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] += v[i];
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[qj & 1]);
+      const int row = J.mb * 128 + lb + lane;
+      if (row < J.n) {
+        float4* o = reinterpret_cast<float4*>(uloc + (J.base + row) * BW + half * 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+      }
+      return true;
+    };
+    int g = 0;
+    bool ok = true;
+    for (int q = 0; q < nq && ok; ++q) {
+      const ItemS I = items[q];
+      for (int kc = 0; kc < I.T; ++kc, ++g) {
+        const int st = g % NST, slot = g & 1;
+        // every lane polls; the warp continues only if all its lanes' waits succeeded
+        bool w = wait_tc(&full[st], (uint32_t)((g / NST) & 1), err, abort);
+        if (g >= 2) w = wait_tc(&done[slot], (uint32_t)(((g - 2) >> 1) & 1), err, abort) && w;
+        if (!__all_sync(0xffffffffu, w)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* rs = raw + (size_t)st * RAW_BYTES;
+        split_a<SCHEME>(reinterpret_cast<const float*>(rs), opA + (size_t)slot * P::NA * P::A_SLICE, I.nmg);
+        const float* rb = reinterpret_cast<const float*>(rs + RAW_A);
+        const int vb = min(32, I.n - kc * 32);
+        float bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = kq * 4 + r;
+          bv[r] = row < vb ? rb[row * BW + lane] : 0.f;
+        }
+        split_b<SCHEME>(bv, opB + (size_t)slot * P::B_BYTES, kq, lane);
+        fence_proxy_async();
+        mbar_arrive(&opready[slot]);
+        mbar_arrive(&empty[st]);
+        if (kc == 0 && q > 0 && !drain(items[q - 1], q - 1)) {
+          ok = false;
+          break;
+        }
+      }
     }
-    committed = g;
-    if (kc == 0 && q > 0 && !drain(Iprev, q - 1)) {
-      ok = false;
-      break;
-    }
-    ++g;
-    if (++kc == I.T) {
-      kc = 0;
-      Iprev = I;
-      if (++q == nq) break;
-      I = item_info(A, goff, item_of(q));
-    }
+    if (ok) drain(items[nq - 1], nq - 1);
   }
-  if (ok) ok = drain(Iprev, nq - 1);
-  if (!ok) {
-    // leave after the copies and products in flight have landed (bounded waits)
-    for (int t = consumed; t < issued; ++t) mbar_wait_bounded(&full[t % NST], (uint32_t)((t / NST) & 1), nullptr);
-    if (committed >= 0) mbar_wait_bounded(&done[committed & 1], (uint32_t)((committed >> 1) & 1), nullptr);
+  __syncthreads();
+  if (*abort && tid == 0) {
+    // leave after the copies and products in flight have landed (bounded waits): the
+    // last tile issued into each stage, and the last committed products
+    const int issued = ctl[2];
+    for (int st = 0; st < NST; ++st) {
+      const int t = issued - 1 - (((issued - 1 - st) % NST) + NST) % NST;
+      if (t >= 0) mbar_wait_bounded(&full[st], (uint32_t)((t / NST) & 1), nullptr);
+    }
+    if (ctl[3] >= 0) mbar_wait_bounded(&done[ctl[3] & 1], (uint32_t)((ctl[3] >> 1) & 1), nullptr);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS) : "memory");
 }
-
 
 // full rows of N_i in the tile order [kc][kg][mg][8][4] from the packed upper tiles
 __global__ void k_expand_tc(SymTiles S, TcMats A) {
@@ -488,7 +543,8 @@ static int sm_count() {
 void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, int scheme,
                    cudaStream_t s) {
   if (A.n_items == 0) return;
-  const int grid = std::min(A.n_items, sm_count());  // one persistent CTA per SM
+  // one persistent CTA per SM, more when an SM would hold more than MAXQ items
+  const int grid = std::max(std::min(A.n_items, sm_count()), (A.n_items + MAXQ - 1) / MAXQ);
   if (scheme == TC_BF16X3) {
     max_smem(k_nmm_tc<TC_BF16X3>, smem_bytes<TC_BF16X3>());
     k_nmm_tc<TC_BF16X3><<<grid, TC_THREADS, smem_bytes<TC_BF16X3>(), s>>>(A, goff, rloc, uloc, err);
