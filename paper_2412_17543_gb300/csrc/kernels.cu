@@ -565,7 +565,9 @@ void launch_restrict(int64_t nflat, const int* gmap, const double* D, const doub
 // staged once per block in shared memory, converted to the matrix type T, so FP32
 // operators also do FP32 arithmetic (the BDDC preconditioner in FP32 mode).
 //   k_bgemv:   y_m = alpha A_m x_m (+ add), warp per row, lanes along the row (coalesced)
-//   k_bgemv_t: y_m = alpha A_m^T x_m (+ add), thread per column, rows streamed in order
+//   k_bgemv_t: y_m = alpha A_m^T x_m (+ add), thread per column; the rows are split into
+//              blockDim.y slices (slice s takes rows s, s + RS, ...) for tall matrices, and the
+//              slice sums are added in slice order
 constexpr int BGEMV_ROWS = 32;    // rows per block of k_bgemv (8 warps x 4 rows)
 constexpr int BGEMV_T_COLS = 128; // columns per block of k_bgemv_t
 
@@ -625,48 +627,58 @@ void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map
 }
 
 template <class T>
-__global__ void __launch_bounds__(BGEMV_T_COLS) k_bgemv_t(const int64_t* __restrict__ row0,
-                                                          const int* __restrict__ cols,
-                                                          const int64_t* __restrict__ moff, const T* __restrict__ M,
-                                                          const int64_t* __restrict__ in_off,
-                                                          const int* __restrict__ in_map,
-                                                          const double* __restrict__ in,
-                                                          const int64_t* __restrict__ out_off,
-                                                          double* __restrict__ out, double alpha,
-                                                          const double* __restrict__ add) {
+__global__ void __launch_bounds__(1024) k_bgemv_t(const int64_t* __restrict__ row0, const int* __restrict__ cols,
+                                                  const int64_t* __restrict__ moff, const T* __restrict__ M,
+                                                  const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
+                                                  const double* __restrict__ in, const int64_t* __restrict__ out_off,
+                                                  double* __restrict__ out, double alpha,
+                                                  const double* __restrict__ add, int xs_len) {
   extern __shared__ __align__(16) unsigned char bg_smem[];
-  T* xs = reinterpret_cast<T*>(bg_smem);
+  T* xs = reinterpret_cast<T*>(bg_smem);  // [xs_len]
+  T* part = xs + xs_len;                   // [RS][BGEMV_T_COLS]
   const int m = blockIdx.x;
   const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
-  const int j = blockIdx.y * BGEMV_T_COLS + threadIdx.x;
-  if (blockIdx.y * BGEMV_T_COLS >= C) return;
+  if (blockIdx.y * BGEMV_T_COLS >= C) return;  // uniform over the block
+  const int RS = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * BGEMV_T_COLS + tx;
+  const int j = blockIdx.y * BGEMV_T_COLS + tx;
   const int64_t io = in_off[m];
-  for (int i = threadIdx.x; i < R; i += blockDim.x) xs[i] = (T)in[in_map ? in_map[io + i] : io + i];
+  for (int i = tid; i < R; i += BGEMV_T_COLS * RS) xs[i] = (T)in[in_map ? in_map[io + i] : io + i];
   __syncthreads();
-  if (j >= C) return;
-  const T* A = M + moff[m] + j;
   T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int i = 0;
-  for (; i + 3 < R; i += 4) {
-    a0 = fma(A[(int64_t)i * C], xs[i], a0);
-    a1 = fma(A[(int64_t)(i + 1) * C], xs[i + 1], a1);
-    a2 = fma(A[(int64_t)(i + 2) * C], xs[i + 2], a2);
-    a3 = fma(A[(int64_t)(i + 3) * C], xs[i + 3], a3);
+  if (j < C) {
+    const T* A = M + moff[m] + j;
+    int i = ty;
+    for (; i + 3 * RS < R; i += 4 * RS) {
+      a0 = fma(A[(int64_t)i * C], xs[i], a0);
+      a1 = fma(A[(int64_t)(i + RS) * C], xs[i + RS], a1);
+      a2 = fma(A[(int64_t)(i + 2 * RS) * C], xs[i + 2 * RS], a2);
+      a3 = fma(A[(int64_t)(i + 3 * RS) * C], xs[i + 3 * RS], a3);
+    }
+    for (; i < R; i += RS) a0 = fma(A[(int64_t)i * C], xs[i], a0);
   }
-  for (; i < R; ++i) a0 = fma(A[(int64_t)i * C], xs[i], a0);
-  const int64_t oo = out_off[m];
-  out[oo + j] = alpha * (double)((a0 + a1) + (a2 + a3)) + (add ? add[oo + j] : 0.0);
+  part[ty * BGEMV_T_COLS + tx] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (ty == 0 && j < C) {
+    T v = part[tx];
+    for (int q = 1; q < RS; ++q) v += part[q * BGEMV_T_COLS + tx];
+    const int64_t oo = out_off[m];
+    out[oo + j] = alpha * (double)v + (add ? add[oo + j] : 0.0);
+  }
 }
 
 template <class T>
 static void bgemv_t_go(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                        const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
-  size_t smem = (size_t)std::max(B.max_rows, 1) * sizeof(T);
+  // row slices: one per 32 rows of the tallest matrix, at most 8 (1024 threads)
+  const int rs = std::min(8, std::max(1, B.max_rows / 32));
+  const int xs_len = (std::max(B.max_rows, 1) + 3) / 4 * 4;
+  size_t smem = ((size_t)xs_len + (size_t)rs * BGEMV_T_COLS) * sizeof(T);
   if (smem > 48 * 1024)
     max_smem(k_bgemv_t<T>, smem);
   dim3 grid(B.count, (B.max_cols + BGEMV_T_COLS - 1) / BGEMV_T_COLS);
-  k_bgemv_t<T><<<grid, BGEMV_T_COLS, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off,
-                                                 in_map, in, out_off, out, alpha, add);
+  k_bgemv_t<T><<<grid, dim3(BGEMV_T_COLS, rs), smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data),
+                                                           in_off, in_map, in, out_off, out, alpha, add, xs_len);
 }
 
 void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,

@@ -174,13 +174,21 @@ __global__ void __launch_bounds__(RB) k_wdots2(int64_t n, int64_t per, const dou
 // per output row forms Ginv d the same way
 __global__ void __launch_bounds__(1024) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
                                                 const double* __restrict__ Ginv, double* mu) {
+  // warp w sums the blocks w, w + 32, ... with the lanes along the columns (rows of wpart
+  // read whole); the 32 warp sums are then added in warp order
+  __shared__ double part[32][MAXK];
   __shared__ double d[MAXK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = warp; c < k; c += nw) {
+  for (int c = lane; c < k; c += 32) {
     double sum = 0.0;
-    for (int b = lane; b < nblk; b += 32) sum += wpart[(int64_t)b * MAXK + c];
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) d[c] = sum;
+    for (int b = warp; b < nblk; b += nw) sum += wpart[(int64_t)b * MAXK + c];
+    part[warp][c] = sum;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double sum = 0.0;
+    for (int w = 0; w < nw; ++w) sum += part[w][c];
+    d[c] = sum;
   }
   __syncthreads();
   for (int a = warp; a < k; a += nw) {
