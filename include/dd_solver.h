@@ -134,8 +134,13 @@ typedef struct {
 } dd_stats;
 
 /* Defaults: 3 levels, group 4, corners+edges+faces, diag weights, no adaptivity,
- * FP64 everywhere, not flexible, stop on ||r||/||b||, maxit 500. */
+ * FP64 everywhere, not flexible, stop on ||r||/||b||, maxit 500, device-resident loop. */
 dd_status dd_default_options(dd_options* opt /* host, out */);
+
+/* sizes[0..4] = sizeof dd_mesh_desc, dd_options, dd_info_t, dd_stats, dd_kernel_prof as
+ * this library was built: a binding checks its own struct layouts against them
+ * (host only, no device needed). */
+void dd_abi_struct_sizes(size_t* sizes /* host, out [5] */);
 
 /* Builds the partition, globs, constraints, local factorizations, coarse levels
  * and uploads them to the current device (Sects. 3.1-3.3). Host inputs are

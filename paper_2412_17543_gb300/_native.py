@@ -62,6 +62,7 @@ _P = ctypes.c_void_p
 _D = ctypes.c_double
 SIGNATURES = {
     "dd_default_options": (ctypes.c_int, [ctypes.POINTER(Options)]),
+    "dd_abi_struct_sizes": (None, [ctypes.POINTER(ctypes.c_size_t)]),
     "dd_setup": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
     "dd_destroy": (None, [_P]),
     "dd_last_error": (ctypes.c_char_p, []),

@@ -405,6 +405,15 @@ dd_status dd_default_options(dd_options* o) {
   return DD_OK;
 }
 
+void dd_abi_struct_sizes(size_t* sizes) {
+  if (!sizes) return;
+  sizes[0] = sizeof(dd_mesh_desc);
+  sizes[1] = sizeof(dd_options);
+  sizes[2] = sizeof(dd_info_t);
+  sizes[3] = sizeof(dd_stats);
+  sizes[4] = sizeof(dd_kernel_prof);
+}
+
 dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, dd_ctx** out) {
   if (!md || !opt || !out) {
     g_last_error = "dd_setup: NULL argument";

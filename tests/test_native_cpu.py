@@ -41,6 +41,20 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(_native.SIGNATURES), "binding must declare exactly the header's functions"
 
 
+def test_binding_struct_layouts_match_the_library():
+    """The ctypes mirrors of the public structs have the C sizes (a field added on one side
+    only would shift every later field); the defaults read back through them."""
+    lib = _lib()
+    from paper_2412_17543_gb300 import _native as nat
+    sizes = (ctypes.c_size_t * 5)()
+    lib.dd_abi_struct_sizes(sizes)
+    mine = [ctypes.sizeof(c) for c in (nat.MeshDesc, nat.Options, nat.Info, nat.Stats, nat.KernelProf)]
+    assert list(sizes) == mine
+    o = nat.Options()
+    assert lib.dd_default_options(ctypes.byref(o)) == 0
+    assert (o.levels, o.maxit, o.loop_graph, o.ens_nmm, o.ens_elem_rc, o.ens_fdm_rc) == (3, 500, 1, 0, 0, 0)
+
+
 @pytest.mark.parametrize("n,sub,levels,kinds", [(16, 4, 2, dict(use_edges=0)), (16, 2, 3, {}), (12, 4, 2, {})])
 def test_plan_matches_oracle_partition(n, sub, levels, kinds):
     _lib()
