@@ -72,16 +72,6 @@ void launch_to_float(int64_t n, const double* in, float* out, cudaStream_t s) {
   DD_CHECK_LAUNCH();
 }
 
-__global__ void k_extract_col(int64_t n, const df64* __restrict__ in, int col, double* __restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = df64_to_double_bits(in[i * BW + col]);
-}
-void launch_extract_col(int64_t n, const df64* in, int col, double* out, cudaStream_t s) {
-  if (n == 0) return;
-  k_extract_col<<<grid_for_b(n, 256), 256, 0, s>>>(n, in, col, out);
-  DD_CHECK_LAUNCH();
-}
-
 // ---------------------------------------------------------------------------
 // element passes (work lists as in the single-vector kernels). A block takes one
 // subdomain and a chunk of RC members; lane = (item within the warp) * RC + member.

@@ -66,8 +66,6 @@ enum { BOP_N1 = 0, BOP_KII2 = 1, BOP_N2 = 2 };
 void launch_pack_in(int64_t n, int nrhs, const double* F, df64* out, cudaStream_t s);
 // X[m * n + i] = in[i * BW + m] for m < nrhs
 void launch_pack_out(int64_t n, int nrhs, const df64* in, double* X, cudaStream_t s);
-// out[i] = in[i * BW + col]
-void launch_extract_col(int64_t n, const df64* in, int col, double* out, cudaStream_t s);
 void launch_to_float(int64_t n, const double* in, float* out, cudaStream_t s);
 
 // ---- Schur-complement operator (interleaved counterparts of the single-vector kernels) ----

@@ -488,10 +488,6 @@ __global__ void k_expand_tc(SymTiles S, TcMats A) {
 
 }  // namespace
 
-size_t tc_smem_bytes(int scheme) {
-  return scheme == TC_BF16X3 ? smem_bytes<TC_BF16X3>() : smem_bytes<TC_TF32X3>();
-}
-
 TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<int>& n_host, cudaStream_t s) {
   TcMats A;
   A.count = S.count;

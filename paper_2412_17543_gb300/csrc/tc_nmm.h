@@ -32,6 +32,5 @@ TcMats build_tc_mats(DeviceArena& arena, const SymTiles& S, const std::vector<in
 // with the split `scheme` (TC_TF32X3 or TC_BF16X3); a persistent CTA per SM
 void launch_nmm_tc(const TcMats& A, const int64_t* goff, const float* rloc, float* uloc, int* err, int scheme,
                    cudaStream_t s);
-size_t tc_smem_bytes(int scheme);
 
 }  // namespace dd

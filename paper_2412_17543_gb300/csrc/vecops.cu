@@ -139,43 +139,12 @@ void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_
 // ---------------------------------------------------------------------------
 // deflation
 // ---------------------------------------------------------------------------
-// wpart[b][c] = sum over the rows of chunk b of V_c[i] v[i]: one block per (row chunk,
-// column), so every block streams one contiguous piece of one column (long DRAM bursts)
-// instead of every thread touching all k columns of its row
-__global__ void __launch_bounds__(RB) k_wdots2(int64_t n, int64_t per, const double* __restrict__ V, int64_t ld,
-                                               const double* __restrict__ v, double* wpart) {
-  const int b = blockIdx.x, c = blockIdx.y;
-  const int64_t i0 = (int64_t)b * per, i1 = min(n, i0 + per);
-  const double* col = V + (int64_t)c * ld;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int64_t i = i0 + threadIdx.x;
-  for (; i + 3 * RB < i1; i += 4 * RB) {
-    a0 = fma(col[i], v[i], a0);
-    a1 = fma(col[i + RB], v[i + RB], a1);
-    a2 = fma(col[i + 2 * RB], v[i + 2 * RB], a2);
-    a3 = fma(col[i + 3 * RB], v[i + 3 * RB], a3);
-  }
-  for (; i < i1; i += RB) a0 = fma(col[i], v[i], a0);
-  double x = (a0 + a1) + (a2 + a3);
-  __shared__ double sh[RB / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  if (lane == 0) sh[warp] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < RB / 32; ++w) sum += sh[w];
-    wpart[(int64_t)b * MAXK + c] = sum;
-  }
-}
-
-// mu = Ginv * (sum of partials)   (k x k, one block of 1024 threads): a warp per column
-// sums the block partials (lanes stride over the blocks, fixed shuffle tree), then a warp
-// per output row forms Ginv d the same way
+// mu = Ginv * (sum of partials)   (k x k, one block of 1024 threads): warp w sums the
+// block partials w, w + 32, ... with the lanes along the columns (rows of wpart read
+// whole), the 32 warp sums are added in warp order, then a warp per output row forms
+// Ginv d (fixed shuffle tree): a fixed reduction order throughout
 __global__ void __launch_bounds__(1024) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
                                                 const double* __restrict__ Ginv, double* mu) {
-  // warp w sums the blocks w, w + 32, ... with the lanes along the columns (rows of wpart
-  // read whole); the 32 warp sums are then added in warp order
   __shared__ double part[32][MAXK];
   __shared__ double d[MAXK];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -197,38 +166,6 @@ __global__ void __launch_bounds__(1024) k_wfinal(int nblk, int k, const double* 
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) mu[a] = sum;
   }
-}
-
-void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, const double* Ginv, double* wpart,
-             double* mu, cudaStream_t s) {
-  if (k == 0) return;
-  const int64_t per = (n + NBLK - 1) / NBLK;
-  k_wdots2<<<dim3(NBLK, k), RB, 0, s>>>(n, per, W, ld, v, wpart);
-  DD_CHECK_LAUNCH();
-  k_wfinal<<<1, 1024, 0, s>>>(NBLK, k, wpart, Ginv, mu);
-  DD_CHECK_LAUNCH();
-}
-
-// y = alpha_z * z + beta * y - W mu   (beta taken from sc[beta_idx] if beta_idx >= 0, else 0)
-__global__ void k_pupdate(int64_t n, int k, const double* __restrict__ W, int64_t ld, const double* __restrict__ mu,
-                          const double* __restrict__ z, double* __restrict__ y, const double* __restrict__ sc,
-                          int beta_idx, double sign_w) {
-  __shared__ double m[MAXK];
-  for (int c = threadIdx.x; c < k; c += blockDim.x) m[c] = mu[c];
-  __syncthreads();
-  const double beta = beta_idx >= 0 ? sc[beta_idx] : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double v = (z ? z[i] : 0.0) + (beta_idx >= 0 ? beta * y[i] : (z ? 0.0 : y[i]));
-    double wm = 0.0;
-    for (int c = 0; c < k; ++c) wm = fma(W[(int64_t)c * ld + i], m[c], wm);
-    y[i] = v + sign_w * wm;
-  }
-}
-
-void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
-                 const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
-  k_pupdate<<<NBLK, RB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
-  DD_CHECK_LAUNCH();
 }
 
 // ---------------------------------------------------------------------------

@@ -25,12 +25,7 @@ void vec_finalize(const double* partials, double* sc, int op, int flexible, cuda
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
                cudaStream_t s);
 void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
-void defl_mu(int64_t n, int k, const double* W, int64_t ld, const double* v, const double* Ginv, double* wpart,
-             double* mu, cudaStream_t s);
-// y = z + beta*y + sign_w * W mu  (beta from sc[beta_idx] if beta_idx >= 0; with z == NULL and beta_idx < 0: y += sign_w W mu)
-void defl_update(int64_t n, int k, const double* W, int64_t ld, const double* mu, const double* z, double* y,
-                 const double* sc, int beta_idx, double sign_w, cudaStream_t s);
-// df64-stored basis (float pairs) variant of defl_update, and the conversion
+// deflation with the basis stored as df64 (float pairs), and the conversion
 void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s);
 // mu with the basis as df64 (V: k columns, stride ld); wpart: [defl_df_blocks(n)][MAXK]
 int defl_df_blocks(int64_t n);
