@@ -5,7 +5,7 @@ Tolerances (derived from the arithmetic):
     the oracle's LAPACK-based dense path: |y - y_oracle| <= 1e-12 * max|y_oracle|.
   * DF64 Schur operator (float pairs, ~2^-44 per operation): 1e-11 * max|y|.
   * FP32 preconditioner: 1e-4 * max|z| (single-precision storage, FP32 sums).
-  * Solutions (spec tolerance): relative 2-norm error vs the sparse Cholesky
+  * Solutions (the stated solution tolerance): relative 2-norm error vs the sparse Cholesky
     solution <= 1e-7 at rtol 1e-9.
 """
 import numpy as np
