@@ -122,3 +122,30 @@ def assemble(mesh) -> sp.csr_matrix:
     n = mesh.n_free
     K = sp.coo_matrix((vals[keep], (rows[keep], cols[keep])), shape=(n, n))
     return K.tocsr()
+
+
+def load_vector(m, f) -> np.ndarray:
+    """Consistent load vector b_i = integral of f phi_i over the free nodes' hat functions
+    (trilinear phi_i), by 3x3x3 Gauss quadrature per brick; f is a callable f(x, y, z) on
+    arrays (manufactured-solution checks of the discretization, Sect. 2)."""
+    gp = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)]) * 0.5 + 0.5
+    gw = np.array([5 / 9, 8 / 9, 5 / 9]) * 0.5
+    conn, _ = element_arrays(m)
+    ez, ey, ex = np.meshgrid(np.arange(m.nz), np.arange(m.ny), np.arange(m.nx), indexing="ij")
+    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
+    x0, hx = m.xc[ex], np.diff(m.xc)[ex]
+    y0, hy = m.yc[ey], np.diff(m.yc)[ey]
+    z0, hz = m.zc[ez], np.diff(m.zc)[ez]
+    b = np.zeros(m.n_free)
+    for i, qx in enumerate(gp):
+        for j, qy in enumerate(gp):
+            for k, qz in enumerate(gp):
+                w = gw[i] * gw[j] * gw[k] * hx * hy * hz
+                fv = f(x0 + qx * hx, y0 + qy * hy, z0 + qz * hz) * w
+                for a in range(8):
+                    sx, sy, sz = a & 1, (a >> 1) & 1, (a >> 2) & 1
+                    phi = (qx if sx else 1 - qx) * (qy if sy else 1 - qy) * (qz if sz else 1 - qz)
+                    c = conn[:, a]
+                    ok = c >= 0
+                    np.add.at(b, c[ok], (fv * phi)[ok])
+    return b

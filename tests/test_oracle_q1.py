@@ -50,31 +50,6 @@ def test_assembly_constant_nullspace_and_symmetry():
     assert np.abs((K @ np.ones(K.shape[0]))[rows]).max() < 1e-13
 
 
-def _gauss_load(m, f):
-    """b_i = int f phi_i by 3x3x3 Gauss per brick (test-only)."""
-    gp = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)]) * 0.5 + 0.5
-    gw = np.array([5 / 9, 8 / 9, 5 / 9]) * 0.5
-    conn, _ = q1.element_arrays(m)
-    ez, ey, ex = np.meshgrid(np.arange(m.nz), np.arange(m.ny), np.arange(m.nx), indexing="ij")
-    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
-    x0, hx = m.xc[ex], np.diff(m.xc)[ex]
-    y0, hy = m.yc[ey], np.diff(m.yc)[ey]
-    z0, hz = m.zc[ez], np.diff(m.zc)[ez]
-    b = np.zeros(m.n_free)
-    for i, qx in enumerate(gp):
-        for j, qy in enumerate(gp):
-            for k, qz in enumerate(gp):
-                w = gw[i] * gw[j] * gw[k] * hx * hy * hz
-                fv = f(x0 + qx * hx, y0 + qy * hy, z0 + qz * hz) * w
-                for a in range(8):
-                    sx, sy, sz = a & 1, (a >> 1) & 1, (a >> 2) & 1
-                    phi = (qx if sx else 1 - qx) * (qy if sy else 1 - qy) * (qz if sz else 1 - qz)
-                    c = conn[:, a]
-                    ok = c >= 0
-                    np.add.at(b, c[ok], (fv * phi)[ok])
-    return b
-
-
 def _bisect(m):
     """Nested refinement: every element split in two along each axis."""
     from workload import Mesh
@@ -93,7 +68,7 @@ def test_manufactured_solution_second_order(ratio, aspect):
         if level:
             m = _bisect(m)
         K = q1.assemble(m)
-        x = cholesky.factor_mesh(m, K).solve(_gauss_load(m, f))
+        x = cholesky.factor_mesh(m, K).solve(q1.load_vector(m, f))
         pts = m.free_node_coords()
         errs.append(np.abs(x - p(pts[:, 0], pts[:, 1], pts[:, 2])).max())
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
