@@ -122,6 +122,11 @@ typedef struct {
   float ens_nmm_ms[3];      /* its selection timings (SIMT, 3xTF32, BF16x3; 0 when not timed), ms */
   int32_t ens_elem_rc;      /* members per pass of the ensemble element kernels (0 before the first call) */
   int32_t ens_fdm_rc;       /* members per block of the ensemble fast diagonalization (0 before) */
+  int32_t neumann;          /* 1: no Dirichlet face (pure Neumann, Sect. 2): K is semidefinite with the
+                               constants as null space; dd_solve projects the load vector onto the
+                               range of K (removes its mean), keeps the preconditioned residuals
+                               orthogonal to the constants (the constant column of the deflation
+                               basis, Sect. 4.1) and returns the mean-free solution */
 } dd_info_t;
 
 typedef struct {

@@ -29,6 +29,8 @@ struct dd_ctx {
   std::vector<int64_t> gamma_free_host;
   int64_t n_free = 0, n_gamma = 0;
   int levels = 2;
+  bool neumann = false;         // no Dirichlet face: solutions are the mean-free representatives
+  double* fc = nullptr;         // [n_free] the consistent (mean-free) load vector (neumann)
   DevMesh mesh{};
   DevBDDC b1{};
   DevLevel2 l2{};

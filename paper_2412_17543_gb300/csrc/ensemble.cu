@@ -424,6 +424,10 @@ dd_status dd_solve_batch(dd_ctx* c, int32_t nrhs, const double* F, double* X, do
     set_last_error("dd_solve_batch: invalid argument");
     return DD_INVALID_ARG;
   }
+  if (c->neumann) {
+    set_last_error("dd_solve_batch: the pure-Neumann case (no Dirichlet face) is solved by dd_solve only");
+    return DD_INVALID_ARG;
+  }
   if (c->mesh.local_solver != DD_LOCAL_FDM && c->mesh.schur_prec == DD_PREC_DF64) {
     set_last_error("dd_solve_batch: dense K_II^{-1} needs schur_prec FP64 for ensembles");
     return DD_INVALID_ARG;

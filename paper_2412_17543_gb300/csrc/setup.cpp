@@ -543,7 +543,9 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
              "subdomain sizes must be in [1, 8]");
   DD_REQUIRE(md.nx % md.sub_x == 0 && md.ny % md.sub_y == 0 && md.nz % md.sub_z == 0,
              "subdomain sizes must divide the mesh");
-  DD_REQUIRE((md.dirichlet_faces & 63u) != 0, "at least one Dirichlet face is required (SPD matrix)");
+  // no Dirichlet face: the pure-Neumann problem (semidefinite K, Sect. 2)
+  H.neumann = (md.dirichlet_faces & 63u) == 0;
+  DD_REQUIRE(!(H.neumann && opt.adaptive), "adaptive constraints are not supported without a Dirichlet face");
   DD_REQUIRE(opt.levels == 2 || opt.levels == 3, "levels must be 2 or 3");
   DD_REQUIRE(opt.weights == DD_WEIGHTS_CARD || opt.weights == DD_WEIGHTS_DIAG, "weights must be card or diag");
   Mesh1& M = H.mesh;
@@ -821,8 +823,17 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
   }
 
   H.levels = opt.levels;
+  // Without a Dirichlet face the coarse matrix is singular in the coarse coordinates of the
+  // constant function (all ones: corners and averages of a constant are 1), and the coarse
+  // right-hand side of a residual orthogonal to the constants is orthogonal to that vector.
+  // The grounded matrix K_C + K_C[0][0] e_0 e_0^T is SPD, and its solution u of a consistent
+  // system has u_0 = 0 and solves K_C u = g (multiply by the null vector).
+  auto ground = [&](int n, std::vector<double>& KC) {
+    if (H.neumann && n > 0) KC[0] += KC[0];
+  };
   if (opt.levels == 2) {
     std::vector<double> KC = assemble_coarse(L1);
+    ground(L1.n_coarse, KC);
     H.KCinv.resize(KC.size());
     if (!la::spd_inverse(L1.n_coarse, KC.data(), H.KCinv.data()))
       throw Error(DD_SINGULAR_LOCAL, "coarse matrix is not SPD");
@@ -899,6 +910,7 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
         },
         nloc2, I2, G2, true, AdaptiveOpts(), "level 2");
     std::vector<double> KC3 = assemble_coarse(L2);
+    ground(L2.n_coarse, KC3);
     H.KC3inv.resize(KC3.size());
     if (!la::spd_inverse(L2.n_coarse, KC3.data(), H.KC3inv.data()))
       throw Error(DD_SINGULAR_LOCAL, "level-3 coarse matrix is not SPD");

@@ -73,6 +73,9 @@ struct HostSetup {
   std::vector<int> gam2_c;            // level-2 interface index -> level-1 coarse dof
   std::vector<int> imap2;             // flat level-2 interior -> level-1 coarse dof
   std::vector<double> KC3inv;         // n_coarse3^2
+  // no Dirichlet face: K is semidefinite with the constants as null space (Sect. 2); the
+  // coarse inverses are those of the grounded coarse matrices (first coarse dof)
+  bool neumann = false;
   double setup_seconds = 0;
 };
 

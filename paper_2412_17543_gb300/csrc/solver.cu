@@ -269,6 +269,14 @@ void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
              s);
 }
 
+// z = M^{-1} r as the PCG sees it: without a Dirichlet face the constant interface vector
+// is the null-space column of the deflation basis, and z is kept orthogonal to it (its mean
+// removed) so the search directions are too
+void precond_z(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
+  precond_apply(c, r, z, s);
+  if (c->neumann) vec_sub_mean(c->n_gamma, z, z, c->partials, s);
+}
+
 void check_err(dd_ctx* c, cudaStream_t s) {
   int e = 0;
   DD_CUDA(cudaMemcpyAsync(&e, c->w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -438,9 +446,11 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     auto c = std::make_unique<dd_ctx>();
     c->opt = *opt;
     c->levels = H->levels;
+    c->neumann = H->neumann;
     const Mesh1& M = H->mesh;
     DeviceArena& A = c->arena;
     c->n_free = M.n_free;
+    if (c->neumann) c->fc = A.alloc<double>((size_t)std::max<int64_t>(M.n_free, 1));
     c->n_gamma = H->l1.n_gamma;
     c->gamma_free_host = M.gamma_free;
     // ---- level-1 mesh / Schur operator ----
@@ -619,6 +629,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->info.n_sub2 = c->levels == 3 ? H->l2.S : 0;
     c->info.n_coarse3 = c->levels == 3 ? H->l2.n_coarse : 0;
     c->info.local_solver = H->local_solver;
+    c->info.neumann = c->neumann ? 1 : 0;
     c->info.device_bytes = (int64_t)A.bytes;
     c->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = c.release();
@@ -642,6 +653,7 @@ dd_status dd_plan(const dd_mesh_desc* md, const dd_options* opt, dd_info_t* info
     info->n_sub = H.mesh.S;
     info->n_coarse = H.l1.n_coarse;
     info->n_adaptive = H.l1.n_adaptive;
+    info->neumann = H.neumann ? 1 : 0;
     info->n_sub2 = H.levels == 3 ? H.l2.S : 0;
     info->n_coarse3 = H.levels == 3 ? H.l2.n_coarse : 0;
     info->local_solver = H.local_solver;
@@ -855,7 +867,7 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
     if (j + 1 < l)
       zdiff(n, st->Z + (size_t)j * n, st->Z + (size_t)(j + 1) * n, 1.0 / st->alphas[j], st->MAP + (size_t)j * n, s);
     else
-      precond_apply(c, st->AP + (size_t)j * n, st->MAP + (size_t)j * n, s);
+      precond_z(c, st->AP + (size_t)j * n, st->MAP + (size_t)j * n, s);
   }
   std::vector<const double*> V, AV, MAV;
   for (int j = 0; j < st->k; ++j) {
@@ -969,7 +981,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   // q = A p, alpha, x += alpha p, r -= alpha q, stopping test (first pass: beta = 0)
   auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle h, bool in_graph) {
     if (flex) DD_CUDA(cudaMemcpyAsync(c->zold, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, bs));
-    precond_apply(c, c->r, c->z, bs);
+    precond_z(c, c->r, c->z, bs);
     if (rec) launch_record(c->ctl, c->z, st->Z, n, st->hmax, 1, bs);
     vec_dots(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, nullptr, nullptr, c->partials, bs);
     vec_finalize(c->partials, c->sc, FIN_RZL, flex, bs, &c->ctl->its);
@@ -1006,7 +1018,8 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
                                      (uint64_t)(uintptr_t)(st ? st->WWinv : nullptr),
                                      (uint64_t)(uintptr_t)(st ? st->P : nullptr),
                                      (uint64_t)(uintptr_t)(st ? st->AP : nullptr),
-                                     (uint64_t)(uintptr_t)(st ? st->Z : nullptr)};
+                                     (uint64_t)(uintptr_t)(st ? st->Z : nullptr),
+                                     (uint64_t)c->neumann};
   (st ? st->loop : c->loop).run(key, body, c->ctl, c->ctl_host, o.loop_graph && !c->prof_on, s);
   const LoopCtl L = *c->ctl_host;
   const int its = L.its;
@@ -1043,11 +1056,17 @@ dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycl
   dd_status gs = guard([&] {
     cudaStream_t s = (cudaStream_t)stream;
     DD_CUDA(cudaEventRecord(c->ev0, s));
+    if (c->neumann) {
+      // pure Neumann: the load vector projected onto the range of K (its mean removed)
+      vec_sub_mean(c->n_free, f, c->fc, c->partials, s);
+      f = c->fc;
+    }
     condense(c, f, c->bvec, s);
     DD_CUDA(cudaMemcpyAsync(c->xg, st->xg_prev, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
     bool record = st->kmax > 0 && !st->frozen;
     result = pcg_solve(c, st, rtol, record, stats, s);
     recover(c, f, c->xg, x, s);
+    if (c->neumann) vec_sub_mean(c->n_free, x, x, c->partials, s);  // the mean-free representative
     DD_CUDA(cudaMemcpyAsync(st->xg_prev, c->xg, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
     if (record && (result == DD_OK || result == DD_NOT_CONVERGED)) {
       ProfScope pr(c, DD_PROF_RECYCLE, s);
@@ -1096,6 +1115,10 @@ dd_status dd_adjoint(dd_ctx* c, const double* grad_x, const double* x, double* g
                      double rtol, dd_recycle* st, dd_stats* stats, void* stream) {
   if (!c || !grad_x || !grad_f || (grad_coef && !x) || !(rtol > 0.0) || (st && st->ctx != c)) {
     g_last_error = "dd_adjoint: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  if (c->neumann) {
+    g_last_error = "dd_adjoint: the pure-Neumann case (no Dirichlet face) has no adjoint solve";
     return DD_INVALID_ARG;
   }
   dd_status result = DD_OK;

@@ -136,6 +136,34 @@ void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_
   DD_CHECK_LAUNCH();
 }
 
+// out = in - mean(in) (the l2 projection onto the complement of the constants): block sums
+// on the fixed reduction grid, then every block adds the partial sums in the same order, so
+// all subtract the same value
+__global__ void __launch_bounds__(RB) k_sum(int64_t n, const double* __restrict__ in, double* partials) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) v[0] += in[i];
+  block_reduce_store<1>(v, partials);
+}
+__global__ void __launch_bounds__(RB) k_sub_mean(int64_t n, const double* in, double* out,
+                                                 const double* __restrict__ partials, int nblk) {
+  __shared__ double mean;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) s += partials[b * MAXDOT];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) mean = s / (double)n;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) out[i] = in[i] - mean;
+}
+void vec_sub_mean(int64_t n, const double* in, double* out, double* partials, cudaStream_t s) {
+  if (n == 0) return;
+  k_sum<<<NBLK, RB, 0, s>>>(n, in, partials);
+  DD_CHECK_LAUNCH();
+  k_sub_mean<<<NBLK, RB, 0, s>>>(n, in, out, partials, NBLK);
+  DD_CHECK_LAUNCH();
+}
+
 // ---------------------------------------------------------------------------
 // deflation
 // ---------------------------------------------------------------------------

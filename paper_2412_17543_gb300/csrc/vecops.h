@@ -25,6 +25,8 @@ void vec_finalize(const double* partials, double* sc, int op, int flexible, cuda
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
                cudaStream_t s);
 void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+// out = in - mean(in) (in == out allowed); partials: [NBLK * MAXDOT] scratch
+void vec_sub_mean(int64_t n, const double* in, double* out, double* partials, cudaStream_t s);
 // deflation with the basis stored as df64 (float pairs), and the conversion
 void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s);
 // mu with the basis as df64 (V: k columns, stride ld); wpart: [defl_df_blocks(n)][MAXK]

@@ -55,12 +55,16 @@ def test_binding_struct_layouts_match_the_library():
     assert (o.levels, o.maxit, o.loop_graph, o.ens_nmm, o.ens_elem_rc, o.ens_fdm_rc) == (3, 500, 1, 0, 0, 0)
 
 
-@pytest.mark.parametrize("n,sub,levels,kinds", [(16, 4, 2, dict(use_edges=0)), (16, 2, 3, {}), (12, 4, 2, {})])
-def test_plan_matches_oracle_partition(n, sub, levels, kinds):
+@pytest.mark.parametrize("n,sub,levels,kinds,dirichlet", [(16, 4, 2, dict(use_edges=0), FACE_X1), (16, 2, 3, {}, FACE_X1),
+                                                          (12, 4, 2, {}, FACE_X1), (16, 4, 2, {}, 0), (16, 2, 3, {}, 0)])
+def test_plan_matches_oracle_partition(n, sub, levels, kinds, dirichlet):
+    """Host setup against the oracle's partition; dirichlet = 0 is the pure-Neumann case
+    (semidefinite K: the coarse matrices are inverted in grounded form)."""
     _lib()
     import paper_2412_17543_gb300 as P
-    m = make_mesh(n, sub, 1.08, 20.0)
+    m = make_mesh(n, sub, 1.08, 20.0, dirichlet=dirichlet)
     info, nodes = P.plan(m, levels=levels, coarse_group=4, **kinds)
+    assert info["neumann"] == (dirichlet == 0)
     subs = dd.q1_substructures(m)
     assert info["n_free"] == m.n_free
     assert info["n_gamma"] == len(subs.gamma)
@@ -81,9 +85,9 @@ def test_plan_rejects_bad_input():
     with pytest.raises(P.DDError) as e:
         P.plan(m, levels=2)
     assert e.value.code == 1
-    m = make_mesh(8, 4, dirichlet=0)  # pure Neumann: K singular
+    m = make_mesh(8, 4, dirichlet=0)  # pure Neumann takes no adaptive constraints
     with pytest.raises(P.DDError):
-        P.plan(m, levels=2)
+        P.plan(m, levels=2, adaptive=1)
     m = make_mesh(8, 4, coef=-np.ones((8, 8, 8)))
     with pytest.raises(P.DDError):
         P.plan(m, levels=2)
