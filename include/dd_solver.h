@@ -104,6 +104,8 @@ typedef struct {
                                0: the host issues each iteration and reads the stopping test back.
                                Both run the same kernels in the same order (identical results); while
                                profiling (dd_profile) the host-issued form is used */
+  int32_t zero_initial_guess; /* 1: every dd_solve starts from x = 0; 0 (default): from the previous
+                               solution of the recycle state (Sect. 5 compares the two) */
 } dd_options;
 
 typedef struct {

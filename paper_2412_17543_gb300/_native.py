@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
                 ("flexible", ctypes.c_int32), ("reorth", ctypes.c_int32), ("stop_rhs_norm", ctypes.c_int32),
                 ("maxit", ctypes.c_int32), ("local_solver", ctypes.c_int32),
                 ("ens_nmm", ctypes.c_int32), ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32),
-                ("loop_graph", ctypes.c_int32)]
+                ("loop_graph", ctypes.c_int32), ("zero_initial_guess", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -410,6 +410,7 @@ dd_status dd_default_options(dd_options* o) {
   o->ens_elem_rc = 0;
   o->ens_fdm_rc = 0;
   o->loop_graph = 1;
+  o->zero_initial_guess = 0;
   return DD_OK;
 }
 
@@ -441,6 +442,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
                "ens_elem_rc must be 0, 4, 8 or 16");
     DD_REQUIRE(opt->ens_fdm_rc == 0 || opt->ens_fdm_rc == 4 || opt->ens_fdm_rc == 8, "ens_fdm_rc must be 0, 4 or 8");
     DD_REQUIRE(opt->loop_graph == 0 || opt->loop_graph == 1, "loop_graph must be 0 or 1");
+    DD_REQUIRE(opt->zero_initial_guess == 0 || opt->zero_initial_guess == 1, "zero_initial_guess must be 0 or 1");
     auto H = std::make_unique<HostSetup>();
     build_host_setup(*md, *opt, *H);
     auto c = std::make_unique<dd_ctx>();
@@ -1062,7 +1064,11 @@ dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycl
       f = c->fc;
     }
     condense(c, f, c->bvec, s);
-    DD_CUDA(cudaMemcpyAsync(c->xg, st->xg_prev, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
+    // initial guess: the previous solution (Sect. 5) or zero
+    if (c->opt.zero_initial_guess)
+      DD_CUDA(cudaMemsetAsync(c->xg, 0, c->n_gamma * 8, s));
+    else
+      DD_CUDA(cudaMemcpyAsync(c->xg, st->xg_prev, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
     bool record = st->kmax > 0 && !st->frozen;
     result = pcg_solve(c, st, rtol, record, stats, s);
     recover(c, f, c->xg, x, s);
