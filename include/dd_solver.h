@@ -5,7 +5,8 @@
  *
  * The method (arXiv 2412.17543):
  *   - Sect. 2, eq. systems: one SPD matrix K (Q1 pressure Laplacian, Dirichlet
- *     data on part of the boundary) and a sequence of right-hand sides f.
+ *     data on part of the boundary) and a sequence of right-hand sides f; without
+ *     a Dirichlet part K is semidefinite (pure Neumann, handled as in Sect. 4.1).
  *   - Sect. 3.1, eq. Sug: the interface problem A x_G = b, A = sum_i R_i^T S_i R_i
  *     with S_i = K_GG - K_GI K_II^{-1} K_IG never assembled.
  *   - Sect. 3.2, eqs. averaging_subdomain_solves, coarse_problem, localCorr:
@@ -65,7 +66,8 @@ typedef struct {
   const double* zc;
   const double* coef;            /* [nz][ny][nx] per-element coefficient k_e > 0, x fastest; NULL means 1 */
   int32_t sub_x, sub_y, sub_z;   /* elements per subdomain per axis (must divide nx, ny, nz; each <= 8) */
-  uint32_t dirichlet_faces;      /* DD_FACE_* bits, at least one (K must be SPD, Sect. 2) */
+  uint32_t dirichlet_faces;      /* DD_FACE_* bits; 0 is the pure-Neumann problem (Sect. 2: K semidefinite,
+                                    the constants as null space; see dd_info_t.neumann) */
 } dd_mesh_desc;
 
 enum { DD_WEIGHTS_CARD = 0, DD_WEIGHTS_DIAG = 1 };                 /* Sect. 3.2 interface weights D_i */
