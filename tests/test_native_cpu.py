@@ -106,3 +106,22 @@ def test_plan_adaptive_count_matches_oracle(tau):
     rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau)
     info, _ = P.plan(m, levels=2, adaptive=1, tau=tau, weights="diag")
     assert info["n_adaptive"] == sum(len(r) for r in rows.values())
+
+
+@pytest.mark.parametrize("field,value", [("loop_graph", 2), ("zero_initial_guess", -1), ("ens_elem_rc", 3),
+                                         ("ens_fdm_rc", 16), ("ens_nmm", 7), ("maxit", 0), ("schur_prec", 1)])
+def test_setup_validates_options_before_any_device_work(field, value):
+    """dd_setup rejects an invalid option with DD_INVALID_ARG and a message naming it; the
+    checks come before any device call, so they run without a GPU."""
+    lib = _lib()
+    from paper_2412_17543_gb300 import _native as nat
+    from paper_2412_17543_gb300.api import _mesh_desc, make_options
+    keep = []
+    d = _mesh_desc(make_mesh(8, 4), keep)
+    o = make_options()
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    code = lib.dd_setup(ctypes.byref(d), ctypes.byref(o), None, ctypes.byref(h))
+    assert code == 1 and not h.value
+    msg = lib.dd_last_error().decode()
+    assert field.split("_")[0] in msg or field in msg, msg
