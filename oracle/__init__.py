@@ -6,12 +6,12 @@ import it. It shares no code with the CUDA path: the only common input is the
 seeded generator in `workload/`.
 
 Contents (each function cites the part of the paper it restates):
-  q1        Q1 element matrices by Gauss quadrature, global assembly (Sect. 2, eq. systems)
-  cholesky  nested-dissection multifrontal sparse Cholesky of K (direct solve of eq. systems)
+  q1        Q1 element matrices by Gauss quadrature, global assembly (Sect. 2, eq. 5)
+  cholesky  nested-dissection multifrontal sparse Cholesky of K (direct solve of eq. 5)
   dd        substructuring, Schur complement, globs, BDDC two-/three-level, adaptive
             face constraints (Sect. 3.1-3.3)
-  pcg       deflated PCG (Algorithm 1), recycling B1-B4, harmonic Ritz (eq. harmonicRitz),
-            freezing criterion (eq. harmritzstopcrit), stopping criteria (Sect. 5)
+  pcg       deflated PCG (Algorithm 1), recycling B1-B4, harmonic Ritz (eq. 15),
+            freezing criterion (eq. 16), stopping criteria (Sect. 5)
   adjoint   adjoint solve and coefficient gradient of a quadratic loss
 
 Parity status: every function is pinned by a `-m "not gpu"` test except the

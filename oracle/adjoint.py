@@ -1,6 +1,6 @@
 """Adjoint of the Poisson solve (oracle; test infrastructure).
 
-K(k) x = f with K = sum_e k_e K_e^0 symmetric positive definite (eq. systems).
+K(k) x = f with K = sum_e k_e K_e^0 symmetric positive definite (eq. 5).
 For a loss L(x): lambda = K^{-1} dL/dx, dL/df = lambda, and
 dL/dk_e = -lambda_e^T K_e^0 x_e (derivative of K^{-1} f with respect to k_e);
 with k_e = exp(g_e), dL/dg_e = k_e dL/dk_e.

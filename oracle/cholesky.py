@@ -1,6 +1,6 @@
 """Sparse Cholesky of the global Q1 matrix by nested dissection + multifrontal elimination.
 
-Oracle (test infrastructure). It solves K x = f (eq. systems) directly, so the
+Oracle (test infrastructure). It solves K x = f (eq. 5) directly, so the
 result is the exact discrete solution that the iterative method approaches.
 
 Ordering: the free nodes form a box of a structured grid whose matrix graph is

@@ -4,16 +4,15 @@ Sect. 3.1: the free nodes are split into subdomains of s^3 elements; a node is a
 *interface* node if it belongs to more than one subdomain and an *interior* node
 otherwise. The global Schur complement A = sum_i R_i^T S_i R_i with
 S_i = K_GG - K_GI K_II^{-1} K_IG is applied per subdomain and never assembled
-(eq. Sug), and the reduced right-hand side is b = f_G - sum_i R_i^T K_GI K_II^{-1} f_I.
+(eq. 6), and the reduced right-hand side is b = f_G - sum_i R_i^T K_GI K_II^{-1} f_I.
 
-Sect. 3.2: the BDDC preconditioner (eqs. averaging_subdomain_solves,
-coarse_problem, localCorr) with card or diag weights, coarse degrees of freedom
+Sect. 3.2: the BDDC preconditioner (eqs. 7-9) with card or diag weights, coarse degrees of freedom
 at corners and arithmetic averages over edges and faces, and the multilevel
 variant in which the coarse problem is itself preconditioned by BDDC with the
 level-1 subdomains playing the role of elements.
 
 Sect. 3.3: adaptive face constraints from the generalized eigenproblem
-(eq. eig-matrix) with the constraint row of eq. c-def.
+(eq. 10) with the constraint row of eq. 12.
 
 Interface vectors are indexed by the interface nodes in increasing free-node
 index. Each subdomain problem is solved with dense LAPACK factorizations.
@@ -90,7 +89,7 @@ class Substructures:
         return K[np.ix_(G, G)] - K[np.ix_(G, I)] @ X
 
     def schur_apply(self, x: np.ndarray) -> np.ndarray:
-        """A x = sum_i R_i^T S_i R_i x (eq. Sug), S_i formed densely."""
+        """A x = sum_i R_i^T S_i R_i x (eq. 6), S_i formed densely."""
         y = np.zeros(len(self.gamma))
         for i in range(self.S):
             S = self.local_schur(i)
@@ -210,7 +209,7 @@ class BDDC:
             for i in range(subs.S):
                 g = subs.dofs[i][subs.locG[i]]
                 self.D.append(np.diag(subs.K[i])[subs.locG[i]] / dsum[g])
-        # saddle-point factorizations, coarse basis, coarse matrix (eq. localCorr, coarse_problem)
+        # saddle-point factorizations, coarse basis, coarse matrix (eqs. 8-9)
         self.lu, self.Phi, self.KCi = [], [], []
         KC = np.zeros((self.nC, self.nC))
         for i in range(subs.S):
@@ -239,7 +238,7 @@ class BDDC:
         return dofs, Ks
 
     def apply(self, r: np.ndarray, coarse_solve=None) -> np.ndarray:
-        """z = M_BDDC^{-1} r on the interface (eqs. averaging_subdomain_solves, coarse_problem, localCorr)."""
+        """z = M_BDDC^{-1} r on the interface (eqs. 7, 8, 9)."""
         subs = self.subs
         if coarse_solve is None:
             coarse_solve = lambda g: np.linalg.solve(self.KC, g)
@@ -339,7 +338,7 @@ def face_schur(subs: Substructures, i: int, face_dofs: np.ndarray) -> np.ndarray
 
 def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: float, max_per_face: int = 10,
                               drop_tol: float = 1e-10, kinds=(CORNER, EDGE, FACE)):
-    """Extra face constraints from eq. eig-matrix, one problem per face shared by two subdomains s, t.
+    """Extra face constraints from eq. 10, one problem per face shared by two subdomains s, t.
 
     Reading used here: the pair problem lives on the common interface of s and t
     (the face together with the edges and corners it touches, i.e. every glob whose
@@ -348,7 +347,7 @@ def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: floa
     space where the two copies agree in every initial coarse dof of the common
     interface (corner values, edge and face averages); E averages the two copies
     with the BDDC weights. Eigenvectors with lambda > tau (at most max_per_face,
-    largest first) give c = w^T Pi (I-E)^T A (I-E) Pi (eq. c-def); its entries on
+    largest first) give c = w^T Pi (I-E)^T A (I-E) Pi (eq. 12); its entries on
     the face itself, first copy, form the new row, orthogonalized against the face
     average and the rows before it (rows whose remaining relative norm is below
     drop_tol are dropped). Returns {face glob index: [rows]}.

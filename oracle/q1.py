@@ -3,7 +3,7 @@
 The pressure space is continuous piecewise trilinear on hexahedra (Sect. 2,
 Taylor-Hood Q2-Q1, pressure part), and the Poisson problem for the pressure
 corrector with Dirichlet data on the outflow part and Neumann data elsewhere
-gives the SPD system K x = f (eq. systems).
+gives the SPD system K x = f (eq. 5).
 
 Written from the definition: K_ab = sum_e int_e k_e grad(phi_a) . grad(phi_b) dx,
 integrated on each brick by 2x2x2 Gauss quadrature (exact for these integrands).

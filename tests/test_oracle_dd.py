@@ -121,9 +121,16 @@ def test_adaptive_constraints_invariants():
     N = len(subs.gamma)
     base = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag")
     e0 = np.linalg.eigvalsh(L.T @ base.dense(N) @ L)
-    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=3.0)
-    assert sum(len(r) for r in rows.values()) > 0
-    ad = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag", extra_rows=rows)
-    e1 = np.linalg.eigvalsh(L.T @ ad.dense(N) @ L)
-    assert e1[0] >= 1 - 1e-10
-    assert e1[-1] <= e0[-1] + 1e-9
+    counts, lmax = [], []
+    for tau in (3.0, 2.0, 1.5):
+        rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau)
+        counts.append(sum(len(r) for r in rows.values()))
+        ad = dd.Preconditioner(subs, 2, (dd.CORNER, dd.EDGE, dd.FACE), "diag", extra_rows=rows)
+        e1 = np.linalg.eigvalsh(L.T @ ad.dense(N) @ L)
+        assert e1[0] >= 1 - 1e-10          # lambda_min >= 1 is kept (Sect. 3.2)
+        assert e1[-1] <= e0[-1] + 1e-9     # added constraints cannot raise lambda_max
+        lmax.append(e1[-1])
+    assert counts[0] > 0
+    # a smaller threshold adds at least the constraints of a larger one and lowers lambda_max
+    assert counts[0] <= counts[1] <= counts[2]
+    assert lmax[0] >= lmax[1] - 1e-9 >= lmax[2] - 2e-9

@@ -43,7 +43,7 @@ def test_k0_equals_textbook_pcg(problem):
 
 
 def test_stop_criteria_coincide_from_zero(problem):
-    # from x0 = 0, r0 = b, so eqs. stopping_residual and stopping_rhs give the same iterations
+    # from x0 = 0, r0 = b, so eqs. 17, 18 give the same iterations
     m, subs, A, M, F, bs = problem
     for b in bs[:3]:
         _, i1 = pcg.deflated_pcg(lambda v: A @ v, lambda v: M @ v, b, np.zeros_like(b), rtol=1e-8, stop="rhs")
