@@ -381,7 +381,7 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
                   3: "k_nmm_tc<BF16X3> (persistent, tcgen05 kind::f16, bf16 slices)"}.get(S.info["ens_nmm"], "none")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": None,
-            "kernel": f"{nmm_kernel}: ensemble constrained-Neumann products N_i R_i, eq. localCorr",
+            "kernel": f"{nmm_kernel}: ensemble constrained-Neumann products N_i R_i, eq. 9",
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
             "avg_launch_ms": nn_ms, "launches": nn[1], "timing": PROF_TIMING,
             "replay_ms_per_step": 1e3 * prof_sec / args.steps}
@@ -510,7 +510,7 @@ def main():
     traffic = 155282688.0 * mixed.info["n_sub"] / 512 if args.workload == "graded128" and args.n is None else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-            "kernel": "k_symv<FP32> (batched constrained-Neumann N_i GEMV, eq. localCorr)",
+            "kernel": "k_symv<FP32> (batched constrained-Neumann N_i GEMV, eq. 9)",
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
             "avg_launch_ms": nn_ms, "launches": nn[1], "timing": PROF_TIMING,
             "replay_ms_per_step": 1e3 * prof_sec / args.steps}

@@ -4,18 +4,18 @@
  * two-/three-level (and adaptive) BDDC, with Krylov subspace recycling.
  *
  * The method (arXiv 2412.17543):
- *   - Sect. 2, eq. systems: one SPD matrix K (Q1 pressure Laplacian, Dirichlet
+ *   - Sect. 2, eq. 5: one SPD matrix K (Q1 pressure Laplacian, Dirichlet
  *     data on part of the boundary) and a sequence of right-hand sides f; without
  *     a Dirichlet part K is semidefinite (pure Neumann, handled as in Sect. 4.1).
- *   - Sect. 3.1, eq. Sug: the interface problem A x_G = b, A = sum_i R_i^T S_i R_i
+ *   - Sect. 3.1, eq. 6: the interface problem A x_G = b, A = sum_i R_i^T S_i R_i
  *     with S_i = K_GG - K_GI K_II^{-1} K_IG never assembled.
- *   - Sect. 3.2, eqs. averaging_subdomain_solves, coarse_problem, localCorr:
- *     the BDDC preconditioner; Sect. 3.3, eqs. eig-matrix, c-def: adaptive
+ *   - Sect. 3.2, eqs. 7, 8, 9:
+ *     the BDDC preconditioner; Sect. 3.3, eqs. 10, 12: adaptive
  *     face constraints.
  *   - Sect. 4.1, Algorithm 1: deflated PCG; Sect. 4.2: recycling strategies
- *     B1-B4, harmonic Ritz vectors (eq. harmonicRitz) and the freezing
- *     criterion (eq. harmritzstopcrit).
- *   - Sect. 5, eqs. stopping_rhs / stopping_residual: stopping criteria.
+ *     B1-B4, harmonic Ritz vectors (eq. 15) and the freezing
+ *     criterion (eq. 16).
+ *   - Sect. 5, eqs. 18 / 17: stopping criteria.
  *
  * Conventions (all entry points):
  *   - Every call returns dd_status; no C++ exception crosses the ABI. On an
@@ -80,7 +80,7 @@ typedef struct {
   int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
   int32_t coarse_group;     /* 3 levels: level-1 subdomains per level-2 subdomain per axis (e.g. 4) */
   int32_t use_corners, use_edges, use_faces;  /* coarse dofs: corner values, edge and face averages */
-  int32_t adaptive;         /* 1: add face constraints from eq. eig-matrix (Sect. 3.3) */
+  int32_t adaptive;         /* 1: add face constraints from eq. 10 (Sect. 3.3) */
   double tau;               /* adaptive threshold on the face eigenvalues */
   int32_t max_eig_per_face; /* at most this many adaptive constraints per face */
   int32_t weights;          /* DD_WEIGHTS_CARD or DD_WEIGHTS_DIAG */
@@ -88,8 +88,8 @@ typedef struct {
   int32_t schur_prec;       /* DD_PREC_FP64 or DD_PREC_DF64: Schur-complement operator arithmetic
                                (DF64 = float pairs with error-free transformations on the FP32 pipes) */
   int32_t flexible;         /* 1: Polak-Ribiere beta (for the FP32 preconditioner) */
-  int32_t reorth;           /* 1: residual re-orthogonalization against W (Algorithm 1, greyed line) */
-  int32_t stop_rhs_norm;    /* 1: ||r_k||/||b|| (eq. stopping_rhs); 0: ||r_k||/||r_0|| (eq. stopping_residual) */
+  int32_t reorth;           /* 1: residual re-orthogonalization against W (optional step of Algorithm 1) */
+  int32_t stop_rhs_norm;    /* 1: ||r_k||/||b|| (eq. 18); 0: ||r_k||/||r_0|| (eq. 17) */
   int32_t maxit;            /* iteration limit per solve */
   int32_t local_solver;     /* K_II^{-1} representation: DD_LOCAL_AUTO (fast diagonalization when every
                                subdomain has a constant coefficient, else dense), DD_LOCAL_DENSE, DD_LOCAL_FDM */
@@ -138,7 +138,7 @@ typedef struct {
   double rel_res0;          /* initial residual norm over the stopping reference */
   double rel_res;           /* final recursive residual norm over the stopping reference */
   int32_t recycled_k;       /* columns of W used in the solve */
-  int32_t frozen;           /* 1 once eq. harmritzstopcrit has frozen W */
+  int32_t frozen;           /* 1 once eq. 16 has frozen W */
   float ms;                 /* device time of the solve (CUDA events) */
 } dd_stats;
 
@@ -173,10 +173,10 @@ dd_status dd_interface_nodes(const dd_ctx* ctx, int64_t* nodes /* host, out */);
 
 /* ---- operator-level entry points (Sect. 3.1-3.2); all vectors device, float64 ---- */
 
-/* y = A x (eq. Sug): batched subdomain Dirichlet solves with the matrix-free Q1
+/* y = A x (eq. 6): batched subdomain Dirichlet solves with the matrix-free Q1
  * operator, assembled over the interface. x, y: [n_gamma]. */
 dd_status dd_schur_apply(dd_ctx* ctx, const double* x, double* y, void* stream);
-/* z = M_BDDC^{-1} r (eqs. averaging_subdomain_solves, coarse_problem, localCorr). [n_gamma]. */
+/* z = M_BDDC^{-1} r (eqs. 7, 8, 9). [n_gamma]. */
 dd_status dd_precond_apply(dd_ctx* ctx, const double* r, double* z, void* stream);
 /* Reduced right-hand side b = f_G - sum_i R_i^T K_GI K_II^{-1} f_I (Sect. 3.1). f: [n_free], b: [n_gamma]. */
 dd_status dd_condense(dd_ctx* ctx, const double* f, double* b, void* stream);
@@ -210,7 +210,7 @@ dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double* y, void* 
 /* ---- solves ---- */
 
 /* Recycle state for a sequence of solves: deflation basis of at most k columns built
- * by `strategy` (DD_B1..DD_B4), frozen by eq. harmritzstopcrit with freeze_tol
+ * by `strategy` (DD_B1..DD_B4), frozen by eq. 16 with freeze_tol
  * (B3/B4). k = 0 gives plain PCG. Holds x_prev (the initial guess of the next
  * solve, Sect. 5). Owned by the caller; release with dd_recycle_destroy. */
 dd_status dd_recycle_create(dd_ctx* ctx, int32_t k, int32_t strategy, double freeze_tol,
@@ -235,7 +235,7 @@ dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double*
 
 /* ---- profiling (CUDA events on the launching stream) ---- */
 enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} application of the Schur operator (Sect. 3.1) */
-       DD_PROF_SYMV_N = 1,     /* batched constrained-Neumann GEMV of BDDC (eq. localCorr) */
+       DD_PROF_SYMV_N = 1,     /* batched constrained-Neumann GEMV of BDDC (eq. 9) */
        DD_PROF_SCHUR = 2,      /* whole Schur-complement applications */
        DD_PROF_PRECOND = 3,    /* whole BDDC applications */
        DD_PROF_RECYCLE = 4,    /* recycling updates between solves (Sect. 4.2) */
@@ -285,8 +285,7 @@ dd_status dd_recycle_create_batch(dd_ctx* ctx, int32_t k, int32_t strategy, doub
 dd_status dd_solve_batch(dd_ctx* ctx, int32_t nrhs, const double* F, double* X, double rtol, dd_recycle* st,
                          dd_stats* stats, void* stream);
 
-/* Ensemble counterparts of dd_schur_apply and dd_precond_apply (eq. Sug; eqs.
- * averaging_subdomain_solves, coarse_problem, localCorr) on nrhs interface vectors at
+/* Ensemble counterparts of dd_schur_apply and dd_precond_apply (eq. 6; eqs. 7-9) on nrhs interface vectors at
  * once: X, R: [nrhs][n_gamma] device in; Y, Z: [nrhs][n_gamma] device out. Same
  * arithmetic as dd_solve_batch uses. Errors: DD_INVALID_ARG, DD_CUDA_ERROR. */
 dd_status dd_schur_apply_batch(dd_ctx* ctx, int32_t nrhs, const double* X, double* Y, void* stream);

@@ -691,7 +691,7 @@ void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_m
   DD_CHECK_LAUNCH();
 }
 
-// z[g] = sum over copies k of D[k] (uloc[k] + vloc[k])   (eq. averaging_subdomain_solves)
+// z[g] = sum over copies k of D[k] (uloc[k] + vloc[k])   (eq. 7)
 __global__ void k_wgather(int64_t n, const int* __restrict__ ptr, const int* __restrict__ idx,
                           const double* __restrict__ D, const double* __restrict__ uloc,
                           const double* __restrict__ vloc, double* __restrict__ z) {

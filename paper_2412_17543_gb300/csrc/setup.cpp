@@ -128,7 +128,7 @@ bool dense_schur(int nloc, const double* K, const std::vector<int>& I, const std
   return true;
 }
 
-// Phase C of one subdomain: the constrained Neumann problem of eq. localCorr with a
+// Phase C of one subdomain: the constrained Neumann problem of eq. 9 with a
 // right-hand side on G. With S^ = S + rho C^T C (equal to S on ker C):
 // N = S^{-1} - S^{-1}C^T (C S^{-1} C^T)^{-1} C S^{-1}, Phi = S^{-1} C^T (C S^{-1} C^T)^{-1},
 // KC = Phi^T S Phi = (C S^{-1} C^T)^{-1} - rho I.
@@ -256,7 +256,7 @@ bool face_schur(int nG, const std::vector<double>& S, const std::vector<int>& F,
   return true;
 }
 
-// Adaptive constraints of one face shared by two subdomains (Sect. 3.3, eqs. eig-matrix and c-def),
+// Adaptive constraints of one face shared by two subdomains (Sect. 3.3, eqs. 10, 12),
 // posed on their common interface (the face with the edges and corners it touches).
 // As, At: Schur complements of the two subdomains onto the common interface; ws, wt: BDDC weights
 // there; cq: the initial coarse dofs of the common interface (rows over its dofs). Pi projects onto

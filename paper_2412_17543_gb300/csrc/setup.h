@@ -10,7 +10,7 @@
 namespace dd {
 
 // One subdomain of a BDDC level after setup. Local dofs are split into interior
-// (I) and interface (G) dofs; the constrained Neumann problem (eq. localCorr) with
+// (I) and interface (G) dofs; the constrained Neumann problem (eq. 9) with
 // a right-hand side on G only is represented by N (its G-block of the inverse),
 // the coarse basis restricted to G (Phi) and the local coarse matrix KC.
 struct DenseSub {

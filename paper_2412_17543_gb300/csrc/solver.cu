@@ -863,7 +863,7 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
     refresh_gram(c, st, s);
     return;
   }
-  // B3 / B4: harmonic Ritz vectors of V = [W, P]  (eq. harmonicRitz)
+  // B3 / B4: harmonic Ritz vectors of V = [W, P]  (eq. 15)
   // M^{-1} A p_j = (z_j - z_{j+1}) / alpha_j, and for the last one one extra preconditioner solve
   for (int j = 0; j < l; ++j) {
     if (j + 1 < l)
@@ -892,8 +892,15 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
       v = 0.5 * (Gh[a * m + b] + Gh[b * m + a]);
       Gh[a * m + b] = Gh[b * m + a] = v;
     }
-  // restrict to the numerically nonsingular part of F: F = Q L Q^T, T = Q_r L_r^{-1/2}
+  // The pencil's eigenpairs do not depend on the scaling of V's columns, and the search
+  // vectors shrink with the residual by many orders of magnitude: scale the columns to unit
+  // A-norm, D = diag(F)^{-1/2}, then restrict to the numerically nonsingular part of D F D =
+  // Q L Q^T, T = D Q_r L_r^{-1/2} (so that only numerically dependent directions are dropped)
+  std::vector<double> dsc(m);
+  for (int a = 0; a < m; ++a) dsc[a] = F[(size_t)a * m + a] > 0.0 ? 1.0 / std::sqrt(F[(size_t)a * m + a]) : 0.0;
   std::vector<double> Fw(F), lam(m), Q((size_t)m * m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) Fw[(size_t)a * m + b] *= dsc[a] * dsc[b];
   la::sym_eig(m, Fw.data(), lam.data(), Q.data());
   double lmax = lam[m - 1];
   std::vector<int> keep;
@@ -903,7 +910,7 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
   if (r == 0) return;
   std::vector<double> T((size_t)m * r);
   for (int a = 0; a < m; ++a)
-    for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = Q[(size_t)a * m + keep[j]] / std::sqrt(lam[keep[j]]);
+    for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = dsc[a] * Q[(size_t)a * m + keep[j]] / std::sqrt(lam[keep[j]]);
   // C = T^T Gh T
   std::vector<double> GT((size_t)m * r), Cm((size_t)r * r);
   la::gemm_nn(m, r, m, Gh.data(), T.data(), GT.data());
@@ -926,7 +933,7 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
       num += (theta[j] - st->theta[j]) * (theta[j] - st->theta[j]);
       den += theta[j] * theta[j];
     }
-    if (std::sqrt(num) <= st->freeze_tol * std::sqrt(den)) st->frozen = true;  // eq. harmritzstopcrit
+    if (std::sqrt(num) <= st->freeze_tol * std::sqrt(den)) st->frozen = true;  // eq. 16
   }
   st->theta = theta;
   // Y = T U_sel (m x kn)

@@ -1,4 +1,4 @@
-// Ensemble constrained-Neumann products U_i = N_i R_i (eq. localCorr) on the 5th-generation
+// Ensemble constrained-Neumann products U_i = N_i R_i (eq. 9) on the 5th-generation
 // tensor cores, in a persistent kernel: one CTA per SM walks a list of work items (a
 // subdomain and a 128-row block of its N_i, full blocks first), streaming the items'
 // 32-wide k chunks through one ring of bulk copies that runs on across item boundaries.

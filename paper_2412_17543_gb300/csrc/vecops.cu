@@ -2,7 +2,7 @@
 // two-stage reduction, no floating-point atomics), fused PCG updates, the
 // deflation projection (Algorithm 1: mu = (W^T A W)^{-1} (AW)^T z, p = z + beta p - W mu),
 // and tall-skinny Gram / combination kernels for the recycling update
-// (eq. harmonicRitz).
+// (eq. 15).
 #include <algorithm>
 
 #include "vecops.h"

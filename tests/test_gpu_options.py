@@ -1,5 +1,5 @@
 """Solver options through the C ABI: the initial guess (previous solution or zero) and the
-two stopping criteria (eq. stopping_rhs and eq. stopping_residual, Sect. 5)."""
+two stopping criteria (eq. 18 and eq. 17, Sect. 5)."""
 import numpy as np
 import pytest
 

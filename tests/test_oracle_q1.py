@@ -1,4 +1,4 @@
-"""Pins for the oracle's Q1 discretization (Sect. 2, eq. systems) and its sparse Cholesky."""
+"""Pins for the oracle's Q1 discretization (Sect. 2, eq. 5) and its sparse Cholesky."""
 import os
 
 import numpy as np
