@@ -197,8 +197,13 @@ dd_status dd_recover(dd_ctx* ctx, const double* f, const double* xg, double* x, 
  *    subdomains' interface sizes; a larger problem returns DD_INVALID_ARG with a
  *    message giving both numbers (meshes up to about 64^3 with 8^3 subdomains fit);
  *  - the first call on a device looks up the array's device address for that
- *    device (make that device current first) and must therefore come before any
+ *    device (make that device current first); make that first call before any
  *    stream capture that includes this entry point;
+ *  - the call only enqueues kernels on `stream` and returns without waiting for the
+ *    GPU (the scratch size is checked on the host). A bounded device-side wait that
+ *    gives up in its kernels (dense K_II^{-1} streaming only) is recorded in the
+ *    context's device error word and returned as DD_TIMEOUT by the next entry point
+ *    of this context that synchronizes (dd_schur_apply, dd_solve, ...);
  *  - all calls share the array and it keeps the previous call's contents; every
  *    scratch entry read by a call is written earlier in the same call, so nothing
  *    needs clearing, but calls whose executions overlap on the GPU (different
@@ -206,6 +211,15 @@ dd_status dd_recover(dd_ctx* ctx, const double* f, const double* xg, double* x, 
  *    by the caller. x, y: [n_gamma] device. */
 #define DD_NOALLOC_SCRATCH_BYTES (8u << 20)
 dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double* y, void* stream);
+
+/* Failure-path self-test (no counterpart in the paper): launches one thread that
+ * waits on an mbarrier nothing arrives at, through the same bounded wait that the
+ * streaming kernels use for their bulk copies, giving up after `polls` (>= 1) attempts.
+ * Returns DD_TIMEOUT, as any entry point does when one of its kernels gave up a wait;
+ * the context's device error word is cleared when it is read, so the next call on the
+ * context starts clean. Nothing is in flight while it waits and no memory is touched
+ * besides the error word. Errors: DD_INVALID_ARG (NULL ctx, polls < 1), DD_CUDA_ERROR. */
+dd_status dd_selftest_bounded_wait(dd_ctx* ctx, int64_t polls, void* stream);
 
 /* ---- solves ---- */
 

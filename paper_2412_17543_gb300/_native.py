@@ -75,6 +75,7 @@ SIGNATURES = {
     "dd_condense": (ctypes.c_int, [_P, _P, _P, _P]),
     "dd_recover": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "dd_schur_apply_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
+    "dd_selftest_bounded_wait": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
     "dd_recycle_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D, ctypes.POINTER(_P)]),
     "dd_recycle_destroy": (None, [_P]),
     "dd_solve": (ctypes.c_int, [_P, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),

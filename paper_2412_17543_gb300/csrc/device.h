@@ -44,6 +44,7 @@ struct DevMesh {
   int fx0, fx1, fy0, fy1, fz0, fz1;
   int NLx, NLy, NLz, NL;
   int64_t n_free, n_gamma, n_int;
+  int64_t n_flat;           // sum of the subdomains' local interface sizes (host copy of goff[S])
   const int16_t* lidx;
   const int* sub_type;      // [S] work-list type of each subdomain
   const int* type_off;      // [types][6]: first/last item of the interior pass, of the interface pass,
@@ -140,6 +141,7 @@ void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const d
 // s_I = K_II^{-1} t_I for every subdomain (dense tiles or fast diagonalization)
 void launch_kii_apply(const DevMesh& m, const double* tI, double* sI, int* err, cudaStream_t s);
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s);
+void launch_wait_selftest(int* err, long long limit, cudaStream_t s);
 // y[g] = (base ? base[bmap ? bmap[g] : g] : 0) + sum over copies of loc[idx[k]]
 void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
                    const int64_t* bmap, double* y, cudaStream_t s);

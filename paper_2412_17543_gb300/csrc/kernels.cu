@@ -360,6 +360,21 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
   }
 }
 
+// Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing arrives
+// at (no copy is in flight), gives up after `limit` attempts and raises the error word,
+// exactly as the streaming kernels do when a bulk copy never lands.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  mbar_wait_bounded(&bar, 0u, err, limit);
+}
+
+void launch_wait_selftest(int* err, long long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(err, limit);
+  DD_CHECK_LAUNCH();
+}
+
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s) {
   if (A.count == 0) return;
   int maxpad = ((A.max_n + 31) / 32) * 32;

@@ -25,8 +25,10 @@ __global__ void k_loop_begin(LoopCtl* ctl, const double* __restrict__ sc, double
   ctl->rel = rel;
   ctl->its = 0;
   ctl->maxit = maxit;
-  ctl->status = LOOP_OK;
-  ctl->go = (rel >= rtol) ? 1 : 0;
+  // a non-finite right-hand side or initial residual is a breakdown, not convergence
+  const bool finite = isfinite(rel) && isfinite(ref);
+  ctl->status = finite ? LOOP_OK : LOOP_BREAKDOWN;
+  ctl->go = (finite && rel >= rtol) ? 1 : 0;
   ctl->rec0 = 0;
   ctl->nalpha = 0;
 }
@@ -48,7 +50,10 @@ __global__ void k_loop_check(LoopCtl* ctl, const double* __restrict__ sc, double
   } else {
     const double rel = sqrt(sc[SC_RR]) / ctl->ref;
     ctl->rel = rel;
-    if (rel < ctl->rtol) {
+    if (!isfinite(rel)) {
+      ctl->status = LOOP_BREAKDOWN;
+      go = 0;
+    } else if (rel < ctl->rtol) {
       go = 0;
     } else if (its >= ctl->maxit) {
       ctl->status = LOOP_NOT_CONVERGED;

@@ -53,9 +53,7 @@ extern "C" dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double
     const dd::DevMesh& m = *dd::context_mesh(ctx);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_int = (size_t)m.n_int;
-    size_t n_flat = 0;
-    DD_CUDA(cudaMemcpyAsync(&n_flat, m.goff + m.S, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    DD_CUDA(cudaStreamSynchronize(s));
+    const size_t n_flat = (size_t)m.n_flat;  // host copy, fixed at setup: no device read-back
     const size_t need = 2 * n_int + n_flat;
     if (need > kScratchDoubles)
       throw dd::Error(DD_INVALID_ARG, "dd_schur_apply_noalloc: problem needs " + std::to_string(need * 8) +
@@ -65,14 +63,13 @@ extern "C" dd_status dd_schur_apply_noalloc(dd_ctx* ctx, const double* x, double
     double* tI = base;
     double* sI = base + n_int;
     double* yloc = base + 2 * n_int;
+    // stream-ordered launches only: the call returns without waiting for the GPU. A bounded
+    // wait that gives up in these kernels sets the context's error word, which the next
+    // entry point of the context that reads it reports as DD_TIMEOUT.
     dd::launch_elem_interior(m, dd::ELEM_SCHUR, x, nullptr, tI, s);
     dd::launch_kii_apply(m, tI, sI, dd::context_err(ctx), s);
     dd::launch_elem_interface(m, dd::ELEM_SCHUR, x, sI, yloc, s);
     dd::launch_gather(m.n_gamma, m.gptr, m.gidx, yloc, nullptr, nullptr, y, s);
-    int e = 0;
-    DD_CUDA(cudaMemcpyAsync(&e, dd::context_err(ctx), sizeof(int), cudaMemcpyDeviceToHost, s));
-    DD_CUDA(cudaStreamSynchronize(s));
-    if (e) throw dd::Error((dd_status)e, "a bounded device-side wait timed out");
     return DD_OK;
   } catch (const dd::Error& err) {
     dd::set_last_error(err.what());

@@ -41,9 +41,10 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 constexpr long long WAIT_LIMIT = 1ll << 24;  // try_wait attempts before giving up (seconds)
 
-// bounded wait on an mbarrier phase; returns false (and raises *err) on timeout
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it)
+// bounded wait on an mbarrier phase; returns false (and raises *err) after `limit` attempts
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  long long limit = WAIT_LIMIT) {
+  for (long long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicExch(err, (int)DD_TIMEOUT);
   return false;

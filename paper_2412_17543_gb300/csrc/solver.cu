@@ -277,11 +277,17 @@ void precond_z(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
   if (c->neumann) vec_sub_mean(c->n_gamma, z, z, c->partials, s);
 }
 
+// Reads the context's device error word (set by a bounded wait that gave up) and clears
+// it, so that a failure is reported once and later calls on the context start clean.
 void check_err(dd_ctx* c, cudaStream_t s) {
   int e = 0;
   DD_CUDA(cudaMemcpyAsync(&e, c->w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   DD_CUDA(cudaStreamSynchronize(s));
-  if (e) throw Error((dd_status)e, "a bounded device-side wait timed out");
+  if (e) {
+    DD_CUDA(cudaMemsetAsync(c->w.err, 0, sizeof(int), s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    throw Error((dd_status)e, "a bounded device-side wait timed out");
+  }
 }
 
 template <class F>
@@ -464,6 +470,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     dm.n_free = M.n_free;
     dm.n_gamma = H->l1.n_gamma;
     dm.n_int = H->l1.ioff[M.S];
+    dm.n_flat = H->l1.goff[M.S];
     dm.schur_prec = opt->schur_prec;
     dm.lidx = A.upload(M.lidx, s);
     {
@@ -703,6 +710,17 @@ dd_status dd_condense(dd_ctx* c, const double* f, double* b, void* stream) {
 dd_status dd_recover(dd_ctx* c, const double* f, const double* xg, double* x, void* stream) {
   if (!c || !f || !xg || !x) return DD_INVALID_ARG;
   return guard([&] { recover(c, f, xg, x, (cudaStream_t)stream); check_err(c, (cudaStream_t)stream); });
+}
+
+dd_status dd_selftest_bounded_wait(dd_ctx* c, int64_t polls, void* stream) {
+  if (!c || polls < 1) {
+    g_last_error = "dd_selftest_bounded_wait: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  return guard([&] {
+    launch_wait_selftest(c->w.err, (long long)polls, (cudaStream_t)stream);
+    check_err(c, (cudaStream_t)stream);
+  });
 }
 
 dd_status dd_recycle_create(dd_ctx* c, int32_t k, int32_t strategy, double freeze_tol, dd_recycle** out) {
@@ -1080,7 +1098,10 @@ dd_status dd_solve(dd_ctx* c, const double* f, double* x, double rtol, dd_recycl
     result = pcg_solve(c, st, rtol, record, stats, s);
     recover(c, f, c->xg, x, s);
     if (c->neumann) vec_sub_mean(c->n_free, x, x, c->partials, s);  // the mean-free representative
-    DD_CUDA(cudaMemcpyAsync(st->xg_prev, c->xg, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
+    // a breakdown (non-finite or non-positive PCG scalars, e.g. from a non-finite load
+    // vector) leaves the recycle state as it was: previous solution, basis and histories
+    if (result != DD_BREAKDOWN)
+      DD_CUDA(cudaMemcpyAsync(st->xg_prev, c->xg, c->n_gamma * 8, cudaMemcpyDeviceToDevice, s));
     if (record && (result == DD_OK || result == DD_NOT_CONVERGED)) {
       ProfScope pr(c, DD_PROF_RECYCLE, s);
       recycle_update(c, st, (int)st->alphas.size(), s);

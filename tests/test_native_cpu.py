@@ -125,3 +125,17 @@ def test_setup_validates_options_before_any_device_work(field, value):
     assert code == 1 and not h.value
     msg = lib.dd_last_error().decode()
     assert field.split("_")[0] in msg or field in msg, msg
+
+
+@pytest.mark.parametrize("bad", [0.0, -1e-3, float("nan"), float("inf")])
+def test_plan_rejects_nonpositive_or_nonfinite_coefficient(bad):
+    """One bad k_e among valid ones makes K indefinite, singular or undefined: setup refuses
+    it with DD_INVALID_ARG before any factorization (host-side failure detection)."""
+    _lib()
+    import paper_2412_17543_gb300 as P
+    coef = np.ones((8, 8, 8))
+    coef[3, 5, 2] = bad
+    with pytest.raises(P.DDError) as e:
+        P.plan(make_mesh(8, 4, coef=coef), levels=2)
+    assert e.value.code == 1
+    assert "coefficient" in str(e.value)
