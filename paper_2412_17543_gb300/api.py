@@ -275,6 +275,15 @@ class Recycler:
         nat.check(lib.dd_recycle_export(self.handle, buf, ctypes.byref(n)), "dd_recycle_export")
         return buf.raw[: n.value]
 
+    def state(self) -> dict:
+        """Basis size, frozen flag, step count and the selected harmonic Ritz values, read
+        from the checkpoint header (layout of dd_recycle_export)."""
+        import struct
+        blob = self.export()
+        magic, n_gamma, kmax, strategy, k, frozen, step, ntheta, tol = struct.unpack_from("<8sq6id", blob, 0)
+        theta = np.frombuffer(blob, dtype=np.float64, count=ntheta, offset=struct.calcsize("<8sq6id"))
+        return dict(k=k, frozen=bool(frozen), step=step, theta=theta.copy(), kmax=kmax, freeze_tol=tol)
+
     @classmethod
     def restore(cls, solver: "Solver", data: bytes) -> "Recycler":
         obj = cls.__new__(cls)

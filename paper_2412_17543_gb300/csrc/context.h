@@ -146,6 +146,12 @@ struct dd_recycle {
   double *P = nullptr, *AP = nullptr, *Z = nullptr, *MAP = nullptr;  // histories [hmax][n_gamma]
   std::vector<double> alphas;
   dd::LoopGraph loop;                                       // captured PCG loop of this sequence
+  // recycling-update work space (allocated on first use) and the host copy of G = W^T A W
+  void** rptr = nullptr;                                    // [REC_PTRS] device pointer table
+  short2* rblk = nullptr;                                   // [3][REC_BLOCKS] Gram block lists
+  double *rpart = nullptr, *rout = nullptr;                 // Gram partials and results
+  double *rY = nullptr, *ralpha = nullptr;                  // combination coefficients, step lengths
+  std::vector<double> G_host;                               // [k*k] of the current basis
 };
 
 

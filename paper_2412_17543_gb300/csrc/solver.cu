@@ -21,6 +21,7 @@
 #include "vecops.h"
 #include "context.h"
 #include "batch.h"
+#include "recycle.h"
 
 using namespace dd;
 
@@ -767,45 +768,6 @@ void dd_recycle_destroy(dd_recycle* st) { delete st; }
 // ---------------------------------------------------------------------------
 namespace dd {
 
-void set_ptrs(dd_ctx* c, const std::vector<const double*>& v, int at, cudaStream_t s) {
-  DD_CUDA(cudaMemcpyAsync(c->ptrs + at, v.data(), v.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
-}
-
-// C[a][b] = X_a . Y_b, computed in column blocks of at most 64 x 64
-std::vector<double> gram_host(dd_ctx* c, const std::vector<const double*>& X, const std::vector<const double*>& Y,
-                              cudaStream_t s) {
-  int na = (int)X.size(), nb = (int)Y.size();
-  std::vector<double> C((size_t)na * nb, 0.0);
-  if (!na || !nb) return C;
-  DD_REQUIRE(na <= 256 && nb <= 256, "gram: at most 256 columns");
-  set_ptrs(c, X, 0, s);
-  set_ptrs(c, Y, 256, s);
-  std::vector<double> blk(64 * 64);
-  for (int a0 = 0; a0 < na; a0 += 64)
-    for (int b0 = 0; b0 < nb; b0 += 64) {
-      int ma = std::min(64, na - a0), mb = std::min(64, nb - b0);
-      gram(c->n_gamma, ma, c->ptrs + a0, mb, c->ptrs + 256 + b0, c->gram_part, c->gram_out, s);
-      DD_CUDA(cudaMemcpyAsync(blk.data(), c->gram_out, (size_t)ma * mb * sizeof(double), cudaMemcpyDeviceToHost, s));
-      DD_CUDA(cudaStreamSynchronize(s));
-      for (int a = 0; a < ma; ++a)
-        for (int b = 0; b < mb; ++b) C[(size_t)(a0 + a) * nb + b0 + b] = blk[(size_t)a * mb + b];
-    }
-  return C;
-}
-
-void lincomb_dev(dd_ctx* c, const std::vector<const double*>& V, const std::vector<double>& Y, int kc,
-                 const std::vector<double*>& out, cudaStream_t s) {
-  std::vector<const double*> o(out.begin(), out.end());
-  set_ptrs(c, V, 0, s);
-  set_ptrs(c, o, 256, s);
-  DD_REQUIRE(V.size() <= 256 && kc <= 256 && Y.size() <= (size_t)128 * 128, "lincomb: too many columns");
-  double* Yd = c->ybuf;
-  DD_CUDA(cudaMemcpyAsync(Yd, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  lincomb(c->n_gamma, (int)V.size(), c->ptrs, Yd, kc, (double* const*)(c->ptrs + 256), s);
-  DD_CUDA(cudaStreamSynchronize(s));
-}
-
-// G = W^T A W and its inverse (k x k, FP64, on the host)
 // df64 copies of the basis used by the deflation kernels
 void refresh_df(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
   if (st->k == 0) return;
@@ -814,37 +776,82 @@ void refresh_df(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
   to_df64(kn, st->AW, st->AWd, s);
 }
 
-void refresh_gram(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
-  int k = st->k;
-  if (k == 0) return;
-  int64_t n = c->n_gamma;
-  std::vector<const double*> Wc, AWc;
-  for (int j = 0; j < k; ++j) {
-    Wc.push_back(st->W + (size_t)j * n);
-    AWc.push_back(st->AW + (size_t)j * n);
+// Device work space of the recycling update, allocated once per recycle state.
+void recycle_work(dd_recycle* st) {
+  if (st->rptr) return;
+  st->rptr = st->arena.alloc<void*>(REC_PTRS);
+  st->rblk = st->arena.alloc<short2>(3 * REC_BLOCKS);
+  st->rpart = st->arena.alloc<double>((size_t)REC_CHUNKS * REC_BLOCKS * 16);
+  st->rout = st->arena.alloc<double>((size_t)2 * REC_BLOCKS * 16);
+  st->rY = st->arena.alloc<double>((size_t)REC_MAXM * REC_MAXM);
+  st->ralpha = st->arena.alloc<double>(REC_MAXM);
+}
+
+// Host image of the pointer table and block lists, uploaded with one copy.
+struct RecTables {
+  std::vector<void*> ptr = std::vector<void*>(REC_PTRS, nullptr);
+  std::vector<short2> blk = std::vector<short2>(3 * REC_BLOCKS, short2{0, 0});
+  void upload(dd_recycle* st, cudaStream_t s) {
+    DD_CUDA(cudaMemcpyAsync(st->rptr, ptr.data(), ptr.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaMemcpyAsync(st->rblk, blk.data(), blk.size() * sizeof(short2), cudaMemcpyHostToDevice, s));
   }
-  std::vector<double> G = gram_host(c, Wc, AWc, s);
-  for (int a = 0; a < k; ++a)
-    for (int b = 0; b < a; ++b) {
-      double v = 0.5 * (G[a * k + b] + G[b * k + a]);
-      G[a * k + b] = G[b * k + a] = v;
-    }
-  std::vector<double> Gi((size_t)k * k);
+};
+
+// Scatters the upper 4 x 4 blocks of a Gram product into the full symmetric m x m matrix.
+void blocks_to_sym(int m, const std::vector<short2>& q, const double* vals, std::vector<double>& M) {
+  for (size_t t = 0; t < q.size(); ++t)
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) {
+        const int a = 4 * q[t].x + u, b = 4 * q[t].y + v;
+        if (a >= m || b >= m || a > b) continue;
+        M[(size_t)a * m + b] = M[(size_t)b * m + a] = vals[t * 16 + 4 * u + v];
+      }
+}
+
+// G = W^T A W (symmetric, df64 products) and its inverse; with re-orthogonalization also
+// (W^T W)^{-1}. The df64 copies of W and A W used by the deflation kernels are refreshed
+// unless the caller wrote them already.
+void refresh_gram(dd_ctx* c, dd_recycle* st, cudaStream_t s, bool df_done = false) {
+  const int k = st->k;
+  st->G_host.clear();
+  if (k == 0) return;
+  recycle_work(st);
+  const int64_t n = c->n_gamma;
+  RecTables tab;
+  for (int j = 0; j < k; ++j) {
+    tab.ptr[j] = (void*)(st->W + (size_t)j * n);
+    tab.ptr[REC_MAXM + j] = (void*)(st->AW + (size_t)j * n);
+  }
+  const std::vector<short2> q = gram_block_list(k, 0);
+  std::copy(q.begin(), q.end(), tab.blk.begin());
+  tab.upload(st, s);
+  const double* const* P = reinterpret_cast<const double* const*>(st->rptr);
+  gram_blocks(n, k, P, P + REC_MAXM, st->rblk, (int)q.size(), true, st->rpart, st->rout, s);
+  const bool reo = c->opt.reorth != 0;
+  if (reo) gram_blocks(n, k, P, P, st->rblk, (int)q.size(), true, st->rpart, st->rout + REC_BLOCKS * 16, s);
+  std::vector<double> hv((size_t)2 * REC_BLOCKS * 16);
+  DD_CUDA(cudaMemcpyAsync(hv.data(), st->rout, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> G((size_t)k * k, 0.0), Gi((size_t)k * k);
+  blocks_to_sym(k, q, hv.data(), G);
   if (!la::spd_inverse(k, G.data(), Gi.data())) {
     // basis numerically dependent: drop it (plain PCG until it is rebuilt)
     st->k = 0;
     return;
   }
+  st->G_host = G;
   DD_CUDA(cudaMemcpyAsync(st->Ginv, Gi.data(), Gi.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  if (c->opt.reorth) {
-    std::vector<double> WW = gram_host(c, Wc, Wc, s), WWi((size_t)k * k);
+  if (reo) {
+    std::vector<double> WW((size_t)k * k, 0.0), WWi((size_t)k * k);
+    blocks_to_sym(k, q, hv.data() + REC_BLOCKS * 16, WW);
     if (!la::spd_inverse(k, WW.data(), WWi.data())) {
       st->k = 0;
+      st->G_host.clear();
       return;
     }
     DD_CUDA(cudaMemcpyAsync(st->WWinv, WWi.data(), WWi.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  refresh_df(c, st, s);
+  if (!df_done) refresh_df(c, st, s);
   DD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -882,34 +889,43 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
     return;
   }
   // B3 / B4: harmonic Ritz vectors of V = [W, P]  (eq. 15)
-  // M^{-1} A p_j = (z_j - z_{j+1}) / alpha_j, and for the last one one extra preconditioner solve
-  for (int j = 0; j < l; ++j) {
-    if (j + 1 < l)
-      zdiff(n, st->Z + (size_t)j * n, st->Z + (size_t)(j + 1) * n, 1.0 / st->alphas[j], st->MAP + (size_t)j * n, s);
-    else
-      precond_z(c, st->AP + (size_t)j * n, st->MAP + (size_t)j * n, s);
+  recycle_work(st);
+  const int k = st->k;
+  const int m = k + l;
+  DD_REQUIRE(m <= REC_MAXM, "recycling: more than 128 columns in V = [W, P]");
+  if (k > 0 && (int)st->G_host.size() != k * k) refresh_gram(c, st, s);  // e.g. after a checkpoint import
+  // M^{-1} A p_j = (z_j - z_{j+1}) / alpha_j, and one preconditioner application for the last
+  DD_CUDA(cudaMemcpyAsync(st->ralpha, st->alphas.data(), (size_t)l * sizeof(double), cudaMemcpyHostToDevice, s));
+  zdiff_all(n, l - 1, st->Z, st->ralpha, st->MAP, s);
+  precond_z(c, st->AP + (size_t)(l - 1) * n, st->MAP + (size_t)(l - 1) * n, s);
+  // F = V^T A V: the leading block W^T A W is G of the current basis; the rest in df64.
+  // Gh = (AV)^T M^{-1} (AV): df64 for an FP64 preconditioner; for an FP32 one the vectors
+  // M^{-1} A v carry FP32 accuracy only and the products accumulate in FP32 per stage.
+  RecTables tab;
+  for (int j = 0; j < m; ++j) {
+    const bool w = j < k;
+    const size_t off = (size_t)(w ? j : j - k) * n;
+    tab.ptr[j] = (void*)((w ? st->W : st->P) + off);
+    tab.ptr[REC_MAXM + j] = (void*)((w ? st->AW : st->AP) + off);
+    tab.ptr[2 * REC_MAXM + j] = (void*)((w ? st->MAW : st->MAP) + off);
   }
-  std::vector<const double*> V, AV, MAV;
-  for (int j = 0; j < st->k; ++j) {
-    V.push_back(st->W + (size_t)j * n);
-    AV.push_back(st->AW + (size_t)j * n);
-    MAV.push_back(st->MAW + (size_t)j * n);
-  }
-  for (int j = 0; j < l; ++j) {
-    V.push_back(st->P + (size_t)j * n);
-    AV.push_back(st->AP + (size_t)j * n);
-    MAV.push_back(st->MAP + (size_t)j * n);
-  }
-  int m = (int)V.size();
-  std::vector<double> F = gram_host(c, V, AV, s);    // V^T A V
-  std::vector<double> Gh = gram_host(c, AV, MAV, s); // (AV)^T M^{-1} (AV)
-  for (int a = 0; a < m; ++a)
-    for (int b = 0; b < a; ++b) {
-      double v = 0.5 * (F[a * m + b] + F[b * m + a]);
-      F[a * m + b] = F[b * m + a] = v;
-      v = 0.5 * (Gh[a * m + b] + Gh[b * m + a]);
-      Gh[a * m + b] = Gh[b * m + a] = v;
-    }
+  const std::vector<short2> qF = gram_block_list(m, k), qG = gram_block_list(m, 0);
+  std::copy(qF.begin(), qF.end(), tab.blk.begin());
+  std::copy(qG.begin(), qG.end(), tab.blk.begin() + REC_BLOCKS);
+  tab.upload(st, s);
+  const double* const* PV = reinterpret_cast<const double* const*>(st->rptr);
+  const bool gh_df = c->opt.precond_prec == DD_PREC_FP64;
+  gram_blocks(n, m, PV, PV + REC_MAXM, st->rblk, (int)qF.size(), true, st->rpart, st->rout, s);
+  gram_blocks(n, m, PV + REC_MAXM, PV + 2 * REC_MAXM, st->rblk + REC_BLOCKS, (int)qG.size(), gh_df, st->rpart,
+              st->rout + REC_BLOCKS * 16, s);
+  std::vector<double> hv((size_t)2 * REC_BLOCKS * 16);
+  DD_CUDA(cudaMemcpyAsync(hv.data(), st->rout, hv.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> F((size_t)m * m, 0.0), Gh((size_t)m * m, 0.0);
+  blocks_to_sym(m, qF, hv.data(), F);
+  blocks_to_sym(m, qG, hv.data() + REC_BLOCKS * 16, Gh);
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) F[(size_t)a * m + b] = st->G_host[(size_t)a * k + b];
   // The pencil's eigenpairs do not depend on the scaling of V's columns, and the search
   // vectors shrink with the residual by many orders of magnitude: scale the columns to unit
   // A-norm, D = diag(F)^{-1/2}, then restrict to the numerically nonsingular part of D F D =
@@ -920,10 +936,15 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b) Fw[(size_t)a * m + b] *= dsc[a] * dsc[b];
   la::sym_eig(m, Fw.data(), lam.data(), Q.data());
+  // Numerical rank of D F D at the accuracy of the pencil's data: with an FP32 preconditioner
+  // the vectors M^{-1} A v carry about 1e-7 relative error, which a direction with eigenvalue
+  // lam of D F D amplifies by 1/lam in T^T Gh T; directions below 1e-5 would produce spurious
+  // harmonic Ritz values (and B4 would select the largest of them). FP64 data: 1e-12.
+  const double rank_tol = c->opt.precond_prec == DD_PREC_FP32 ? 1e-5 : 1e-12;
   double lmax = lam[m - 1];
   std::vector<int> keep;
   for (int a = 0; a < m; ++a)
-    if (lam[a] > 1e-12 * lmax) keep.push_back(a);
+    if (lam[a] > rank_tol * lmax) keep.push_back(a);
   int r = (int)keep.size();
   if (r == 0) return;
   std::vector<double> T((size_t)m * r);
@@ -962,20 +983,27 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
       for (int i = 0; i < r; ++i) sacc += T[(size_t)a * r + i] * U[(size_t)i * r + sel[j]];
       Y[(size_t)a * kn + j] = sacc;
     }
-  std::vector<double*> oW, oAW, oMAW;
+  // W = V Y, A W = (A V) Y in df64 (their df64 copies written alongside), M^{-1} A W = (M^{-1} A V) Y
+  DD_CUDA(cudaMemcpyAsync(st->rY, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   for (int j = 0; j < kn; ++j) {
-    oW.push_back(st->W2 + (size_t)j * n);
-    oAW.push_back(st->AW2 + (size_t)j * n);
-    oMAW.push_back(st->MAW2 + (size_t)j * n);
+    tab.ptr[3 * REC_MAXM + j] = (void*)(st->W2 + (size_t)j * n);
+    tab.ptr[4 * REC_MAXM + j] = (void*)(st->AW2 + (size_t)j * n);
+    tab.ptr[5 * REC_MAXM + j] = (void*)(st->MAW2 + (size_t)j * n);
+    tab.ptr[6 * REC_MAXM + j] = (void*)(st->Wd + (size_t)j * n);
+    tab.ptr[7 * REC_MAXM + j] = (void*)(st->AWd + (size_t)j * n);
   }
-  lincomb_dev(c, V, Y, kn, oW, s);
-  lincomb_dev(c, AV, Y, kn, oAW, s);
-  lincomb_dev(c, MAV, Y, kn, oMAW, s);
+  DD_CUDA(cudaMemcpyAsync(st->rptr + 3 * REC_MAXM, tab.ptr.data() + 3 * REC_MAXM, 5 * REC_MAXM * sizeof(void*),
+                          cudaMemcpyHostToDevice, s));
+  double* const* PO = reinterpret_cast<double* const*>(st->rptr);
+  df64* const* PD = reinterpret_cast<df64* const*>(st->rptr);
+  lincomb_src(n, m, kn, PV, st->rY, PO + 3 * REC_MAXM, PD + 6 * REC_MAXM, true, s);
+  lincomb_src(n, m, kn, PV + REC_MAXM, st->rY, PO + 4 * REC_MAXM, PD + 7 * REC_MAXM, true, s);
+  lincomb_src(n, m, kn, PV + 2 * REC_MAXM, st->rY, PO + 5 * REC_MAXM, nullptr, gh_df, s);
   std::swap(st->W, st->W2);
   std::swap(st->AW, st->AW2);
   std::swap(st->MAW, st->MAW2);
   st->k = kn;
-  refresh_gram(c, st, s);
+  refresh_gram(c, st, s, true);
 }
 
 
