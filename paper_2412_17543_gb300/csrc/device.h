@@ -9,18 +9,57 @@ namespace dd {
 
 constexpr int TILE = 32;  // symmetric matrices are stored as 32x32 upper tiles
 
-// Batched symmetric matrices as upper-triangular 32x32 tiles (bi <= bj, row-major
-// over the tile pairs; each tile row-major). FP64: 1024 doubles per tile;
-// FP32: 1024 floats; DF64: 1024 (hi, lo) float pairs.
+// Batched symmetric matrices. Streamed form ("packed panels", read by k_symv): each
+// matrix is cut into 32-row block rows; block row b holds its diagonal block as the packed
+// upper triangle (row-major), then the full 32 x 32 blocks to its right, then the block of
+// the ragged last w = n % 32 columns (32 rows of w values padded to a multiple of 16
+// bytes); the ragged last block row is its packed w x w triangle padded likewise. Only the
+// padding to 16 bytes (the bulk-copy granule) is stored beyond the n(n+1)/2 entries.
+// Tiled form (read by the ensemble kernels, built from the packed form on the first
+// ensemble call): upper-triangular 32x32 tiles (bi <= bj, row-major over the tile pairs;
+// each tile row-major, zero-padded). FP64: doubles; FP32: floats; DF64: (hi, lo) pairs.
 struct SymTiles {
   int prec = DD_PREC_FP64;
   int count = 0;
   int max_n = 0;
   const int* n = nullptr;         // [count] dimension of each matrix
-  const int64_t* toff = nullptr;  // [count] first tile of each matrix
-  const void* data = nullptr;
+  const int64_t* poff = nullptr;  // [count] first element of each matrix in the packed form
+  const void* pdata = nullptr;    // packed form
+  int64_t pelems = 0;             // elements of the packed form
+  const int64_t* toff = nullptr;  // [count] first tile of each matrix (tiled form, nullptr until built)
+  const void* data = nullptr;     // tiled form
   int64_t ntiles = 0;
 };
+
+// Geometry of one matrix in the packed form (element counts; eb = bytes per element).
+struct PackGeom {
+  int nf, w, wp, dw;  // full block rows, ragged width, padded ragged width, padded ragged triangle
+};
+__host__ __device__ inline PackGeom pack_geom(int n, int eb) {
+  const int g = 16 / eb;  // elements per 16 bytes
+  PackGeom p;
+  p.nf = n / 32;
+  p.w = n % 32;
+  p.wp = (p.w + g - 1) / g * g;
+  p.dw = (p.w * (p.w + 1) / 2 + g - 1) / g * g;
+  return p;
+}
+__host__ __device__ inline int64_t pack_row_off(const PackGeom& p, int b) {
+  const int64_t rc = p.w ? 32 * p.wp : 0;
+  return (int64_t)b * (528 + rc) + 1024 * ((int64_t)b * (p.nf - 1) - (int64_t)b * (b - 1) / 2);
+}
+__host__ __device__ inline int64_t pack_tile_off(const PackGeom& p, int bi, int bj) {
+  const int64_t r = pack_row_off(p, bi);
+  if (bi == bj) return r;
+  return r + 528 + 1024 * (int64_t)((bj < p.nf ? bj : p.nf) - bi - 1);
+}
+__host__ __device__ inline int pack_tile_elems(const PackGeom& p, int bi, int bj) {
+  if (bi == bj) return bi < p.nf ? 528 : p.dw;
+  return bj < p.nf ? 1024 : 32 * p.wp;
+}
+__host__ __device__ inline int64_t pack_total(const PackGeom& p) { return pack_row_off(p, p.nf) + (p.w ? p.dw : 0); }
+// index of (r, c), c >= r, in a packed upper triangle of size h
+__host__ __device__ inline int tri_index(int h, int r, int c) { return r * h - r * (r - 1) / 2 + (c - r); }
 
 inline size_t tile_bytes(int prec) { return prec == DD_PREC_FP32 ? 4096 : 8192; }
 
@@ -51,6 +90,8 @@ struct DevMesh {
                             //             first/last boundary-layer element
   const int16_t* type_items;  // items: node, then 8 slots (element * 8 + corner, -1 = none)
   const int16_t* type_bl;     // boundary-layer element ids
+  const int16_t* type_citems; // the items with slots (position in the type's boundary-layer list) * 8 + corner
+  int max_nbl;                // largest boundary-layer list of a subdomain type
   const int64_t* ioff;
   const int64_t* goff;
   const int* gmap;
@@ -140,7 +181,12 @@ void launch_elem_interface(const DevMesh& m, int mode, const double* xg, const d
                            cudaStream_t s);
 // s_I = K_II^{-1} t_I for every subdomain (dense tiles or fast diagonalization)
 void launch_kii_apply(const DevMesh& m, const double* tI, double* sI, int* err, cudaStream_t s);
+// fused Schur application (one CTA per subdomain) for the fast-diagonalization solver of 8^3 subdomains
+bool schur_fused_available(const DevMesh& m);
+void launch_schur_fused(const DevMesh& m, const double* xg, double* yloc, cudaStream_t s);
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s);
+// builds the tiled form of A from its packed form (once; the ensemble kernels read tiles)
+void ensure_tiles(DeviceArena& arena, SymTiles& A, cudaStream_t s);
 void launch_wait_selftest(int* err, long long limit, cudaStream_t s);
 // y[g] = (base ? base[bmap ? bmap[g] : g] : 0) + sum over copies of loc[idx[k]]
 void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,

@@ -138,6 +138,14 @@ void select_ops(dd_ctx* c, cudaStream_t s) {
 
 BatchWork& batch_work(dd_ctx* c, cudaStream_t s) {
   if (c->bw) return *c->bw;
+  // the ensemble kernels read the symmetric operators as 32 x 32 tiles: build that form from
+  // the packed panels once (kept by the context)
+  ensure_tiles(c->arena, c->b1.N, s);
+  if (c->mesh.local_solver != DD_LOCAL_FDM) ensure_tiles(c->arena, c->mesh.KIIinv, s);
+  if (c->levels == 3) {
+    ensure_tiles(c->arena, c->l2.KIIinv, s);
+    ensure_tiles(c->arena, c->l2.b.N, s);
+  }
   auto B = std::make_unique<BatchWork>();
   DeviceArena& A = B->arena;
   const DevMesh& m = c->mesh;

@@ -114,11 +114,13 @@ void trmm_lower(int n, int m, const double* L, const double* X, double* Y) {
 }
 
 void sym_eig(int n, double* A, double* w, double* V) {
-  // 1) Householder reduction A = Q T Q^T (T tridiagonal), Q accumulated in V (Golub & Van Loan Sect. 8.3.1)
+  // 1) Householder reduction A = Q T Q^T (T tridiagonal), Q accumulated (Golub & Van Loan Sect. 8.3.1).
+  //    Q is kept transposed (row r of Qt = column r of Q), so that the reflections and the
+  //    rotations of step 2 update contiguous rows.
   auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
-  std::fill(V, V + (size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  std::vector<double> v(n), p(n), q(n);
+  std::vector<double> Qt((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), p(n), q(n), dots(n);
   for (int k = 0; k + 2 < n; ++k) {
     int m = n - k - 1;  // trailing size
     double alpha = 0.0;
@@ -146,84 +148,93 @@ void sym_eig(int n, double* A, double* w, double* V) {
     for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
     for (int i = 0; i < m; ++i) {  // B -= v q^T + q v^T
       double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
-      for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+      const double vi = v[i], qi = q[i];
+      for (int j = 0; j < m; ++j) row[j] -= vi * q[j] + qi * v[j];
     }
     a(k + 1, k) = alpha;
     a(k, k + 1) = alpha;
     for (int i = 1; i < m; ++i) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
-    for (int r = 0; r < n; ++r) {  // V = V H
-      double* row = V + (size_t)r * n + (k + 1);
-      double sacc = 0.0;
-      for (int j = 0; j < m; ++j) sacc += row[j] * v[j];
-      sacc *= beta;
-      for (int j = 0; j < m; ++j) row[j] -= sacc * v[j];
+    // Q = Q H, i.e. Qt = H Qt on rows k+1 .. n-1: Qt_rows -= beta v (v^T Qt_rows)
+    std::fill(dots.begin(), dots.end(), 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double* row = Qt.data() + (size_t)(k + 1 + i) * n;
+      const double vi = v[i];
+      for (int c = 0; c < n; ++c) dots[c] += vi * row[c];
+    }
+    for (int i = 0; i < m; ++i) {
+      double* row = Qt.data() + (size_t)(k + 1 + i) * n;
+      const double f = beta * v[i];
+      for (int c = 0; c < n; ++c) row[c] -= f * dots[c];
     }
   }
-  // 2) implicit symmetric QR steps with Wilkinson shifts, bulge chased by Givens rotations
-  //    applied as similarities on the band (Golub & Van Loan Alg. 8.3.2), rotations accumulated in V
-  auto rot = [&](int k, int lo, int hi, double c, double sn) {
-    for (int j = std::max(lo, k - 1); j <= std::min(hi, k + 2); ++j) {  // rows k, k+1
-      double x = a(k, j), y = a(k + 1, j);
-      a(k, j) = c * x + sn * y;
-      a(k + 1, j) = -sn * x + c * y;
-    }
-    for (int i = std::max(lo, k - 1); i <= std::min(hi, k + 2); ++i) {  // columns k, k+1
-      double x = a(i, k), y = a(i, k + 1);
-      a(i, k) = c * x + sn * y;
-      a(i, k + 1) = -sn * x + c * y;
-    }
-    for (int r = 0; r < n; ++r) {
-      double x = V[(size_t)r * n + k], y = V[(size_t)r * n + k + 1];
-      V[(size_t)r * n + k] = c * x + sn * y;
-      V[(size_t)r * n + k + 1] = -sn * x + c * y;
-    }
-  };
+  // 2) implicit symmetric QR steps with Wilkinson shifts on the tridiagonal (d, e), bulge
+  //    chased by Givens rotations (Golub & Van Loan Alg. 8.3.2), rotations accumulated in Qt
+  std::vector<double> d(n), e(n, 0.0);  // e[i] = T(i, i-1)
+  for (int i = 0; i < n; ++i) d[i] = a(i, i);
+  for (int i = 1; i < n; ++i) e[i] = a(i, i - 1);
   const double eps = 2.220446049250313e-16;
   // an off-diagonal entry is negligible relative to its diagonal neighbours or to the norm of T
   // (the latter deflates blocks of numerically zero eigenvalues, whose neighbours are ~0 too)
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i) {
-    double rs = std::fabs(a(i, i)) + (i > 0 ? std::fabs(a(i, i - 1)) : 0.0) + (i + 1 < n ? std::fabs(a(i + 1, i)) : 0.0);
+    double rs = std::fabs(d[i]) + (i > 0 ? std::fabs(e[i]) : 0.0) + (i + 1 < n ? std::fabs(e[i + 1]) : 0.0);
     tnorm = std::max(tnorm, rs);
   }
   auto small = [&](int i) {  // entry (i, i-1)
-    double e = std::fabs(a(i, i - 1));
-    return e <= eps * (std::fabs(a(i, i)) + std::fabs(a(i - 1, i - 1))) || e <= 4 * eps * tnorm;
+    double ei = std::fabs(e[i]);
+    return ei <= eps * (std::fabs(d[i]) + std::fabs(d[i - 1])) || ei <= 4 * eps * tnorm;
   };
   int hi = n - 1, iter = 0;
   while (hi > 0 && iter < 100 * n) {
     if (small(hi)) {
-      a(hi, hi - 1) = a(hi - 1, hi) = 0.0;
+      e[hi] = 0.0;
       --hi;
       continue;
     }
     int lo = hi - 1;
     while (lo > 0 && !small(lo)) --lo;
-    if (lo > 0) a(lo, lo - 1) = a(lo - 1, lo) = 0.0;
-    double dd = 0.5 * (a(hi - 1, hi - 1) - a(hi, hi)), eh = a(hi, hi - 1);
+    if (lo > 0) e[lo] = 0.0;
+    double dd = 0.5 * (d[hi - 1] - d[hi]), eh = e[hi];
     double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + eh * eh);
-    double mu = a(hi, hi) - (den != 0.0 ? eh * eh / den : 0.0);
-    double x = a(lo, lo) - mu, z = a(lo + 1, lo);
+    double mu = d[hi] - (den != 0.0 ? eh * eh / den : 0.0);
+    double x = d[lo] - mu, z = e[lo + 1];
+    double bulge = 0.0;  // T(k+2, k) while chasing
     for (int k = lo; k < hi; ++k) {
       double r = std::hypot(x, z);
       double c = r > 0 ? x / r : 1.0, sn = r > 0 ? z / r : 0.0;
-      rot(k, lo, hi, c, sn);
+      // similarity with the rotation G(k, k+1) on the 4 x 4 band window rows/columns k-1 .. k+2
+      if (k > lo) e[k] = r;  // the rotated (k, k-1) entry; the bulge (k+1, k-1) becomes 0
+      const double dk = d[k], dk1 = d[k + 1], ek1 = e[k + 1];
+      d[k] = c * c * dk + 2 * c * sn * ek1 + sn * sn * dk1;
+      d[k + 1] = sn * sn * dk - 2 * c * sn * ek1 + c * c * dk1;
+      e[k + 1] = c * sn * (dk1 - dk) + (c * c - sn * sn) * ek1;
       if (k + 1 < hi) {
-        x = a(k + 1, k);
-        z = a(k + 2, k);
+        const double ek2 = e[k + 2];
+        bulge = sn * ek2;
+        e[k + 2] = c * ek2;
+        x = e[k + 1];
+        z = bulge;
+      }
+      double* r0 = Qt.data() + (size_t)k * n;
+      double* r1 = r0 + n;
+      for (int t = 0; t < n; ++t) {
+        const double xx = r0[t], yy = r1[t];
+        r0[t] = c * xx + sn * yy;
+        r1[t] = -sn * xx + c * yy;
       }
     }
     ++iter;
   }
   std::vector<int> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
-  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return a(i, i) < a(j, j); });
-  std::vector<double> Vs((size_t)n * n);
+  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] < d[j]; });
   for (int c = 0; c < n; ++c) {
-    w[c] = a(idx[c], idx[c]);
-    for (int k = 0; k < n; ++k) Vs[(size_t)k * n + c] = V[(size_t)k * n + idx[c]];
+    w[c] = d[idx[c]];
+    const double* row = Qt.data() + (size_t)idx[c] * n;
+    for (int k = 0; k < n; ++k) V[(size_t)k * n + c] = row[k];
   }
-  std::copy(Vs.begin(), Vs.end(), V);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) a(i, j) = i == j ? d[i] : (std::abs(i - j) == 1 ? e[std::max(i, j)] : 0.0);
 }
 
 }  // namespace la

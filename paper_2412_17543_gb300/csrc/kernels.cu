@@ -277,6 +277,96 @@ __device__ __forceinline__ void tile_coords(int t, int nb, int& bi, int& bj) {
   bj = b + (t - start);
 }
 
+// element i of a staged tile as the policy's value type
+template <class P>
+struct TileElem;
+template <>
+struct TileElem<PolF32> {
+  __device__ static float ld(const unsigned char* T, int i) { return reinterpret_cast<const float*>(T)[i]; }
+};
+template <>
+struct TileElem<PolF64> {
+  __device__ static double ld(const unsigned char* T, int i) { return reinterpret_cast<const double*>(T)[i]; }
+};
+template <>
+struct TileElem<PolDF> {
+  __device__ static df64 ld(const unsigned char* T, int i) {
+    const float2 e = reinterpret_cast<const float2*>(T)[i];
+    return {e.x, e.y};
+  }
+};
+
+template <class P>
+__device__ __forceinline__ typename P::V warp_sum(typename P::V v);
+template <>
+__device__ __forceinline__ float warp_sum<PolF32>(float v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <>
+__device__ __forceinline__ double warp_sum<PolF64>(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <>
+__device__ __forceinline__ df64 warp_sum<PolDF>(df64 v) {
+  for (int o = 16; o; o >>= 1) {
+    df64 u{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df64_add(v, u);
+  }
+  return v;
+}
+
+// diagonal block of height h stored as its packed upper triangle: lane l < h returns
+// sum_c T(l, c) x_c with T(l, c) = T(c, l) read from the triangle
+template <class P>
+__device__ __forceinline__ typename P::V packed_diag_part(const unsigned char* T, const typename P::V* tv, int l,
+                                                          int h) {
+  typename P::Acc a0, a1;
+  P::init(a0);
+  P::init(a1);
+  if (l < h) {
+    for (int t = 0; t < h; t += 2) {
+      int c0 = t + l;
+      c0 -= c0 >= h ? h : 0;
+      const int i0 = l <= c0 ? tri_index(h, l, c0) : tri_index(h, c0, l);
+      P::fma(a0, TileElem<P>::ld(T, i0), tv[c0]);
+      if (t + 1 < h) {
+        int c1 = t + 1 + l;
+        c1 -= c1 >= h ? h : 0;
+        const int i1 = l <= c1 ? tri_index(h, l, c1) : tri_index(h, c1, l);
+        P::fma(a1, TileElem<P>::ld(T, i1), tv[c1]);
+      }
+    }
+  }
+  return P::add(P::get(a0), P::get(a1));
+}
+
+// block of the ragged last w columns (32 rows of wp stored values): lane l returns the row
+// part sum_{c<w} T(l, c) x_j[c] and, for l < w, the column part sum_r T(r, l) x_i[r]
+template <class P>
+__device__ __forceinline__ void packed_ragged_parts(const unsigned char* T, int wp, int w, const typename P::V* ti,
+                                                    const typename P::V* tj, int l, typename P::V& row,
+                                                    typename P::V& col) {
+  typename P::Acc ar;
+  P::init(ar);
+  col = P::zero();
+  for (int c = 0; c < w; ++c) {
+    const typename P::V e = TileElem<P>::ld(T, l * wp + c);
+    P::fma(ar, e, tj[c]);
+    typename P::Acc pc;
+    P::init(pc);
+    P::fma(pc, e, ti[l]);
+    const typename P::V sc = warp_sum<P>(P::get(pc));
+    if (l == c) col = sc;
+  }
+  row = P::get(ar);
+}
+
+// Batched symmetric GEMV over the packed panels of SymTiles (one CTA per matrix): each warp
+// streams its share of the blocks (round robin) global -> shared through a ring of bulk
+// copies completing on mbarriers; an off-diagonal block serves its block row and (by
+// symmetry) its block column, so every stored entry is read from HBM once.
 template <int PREC>
 __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int64_t* __restrict__ voff,
                                                           const double* __restrict__ in,
@@ -284,12 +374,14 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
   using Ops = TileOps<PREC>;
   using P = typename Ops::P;
   using V = typename Ops::V;
-  constexpr int TB = Ops::BYTES;
+  constexpr int EB = PREC == DD_PREC_FP32 ? 4 : 8;
+  constexpr int TB = Ops::BYTES;  // the largest block (32 x 32)
   extern __shared__ __align__(128) unsigned char smem_symv[];
   unsigned char* smem_raw = smem_symv;
   const int m = blockIdx.x;
   const int n = A.n[m];
-  const int nb = (n + 31) / 32;
+  const PackGeom g = pack_geom(n, EB);
+  const int nb = g.nf + (g.w > 0);
   const int npad = nb * 32;
   const int maxpad = ((A.max_n + 31) / 32) * 32;
   unsigned char* slots = smem_raw;                                            // [W][SLOTS][TB]
@@ -307,16 +399,18 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
 
   const int ntl = nb * (nb + 1) / 2;
   const int mine = (warp < ntl) ? (ntl - warp + SYMV_WARPS - 1) / SYMV_WARPS : 0;
-  const unsigned char* gt = reinterpret_cast<const unsigned char*>(A.data) + (size_t)A.toff[m] * TB;
+  const unsigned char* gm = reinterpret_cast<const unsigned char*>(A.pdata) + (size_t)A.poff[m] * EB;
   unsigned char* wslots = slots + (size_t)warp * SYMV_SLOTS * TB;
   uint64_t* wbars = bars + warp * SYMV_SLOTS;
-  if (lane == 0) {
-    for (int k = 0; k < SYMV_SLOTS && k < mine; ++k) {
-      int t = warp + k * SYMV_WARPS;
-      mbar_arrive_expect_tx(&wbars[k], TB);
-      bulk_g2s(wslots + (size_t)k * TB, gt + (size_t)t * TB, TB, &wbars[k]);
-    }
-  }
+  auto issue = [&](int k, int slot) {
+    int bi, bj;
+    tile_coords(warp + k * SYMV_WARPS, nb, bi, bj);
+    const uint32_t bytes = (uint32_t)pack_tile_elems(g, bi, bj) * EB;
+    mbar_arrive_expect_tx(&wbars[slot], bytes);
+    bulk_g2s(wslots + (size_t)slot * TB, gm + (size_t)pack_tile_off(g, bi, bj) * EB, bytes, &wbars[slot]);
+  };
+  if (lane == 0)
+    for (int k = 0; k < SYMV_SLOTS && k < mine; ++k) issue(k, k);
   V* mypart = part + warp * maxpad;
   bool ok = true;
   int k = 0;
@@ -326,25 +420,28 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
       ok = false;
       break;
     }
-    const int t = warp + k * SYMV_WARPS;
     int bi, bj;
-    tile_coords(t, nb, bi, bj);
+    tile_coords(warp + k * SYMV_WARPS, nb, bi, bj);
     const unsigned char* T = wslots + (size_t)slot * TB;
-    if (bi != bj) {
+    if (bi == bj) {
+      const int h = bi < g.nf ? 32 : g.w;
+      const V r = packed_diag_part<P>(T, tv + bi * 32, lane, h);
+      if (lane < h) mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
+    } else if (bj < g.nf) {
       V r, c;
       Ops::both_parts(T, tv + bi * 32, tv + bj * 32, lane, r, c);
       mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
       mypart[bj * 32 + lane] = P::add(mypart[bj * 32 + lane], c);
     } else {
-      V r = Ops::row_part(T, tv + bj * 32, lane);
+      V r, c;
+      packed_ragged_parts<P>(T, g.wp, g.w, tv + bi * 32, tv + bj * 32, lane, r, c);
       mypart[bi * 32 + lane] = P::add(mypart[bi * 32 + lane], r);
+      if (lane < g.w) mypart[bj * 32 + lane] = P::add(mypart[bj * 32 + lane], c);
     }
     __syncwarp();
     if (lane == 0 && k + SYMV_SLOTS < mine) {
       fence_proxy_async();
-      int tn = warp + (k + SYMV_SLOTS) * SYMV_WARPS;
-      mbar_arrive_expect_tx(&wbars[slot], TB);
-      bulk_g2s(wslots + (size_t)slot * TB, gt + (size_t)tn * TB, TB, &wbars[slot]);
+      issue(k + SYMV_SLOTS, slot);
     }
   }
   if (!ok) {
@@ -358,21 +455,6 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
     for (int w = 1; w < SYMV_WARPS; ++w) s = P::add(s, part[w * maxpad + i]);
     out[vo + i] = P::to_d(s);
   }
-}
-
-// Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing arrives
-// at (no copy is in flight), gives up after `limit` attempts and raises the error word,
-// exactly as the streaming kernels do when a bulk copy never lands.
-__global__ void k_wait_selftest(int* err, long long limit) {
-  __shared__ __align__(8) uint64_t bar;
-  mbar_init(&bar, 1);
-  fence_mbar_init();
-  mbar_wait_bounded(&bar, 0u, err, limit);
-}
-
-void launch_wait_selftest(int* err, long long limit, cudaStream_t s) {
-  k_wait_selftest<<<1, 1, 0, s>>>(err, limit);
-  DD_CHECK_LAUNCH();
 }
 
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s) {
@@ -397,6 +479,88 @@ void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, doubl
   }
   DD_CHECK_LAUNCH();
 }
+
+// Tiled form from the packed form: tile t of matrix m (32 x 32, zero-padded, diagonal tiles
+// with both triangles). One CTA per tile.
+template <typename E>
+__global__ void k_packed_to_tiles(SymTiles A, const int* __restrict__ tmat, const int* __restrict__ tidx,
+                                  E* __restrict__ tiles) {
+  const int64_t t = blockIdx.x;
+  const int m = tmat[t], ti = tidx[t];
+  const int n = A.n[m];
+  const PackGeom g = pack_geom(n, sizeof(E) == 4 ? 4 : 8);
+  const int nb = g.nf + (g.w > 0);
+  int bi, bj;
+  tile_coords(ti, nb, bi, bj);
+  const E* src = static_cast<const E*>(A.pdata) + A.poff[m] + pack_tile_off(g, bi, bj);
+  const int h = bi < g.nf ? 32 : g.w;
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int r = e / 32, c = e % 32;
+    E v{};
+    if (bi == bj) {
+      if (r < h && c < h) v = src[r <= c ? tri_index(h, r, c) : tri_index(h, c, r)];
+    } else if (bj < g.nf) {
+      v = src[r * 32 + c];
+    } else if (c < g.w) {
+      v = src[r * g.wp + c];
+    }
+    tiles[t * 1024 + e] = v;
+  }
+}
+
+void ensure_tiles(DeviceArena& arena, SymTiles& A, cudaStream_t s) {
+  if (A.data || A.count == 0) return;
+  std::vector<int> n(A.count);
+  DD_CUDA(cudaMemcpyAsync(n.data(), A.n, n.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> toff(A.count);
+  std::vector<int> tmat, tidx;
+  int64_t nt = 0;
+  for (int m = 0; m < A.count; ++m) {
+    const int nb = (n[m] + 31) / 32;
+    toff[m] = nt;
+    for (int t = 0; t < nb * (nb + 1) / 2; ++t) {
+      tmat.push_back(m);
+      tidx.push_back(t);
+    }
+    nt += (int64_t)nb * (nb + 1) / 2;
+  }
+  A.ntiles = nt;
+  A.toff = arena.upload(toff, s);
+  const int* dm = arena.upload(tmat, s);
+  const int* di = arena.upload(tidx, s);
+  if (nt == 0) return;
+  if (A.prec == DD_PREC_FP32) {
+    float* d = arena.alloc<float>((size_t)nt * 1024);
+    k_packed_to_tiles<float><<<(unsigned)nt, 256, 0, s>>>(A, dm, di, d);
+    A.data = d;
+  } else if (A.prec == DD_PREC_FP64) {
+    double* d = arena.alloc<double>((size_t)nt * 1024);
+    k_packed_to_tiles<double><<<(unsigned)nt, 256, 0, s>>>(A, dm, di, d);
+    A.data = d;
+  } else {
+    float2* d = arena.alloc<float2>((size_t)nt * 1024);
+    k_packed_to_tiles<float2><<<(unsigned)nt, 256, 0, s>>>(A, dm, di, d);
+    A.data = d;
+  }
+  DD_CHECK_LAUNCH();
+}
+
+// Self-test of the bounded-wait path: one thread waits on an mbarrier that nothing arrives
+// at (no copy is in flight), gives up after `limit` attempts and raises the error word,
+// exactly as the streaming kernels do when a bulk copy never lands.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  mbar_wait_bounded(&bar, 0u, err, limit);
+}
+
+void launch_wait_selftest(int* err, long long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(err, limit);
+  DD_CHECK_LAUNCH();
+}
+
 
 // ---------------------------------------------------------------------------
 // Fast diagonalization: s = V D^{-1} V^T t with V = Vz (x) Vy (x) Vx, one CTA per subdomain,
@@ -458,6 +622,177 @@ __global__ void __launch_bounds__(128) k_fdm_apply(DevMesh m, const double* __re
   fdm_contract<P>(Vs[2], 2, false, n, b1, b0);
   __syncthreads();
   for (int i = threadIdx.x; i < N; i += blockDim.x) sI[off + i] = P::to_d(b0[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Fused Schur-complement application y_i = (K_GG - K_GI K_II^{-1} K_IG) x_i of one
+// subdomain per CTA (eq. 6) for the fast-diagonalization local solver: the interior pass
+// (t_I = K_IG x_G), the six contractions of K_II^{-1} and the interface pass
+// (y_G = K_GG x_G - K_GI s_I) run back to back on shared memory, so the interior
+// vectors never leave the SM and the element entries of the boundary-layer elements
+// are formed once. The arithmetic and its order are those of k_elem_interior,
+// k_fdm_apply and k_elem_interface.
+// ---------------------------------------------------------------------------
+// out[..j..] = sum_i A(i, j) in[..i..] (trans) or sum_i A(j, i) in[..i..] along axis ax, for
+// the 7 x 7 x 7 interior index box of an 8^3-element subdomain off the domain boundary
+template <class P, int AX>
+__device__ __forceinline__ void fdm_contract7(const typename P::V* A, bool trans, const typename P::V* in,
+                                              typename P::V* out) {
+  constexpr int stride = AX == 0 ? 1 : (AX == 1 ? 7 : 49);
+  for (int idx = threadIdx.x; idx < 343; idx += blockDim.x) {
+    const int j = (idx / stride) % 7;
+    const int base = idx - j * stride;
+    typename P::Acc acc[2];
+    P::init(acc[0]);
+    P::init(acc[1]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
+      P::fma(acc[i & 1], a, in[base + i * stride]);
+    }
+    out[idx] = P::add(P::get(acc[0]), P::get(acc[1]));
+  }
+}
+
+// element-pass item with slots (position in the type's boundary-layer list) * 8 + corner;
+// kd holds the 8 entry classes of the listed elements with stride nbl
+template <class P, int S>
+__device__ __forceinline__ typename P::V apply_citem(const DevMesh& m, const int16_t* it, const typename P::V* xl,
+                                                     const typename P::V* kd, const int16_t* bll, int nbl) {
+  const int sx = S ? S : m.sx, sy = S ? S : m.sy;
+  const int NLx = sx + 1, NLy = sy + 1;
+  typename P::Acc acc[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) P::init(acc[t]);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int v = it[1 + k];
+    if (v < 0) break;
+    const int b = v >> 3, p = v & 7;
+    const int el = bll[b];
+    const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
+    const int base = ea + NLx * (eb + NLy * ec);
+    const typename P::V* kp = kd + b;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int lq = base + (q & 1) + NLx * (((q >> 1) & 1) + NLy * (q >> 2));
+      P::fma(acc[q & 3], kp[(p ^ q) * nbl], xl[lq]);
+    }
+  }
+  return P::add(P::add(P::get(acc[0]), P::get(acc[1])), P::add(P::get(acc[2]), P::get(acc[3])));
+}
+
+template <class P, int S>
+__global__ void __launch_bounds__(256) k_schur_fused(DevMesh m, const double* __restrict__ xg,
+                                                     double* __restrict__ yloc) {
+  using V = typename P::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xl = reinterpret_cast<V*>(smem_raw);  // [NL] local nodal vector
+  V* f0 = xl + m.NL;                        // [NL] interior vector buffers of the fast diagonalization
+  V* f1 = f0 + m.NL;
+  V* Vs = f1 + m.NL;                        // [3][81] 1D eigenbases (stride 9)
+  V* kd = Vs + 243;                         // [8][nbl] entry classes of the boundary-layer elements
+  int16_t* bll = reinterpret_cast<int16_t*>(kd + 8 * m.max_nbl);  // [nbl] boundary-layer elements
+  __shared__ int n[3];
+  const int s = blockIdx.x;
+  const int16_t* code = m.lidx + (size_t)s * m.NL;
+  const int* to = m.type_off + 6 * m.sub_type[s];
+  const int nbl = to[5] - to[4];
+  const int64_t io = m.ioff[s], go = m.goff[s];
+  if (threadIdx.x < 3) n[threadIdx.x] = m.fdm_n[3 * s + threadIdx.x];
+  for (int t = threadIdx.x; t < 243; t += blockDim.x) Vs[t] = ld_fdm<P>(m.fdm_V, (int64_t)s * 243 + t);
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    const int cd = code[l];
+    xl[l] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[m.gmap[go + (-1 - cd)]]) : P::zero();
+    if (cd >= 0) f0[cd] = P::zero();
+  }
+  {
+    const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
+    const int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
+    for (int t = threadIdx.x; t < nbl; t += blockDim.x) {
+      const int el = m.type_bl[to[4] + t];
+      bll[t] = (int16_t)el;
+      const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
+      const int64_t e = (int64_t)(I * sx + ea) + (int64_t)m.nx * ((J * sy + eb) + (int64_t)m.ny * (K * sz + ec));
+      V c[3];
+      load_factors<P>(m, e, c);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) kd[d * nbl + t] = P::entry(c, d);
+    }
+  }
+  __syncthreads();
+  // t_I = (K [0; x_G])_I on the interior nodes next to the boundary layer (zero elsewhere)
+  for (int i = to[0] + threadIdx.x; i < to[1]; i += blockDim.x) {
+    const int16_t* it = m.type_citems + 9 * (size_t)i;
+    f0[code[it[0]]] = apply_citem<P, S>(m, it, xl, kd, bll, nbl);
+  }
+  __syncthreads();
+  // s_I = K_II^{-1} t_I = V D^{-1} V^T t_I (V = Vz (x) Vy (x) Vx), result in f0
+  const bool cube7 = n[0] == 7 && n[1] == 7 && n[2] == 7;
+  const int N = n[0] * n[1] * n[2];
+  if (cube7) {
+    fdm_contract7<P, 0>(Vs, true, f0, f1);
+    __syncthreads();
+    fdm_contract7<P, 1>(Vs + 81, true, f1, f0);
+    __syncthreads();
+    fdm_contract7<P, 2>(Vs + 162, true, f0, f1);
+  } else {
+    fdm_contract<P>(Vs, 0, true, n, f0, f1);
+    __syncthreads();
+    fdm_contract<P>(Vs + 81, 1, true, n, f1, f0);
+    __syncthreads();
+    fdm_contract<P>(Vs + 162, 2, true, n, f0, f1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    typename P::Acc acc;
+    P::init(acc);
+    P::fma(acc, f1[i], ld_fdm<P>(m.fdm_Dinv, io + i));
+    f1[i] = P::get(acc);
+  }
+  __syncthreads();
+  if (cube7) {
+    fdm_contract7<P, 0>(Vs, false, f1, f0);
+    __syncthreads();
+    fdm_contract7<P, 1>(Vs + 81, false, f0, f1);
+    __syncthreads();
+    fdm_contract7<P, 2>(Vs + 162, false, f1, f0);
+  } else {
+    fdm_contract<P>(Vs, 0, false, n, f1, f0);
+    __syncthreads();
+    fdm_contract<P>(Vs + 81, 1, false, n, f0, f1);
+    __syncthreads();
+    fdm_contract<P>(Vs + 162, 2, false, n, f1, f0);
+  }
+  __syncthreads();
+  // the interior entries of the local vector become -s_I
+  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
+    const int cd = code[l];
+    if (cd >= 0) xl[l] = P::neg(f0[cd]);
+  }
+  __syncthreads();
+  // y_G = (K [-s_I; x_G])_G
+  for (int i = to[2] + threadIdx.x; i < to[3]; i += blockDim.x) {
+    const int16_t* it = m.type_citems + 9 * (size_t)i;
+    yloc[go + (-1 - code[it[0]])] = P::to_d(apply_citem<P, S>(m, it, xl, kd, bll, nbl));
+  }
+}
+
+bool schur_fused_available(const DevMesh& m) {
+  return m.local_solver == DD_LOCAL_FDM && m.sx == 8 && m.sy == 8 && m.sz == 8 && m.type_citems != nullptr;
+}
+
+void launch_schur_fused(const DevMesh& m, const double* xg, double* yloc, cudaStream_t s) {
+  const size_t vb = m.schur_prec == DD_PREC_DF64 ? sizeof(df64) : sizeof(double);
+  const size_t smem = vb * ((size_t)3 * m.NL + 243 + 8 * (size_t)m.max_nbl) + 2 * (size_t)m.max_nbl;
+  if (m.schur_prec == DD_PREC_DF64) {
+    max_smem(k_schur_fused<PolDF, 8>, smem);
+    k_schur_fused<PolDF, 8><<<m.S, 256, smem, s>>>(m, xg, yloc);
+  } else {
+    max_smem(k_schur_fused<PolF64, 8>, smem);
+    k_schur_fused<PolF64, 8><<<m.S, 256, smem, s>>>(m, xg, yloc);
+  }
+  DD_CHECK_LAUNCH();
 }
 
 void launch_kii_apply(const DevMesh& m, const double* tI, double* sI, int* err, cudaStream_t s) {

@@ -55,47 +55,58 @@ SymTiles upload_sym(DeviceArena& A, const std::vector<const double*>& mats, cons
   SymTiles T;
   T.prec = prec;
   T.count = (int)mats.size();
-  std::vector<int64_t> toff(T.count);
-  int64_t nt = 0;
+  const int eb = prec == DD_PREC_FP32 ? 4 : 8;
+  std::vector<int64_t> poff(T.count);
+  int64_t ne = 0;
   int maxn = 0;
   for (int m = 0; m < T.count; ++m) {
-    int nb = (dims[m] + 31) / 32;
-    toff[m] = nt;
-    nt += (int64_t)nb * (nb + 1) / 2;
+    poff[m] = ne;
+    ne += pack_total(pack_geom(dims[m], eb));
     maxn = std::max(maxn, dims[m]);
   }
-  T.ntiles = nt;
+  T.pelems = ne;
   T.max_n = maxn;
-  size_t tb = tile_bytes(prec);
-  std::vector<unsigned char> buf((size_t)nt * tb, 0);
+  std::vector<unsigned char> buf((size_t)ne * eb, 0);
+  auto put = [&](int64_t at, double v) {
+    unsigned char* d = buf.data() + (size_t)at * eb;
+    if (prec == DD_PREC_FP64) {
+      std::memcpy(d, &v, 8);
+    } else if (prec == DD_PREC_FP32) {
+      float f = (float)v;
+      std::memcpy(d, &f, 4);
+    } else {  // float pair (hi, lo)
+      df64 x = df64_from_double(v);
+      std::memcpy(d, &x.hi, 4);
+      std::memcpy(d + 4, &x.lo, 4);
+    }
+  };
+#pragma omp parallel for schedule(dynamic, 16)
   for (int m = 0; m < T.count; ++m) {
-    int n = dims[m], nb = (n + 31) / 32;
+    const int n = dims[m];
+    const PackGeom g = pack_geom(n, eb);
+    const int nb = g.nf + (g.w > 0);
     const double* M = mats[m];
-    int64_t t = toff[m];
     for (int bi = 0; bi < nb; ++bi)
-      for (int bj = bi; bj < nb; ++bj, ++t) {
-        unsigned char* tile = buf.data() + (size_t)t * tb;
-        for (int r = 0; r < 32; ++r)
-          for (int c = 0; c < 32; ++c) {
-            int i = bi * 32 + r, j = bj * 32 + c;
-            double v = (i < n && j < n) ? M[(size_t)i * n + j] : 0.0;
-            if (prec == DD_PREC_FP64) {
-              reinterpret_cast<double*>(tile)[r * 32 + c] = v;
-            } else if (prec == DD_PREC_FP32) {
-              reinterpret_cast<float*>(tile)[r * 32 + c] = (float)v;
-            } else {  // float pair (hi, lo) per element
-              df64 d = df64_from_double(v);
-              reinterpret_cast<float*>(tile)[2 * (r * 32 + c)] = d.hi;
-              reinterpret_cast<float*>(tile)[2 * (r * 32 + c) + 1] = d.lo;
-            }
-          }
+      for (int bj = bi; bj < nb; ++bj) {
+        const int64_t o = poff[m] + pack_tile_off(g, bi, bj);
+        const int h = bi < g.nf ? 32 : g.w;
+        if (bi == bj) {
+          for (int r = 0; r < h; ++r)
+            for (int c = r; c < h; ++c) put(o + tri_index(h, r, c), M[(size_t)(bi * 32 + r) * n + bi * 32 + c]);
+        } else if (bj < g.nf) {
+          for (int r = 0; r < 32; ++r)
+            for (int c = 0; c < 32; ++c) put(o + r * 32 + c, M[(size_t)(bi * 32 + r) * n + bj * 32 + c]);
+        } else {
+          for (int r = 0; r < 32; ++r)
+            for (int c = 0; c < g.w; ++c) put(o + r * g.wp + c, M[(size_t)(bi * 32 + r) * n + bj * 32 + c]);
+        }
       }
   }
   T.n = A.upload(dims, s);
-  T.toff = A.upload(toff, s);
+  T.poff = A.upload(poff, s);
   unsigned char* d = A.alloc<unsigned char>(buf.size());
   DD_CUDA(cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice));
-  T.data = d;
+  T.pdata = d;
   return T;
 }
 
@@ -204,6 +215,11 @@ const void* upload_dense(DeviceArena& A, const std::vector<double>& M, int prec)
 // ---------------------------------------------------------------------------
 void schur_apply(dd_ctx* c, const double* x, double* y, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_SCHUR, s);
+  if (schur_fused_available(c->mesh)) {
+    launch_schur_fused(c->mesh, x, c->w.yloc, s);
+    launch_gather(c->n_gamma, c->mesh.gptr, c->mesh.gidx, c->w.yloc, nullptr, nullptr, y, s);
+    return;
+  }
   launch_elem_interior(c->mesh, ELEM_SCHUR, x, nullptr, c->w.tI, s);
   {
     ProfScope pk(c, DD_PROF_SYMV_KII, s);
@@ -316,6 +332,8 @@ struct WorkLists {
   std::vector<int> type_off;          // [types][6]
   std::vector<int16_t> items;         // [items][9]
   std::vector<int16_t> bl;            // boundary-layer element ids
+  std::vector<int16_t> citems;        // items with slots (position in the type's boundary-layer list) * 8 + corner
+  int max_nbl = 0;                    // largest boundary-layer list of a type
 };
 
 WorkLists build_work_lists(const Mesh1& M) {
@@ -383,6 +401,19 @@ WorkLists build_work_lists(const Mesh1& M) {
     o[4] = bl0;
     o[5] = (int)W.bl.size();
     W.type_off.insert(W.type_off.end(), o, o + 6);
+    // the same items with each element named by its position in this type's boundary-layer
+    // list, so that a kernel can keep the element entries of these elements only
+    std::vector<int> blpos(NE, -1);
+    for (int t = o[4]; t < o[5]; ++t) blpos[W.bl[t]] = t - o[4];
+    W.max_nbl = std::max(W.max_nbl, o[5] - o[4]);
+    W.citems.resize(W.items.size());
+    for (int i = o[0]; i < o[3]; ++i) {
+      W.citems[9 * (size_t)i] = W.items[9 * (size_t)i];
+      for (int k = 1; k < 9; ++k) {
+        const int16_t v = W.items[9 * (size_t)i + k];
+        W.citems[9 * (size_t)i + k] = v < 0 ? v : (int16_t)(blpos[v >> 3] * 8 + (v & 7));
+      }
+    }
   }
   return W;
 }
@@ -480,6 +511,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       dm.type_off = A.upload(W.type_off, s);
       dm.type_items = A.upload(W.items, s);
       dm.type_bl = A.upload(W.bl, s);
+      dm.type_citems = A.upload(W.citems, s);
+      dm.max_nbl = W.max_nbl;
     }
     dm.ioff = A.upload(H->l1.ioff, s);
     dm.goff = A.upload(H->l1.goff, s);
@@ -932,33 +965,64 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
   // Q L Q^T, T = D Q_r L_r^{-1/2} (so that only numerically dependent directions are dropped)
   std::vector<double> dsc(m);
   for (int a = 0; a < m; ++a) dsc[a] = F[(size_t)a * m + a] > 0.0 ? 1.0 / std::sqrt(F[(size_t)a * m + a]) : 0.0;
-  std::vector<double> Fw(F), lam(m), Q((size_t)m * m);
+  std::vector<double> Fw(F);
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b) Fw[(size_t)a * m + b] *= dsc[a] * dsc[b];
-  la::sym_eig(m, Fw.data(), lam.data(), Q.data());
   // Numerical rank of D F D at the accuracy of the pencil's data: with an FP32 preconditioner
   // the vectors M^{-1} A v carry about 1e-7 relative error, which a direction with eigenvalue
   // lam of D F D amplifies by 1/lam in T^T Gh T; directions below 1e-5 would produce spurious
   // harmonic Ritz values (and B4 would select the largest of them). FP64 data: 1e-12.
   const double rank_tol = c->opt.precond_prec == DD_PREC_FP32 ? 1e-5 : 1e-12;
-  double lmax = lam[m - 1];
-  std::vector<int> keep;
-  for (int a = 0; a < m; ++a)
-    if (lam[a] > rank_tol * lmax) keep.push_back(a);
-  int r = (int)keep.size();
-  if (r == 0) return;
-  std::vector<double> T((size_t)m * r);
-  for (int a = 0; a < m; ++a)
-    for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = dsc[a] * Q[(size_t)a * m + keep[j]] / std::sqrt(lam[keep[j]]);
+  int r = 0;
+  std::vector<double> T;
+  {
+    // When a Cholesky factor D F D = L L^T certifies lambda_min(D F D) >= 1 / ||L^{-1}||_F^2 >
+    // rank_tol * ||D F D||_F >= rank_tol * lambda_max, no direction is dropped and T = D L^{-T}
+    // spans the same pencil as the eigenvector form below (one eigen-decomposition less).
+    std::vector<double> L(Fw), Li((size_t)m * m);
+    double fro = 0.0;
+    for (double v : Fw) fro += v * v;
+    fro = std::sqrt(fro);
+    bool full_rank = la::cholesky(m, L.data());
+    if (full_rank) {
+      la::tri_inv_lower(m, L.data(), Li.data());
+      double li2 = 0.0;
+      for (double v : Li) li2 += v * v;
+      full_rank = li2 > 0.0 && 1.0 / li2 > rank_tol * fro;
+    }
+    if (full_rank) {
+      r = m;
+      T.assign((size_t)m * m, 0.0);
+      for (int a = 0; a < m; ++a)
+        for (int j = 0; j < m; ++j) T[(size_t)a * m + j] = dsc[a] * Li[(size_t)j * m + a];  // D L^{-T}
+    } else {
+      // restrict to the numerically nonsingular part: D F D = Q Lam Q^T, T = D Q_r Lam_r^{-1/2}
+      std::vector<double> lam(m), Q((size_t)m * m);
+      la::sym_eig(m, Fw.data(), lam.data(), Q.data());
+      double lmax = lam[m - 1];
+      std::vector<int> keep;
+      for (int a = 0; a < m; ++a)
+        if (lam[a] > rank_tol * lmax) keep.push_back(a);
+      r = (int)keep.size();
+      if (r == 0) return;
+      T.assign((size_t)m * r, 0.0);
+      for (int a = 0; a < m; ++a)
+        for (int j = 0; j < r; ++j) T[(size_t)a * r + j] = dsc[a] * Q[(size_t)a * m + keep[j]] / std::sqrt(lam[keep[j]]);
+    }
+  }
   // C = T^T Gh T
   std::vector<double> GT((size_t)m * r), Cm((size_t)r * r);
   la::gemm_nn(m, r, m, Gh.data(), T.data(), GT.data());
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < r; ++j) {
-      double sacc = 0.0;
-      for (int a = 0; a < m; ++a) sacc += T[(size_t)a * r + i] * GT[(size_t)a * r + j];
-      Cm[(size_t)i * r + j] = sacc;
+  std::fill(Cm.begin(), Cm.end(), 0.0);
+  for (int a = 0; a < m; ++a) {
+    const double* Ta = T.data() + (size_t)a * r;
+    const double* Ga = GT.data() + (size_t)a * r;
+    for (int i = 0; i < r; ++i) {
+      const double t = Ta[i];
+      double* Ci = Cm.data() + (size_t)i * r;
+      for (int j = 0; j < r; ++j) Ci[j] += t * Ga[j];
     }
+  }
   std::vector<double> th(r), U((size_t)r * r);
   la::sym_eig(r, Cm.data(), th.data(), U.data());
   int kn = std::min(R, r);
@@ -976,13 +1040,10 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
   }
   st->theta = theta;
   // Y = T U_sel (m x kn)
-  std::vector<double> Y((size_t)m * kn, 0.0);
-  for (int a = 0; a < m; ++a)
-    for (int j = 0; j < kn; ++j) {
-      double sacc = 0.0;
-      for (int i = 0; i < r; ++i) sacc += T[(size_t)a * r + i] * U[(size_t)i * r + sel[j]];
-      Y[(size_t)a * kn + j] = sacc;
-    }
+  std::vector<double> Y((size_t)m * kn, 0.0), Us((size_t)r * kn);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < kn; ++j) Us[(size_t)i * kn + j] = U[(size_t)i * r + sel[j]];
+  la::gemm_nn(m, kn, r, T.data(), Us.data(), Y.data());
   // W = V Y, A W = (A V) Y in df64 (their df64 copies written alongside), M^{-1} A W = (M^{-1} A V) Y
   DD_CUDA(cudaMemcpyAsync(st->rY, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   for (int j = 0; j < kn; ++j) {
