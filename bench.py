@@ -114,12 +114,15 @@ def solver_options(wl, mixed: bool) -> dict:
     return o
 
 
-def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist, prof=False):
+def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist, prof=False, capture=(),
+            keep_state=None):
     """W untimed solves then K timed solves; returns (seconds, stats list, (profile, kernel launches)).
 
     Without prof the solves run as the library runs them by default: each PCG loop is one
     CUDA-graph launch. With prof, CUDA events bracket every operator application, which
-    needs the host-issued form of the same loop (same kernels, identical results)."""
+    needs the host-issued form of the same loop (same kernels, identical results).
+    capture: step indices whose solutions are copied to the host after the timed region
+    (into the dict keep_state["x"]); keep_state["recycle"] receives the recycle state."""
     rec = solver.recycler(k, strategy)
     x = torch.empty(solver.n_free, dtype=torch.float64, device=F_dev.device)
     for t in range(warmup):
@@ -132,14 +135,20 @@ def run_arm(torch, solver, F_dev, warmup, steps, k, strategy, rtol, world, dist,
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
     torch.cuda.synchronize()
+    kept = {}
     e0.record(stream)
     for t in range(warmup, warmup + steps):
         _, st = solver.solve(F_dev[t], rec, rtol, out=x)
         stats.append(st)
+        if t in capture:
+            kept[t] = x.clone()
     e1.record(stream)
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
     pr = solver.profile(False, read=True)
+    if keep_state is not None:
+        keep_state["x"] = {t: v.cpu().numpy() for t, v in kept.items()}
+        keep_state["recycle"] = rec.state()
     sec = max_over_ranks(torch, sec, dist, F_dev.device)
     rec.close()
     return sec, stats, pr
@@ -174,12 +183,11 @@ def run_e2e(torch, solver, F_host, warmup, steps, k, strategy, rtol, dist=None):
 
 
 class OracleSample:
-    """The oracle (nested-dissection multifrontal sparse Cholesky, FP64) on a bounded sample
-    of a workload: the member of the same graded-mesh family with sample_n^3 elements is
-    factored once (setup, excluded from rates as for the GPU arm); one step solves one
-    right-hand side of the workload's sequence on it (two triangular solves, which stream
-    the factor once), and its time is scaled to the benchmark size by the ratio of factor
-    nonzeros of the two nested-dissection orderings, computed symbolically."""
+    """The oracle (nested-dissection multifrontal sparse Cholesky, FP64) on a member of the
+    workload's graded-mesh family with sample_n^3 elements; sample_n equal to the workload's
+    n solves the workload itself. The factorization is setup (excluded from rates, as the
+    GPU arm's setup is); one step solves one right-hand side of the workload's sequence (two
+    triangular solves that stream the factor once)."""
 
     def __init__(self, workload: str, wl, sample_n: int = 48):
         from oracle import cholesky, q1
@@ -187,7 +195,8 @@ class OracleSample:
         full = workload_mesh(workload)
         self.n_full = full.nx
         self.sample_n = min(sample_n, full.nx)
-        self.mesh = make_mesh(self.sample_n, wl["sub"], wl["ratio"], wl["max_aspect"])
+        self.is_full = self.sample_n == full.nx
+        self.mesh = full if self.is_full else make_mesh(self.sample_n, wl["sub"], wl["ratio"], wl["max_aspect"])
         t0 = time.perf_counter()
         self.ch = cholesky.factor_mesh(self.mesh, q1.assemble(self.mesh))
         self.t_fac = time.perf_counter() - t0
@@ -197,22 +206,34 @@ class OracleSample:
         self.scale = self.nnz_full / self.nnz_s
         self.seed = wl["seed"]
 
-    def run(self, nsolve: int, warmup: int = 0) -> float:
-        """Seconds per solve step on the sample (after `warmup` untimed steps)."""
-        F = load_sequence(self.mesh, self.seed, warmup + nsolve)
+    def run(self, nsolve: int, start: int = 0, warmup: int = 0):
+        """(seconds per solve step, {step: solution}) for steps start .. start + nsolve - 1 of the
+        sequence on the sample, after `warmup` untimed steps before them."""
+        F = load_sequence(self.mesh, self.seed, warmup + nsolve, max(0, start - warmup))
         for t in range(warmup):
             self.ch.solve(F[t])
+        xs = {}
         t0 = time.perf_counter()
-        for t in range(warmup, warmup + nsolve):
-            self.ch.solve(F[t])
-        return (time.perf_counter() - t0) / nsolve
+        for i in range(nsolve):
+            xs[start + i] = self.ch.solve(F[warmup + i])
+        return (time.perf_counter() - t0) / nsolve, xs
 
     def describe(self, nsolve: int, t_sol: float) -> str:
-        return (f"sparse Cholesky of the {self.sample_n}^3 member of the workload's graded-mesh family "
-                f"(factor {self.t_fac:.1f} s, {nsolve} solve steps at {t_sol:.3f} s each); per-step time scaled "
-                f"by nnz(L) {self.nnz_full:.3e}/{self.nnz_s:.3e} = {self.scale:.1f} to {self.n_full}^3; "
-                f"factorization (setup, {self.madd_full:.2e} multiply-adds at {self.n_full}^3) excluded as for "
-                "the GPU arm")
+        what = (f"the {self.n_full}^3 workload itself" if self.is_full else
+                f"the {self.sample_n}^3 member of the workload's graded-mesh family")
+        return (f"sparse Cholesky of {what} on {oracle_threads()} host threads (factor {self.t_fac:.1f} s, "
+                f"setup excluded as for the GPU arm; {nsolve} solve steps at {t_sol:.3f} s each)")
+
+    def measured(self, nsolve: int, t_sol: float) -> dict:
+        return {"n": self.sample_n, "solves_per_s": 1.0 / t_sol, "solve_s": t_sol, "solve_steps": nsolve,
+                "factor_s": self.t_fac, "nnz_L": self.nnz_s}
+
+    def extrapolation(self, t_sol: float):
+        if self.is_full:
+            return None
+        return {"solves_per_s": 1.0 / (t_sol * self.scale), "kind": "estimate, not measured",
+                "basis": (f"solve time scaled by the ratio of factor nonzeros of the two nested-dissection "
+                          f"orderings, {self.nnz_full:.3e} / {self.nnz_s:.3e} = {self.scale:.1f} (symbolic counts)")}
 
 
 def oracle_threads() -> int:
@@ -224,35 +245,53 @@ def oracle_threads() -> int:
     return os.cpu_count() or 1
 
 
-def cpu_baseline(args, wl, nsolve=3, sample_n=48):
-    """Timed CPU baseline: the oracle on a bounded sample of the workload (OracleSample)."""
-    smp = OracleSample(args.workload, wl, sample_n)
-    t_sol = smp.run(nsolve)
-    t_step = t_sol * smp.scale
-    return {"value": 1.0 / t_step, "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
-            "sample": smp.describe(nsolve, t_sol), "sample_factor_s": smp.t_fac, "sample_solve_s": t_sol,
-            "nnz_scale": smp.scale}
+def cpu_baseline(args, wl, nsolve=3, gpu_x=None, steps_from=0):
+    """Timed CPU baseline: the oracle on a bounded sample of the workload (OracleSample).
+
+    value is in the metric's unit: measured when the sample is the workload itself, else the
+    measured sample rate scaled to the workload (marked as an estimate). When the sample is
+    the workload, the same time steps' GPU solutions (gpu_x) are compared with the oracle's:
+    relative 2-norm error of the full free-node solution per step."""
+    smp = OracleSample(args.workload, wl, args.cpu_baseline_n)
+    t_sol, xs = smp.run(nsolve, start=steps_from)
+    ext = smp.extrapolation(t_sol)
+    out = {"value": ext["solves_per_s"] if ext else 1.0 / t_sol, "unit": "solves/s", "cores": oracle_threads(),
+           "kind": "oracle", "sample": smp.describe(nsolve, t_sol), "measured": smp.measured(nsolve, t_sol),
+           "value_is": "scaled estimate (see extrapolation)" if ext else "measured on the workload",
+           "extrapolation": ext}
+    if smp.is_full and gpu_x:
+        errs = {}
+        for t, xo in xs.items():
+            if t in gpu_x:
+                errs[t] = float(np.linalg.norm(gpu_x[t] - xo) / np.linalg.norm(xo))
+        out["gpu_rel_err_vs_oracle"] = {"steps": sorted(errs), "rel_err": [errs[t] for t in sorted(errs)],
+                                        "max": max(errs.values()) if errs else None, "rtol": wl["rtol"]}
+    return out
 
 
 def reference_arm(args, wl, world, rank):
     """The oracle as the reference arm: W + K sparse-Cholesky solve steps on the host cores,
-    each on the bounded sample of the workload and scaled to its size (OracleSample)."""
+    on the bounded sample of the workload (OracleSample). Every number is the measured one of
+    what ran; the workload-size rate from the factor-size ratio is reported separately as an
+    estimate."""
     if rank != 0:
         return None
-    smp = OracleSample(args.workload, wl)
-    t_sol = smp.run(args.steps, args.warmup)
-    sec = t_sol * smp.scale * args.steps
+    smp = OracleSample(args.workload, wl, args.cpu_baseline_n)
+    t_sol, _ = smp.run(args.steps, warmup=args.warmup)
+    sec = t_sol * args.steps
     value = args.steps / sec
+    ext = smp.extrapolation(t_sol)
+    wname = args.workload if smp.is_full else f"{args.workload} (oracle on its {smp.sample_n}^3 member)"
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_sol, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "n": wl["n"], "subdomains": (wl["n"] // wl["sub"]) ** 3,
+            "config": {"workload": wname, "n": smp.sample_n, "subdomains": (wl["n"] // wl["sub"]) ** 3,
                        "rtol": wl["rtol"], "method": "sparse Cholesky (oracle), exact solve per step"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
                              "sample": smp.describe(args.steps, t_sol)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "setup_s": smp.t_fac}
+            "extrapolated_to_workload": ext, "setup_s": smp.t_fac}
     print(json.dumps(line), flush=True)
     return line
 
@@ -269,6 +308,33 @@ def max_over_ranks(torch, sec: float, dist, device) -> float:
 def rank_seed(wl, rank: int) -> int:
     """Each rank solves its own independent sequence (replicas, no data exchange)."""
     return wl["seed"] + 1000 * rank
+
+
+# FP32 instruction issue of GB300: 152 SMs x 128 FP32 lanes x 2070 MHz (maximum SM clock);
+# a df64 multiply-add (error-free two-product plus two-sum accumulation) takes 12 FP32
+# instructions, so the df64 arithmetic of the Schur operator peaks at 40.3e12 / 12 df64
+# multiply-adds per second, i.e. 6.71 TFLOP/s counted as FP64-equivalent flops
+FP32_INSTR_PEAK = 152 * 128 * 2070e6
+DF64_MADD_INSTR = 12
+DF64_TFLOPS_PEAK = 2 * FP32_INSTR_PEAK / DF64_MADD_INSTR / 1e12
+
+
+def kernel_table(prof, hbm):
+    """Per profiled class: device time, and against its roofline the achieved rate on
+    algorithmic bytes (HBM) or algorithmic flops (df64 arithmetic on the FP32 pipes)."""
+    out = {}
+    for name, v in prof.items():
+        ms, n, ab, af = v
+        avg = ms / n if n else None
+        e = {"ms_total": ms, "launches": n, "avg_ms": avg}
+        if n and ab:
+            gbs = ab / (avg / 1e3) / 1e9
+            e.update(alg_bytes=ab, achieved_gbs=gbs, hbm_frac=gbs / hbm)
+        if n and af:
+            tf = af / (avg / 1e3) / 1e12
+            e.update(alg_flops=af, achieved_tflops=tf, alu_peak_tflops=DF64_TFLOPS_PEAK, alu_frac=tf / DF64_TFLOPS_PEAK)
+        out[name] = e
+    return out
 
 
 PROF_TIMING = ("CUDA events around every launch of the kernel on its stream, in a replay of the same warm-up and "
@@ -387,10 +453,9 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
             "replay_ms_per_step": 1e3 * prof_sec / args.steps}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, wl)
+        cpu = cpu_baseline(args, wl, args.cpu_baseline_steps)
     if rank == 0:
-        per_kernel = {name: {"ms_total": v[0], "launches": v[1], "avg_ms": (v[0] / v[1]) if v[1] else None}
-                      for name, v in prof.items()}
+        per_kernel = kernel_table(prof, hbm)
         line = {"metric": ENS_METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64 (df64 Schur, f32 BDDC)", "data": "synthetic",
@@ -427,6 +492,10 @@ def main():
     ap.add_argument("--workload", default="graded128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-n", type=int, default=48,
+                    help="elements per axis of the oracle's sample (the workload's n: the workload itself, "
+                         "factored once, with the GPU solutions of the same steps compared)")
+    ap.add_argument("--cpu-baseline-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--ens-nmm", default="auto", choices=["auto", "simt", "tc", "bf16x3"],
@@ -472,8 +541,10 @@ def main():
     clocks = clk.summary()
     # per-kernel device times: a replay of the same warm-up and timed steps with CUDA
     # events around every operator application (host-issued loop, identical iterates)
+    keep = {}
+    cap = set(range(args.warmup, args.warmup + min(args.cpu_baseline_steps, args.steps)))
     prof_sec, prof_stats, (prof, _) = run_arm(torch, mixed, F_dev, args.warmup, args.steps, k, "B4", rtol, world,
-                                              dist, prof=True)
+                                              dist, prof=True, capture=cap, keep_state=keep)
     assert [s["iters"] for s in prof_stats] == [s["iters"] for s in stats]
     total_solves = args.steps * world
     value = total_solves / sec
@@ -516,11 +587,15 @@ def main():
             "replay_ms_per_step": 1e3 * prof_sec / args.steps}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, wl)
+        cpu = cpu_baseline(args, wl, args.cpu_baseline_steps, keep.get("x"), args.warmup)
 
     if rank == 0:
-        per_kernel = {name: {"ms_total": v[0], "launches": v[1], "avg_ms": (v[0] / v[1]) if v[1] else None}
-                      for name, v in prof.items()}
+        per_kernel = kernel_table(prof, hbm)
+        rs = keep.get("recycle", {})
+        recycle = {"k": rs.get("k"), "frozen": rs.get("frozen"),
+                   "theta_max": float(max(rs["theta"])) if rs.get("theta") is not None and len(rs["theta"]) else None,
+                   "theta_min": float(min(rs["theta"])) if rs.get("theta") is not None and len(rs["theta"]) else None,
+                   "updates": per_kernel.get("recycle_update", {}).get("launches")}
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64 (df64 Schur, f32 BDDC)", "data": "synthetic",
@@ -533,7 +608,7 @@ def main():
                            "l2": "operators of 3.1 GB stream from HBM every iteration (inputs larger than L2)",
                            "rhs_seed": seed},
                 "iters_min_max_avg": [min(its), max(its), sum(its) / len(its)],
-                "frozen_at_end": bool(stats[-1]["frozen"]),
+                "frozen_at_end": bool(stats[-1]["frozen"]), "recycle": recycle,
                 "setup_s": setup_mixed, "rhs_gen_s": t_rhs,
                 "plain_fp64": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,

@@ -240,12 +240,23 @@ dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, double rtol, dd_recy
                    dd_stats* stats, void* stream);
 
 /* Adjoint of the solve x = K^{-1} f with K = sum_e k_e K_e^0 (K symmetric):
- * lambda = K^{-1} grad_x; grad_f = lambda; grad_coef[e] = -lambda_e^T K_e^0 x_e.
+ * lambda = K^{-1} grad_x; grad_f = lambda; grad_coef[e] = -lambda_e^T K_e^0 x_e, or with
+ * coef_grad_log = 1 the derivative with respect to g_e = log k_e, k_e * (-lambda_e^T K_e^0 x_e)
+ * (the chain rule of a log-parametrized coefficient field k = exp(g)).
  * grad_x, x: [n_free] device in; grad_f: [n_free] device out; grad_coef:
  * [nz][ny][nx] device out or NULL. Uses the same preconditioner; st (may be NULL)
- * supplies a deflation basis, which is not updated. */
-dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double* grad_f,
-                     double* grad_coef, double rtol, dd_recycle* st, dd_stats* stats, void* stream);
+ * supplies a deflation basis (e.g. the one recycled over the forward sequence), which is
+ * not updated. Errors: DD_INVALID_ARG (NULL ctx/grad_x/grad_f, grad_coef without x, rtol <= 0,
+ * coef_grad_log not 0 or 1, a state of another context, the pure-Neumann case),
+ * DD_NOT_CONVERGED, DD_BREAKDOWN, DD_CUDA_ERROR. */
+dd_status dd_adjoint(dd_ctx* ctx, const double* grad_x, const double* x, double* grad_f, double* grad_coef,
+                     int32_t coef_grad_log, double rtol, dd_recycle* st, dd_stats* stats, void* stream);
+
+/* Largest relative difference between the context's coefficient field (set up by dd_setup)
+ * and a given one: max_e |k_e - c_e| / |k_e| with c_e = coef[e], or exp(coef[e]) when
+ * coef_is_log = 1. coef: [nz][ny][nx] device; *max_rel_diff: host out (synchronizes
+ * `stream`). Lets a caller check that the operator it differentiates is the one it set up. */
+dd_status dd_coef_mismatch(dd_ctx* ctx, const double* coef, int32_t coef_is_log, double* max_rel_diff, void* stream);
 
 /* ---- profiling (CUDA events on the launching stream) ---- */
 enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} application of the Schur operator (Sect. 3.1) */
@@ -256,11 +267,15 @@ enum { DD_PROF_SYMV_KII = 0,   /* batched K_II^{-1} application of the Schur ope
        DD_PROF_ENS_SCHUR = 5,  /* ensemble Schur-complement applications (dd_solve_batch) */
        DD_PROF_ENS_PRECOND = 6,/* ensemble BDDC applications */
        DD_PROF_ENS_N = 7,      /* ensemble constrained-Neumann products N_i [r_i of every member] */
-       DD_PROF_COUNT = 8 };
+       DD_PROF_DEFL = 8,       /* deflation projection of one iteration, mu = G^{-1} (AW)^T z and
+                                  p = z + beta p - W mu (Algorithm 1, eq. 13); only with k > 0 */
+       DD_PROF_COUNT = 9 };
 typedef struct {
   double ms;                /* summed device time of the timed launches/regions */
   int64_t launches;         /* number of timed launches/regions */
   double alg_bytes;         /* algorithmic bytes of one launch (matrix entries once, vectors in and out) */
+  double alg_flops;         /* algorithmic floating-point operations of one launch (multiply-add = 2),
+                               counted for the arithmetic-bound Schur operator; 0 where not counted */
 } dd_kernel_prof;
 /* enable != 0 starts event timing of the classes above (adds two event records
  * per timed launch; while it is on, solves issue their PCG iterations from the host,

@@ -45,11 +45,12 @@ class Info(ctypes.Structure):
 
 
 class KernelProf(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("alg_bytes", ctypes.c_double)]
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("alg_bytes", ctypes.c_double),
+                ("alg_flops", ctypes.c_double)]
 
 
 PROF_CLASSES = ["KIIinv_apply", "symv_N", "schur_apply", "precond_apply", "recycle_update", "ens_schur_apply",
-                "ens_precond_apply", "ens_N"]
+                "ens_precond_apply", "ens_N", "deflation"]
 
 
 class Stats(ctypes.Structure):
@@ -79,7 +80,8 @@ SIGNATURES = {
     "dd_recycle_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D, ctypes.POINTER(_P)]),
     "dd_recycle_destroy": (None, [_P]),
     "dd_solve": (ctypes.c_int, [_P, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),
-    "dd_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _P, ctypes.POINTER(Stats), _P]),
+    "dd_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _D, _P, ctypes.POINTER(Stats), _P]),
+    "dd_coef_mismatch": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(_D), _P]),
     "dd_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(KernelProf), ctypes.POINTER(ctypes.c_int64), _P]),
     "dd_recycle_export": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "dd_recycle_import": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),

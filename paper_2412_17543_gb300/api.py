@@ -149,14 +149,16 @@ class Solver:
         return x
 
     def profile(self, enable: bool, read: bool = True):
-        """Starts/stops kernel timing; returns ({class: (ms, launches, alg_bytes)}, kernel launches) if read."""
+        """Starts/stops kernel timing; returns ({class: (ms, launches, alg_bytes, alg_flops)}, kernel launches)
+        if read."""
         if not read:
             nat.check(self.lib.dd_profile(self.handle, int(enable), None, None, _stream_ptr()), "dd_profile")
             return None
         prof = (nat.KernelProf * len(nat.PROF_CLASSES))()
         nl = ctypes.c_int64()
         nat.check(self.lib.dd_profile(self.handle, int(enable), prof, ctypes.byref(nl), _stream_ptr()), "dd_profile")
-        out = {name: (prof[i].ms, prof[i].launches, prof[i].alg_bytes) for i, name in enumerate(nat.PROF_CLASSES)}
+        out = {name: (prof[i].ms, prof[i].launches, prof[i].alg_bytes, prof[i].alg_flops)
+               for i, name in enumerate(nat.PROF_CLASSES)}
         return out, nl.value
 
     def recycler(self, k=0, strategy="B4", freeze_tol=1e-5) -> "Recycler":
@@ -208,8 +210,10 @@ class Solver:
             stats.append(d)
         return X, stats
 
-    def adjoint(self, grad_x, x=None, rec: "Recycler" = None, rtol=1e-10, coef_grad=True):
-        """lambda = K^{-1} grad_x (K symmetric); returns (dL/df = lambda, dL/dk per element or None, stats)."""
+    def adjoint(self, grad_x, x=None, rec: "Recycler" = None, rtol=1e-10, coef_grad=True, log_coef=False):
+        """lambda = K^{-1} grad_x (K symmetric); returns (dL/df = lambda, dL/dk per element or None, stats).
+        With log_coef the coefficient gradient is taken with respect to g = log k (computed in the
+        library). rec (optional) deflates the adjoint solve with its basis, which is not updated."""
         import torch
         gf = self._vec(self.n_free, grad_x)
         gk = None
@@ -219,19 +223,30 @@ class Solver:
             gk = torch.empty(self.n_elem, dtype=torch.float64, device=grad_x.device)
         st = nat.Stats()
         nat.check(self.lib.dd_adjoint(self.handle, _dptr(grad_x), _dptr(x) if x is not None else None, _dptr(gf),
-                                      _dptr(gk) if gk is not None else None, ctypes.c_double(rtol),
-                                      rec.handle if rec is not None else None, ctypes.byref(st), _stream_ptr()),
-                  "dd_adjoint")
+                                      _dptr(gk) if gk is not None else None, int(bool(log_coef)),
+                                      ctypes.c_double(rtol), rec.handle if rec is not None else None,
+                                      ctypes.byref(st), _stream_ptr()), "dd_adjoint")
         return gf, gk, {f: getattr(st, f) for f, _ in nat.Stats._fields_}
+
+    def coef_mismatch(self, coef, log=False) -> float:
+        """max_e |k_e - c_e| / |k_e| between the set-up coefficients and coef (exp(coef) if log)."""
+        out = ctypes.c_double()
+        nat.check(self.lib.dd_coef_mismatch(self.handle, _dptr(coef.reshape(-1)), int(bool(log)), ctypes.byref(out),
+                                            _stream_ptr()), "dd_coef_mismatch")
+        return out.value
 
 
 class PoissonSolve:
     """x = K(k)^{-1} f as a differentiable operation (torch.autograd.Function).
 
-    forward(f, g): solves with the set-up solver (whose coefficient field is k = exp(g));
-    backward: the adjoint solve with the same operator, preconditioner and deflation
-    basis returns dL/df = lambda and dL/dg_e = k_e * (-lambda_e^T K_e^0 x_e).
+    forward(f, g): solves with the set-up solver, whose coefficient field must be k = exp(g)
+    (checked in the library: a field that differs by more than 1e-12 relative raises,
+    since the solver's operator is fixed at setup); backward: the adjoint solve with the same
+    operator, preconditioner and deflation basis returns dL/df = lambda and
+    dL/dg_e = k_e * (-lambda_e^T K_e^0 x_e), both computed by the library.
     """
+
+    COEF_TOL = 1e-12
 
     @staticmethod
     def apply(f, g, solver: "Solver", rec: "Recycler", rtol: float = 1e-10, adjoint_rtol: float = 1e-10):
@@ -240,17 +255,22 @@ class PoissonSolve:
         class _Fn(torch.autograd.Function):
             @staticmethod
             def forward(ctx, f_, g_):
+                gd = g_.detach().contiguous()
+                diff = solver.coef_mismatch(gd, log=True)
+                if not diff <= PoissonSolve.COEF_TOL:
+                    raise ValueError(f"PoissonSolve: exp(g) differs from the solver's coefficients by {diff:.3e} "
+                                     "(relative); set up a solver for this field")
                 x, _ = solver.solve(f_.detach().contiguous(), rec, rtol)
-                ctx.save_for_backward(x, g_)
+                ctx.save_for_backward(x)
+                ctx.g_shape = g_.shape
                 return x
 
             @staticmethod
             def backward(ctx, grad_x):
-                x, g_ = ctx.saved_tensors
-                gf, gk, _ = solver.adjoint(grad_x.contiguous(), x, rec, adjoint_rtol,
-                                           coef_grad=ctx.needs_input_grad[1])
-                gg = gk * torch.exp(g_.reshape(-1)).reshape(gk.shape) if gk is not None else None
-                return gf, (gg.reshape(g_.shape) if gg is not None else None)
+                (x,) = ctx.saved_tensors
+                gf, gg, _ = solver.adjoint(grad_x.contiguous(), x, rec, adjoint_rtol,
+                                           coef_grad=ctx.needs_input_grad[1], log_coef=True)
+                return gf, (gg.reshape(ctx.g_shape) if gg is not None else None)
 
         return _Fn.apply(f, g)
 

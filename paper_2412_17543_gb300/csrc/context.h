@@ -65,6 +65,7 @@ struct dd_ctx {
   double prof_ms[DD_PROF_COUNT] = {0};
   int64_t prof_n[DD_PROF_COUNT] = {0};
   double prof_bytes[DD_PROF_COUNT] = {0};
+  double prof_flops[DD_PROF_COUNT] = {0};
   cudaEvent_t get_event() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();

@@ -192,7 +192,10 @@ void launch_wait_selftest(int* err, long long limit, cudaStream_t s);
 void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc, const double* base,
                    const int64_t* bmap, double* y, cudaStream_t s);
 // grad[e] = -lambda_e^T K_e^0 x_e (coefficient gradient of the adjoint)
-void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, cudaStream_t s);
+void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, int log_coef,
+                      cudaStream_t s);
+// part[b] (b < nblk) = block maxima of |k_e - c_e| / |k_e| (c_e = exp(coef_e) when log)
+void launch_coef_mismatch(const DevMesh& m, const double* coef, int log, double* part, int nblk, cudaStream_t s);
 void launch_scatter_recover(const DevMesh& m, const double* xg, const double* sI, double* x, cudaStream_t s);
 void launch_restrict(int64_t nflat, const int* gmap, const double* D, const double* r, double* rloc, cudaStream_t s);
 void launch_dense_gemv(int n, int prec, const void* A, const double* x, double* y, cudaStream_t s);

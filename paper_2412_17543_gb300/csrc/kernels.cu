@@ -837,7 +837,7 @@ void launch_gather(int64_t n, const int* ptr, const int* idx, const double* loc,
 
 // dL/dk_e = -lambda_e^T K_e^0 x_e with K_e^0 = K_e / k_e; Dirichlet nodes carry 0
 __global__ void k_coef_grad(DevMesh m, const double* __restrict__ x, const double* __restrict__ lam,
-                            double* __restrict__ grad) {
+                            double* __restrict__ grad, int log_coef) {
   const int64_t E = (int64_t)m.nx * m.ny * m.nz;
   const int64_t Nfx = m.fx1 - m.fx0, Nfy = m.fy1 - m.fy0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -865,13 +865,42 @@ __global__ void k_coef_grad(DevMesh m, const double* __restrict__ x, const doubl
       for (int q = 0; q < 8; ++q) row = fma(kd[p ^ q], xv[q], row);
       s = fma(lv[p], row, s);
     }
-    grad[e] = -s;
+    grad[e] = log_coef ? -s * k : -s;  // d/dg_e = k_e d/dk_e for k_e = exp(g_e)
   }
 }
 
-void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, cudaStream_t s) {
+void launch_coef_grad(const DevMesh& m, const double* x, const double* lam, double* grad, int log_coef,
+                      cudaStream_t s) {
   int64_t E = (int64_t)m.nx * m.ny * m.nz;
-  k_coef_grad<<<grid_for(E, 256), 256, 0, s>>>(m, x, lam, grad);
+  k_coef_grad<<<grid_for(E, 256), 256, 0, s>>>(m, x, lam, grad, log_coef);
+  DD_CHECK_LAUNCH();
+}
+
+// part[block] = max over this block's elements of |k_e - c_e| / |k_e| (c_e = exp(coef_e) if log)
+__global__ void k_coef_mismatch(int64_t E, const double* __restrict__ k, const double* __restrict__ coef, int log,
+                                double* __restrict__ part) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const double c = log ? exp(coef[e]) : coef[e];
+    const double d = fabs(k[e] - c) / fabs(k[e]);
+    mx = (d > mx || d != d) ? d : mx;  // a NaN propagates
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = red[threadIdx.x], b = red[threadIdx.x + o];
+      red[threadIdx.x] = (b > a || b != b) ? b : a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+void launch_coef_mismatch(const DevMesh& m, const double* coef, int log, double* part, int nblk, cudaStream_t s) {
+  const int64_t E = (int64_t)m.nx * m.ny * m.nz;
+  k_coef_mismatch<<<nblk, 256, 0, s>>>(E, m.coef, coef, log, part);
   DD_CHECK_LAUNCH();
 }
 

@@ -495,6 +495,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->gamma_free_host = M.gamma_free;
     // ---- level-1 mesh / Schur operator ----
     DevMesh& dm = c->mesh;
+    std::vector<double> elem_madds, elem_nbl;  // per subdomain type (for the profiling counts)
+    std::vector<int> elem_type;
     dm.nx = M.nx; dm.ny = M.ny; dm.nz = M.nz; dm.sx = M.sx; dm.sy = M.sy; dm.sz = M.sz;
     dm.Sx = M.Sx; dm.Sy = M.Sy; dm.Sz = M.Sz; dm.S = M.S;
     dm.fx0 = M.fx0; dm.fx1 = M.fx1; dm.fy0 = M.fy0; dm.fy1 = M.fy1; dm.fz0 = M.fz0; dm.fz1 = M.fz1;
@@ -507,6 +509,18 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     dm.lidx = A.upload(M.lidx, s);
     {
       WorkLists W = build_work_lists(M);
+      // multiply-adds of the element passes of one Schur application per subdomain type
+      // (8 per occupied slot of an output item) and the elements whose entries are formed
+      const int ntypes = (int)W.type_off.size() / 6;
+      elem_madds.assign(ntypes, 0.0);
+      elem_nbl.assign(ntypes, 0.0);
+      for (int t = 0; t < ntypes; ++t) {
+        const int* o = W.type_off.data() + 6 * t;
+        for (int i = o[0]; i < o[3]; ++i)
+          for (int k = 1; k < 9; ++k) elem_madds[t] += W.items[9 * (size_t)i + k] >= 0 ? 8.0 : 0.0;
+        elem_nbl[t] = o[5] - o[4];
+      }
+      elem_type = W.sub_type;
       dm.sub_type = A.upload(W.sub_type, s);
       dm.type_off = A.upload(W.type_off, s);
       dm.type_items = A.upload(W.items, s);
@@ -663,6 +677,55 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       c->prof_bytes[DD_PROF_SYMV_KII] = kii;
       c->prof_bytes[DD_PROF_SYMV_N] = nn;
       c->prof_bytes[DD_PROF_ENS_N] = nne;
+      // Schur application: multiply-adds of the element passes and of K_II^{-1} (fast
+      // diagonalization: six 1D contractions and the diagonal; dense: the symmetric product),
+      // and the data it must stream: x, the element factors of the boundary-layer elements,
+      // the K_II^{-1} data, the local maps, the local results and the assembled y
+      double sm = 0.0, sb = 0.0;
+      const double n_flat = (double)H->l1.goff[M.S], n_g = (double)c->n_gamma;
+      for (int i = 0; i < M.S; ++i) {
+        const int t = elem_type[i];
+        sm += elem_madds[t];
+        sb += elem_nbl[t] * 3 * 8.0 + M.NL * 2.0;
+        const double a = H->l1.sub[i].nI;
+        if (H->local_solver == DD_LOCAL_FDM) {
+          const FdmSub& F = H->fdm[i];
+          sm += 2.0 * a * (F.n[0] + F.n[1] + F.n[2]) + a;
+          sb += 243 * 8.0 + a * 8.0;
+        } else {
+          sm += a * a;
+          sb += a * (a + 1) / 2 * 8.0;
+        }
+      }
+      sb += n_g * 8.0 + n_flat * (8.0 + 4.0) + n_flat * (8.0 + 8.0 + 4.0) + n_g * (8.0 + 4.0);
+      c->prof_flops[DD_PROF_SCHUR] = 2.0 * sm;
+      c->prof_bytes[DD_PROF_SCHUR] = sb;
+      // BDDC application: every operator once per use (N_i packed, Phi^T twice, and at three
+      // levels K_II^{-1} packed, E twice, N, Phi^T twice, dense K_C3^{-1}) and the vectors
+      // (r, z and the local and coarse copies, 8 bytes each)
+      auto level_bytes = [&](const Level& L, int prec) {
+        const double eb = prec == DD_PREC_FP32 ? 4.0 : 8.0;
+        const double lf = (double)L.goff[L.S], lc = (double)L.coff[L.S];
+        double b = 0.0;
+        for (int i = 0; i < L.S; ++i) {
+          const double g = L.sub[i].nG, nc = L.sub[i].nc;
+          b += g * (g + 1) / 2 * eb + 2.0 * g * nc * eb;
+        }
+        return b + 8.0 * (3.0 * (double)L.n_gamma + 6.0 * lf + 3.0 * lc);
+      };
+      double pb = level_bytes(H->l1, pp);
+      if (c->levels == 3) {
+        const double eb = pp == DD_PREC_FP32 ? 4.0 : 8.0;
+        pb += level_bytes(H->l2, pp);
+        for (int j = 0; j < H->l2.S; ++j) {
+          const double a = H->l2.sub[j].nI, g = H->l2.sub[j].nG;
+          pb += a * (a + 1) / 2 * eb + 2.0 * a * g * eb + 8.0 * 4.0 * a;
+        }
+        pb += (double)H->l2.n_coarse * H->l2.n_coarse * eb;
+      } else {
+        pb += (double)H->l1.n_coarse * H->l1.n_coarse * (pp == DD_PREC_FP32 ? 4.0 : 8.0);
+      }
+      c->prof_bytes[DD_PROF_PRECOND] = pb;
     }
     c->info.n_free = c->n_free;
     c->info.n_gamma = c->n_gamma;
@@ -1076,6 +1139,9 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   const df64* Wd = k ? st->Wd : nullptr;
   const df64* AWd = k ? st->AWd : nullptr;
   DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
+  // deflation of one iteration streams the df64 copies of A W and W once each, and z, p
+  // (read) and p (written)
+  c->prof_bytes[DD_PROF_DEFL] = (2.0 * k + 3.0) * 8.0 * (double)n;
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
@@ -1101,8 +1167,11 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     if (rec) launch_record(c->ctl, c->z, st->Z, n, st->hmax, 1, bs);
     vec_dots(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, nullptr, nullptr, c->partials, bs);
     vec_finalize(c->partials, c->sc, FIN_RZL, flex, bs, &c->ctl->its);
-    if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, bs);
-    defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
+    {
+      ProfScope pd(c, k ? DD_PROF_DEFL : DD_PROF_COUNT, bs);
+      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, bs);
+      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
+    }
     schur_apply(c, c->p, c->q, bs);
     vec_dots(n, c->p, c->q, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
     vec_finalize(c->partials, c->sc, FIN_PQ, 0, bs);
@@ -1225,6 +1294,7 @@ dd_status dd_profile(dd_ctx* c, int32_t enable, dd_kernel_prof* prof, int64_t* l
         prof[k].ms = c->prof_ms[k];
         prof[k].launches = c->prof_n[k];
         prof[k].alg_bytes = c->prof_bytes[k];
+        prof[k].alg_flops = c->prof_flops[k];
         c->prof_ms[k] = 0;
         c->prof_n[k] = 0;
       }
@@ -1234,9 +1304,27 @@ dd_status dd_profile(dd_ctx* c, int32_t enable, dd_kernel_prof* prof, int64_t* l
   });
 }
 
+dd_status dd_coef_mismatch(dd_ctx* c, const double* coef, int32_t coef_is_log, double* max_rel_diff, void* stream) {
+  if (!c || !coef || !max_rel_diff || (coef_is_log != 0 && coef_is_log != 1)) {
+    g_last_error = "dd_coef_mismatch: invalid argument";
+    return DD_INVALID_ARG;
+  }
+  return guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_coef_mismatch(c->mesh, coef, coef_is_log, c->partials, NBLK, s);
+    std::vector<double> part(NBLK);
+    DD_CUDA(cudaMemcpyAsync(part.data(), c->partials, NBLK * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    double mx = 0.0;
+    for (double v : part) mx = (v > mx || v != v) ? v : mx;
+    *max_rel_diff = mx;
+  });
+}
+
 dd_status dd_adjoint(dd_ctx* c, const double* grad_x, const double* x, double* grad_f, double* grad_coef,
-                     double rtol, dd_recycle* st, dd_stats* stats, void* stream) {
-  if (!c || !grad_x || !grad_f || (grad_coef && !x) || !(rtol > 0.0) || (st && st->ctx != c)) {
+                     int32_t coef_grad_log, double rtol, dd_recycle* st, dd_stats* stats, void* stream) {
+  if (!c || !grad_x || !grad_f || (grad_coef && !x) || !(rtol > 0.0) || (st && st->ctx != c) ||
+      (coef_grad_log != 0 && coef_grad_log != 1)) {
     g_last_error = "dd_adjoint: invalid argument";
     return DD_INVALID_ARG;
   }
@@ -1253,7 +1341,7 @@ dd_status dd_adjoint(dd_ctx* c, const double* grad_x, const double* x, double* g
     DD_CUDA(cudaMemsetAsync(c->xg, 0, c->n_gamma * sizeof(double), s));
     result = pcg_solve(c, st, rtol, false, stats, s);
     recover(c, grad_x, c->xg, grad_f, s);
-    if (grad_coef) launch_coef_grad(c->mesh, x, grad_f, grad_coef, s);
+    if (grad_coef) launch_coef_grad(c->mesh, x, grad_f, grad_coef, coef_grad_log, s);
     DD_CUDA(cudaEventRecord(c->ev1, s));
     check_err(c, s);
     if (c->prof_on) c->harvest();

@@ -230,3 +230,26 @@ def test_recycle_checkpoint_resume_is_bitwise_identical():
     xb += [N(S.solve(T(f), recC, rtol=1e-9)[0]) for f in F[5:]]
     for t in range(10):
         assert np.array_equal(xa[t], xb[t]), t
+
+
+def test_bench_options_at_32cubed_every_step_against_sparse_cholesky():
+    """The timed configuration's options on a small member of its mesh family: 32^3 graded to
+    aspect 40 with 8^3 subdomains (FDM local solves, fused Schur operator), three levels
+    (groups of 2^3), adaptive face constraints at tau = 10, df64 Schur operator, FP32 BDDC,
+    flexible PCG, B4 recycling; every step's full solution against the oracle's sparse
+    Cholesky: relative 2-norm error <= 1e-7 at rtol 1e-9."""
+    m = make_mesh(32, 8, 1.3, 40.0)
+    S = P.Solver(m, levels=3, coarse_group=2, use_corners=1, use_edges=1, use_faces=1, weights="diag", adaptive=1,
+                 tau=10.0, schur_prec="df64", precond_prec="fp32", flexible=1)
+    assert S.info["n_adaptive"] > 0 and S.info["local_solver"] == 2
+    F = load_sequence(m, 3, 8)
+    ch = cholesky.factor_mesh(m)
+    rec = S.recycler(16, "B4")
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        xe = ch.solve(f)
+        err = np.linalg.norm(N(x) - xe) / np.linalg.norm(xe)
+        assert err <= 1e-7, (t, err, st)
+        assert st["rel_res"] < 1e-9
+    assert rec.state()["k"] > 0
+    S.close()
