@@ -131,6 +131,11 @@ typedef struct {
                                range of K (removes its mean), keeps the preconditioned residuals
                                orthogonal to the constants (the constant column of the deflation
                                basis, Sect. 4.1) and returns the mean-free solution */
+  int32_t symv_slots;       /* bulk copies in flight per warp of the level-1 N_i product (timed at setup) */
+  int32_t schur_threads;    /* threads per block of the fused Schur kernel (timed at setup; 0: not used) */
+  float tune_symv_ms[3];    /* setup timings of the N_i product with 2, 3, 4 copies in flight (0: not timed) */
+  float tune_kii_ms[3];     /* the same for a dense K_II^{-1} */
+  float tune_schur_ms[3];   /* setup timings of the fused Schur kernel with 256, 352, 416 threads */
 } dd_info_t;
 
 typedef struct {

@@ -41,7 +41,10 @@ class Info(ctypes.Structure):
                 ("n_coarse", ctypes.c_int32), ("n_adaptive", ctypes.c_int32), ("n_sub2", ctypes.c_int32),
                 ("n_coarse3", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("setup_seconds", ctypes.c_double), ("ens_nmm", ctypes.c_int32), ("ens_nmm_ms", ctypes.c_float * 3),
-                ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32), ("neumann", ctypes.c_int32)]
+                ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32), ("neumann", ctypes.c_int32),
+                ("symv_slots", ctypes.c_int32), ("schur_threads", ctypes.c_int32),
+                ("tune_symv_ms", ctypes.c_float * 3), ("tune_kii_ms", ctypes.c_float * 3),
+                ("tune_schur_ms", ctypes.c_float * 3)]
 
 
 class KernelProf(ctypes.Structure):

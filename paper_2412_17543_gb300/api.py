@@ -104,7 +104,8 @@ class Solver:
         info = nat.Info()
         nat.check(self.lib.dd_get_info(self.handle, ctypes.byref(info)), "dd_get_info")
         d = _info_dict(info)
-        d["ens_nmm_ms"] = list(info.ens_nmm_ms)
+        for f in ("ens_nmm_ms", "tune_symv_ms", "tune_kii_ms", "tune_schur_ms"):
+            d[f] = list(getattr(info, f))
         return d
 
     def close(self):

@@ -26,6 +26,7 @@ struct SymTiles {
   const int64_t* poff = nullptr;  // [count] first element of each matrix in the packed form
   const void* pdata = nullptr;    // packed form
   int64_t pelems = 0;             // elements of the packed form
+  int slots = 2;                  // bulk-copy ring depth per warp of k_symv (2, 3 or 4; tuned at setup)
   const int64_t* toff = nullptr;  // [count] first tile of each matrix (tiled form, nullptr until built)
   const void* data = nullptr;     // tiled form
   int64_t ntiles = 0;
@@ -92,6 +93,7 @@ struct DevMesh {
   const int16_t* type_bl;     // boundary-layer element ids
   const int16_t* type_citems; // the items with slots (position in the type's boundary-layer list) * 8 + corner
   int max_nbl;                // largest boundary-layer list of a subdomain type
+  int schur_threads;          // threads per CTA of the fused Schur kernel (256, 352 or 416; tuned at setup)
   const int64_t* ioff;
   const int64_t* goff;
   const int* gmap;

@@ -265,7 +265,6 @@ struct TileOps<DD_PREC_DF64> {
 };
 
 constexpr int SYMV_WARPS = 4;
-constexpr int SYMV_SLOTS = 2;
 
 __device__ __forceinline__ void tile_coords(int t, int nb, int& bi, int& bj) {
   int b = 0, start = 0;
@@ -367,7 +366,7 @@ __device__ __forceinline__ void packed_ragged_parts(const unsigned char* T, int 
 // streams its share of the blocks (round robin) global -> shared through a ring of bulk
 // copies completing on mbarriers; an off-diagonal block serves its block row and (by
 // symmetry) its block column, so every stored entry is read from HBM once.
-template <int PREC>
+template <int PREC, int SYMV_SLOTS>
 __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int64_t* __restrict__ voff,
                                                           const double* __restrict__ in,
                                                           double* __restrict__ out, int* err) {
@@ -457,25 +456,33 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
   }
 }
 
+template <int PREC, int SLOTS>
+static void symv_launch(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err,
+                        cudaStream_t s) {
+  const int maxpad = ((A.max_n + 31) / 32) * 32;
+  const size_t vb = (A.prec == DD_PREC_FP32) ? 4 : 8;
+  const size_t tb = tile_bytes(A.prec);
+  const size_t smem = SYMV_WARPS * SLOTS * tb + SYMV_WARPS * SLOTS * 8 + (size_t)maxpad * vb * (1 + SYMV_WARPS);
+  max_smem(k_symv<PREC, SLOTS>, smem);
+  k_symv<PREC, SLOTS><<<A.count, SYMV_WARPS * 32, smem, s>>>(A, voff, in, out, err);
+}
+
+template <int PREC>
+static void symv_slots(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err,
+                       cudaStream_t s) {
+  switch (A.slots) {
+    case 3: symv_launch<PREC, 3>(A, voff, in, out, err, s); break;
+    case 4: symv_launch<PREC, 4>(A, voff, in, out, err, s); break;
+    default: symv_launch<PREC, 2>(A, voff, in, out, err, s);
+  }
+}
+
 void launch_symv(const SymTiles& A, const int64_t* voff, const double* in, double* out, int* err, cudaStream_t s) {
   if (A.count == 0) return;
-  int maxpad = ((A.max_n + 31) / 32) * 32;
-  size_t vb = (A.prec == DD_PREC_FP32) ? 4 : 8;
-  size_t tb = tile_bytes(A.prec);
-  size_t smem = SYMV_WARPS * SYMV_SLOTS * tb + SYMV_WARPS * SYMV_SLOTS * 8 + (size_t)maxpad * vb * (1 + SYMV_WARPS);
-  dim3 grid(A.count), block(SYMV_WARPS * 32);
   switch (A.prec) {
-    case DD_PREC_FP64:
-      max_smem(k_symv<DD_PREC_FP64>, smem);
-      k_symv<DD_PREC_FP64><<<grid, block, smem, s>>>(A, voff, in, out, err);
-      break;
-    case DD_PREC_FP32:
-      max_smem(k_symv<DD_PREC_FP32>, smem);
-      k_symv<DD_PREC_FP32><<<grid, block, smem, s>>>(A, voff, in, out, err);
-      break;
-    default:
-      max_smem(k_symv<DD_PREC_DF64>, smem);
-      k_symv<DD_PREC_DF64><<<grid, block, smem, s>>>(A, voff, in, out, err);
+    case DD_PREC_FP64: symv_slots<DD_PREC_FP64>(A, voff, in, out, err, s); break;
+    case DD_PREC_FP32: symv_slots<DD_PREC_FP32>(A, voff, in, out, err, s); break;
+    default: symv_slots<DD_PREC_DF64>(A, voff, in, out, err, s);
   }
   DD_CHECK_LAUNCH();
 }
@@ -682,9 +689,9 @@ __device__ __forceinline__ typename P::V apply_citem(const DevMesh& m, const int
   return P::add(P::add(P::get(acc[0]), P::get(acc[1])), P::add(P::get(acc[2]), P::get(acc[3])));
 }
 
-template <class P, int S>
-__global__ void __launch_bounds__(256) k_schur_fused(DevMesh m, const double* __restrict__ xg,
-                                                     double* __restrict__ yloc) {
+template <class P, int S, int BS>
+__global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __restrict__ xg,
+                                                    double* __restrict__ yloc) {
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* xl = reinterpret_cast<V*>(smem_raw);  // [NL] local nodal vector
@@ -782,15 +789,27 @@ bool schur_fused_available(const DevMesh& m) {
   return m.local_solver == DD_LOCAL_FDM && m.sx == 8 && m.sy == 8 && m.sz == 8 && m.type_citems != nullptr;
 }
 
+template <class P, int BS>
+static void schur_fused_bs(const DevMesh& m, const double* xg, double* yloc, size_t smem, cudaStream_t s) {
+  max_smem(k_schur_fused<P, 8, BS>, smem);
+  k_schur_fused<P, 8, BS><<<m.S, BS, smem, s>>>(m, xg, yloc);
+}
+
 void launch_schur_fused(const DevMesh& m, const double* xg, double* yloc, cudaStream_t s) {
   const size_t vb = m.schur_prec == DD_PREC_DF64 ? sizeof(df64) : sizeof(double);
   const size_t smem = vb * ((size_t)3 * m.NL + 243 + 8 * (size_t)m.max_nbl) + 2 * (size_t)m.max_nbl;
   if (m.schur_prec == DD_PREC_DF64) {
-    max_smem(k_schur_fused<PolDF, 8>, smem);
-    k_schur_fused<PolDF, 8><<<m.S, 256, smem, s>>>(m, xg, yloc);
+    switch (m.schur_threads) {
+      case 352: schur_fused_bs<PolDF, 352>(m, xg, yloc, smem, s); break;
+      case 416: schur_fused_bs<PolDF, 416>(m, xg, yloc, smem, s); break;
+      default: schur_fused_bs<PolDF, 256>(m, xg, yloc, smem, s);
+    }
   } else {
-    max_smem(k_schur_fused<PolF64, 8>, smem);
-    k_schur_fused<PolF64, 8><<<m.S, 256, smem, s>>>(m, xg, yloc);
+    switch (m.schur_threads) {
+      case 352: schur_fused_bs<PolF64, 352>(m, xg, yloc, smem, s); break;
+      case 416: schur_fused_bs<PolF64, 416>(m, xg, yloc, smem, s); break;
+      default: schur_fused_bs<PolF64, 256>(m, xg, yloc, smem, s);
+    }
   }
   DD_CHECK_LAUNCH();
 }

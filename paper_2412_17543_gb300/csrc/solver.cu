@@ -418,6 +418,68 @@ WorkLists build_work_lists(const Mesh1& M) {
   return W;
 }
 
+// mean device time of three launches of f after one warm-up (ms)
+template <class F>
+float time_launches(F&& f, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  f();
+  DD_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < 3; ++r) f();
+  DD_CUDA(cudaEventRecord(e1, s));
+  DD_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / 3.f;
+}
+
+// Launch shapes of the two per-iteration kernels that stream the most, timed on this
+// context's own operators: the bulk-copy ring depth of the batched symmetric products
+// (level-1 N_i, and dense K_II^{-1}) and the block size of the fused Schur kernel.
+void tune_shapes(dd_ctx* c, cudaStream_t s) {
+  Work& w = c->w;
+  DD_CUDA(cudaMemsetAsync(w.rloc, 0, c->b1.n_flat * sizeof(double), s));
+  DD_CUDA(cudaMemsetAsync(w.tI, 0, c->mesh.n_int * sizeof(double), s));
+  DD_CUDA(cudaMemsetAsync(c->p, 0, c->n_gamma * sizeof(double), s));
+  auto tune_sym = [&](SymTiles& A, const int64_t* voff, const double* in, double* out, float* ms) {
+    if (A.count < 152) return;  // a small batch leaves most SMs idle whatever the ring depth
+    float best = 0.f;
+    int pick = 2;
+    for (int sl : {2, 3, 4}) {
+      A.slots = sl;
+      const float t = time_launches([&] { launch_symv(A, voff, in, out, w.err, s); }, s);
+      ms[sl - 2] = t;
+      if (sl == 2 || t < best) {
+        best = t;
+        pick = sl;
+      }
+    }
+    A.slots = pick;
+  };
+  tune_sym(c->b1.N, c->b1.goff, w.rloc, w.uloc, c->info.tune_symv_ms);
+  if (c->mesh.local_solver != DD_LOCAL_FDM) tune_sym(c->mesh.KIIinv, c->mesh.ioff, w.tI, w.sI, c->info.tune_kii_ms);
+  if (schur_fused_available(c->mesh)) {
+    float best = 0.f;
+    int pick = 256, i = 0;
+    for (int bs : {256, 352, 416}) {
+      c->mesh.schur_threads = bs;
+      const float t = time_launches([&] { launch_schur_fused(c->mesh, c->p, w.yloc, s); }, s);
+      c->info.tune_schur_ms[i++] = t;
+      if (bs == 256 || t < best) {
+        best = t;
+        pick = bs;
+      }
+    }
+    c->mesh.schur_threads = pick;
+  }
+  c->info.symv_slots = c->b1.N.slots;
+  c->info.schur_threads = schur_fused_available(c->mesh) ? c->mesh.schur_threads : 0;
+  check_err(c, s);
+}
+
 }  // namespace dd
 
 // ---------------------------------------------------------------------------
@@ -527,6 +589,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       dm.type_bl = A.upload(W.bl, s);
       dm.type_citems = A.upload(W.citems, s);
       dm.max_nbl = W.max_nbl;
+      dm.schur_threads = 256;
     }
     dm.ioff = A.upload(H->l1.ioff, s);
     dm.goff = A.upload(H->l1.goff, s);
@@ -736,6 +799,7 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->info.n_coarse3 = c->levels == 3 ? H->l2.n_coarse : 0;
     c->info.local_solver = H->local_solver;
     c->info.neumann = c->neumann ? 1 : 0;
+    tune_shapes(c.get(), s);
     c->info.device_bytes = (int64_t)A.bytes;
     c->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = c.release();
