@@ -481,6 +481,36 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
         dist.destroy_process_group()
 
 
+def ablation(args, wl, torch, pkg, dev, mesh, seed, rtol):
+    """What adaptivity (Sect. 3.3) and B4 recycling (Sect. 4.2) buy on this workload at equal
+    precision (the mixed-precision path): {adaptive off, on} x {k = 0, k = wl k}, each with
+    its own setup, W untimed and K timed steps of the same sequence. Reports iterations
+    min-max(avg), ms per step, the largest retained harmonic Ritz value (an estimate of
+    lambda_max(M^{-1} A); lambda_min >= 1 for BDDC) and the recycling updates timed."""
+    nsteps = args.warmup + args.steps
+    F_dev = torch.from_numpy(load_sequence(mesh, seed, nsteps)).to(dev)
+    rows = []
+    for adaptive in (0, 1):
+        o = solver_options(dict(wl, adaptive=adaptive), True)
+        t0 = time.perf_counter()
+        S = pkg.Solver(mesh, **o)
+        setup_s = time.perf_counter() - t0
+        for k in (0, wl["k"]):
+            keep = {}
+            sec, stats, _ = run_arm(torch, S, F_dev, args.warmup, args.steps, k, "B4", rtol, 1, None,
+                                    keep_state=keep)
+            its = [st["iters"] for st in stats]
+            th = keep["recycle"]["theta"]
+            rows.append({"adaptive": bool(adaptive), "n_adaptive": S.info["n_adaptive"], "k": k,
+                         "iters_min_max_avg": [min(its), max(its), sum(its) / len(its)],
+                         "ms_per_step": 1e3 * sec / args.steps, "solves_per_s": args.steps / sec,
+                         "theta_max": float(th.max()) if len(th) else None, "setup_s": setup_s})
+        S.close()
+    line = {"metric": "ablation: adaptive BDDC x B4 recycling at equal (mixed) precision", "workload": args.workload,
+            "n": wl["n"], "steps": args.steps, "warmup": args.warmup, "rtol": rtol, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,6 +526,8 @@ def main():
                     help="elements per axis of the oracle's sample (the workload's n: the workload itself, "
                          "factored once, with the GPU solutions of the same steps compared)")
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
+    ap.add_argument("--ablation", action="store_true",
+                    help="print the adaptive x recycling table at equal precision instead of the bench line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--ens-nmm", default="auto", choices=["auto", "simt", "tc", "bf16x3"],
@@ -526,6 +558,8 @@ def main():
     seed = rank_seed(wl, rank)
     if wl.get("nrhs"):
         return ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, seed, rtol)
+    if args.ablation:
+        return ablation(args, wl, torch, pkg, dev, mesh, seed, rtol)
     nsteps = args.warmup + args.steps
     t0 = time.perf_counter()
     F_host = torch.from_numpy(load_sequence(mesh, seed, nsteps))

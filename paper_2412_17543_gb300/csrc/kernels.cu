@@ -316,29 +316,37 @@ __device__ __forceinline__ df64 warp_sum<PolDF>(df64 v) {
   return v;
 }
 
-// diagonal block of height h stored as its packed upper triangle: lane l < h returns
-// sum_c T(l, c) x_c with T(l, c) = T(c, l) read from the triangle
-template <class P>
-__device__ __forceinline__ typename P::V packed_diag_part(const unsigned char* T, const typename P::V* tv, int l,
-                                                          int h) {
+// diagonal block of height h stored as its packed upper triangle (row r starts at
+// off(r) = r h - r (r - 1) / 2): lane l < h returns sum_c T(l, c) x_c. The lower part is
+// read by symmetry in a first sweep over r (lanes l > r read the contiguous entries
+// T(r, l), at off(r) + l - r), the upper part in a second sweep along the lane's own row.
+template <class P, int H>
+__device__ __forceinline__ typename P::V packed_diag_sweep(const unsigned char* T, const typename P::V* tv, int l,
+                                                           int h) {
   typename P::Acc a0, a1;
   P::init(a0);
   P::init(a1);
-  if (l < h) {
-    for (int t = 0; t < h; t += 2) {
-      int c0 = t + l;
-      c0 -= c0 >= h ? h : 0;
-      const int i0 = l <= c0 ? tri_index(h, l, c0) : tri_index(h, c0, l);
-      P::fma(a0, TileElem<P>::ld(T, i0), tv[c0]);
-      if (t + 1 < h) {
-        int c1 = t + 1 + l;
-        c1 -= c1 >= h ? h : 0;
-        const int i1 = l <= c1 ? tri_index(h, l, c1) : tri_index(h, c1, l);
-        P::fma(a1, TileElem<P>::ld(T, i1), tv[c1]);
-      }
-    }
+  const int hh = H ? H : h;
+  int idx = l;
+#pragma unroll
+  for (int r = 0; r < (H ? H - 1 : 31); ++r) {
+    if (!H && r >= hh - 1) break;
+    if (l > r && l < hh) P::fma(a0, TileElem<P>::ld(T, idx), tv[r]);
+    idx += hh - 1 - r;
+  }
+  const int base = l * hh - l * (l - 1) / 2;
+#pragma unroll
+  for (int t = 0; t < (H ? H : 32); ++t) {
+    if (!H && t >= hh) break;
+    if (l + t < hh) P::fma(a1, TileElem<P>::ld(T, base + t), tv[l + t]);
   }
   return P::add(P::get(a0), P::get(a1));
+}
+
+template <class P>
+__device__ __forceinline__ typename P::V packed_diag_part(const unsigned char* T, const typename P::V* tv, int l,
+                                                          int h) {
+  return h == 32 ? packed_diag_sweep<P, 32>(T, tv, l, 32) : packed_diag_sweep<P, 0>(T, tv, l, h);
 }
 
 // block of the ragged last w columns (32 rows of wp stored values): lane l returns the row

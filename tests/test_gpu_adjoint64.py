@@ -92,13 +92,18 @@ def test_adjoint_deflated_by_forward_basis_matches_oracle_and_fd(case):
     grad = grad.cpu().numpy()
     go = case["grad_o"]
     assert np.linalg.norm(grad - go) <= 1e-7 * np.linalg.norm(go)
-    # central finite differences on the oracle (directional and 16 single elements)
+    # central finite differences on the oracle (directional and 16 single elements). A single
+    # element's derivative is small next to the rounding of two independent factorizations
+    # (about kappa * eps * ||x|| in each solution), which leaves the finite difference itself
+    # noisy at up to ~1e-3 relative; the GPU gradient must agree with it as closely as the
+    # oracle's exact adjoint does, up to the GPU-vs-oracle tolerance
     d = np.random.default_rng(42).standard_normal(n ** 3)
     for kind, e, fd, oracle_val in case["rows"]:
         val = float(np.dot(grad, d)) if kind == "direction" else float(grad[e])
-        scale = max(abs(fd), 1e-12 * np.abs(go).max())
-        assert abs(val - fd) <= 1e-5 * scale, (kind, e, val, fd)
-        assert abs(oracle_val - fd) <= 1e-5 * scale, (kind, e, oracle_val, fd)
+        assert abs(oracle_val - fd) <= 1e-3 * abs(fd), (kind, e, oracle_val, fd)  # the FD noise level
+        slack = 1e-6 * abs(fd) + (1e-7 * np.linalg.norm(go) * np.linalg.norm(d) if kind == "direction"
+                                  else 1e-7 * np.linalg.norm(go))
+        assert abs(val - fd) <= abs(oracle_val - fd) + slack, (kind, e, val, oracle_val, fd)
 
 
 def test_autograd_wrapper_matches_and_refuses_another_field(case):
