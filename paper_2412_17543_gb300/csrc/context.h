@@ -49,6 +49,7 @@ struct dd_ctx {
   double* partials = nullptr;  // [NBLK*MAXDOT]
   double* wpart = nullptr;     // [NBLK*MAXK]
   double* mu = nullptr;        // [MAXK]
+  unsigned* wticket = nullptr;  // block ticket of the one-launch deflation dots (0 between launches)
   double* gram_part = nullptr; // [NBLK*4096]
   double* gram_out = nullptr;  // [4096]
   double* ybuf = nullptr;      // [128*128] combination coefficients

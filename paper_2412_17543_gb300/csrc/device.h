@@ -27,6 +27,9 @@ struct SymTiles {
   const void* pdata = nullptr;    // packed form
   int64_t pelems = 0;             // elements of the packed form
   int slots = 2;                  // bulk-copy ring depth per warp of k_symv (2, 3 or 4; tuned at setup)
+  int split = 1;                  // CTAs per matrix of k_symv (small batches; tuned at setup)
+  void* spart = nullptr;          // [count * split][padded n] partial vectors (split > 1)
+  unsigned* sticket = nullptr;    // [count] counters, 0 between launches
   const int64_t* toff = nullptr;  // [count] first tile of each matrix (tiled form, nullptr until built)
   const void* data = nullptr;     // tiled form
   int64_t ntiles = 0;
@@ -76,6 +79,10 @@ struct BatchedRows {
   const int* cols = nullptr;
   const int64_t* moff = nullptr;
   const void* data = nullptr;
+  int rows_per_block = 32;        // k_bgemv: rows of one matrix per block (8 warps)
+  int zsplit = 1;                 // k_bgemv_t: row parts per matrix (combined in the kernel); tuned at setup
+  void* zpart = nullptr;          // [count][column blocks][zsplit][128] partial sums (zsplit > 1)
+  unsigned* zticket = nullptr;    // [count][column blocks] counters, 0 between launches
 };
 
 // Level-1 geometry and Schur-complement operator (Sect. 3.1).

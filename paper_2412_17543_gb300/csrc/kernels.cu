@@ -378,6 +378,9 @@ template <int PREC, int SYMV_SLOTS>
 __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int64_t* __restrict__ voff,
                                                           const double* __restrict__ in,
                                                           double* __restrict__ out, int* err) {
+  // A.split CTAs per matrix (small batches): CTA q of matrix m takes the blocks of warps
+  // q * SYMV_WARPS + w, and the last of the matrix's CTAs to finish adds their partial
+  // vectors in CTA order
   using Ops = TileOps<PREC>;
   using P = typename Ops::P;
   using V = typename Ops::V;
@@ -385,7 +388,8 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
   constexpr int TB = Ops::BYTES;  // the largest block (32 x 32)
   extern __shared__ __align__(128) unsigned char smem_symv[];
   unsigned char* smem_raw = smem_symv;
-  const int m = blockIdx.x;
+  const int split = A.split;
+  const int m = blockIdx.x / split, q = blockIdx.x % split;
   const int n = A.n[m];
   const PackGeom g = pack_geom(n, EB);
   const int nb = g.nf + (g.w > 0);
@@ -405,13 +409,14 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
   __syncthreads();
 
   const int ntl = nb * (nb + 1) / 2;
-  const int mine = (warp < ntl) ? (ntl - warp + SYMV_WARPS - 1) / SYMV_WARPS : 0;
+  const int gw = q * SYMV_WARPS + warp, nw = split * SYMV_WARPS;  // this warp among the matrix's warps
+  const int mine = (gw < ntl) ? (ntl - gw + nw - 1) / nw : 0;
   const unsigned char* gm = reinterpret_cast<const unsigned char*>(A.pdata) + (size_t)A.poff[m] * EB;
   unsigned char* wslots = slots + (size_t)warp * SYMV_SLOTS * TB;
   uint64_t* wbars = bars + warp * SYMV_SLOTS;
   auto issue = [&](int k, int slot) {
     int bi, bj;
-    tile_coords(warp + k * SYMV_WARPS, nb, bi, bj);
+    tile_coords(gw + k * nw, nb, bi, bj);
     const uint32_t bytes = (uint32_t)pack_tile_elems(g, bi, bj) * EB;
     mbar_arrive_expect_tx(&wbars[slot], bytes);
     bulk_g2s(wslots + (size_t)slot * TB, gm + (size_t)pack_tile_off(g, bi, bj) * EB, bytes, &wbars[slot]);
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
       break;
     }
     int bi, bj;
-    tile_coords(warp + k * SYMV_WARPS, nb, bi, bj);
+    tile_coords(gw + k * nw, nb, bi, bj);
     const unsigned char* T = wslots + (size_t)slot * TB;
     if (bi == bj) {
       const int h = bi < g.nf ? 32 : g.w;
@@ -457,11 +462,34 @@ __global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int6
       mbar_wait_bounded(&wbars[kk % SYMV_SLOTS], (uint32_t)((kk / SYMV_SLOTS) & 1), nullptr);
   }
   __syncthreads();
+  if (split == 1) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      V s = part[i];
+      for (int w = 1; w < SYMV_WARPS; ++w) s = P::add(s, part[w * maxpad + i]);
+      out[vo + i] = P::to_d(s);
+    }
+    return;
+  }
+  V* sp = reinterpret_cast<V*>(A.spart) + (size_t)blockIdx.x * maxpad;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     V s = part[i];
     for (int w = 1; w < SYMV_WARPS; ++w) s = P::add(s, part[w * maxpad + i]);
+    sp[i] = s;
+  }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&A.sticket[m], 1u) == (unsigned)split - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const V* sm0 = reinterpret_cast<const V*>(A.spart) + (size_t)m * split * maxpad;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    V s = sm0[i];
+    for (int r = 1; r < split; ++r) s = P::add(s, sm0[(size_t)r * maxpad + i]);
     out[vo + i] = P::to_d(s);
   }
+  if (threadIdx.x == 0) A.sticket[m] = 0u;
 }
 
 template <int PREC, int SLOTS>
@@ -472,7 +500,7 @@ static void symv_launch(const SymTiles& A, const int64_t* voff, const double* in
   const size_t tb = tile_bytes(A.prec);
   const size_t smem = SYMV_WARPS * SLOTS * tb + SYMV_WARPS * SLOTS * 8 + (size_t)maxpad * vb * (1 + SYMV_WARPS);
   max_smem(k_symv<PREC, SLOTS>, smem);
-  k_symv<PREC, SLOTS><<<A.count, SYMV_WARPS * 32, smem, s>>>(A, voff, in, out, err);
+  k_symv<PREC, SLOTS><<<A.count * std::max(1, A.split), SYMV_WARPS * 32, smem, s>>>(A, voff, in, out, err);
 }
 
 template <int PREC>
@@ -648,25 +676,65 @@ __global__ void __launch_bounds__(128) k_fdm_apply(DevMesh m, const double* __re
 // are formed once. The arithmetic and its order are those of k_elem_interior,
 // k_fdm_apply and k_elem_interface.
 // ---------------------------------------------------------------------------
-// out[..j..] = sum_i A(i, j) in[..i..] (trans) or sum_i A(j, i) in[..i..] along axis ax, for
-// the 7 x 7 x 7 interior index box of an 8^3-element subdomain off the domain boundary
-template <class P, int AX>
-__device__ __forceinline__ void fdm_contract7(const typename P::V* A, bool trans, const typename P::V* in,
-                                              typename P::V* out) {
-  constexpr int stride = AX == 0 ? 1 : (AX == 1 ? 7 : 49);
-  for (int idx = threadIdx.x; idx < 343; idx += blockDim.x) {
-    const int j = (idx / stride) % 7;
+// The same contractions with an epilogue: EPI 0 stores out[idx], EPI 1 stores
+// out[idx] * dv[idx] (the diagonal D^{-1} of the fast diagonalization), EPI 2 stores
+// -out[idx] at the local node il[idx] of the subdomain vector xl (the interior values -s_I).
+// N7: the 7 x 7 x 7 interior index box (sizes known at compile time); else sizes n[].
+template <class P, bool N7, int EPI>
+__device__ __forceinline__ void fdm_contract_epi(const typename P::V* A, int ax, bool trans, const int* n,
+                                                 const typename P::V* in, typename P::V* out,
+                                                 const typename P::V* dv, const int16_t* il) {
+  const int n0 = N7 ? 7 : n[0], n1 = N7 ? 7 : n[1], n2 = N7 ? 7 : n[2];
+  const int N = n0 * n1 * n2;
+  const int na = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+  const int stride = ax == 0 ? 1 : (ax == 1 ? n0 : n0 * n1);
+  for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
+    const int j = (idx / stride) % na;
     const int base = idx - j * stride;
     typename P::Acc acc[2];
     P::init(acc[0]);
     P::init(acc[1]);
+    if (N7) {
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
-      P::fma(acc[i & 1], a, in[base + i * stride]);
+      for (int i = 0; i < 7; ++i) {
+        typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
+        P::fma(acc[i & 1], a, in[base + i * stride]);
+      }
+    } else {
+      for (int i = 0; i < na; ++i) {
+        typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
+        P::fma(acc[i & 1], a, in[base + i * stride]);
+      }
     }
-    out[idx] = P::add(P::get(acc[0]), P::get(acc[1]));
+    const typename P::V v = P::add(P::get(acc[0]), P::get(acc[1]));
+    if (EPI == 0) {
+      out[idx] = v;
+    } else if (EPI == 1) {
+      typename P::Acc d;
+      P::init(d);
+      P::fma(d, v, dv[idx]);
+      out[idx] = P::get(d);
+    } else {
+      out[il[idx]] = P::neg(v);
+    }
   }
+}
+
+template <class P, bool N7>
+__device__ __forceinline__ void fdm_solve_fused(const typename P::V* Vs, const int* n, typename P::V* f0,
+                                                typename P::V* f1, const typename P::V* dv, const int16_t* il,
+                                                typename P::V* xl) {
+  fdm_contract_epi<P, N7, 0>(Vs, 0, true, n, f0, f1, dv, il);
+  __syncthreads();
+  fdm_contract_epi<P, N7, 0>(Vs + 81, 1, true, n, f1, f0, dv, il);
+  __syncthreads();
+  fdm_contract_epi<P, N7, 1>(Vs + 162, 2, true, n, f0, f1, dv, il);
+  __syncthreads();
+  fdm_contract_epi<P, N7, 0>(Vs, 0, false, n, f1, f0, dv, il);
+  __syncthreads();
+  fdm_contract_epi<P, N7, 0>(Vs + 81, 1, false, n, f0, f1, dv, il);
+  __syncthreads();
+  fdm_contract_epi<P, N7, 2>(Vs + 162, 2, false, n, f1, xl, dv, il);
 }
 
 // element-pass item with slots (position in the type's boundary-layer list) * 8 + corner;
@@ -705,9 +773,11 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
   V* xl = reinterpret_cast<V*>(smem_raw);  // [NL] local nodal vector
   V* f0 = xl + m.NL;                        // [NL] interior vector buffers of the fast diagonalization
   V* f1 = f0 + m.NL;
-  V* Vs = f1 + m.NL;                        // [3][81] 1D eigenbases (stride 9)
+  V* dv = f1 + m.NL;                        // [NL] D^{-1} of the fast diagonalization
+  V* Vs = dv + m.NL;                        // [3][81] 1D eigenbases (stride 9)
   V* kd = Vs + 243;                         // [8][nbl] entry classes of the boundary-layer elements
   int16_t* bll = reinterpret_cast<int16_t*>(kd + 8 * m.max_nbl);  // [nbl] boundary-layer elements
+  int16_t* il = bll + m.max_nbl;                                   // [NL] local node of interior index
   __shared__ int n[3];
   const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
@@ -719,7 +789,11 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
   for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
     const int cd = code[l];
     xl[l] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[m.gmap[go + (-1 - cd)]]) : P::zero();
-    if (cd >= 0) f0[cd] = P::zero();
+    if (cd >= 0) {
+      f0[cd] = P::zero();
+      dv[cd] = ld_fdm<P>(m.fdm_Dinv, io + cd);
+      il[cd] = (int16_t)l;
+    }
   }
   {
     const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
@@ -742,49 +816,12 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
     f0[code[it[0]]] = apply_citem<P, S>(m, it, xl, kd, bll, nbl);
   }
   __syncthreads();
-  // s_I = K_II^{-1} t_I = V D^{-1} V^T t_I (V = Vz (x) Vy (x) Vx), result in f0
-  const bool cube7 = n[0] == 7 && n[1] == 7 && n[2] == 7;
-  const int N = n[0] * n[1] * n[2];
-  if (cube7) {
-    fdm_contract7<P, 0>(Vs, true, f0, f1);
-    __syncthreads();
-    fdm_contract7<P, 1>(Vs + 81, true, f1, f0);
-    __syncthreads();
-    fdm_contract7<P, 2>(Vs + 162, true, f0, f1);
-  } else {
-    fdm_contract<P>(Vs, 0, true, n, f0, f1);
-    __syncthreads();
-    fdm_contract<P>(Vs + 81, 1, true, n, f1, f0);
-    __syncthreads();
-    fdm_contract<P>(Vs + 162, 2, true, n, f0, f1);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    typename P::Acc acc;
-    P::init(acc);
-    P::fma(acc, f1[i], ld_fdm<P>(m.fdm_Dinv, io + i));
-    f1[i] = P::get(acc);
-  }
-  __syncthreads();
-  if (cube7) {
-    fdm_contract7<P, 0>(Vs, false, f1, f0);
-    __syncthreads();
-    fdm_contract7<P, 1>(Vs + 81, false, f0, f1);
-    __syncthreads();
-    fdm_contract7<P, 2>(Vs + 162, false, f1, f0);
-  } else {
-    fdm_contract<P>(Vs, 0, false, n, f1, f0);
-    __syncthreads();
-    fdm_contract<P>(Vs + 81, 1, false, n, f0, f1);
-    __syncthreads();
-    fdm_contract<P>(Vs + 162, 2, false, n, f1, f0);
-  }
-  __syncthreads();
-  // the interior entries of the local vector become -s_I
-  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
-    const int cd = code[l];
-    if (cd >= 0) xl[l] = P::neg(f0[cd]);
-  }
+  // s_I = K_II^{-1} t_I = V D^{-1} V^T t_I (V = Vz (x) Vy (x) Vx); the last contraction writes
+  // -s_I into the interior entries of the local vector
+  if (n[0] == 7 && n[1] == 7 && n[2] == 7)
+    fdm_solve_fused<P, true>(Vs, n, f0, f1, dv, il, xl);
+  else
+    fdm_solve_fused<P, false>(Vs, n, f0, f1, dv, il, xl);
   __syncthreads();
   // y_G = (K [-s_I; x_G])_G
   for (int i = to[2] + threadIdx.x; i < to[3]; i += blockDim.x) {
@@ -805,7 +842,7 @@ static void schur_fused_bs(const DevMesh& m, const double* xg, double* yloc, siz
 
 void launch_schur_fused(const DevMesh& m, const double* xg, double* yloc, cudaStream_t s) {
   const size_t vb = m.schur_prec == DD_PREC_DF64 ? sizeof(df64) : sizeof(double);
-  const size_t smem = vb * ((size_t)3 * m.NL + 243 + 8 * (size_t)m.max_nbl) + 2 * (size_t)m.max_nbl;
+  const size_t smem = vb * ((size_t)4 * m.NL + 243 + 8 * (size_t)m.max_nbl) + 2 * ((size_t)m.max_nbl + m.NL);
   if (m.schur_prec == DD_PREC_DF64) {
     switch (m.schur_threads) {
       case 352: schur_fused_bs<PolDF, 352>(m, xg, yloc, smem, s); break;
@@ -974,41 +1011,51 @@ void launch_restrict(int64_t nflat, const int* gmap, const double* D, const doub
 //   k_bgemv_t: y_m = alpha A_m^T x_m (+ add), thread per column; the rows are split into
 //              blockDim.y slices (slice s takes rows s, s + RS, ...) for tall matrices, and the
 //              slice sums are added in slice order
-constexpr int BGEMV_ROWS = 32;    // rows per block of k_bgemv (8 warps x 4 rows)
 constexpr int BGEMV_T_COLS = 128; // columns per block of k_bgemv_t
+constexpr int BG_CHUNK = 8;       // loads a thread issues before using any of them
 
+// k_bgemv: each warp takes B.rows_per_block / 8 rows of one matrix; per row the lanes load
+// BG_CHUNK entries (32 apart, coalesced) before the multiply-adds, so every lane keeps
+// BG_CHUNK loads in flight
 template <class T>
 __global__ void __launch_bounds__(256) k_bgemv(const int64_t* __restrict__ row0, const int* __restrict__ cols,
                                                const int64_t* __restrict__ moff, const T* __restrict__ M,
                                                const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
                                                const double* __restrict__ in, const int64_t* __restrict__ out_off,
                                                double* __restrict__ out, double alpha,
-                                               const double* __restrict__ add) {
+                                               const double* __restrict__ add, int rows_per_block) {
   extern __shared__ __align__(16) unsigned char bg_smem[];
   T* xs = reinterpret_cast<T*>(bg_smem);
   const int m = blockIdx.x;
   const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
-  const int r0 = blockIdx.y * BGEMV_ROWS;
+  const int r0 = blockIdx.y * rows_per_block;
   if (r0 >= R) return;
   const int64_t io = in_off[m];
   for (int j = threadIdx.x; j < C; j += blockDim.x) xs[j] = (T)in[in_map ? in_map[io + j] : io + j];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r1 = min(R, r0 + BGEMV_ROWS);
+  const int r1 = min(R, r0 + rows_per_block);
   const int64_t oo = out_off[m];
   for (int i = r0 + warp; i < r1; i += blockDim.x >> 5) {
     const T* a = M + moff[m] + (int64_t)i * C;
-    T acc0 = 0, acc1 = 0;
-    int j = lane;
-    for (; j + 32 < C; j += 64) {
-      acc0 = fma(a[j], xs[j], acc0);
-      acc1 = fma(a[j + 32], xs[j + 32], acc1);
-    }
-    if (j < C) acc0 = fma(a[j], xs[j], acc0);
-    T acc = acc0 + acc1;
+    T acc[4] = {0, 0, 0, 0};
+    for (int j0 = 0; j0 < C; j0 += 32 * BG_CHUNK) {
+      T v[BG_CHUNK];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[oo + i] = alpha * (double)acc + (add ? add[oo + i] : 0.0);
+      for (int u = 0; u < BG_CHUNK; ++u) {
+        const int j = j0 + u * 32 + lane;
+        v[u] = j < C ? a[j] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < BG_CHUNK; ++u) {
+        const int j = j0 + u * 32 + lane;
+        if (j < C) acc[u & 3] = fma(v[u], xs[j], acc[u & 3]);
+      }
+    }
+    T sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) out[oo + i] = alpha * (double)sum + (add ? add[oo + i] : 0.0);
   }
 }
 
@@ -1017,9 +1064,10 @@ static void bgemv_go(const BatchedRows& B, const int64_t* in_off, const int* in_
                      const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
   size_t smem = (size_t)std::max(B.max_cols, 1) * sizeof(T);
   if (smem > 48 * 1024) max_smem(k_bgemv<T>, smem);
-  dim3 grid(B.count, (B.max_rows + BGEMV_ROWS - 1) / BGEMV_ROWS);
+  const int rpb = std::max(8, B.rows_per_block);
+  dim3 grid(B.count, (B.max_rows + rpb - 1) / rpb);
   k_bgemv<T><<<grid, 256, smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data), in_off, in_map, in,
-                                      out_off, out, alpha, add);
+                                      out_off, out, alpha, add, rpb);
 }
 
 void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
@@ -1032,59 +1080,94 @@ void launch_bgemv(const BatchedRows& B, const int64_t* in_off, const int* in_map
   DD_CHECK_LAUNCH();
 }
 
+// k_bgemv_t: y_m = alpha A_m^T x_m (+ add). Block (m, column block y, row part z): thread
+// column j, the block's rows split into blockDim.y slices; each thread loads BG_CHUNK rows of
+// its column before the multiply-adds. With gridDim.z > 1 (tall matrices) every row part
+// stores its column sums in zpart, and the last of the gridDim.z blocks of (m, y) to finish
+// (a per-(m, y) ticket, reset by that block) adds them in row-part order.
 template <class T>
 __global__ void __launch_bounds__(1024) k_bgemv_t(const int64_t* __restrict__ row0, const int* __restrict__ cols,
                                                   const int64_t* __restrict__ moff, const T* __restrict__ M,
                                                   const int64_t* __restrict__ in_off, const int* __restrict__ in_map,
                                                   const double* __restrict__ in, const int64_t* __restrict__ out_off,
                                                   double* __restrict__ out, double alpha,
-                                                  const double* __restrict__ add, int xs_len) {
+                                                  const double* __restrict__ add, int xs_len, T* __restrict__ zpart,
+                                                  unsigned* __restrict__ zticket) {
   extern __shared__ __align__(16) unsigned char bg_smem[];
   T* xs = reinterpret_cast<T*>(bg_smem);  // [xs_len]
   T* part = xs + xs_len;                   // [RS][BGEMV_T_COLS]
+  __shared__ bool last;
   const int m = blockIdx.x;
   const int R = (int)(row0[m + 1] - row0[m]), C = cols[m];
   if (blockIdx.y * BGEMV_T_COLS >= C) return;  // uniform over the block
   const int RS = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * BGEMV_T_COLS + tx;
   const int j = blockIdx.y * BGEMV_T_COLS + tx;
+  const int ZS = gridDim.z;
+  const int rz = (R + ZS - 1) / ZS;
+  const int ra = blockIdx.z * rz, rb = min(R, ra + rz);
   const int64_t io = in_off[m];
-  for (int i = tid; i < R; i += BGEMV_T_COLS * RS) xs[i] = (T)in[in_map ? in_map[io + i] : io + i];
+  for (int i = ra + tid; i < rb; i += BGEMV_T_COLS * RS) xs[i - ra] = (T)in[in_map ? in_map[io + i] : io + i];
   __syncthreads();
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  T acc[4] = {0, 0, 0, 0};
   if (j < C) {
     const T* A = M + moff[m] + j;
-    int i = ty;
-    for (; i + 3 * RS < R; i += 4 * RS) {
-      a0 = fma(A[(int64_t)i * C], xs[i], a0);
-      a1 = fma(A[(int64_t)(i + RS) * C], xs[i + RS], a1);
-      a2 = fma(A[(int64_t)(i + 2 * RS) * C], xs[i + 2 * RS], a2);
-      a3 = fma(A[(int64_t)(i + 3 * RS) * C], xs[i + 3 * RS], a3);
+    for (int i0 = ra + ty; i0 < rb; i0 += RS * BG_CHUNK) {
+      T v[BG_CHUNK];
+#pragma unroll
+      for (int u = 0; u < BG_CHUNK; ++u) {
+        const int i = i0 + u * RS;
+        v[u] = i < rb ? A[(int64_t)i * C] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < BG_CHUNK; ++u) {
+        const int i = i0 + u * RS;
+        if (i < rb) acc[u & 3] = fma(v[u], xs[i - ra], acc[u & 3]);
+      }
     }
-    for (; i < R; i += RS) a0 = fma(A[(int64_t)i * C], xs[i], a0);
   }
-  part[ty * BGEMV_T_COLS + tx] = (a0 + a1) + (a2 + a3);
+  part[ty * BGEMV_T_COLS + tx] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   __syncthreads();
-  if (ty == 0 && j < C) {
-    T v = part[tx];
+  T v = 0;
+  if (ty == 0) {
+    v = part[tx];
     for (int q = 1; q < RS; ++q) v += part[q * BGEMV_T_COLS + tx];
-    const int64_t oo = out_off[m];
-    out[oo + j] = alpha * (double)v + (add ? add[oo + j] : 0.0);
   }
+  const int64_t oo = out_off[m];
+  if (ZS == 1) {
+    if (ty == 0 && j < C) out[oo + j] = alpha * (double)v + (add ? add[oo + j] : 0.0);
+    return;
+  }
+  const int64_t slot = (int64_t)m * gridDim.y + blockIdx.y;
+  if (ty == 0) zpart[(slot * ZS + blockIdx.z) * BGEMV_T_COLS + tx] = v;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&zticket[slot], 1u) == (unsigned)ZS - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (ty == 0 && j < C) {
+    T sum = 0;
+    for (int z = 0; z < ZS; ++z) sum += __ldcg(&zpart[(slot * ZS + z) * BGEMV_T_COLS + tx]);
+    out[oo + j] = alpha * (double)sum + (add ? add[oo + j] : 0.0);
+  }
+  if (tid == 0) zticket[slot] = 0u;
 }
 
 template <class T>
 static void bgemv_t_go(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
                        const int64_t* out_off, double* out, double alpha, const double* add, cudaStream_t s) {
-  // row slices: one per 32 rows of the tallest matrix, at most 8 (1024 threads)
-  const int rs = std::min(8, std::max(1, B.max_rows / 32));
-  const int xs_len = (std::max(B.max_rows, 1) + 3) / 4 * 4;
+  const int zs = B.zsplit > 1 && B.zpart ? B.zsplit : 1;
+  const int rmax = (B.max_rows + zs - 1) / zs;
+  // row slices: one per 32 rows of the tallest row part, at most 8 (1024 threads)
+  const int rs = std::min(8, std::max(1, rmax / 32));
+  const int xs_len = (std::max(rmax, 1) + 3) / 4 * 4;
   size_t smem = ((size_t)xs_len + (size_t)rs * BGEMV_T_COLS) * sizeof(T);
-  if (smem > 48 * 1024)
-    max_smem(k_bgemv_t<T>, smem);
-  dim3 grid(B.count, (B.max_cols + BGEMV_T_COLS - 1) / BGEMV_T_COLS);
+  if (smem > 48 * 1024) max_smem(k_bgemv_t<T>, smem);
+  dim3 grid(B.count, (B.max_cols + BGEMV_T_COLS - 1) / BGEMV_T_COLS, zs);
   k_bgemv_t<T><<<grid, dim3(BGEMV_T_COLS, rs), smem, s>>>(B.row0, B.cols, B.moff, static_cast<const T*>(B.data),
-                                                           in_off, in_map, in, out_off, out, alpha, add, xs_len);
+                                                           in_off, in_map, in, out_off, out, alpha, add, xs_len,
+                                                           static_cast<T*>(B.zpart), B.zticket);
 }
 
 void launch_bgemv_t(const BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,

@@ -475,6 +475,84 @@ void tune_shapes(dd_ctx* c, cudaStream_t s) {
     }
     c->mesh.schur_threads = pick;
   }
+  // the batched products of the coarse levels (level-1 Phi, level-2 K_II^{-1}, E, N, Phi):
+  // rows per block of the row-wise GEMV, row parts of the column-wise GEMV, CTAs per matrix
+  // of the symmetric products
+  auto zero = [&](void* p, size_t bytes) { if (p && bytes) DD_CUDA(cudaMemsetAsync(p, 0, bytes, s)); };
+  auto tune_rows = [&](BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                       const int64_t* out_off, double* out, double alpha, const double* add) {
+    if (B.count == 0) return;
+    float best = 0.f;
+    int pick = 32;
+    for (int rpb : {32, 16, 8}) {
+      B.rows_per_block = rpb;
+      const float t = time_launches([&] { launch_bgemv(B, in_off, in_map, in, out_off, out, alpha, add, s); }, s);
+      if (rpb == 32 || t < best) {
+        best = t;
+        pick = rpb;
+      }
+    }
+    B.rows_per_block = pick;
+  };
+  auto tune_cols = [&](BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
+                       const int64_t* out_off, double* out, double alpha, const double* add) {
+    if (B.count == 0) return;
+    const int ycols = (B.max_cols + 127) / 128;
+    const size_t eb = B.prec == DD_PREC_FP32 ? 4 : 8;
+    if (!B.zpart) {
+      B.zpart = c->arena.alloc<unsigned char>((size_t)B.count * ycols * 8 * 128 * eb);
+      B.zticket = c->arena.alloc<unsigned>((size_t)B.count * ycols);
+      zero(B.zticket, (size_t)B.count * ycols * sizeof(unsigned));
+    }
+    float best = 0.f;
+    int pick = 1;
+    for (int zs : {1, 2, 4, 8}) {
+      B.zsplit = zs;
+      const float t = time_launches([&] { launch_bgemv_t(B, in_off, in_map, in, out_off, out, alpha, add, s); }, s);
+      if (zs == 1 || t < best) {
+        best = t;
+        pick = zs;
+      }
+    }
+    B.zsplit = pick;
+  };
+  auto tune_split = [&](SymTiles& A, const int64_t* voff, const double* in, double* out) {
+    if (A.count == 0 || A.count >= 152) return;
+    const int maxpad = (A.max_n + 31) / 32 * 32;
+    if (!A.spart) {
+      A.spart = c->arena.alloc<unsigned char>((size_t)A.count * 8 * maxpad * 8);
+      A.sticket = c->arena.alloc<unsigned>((size_t)A.count);
+      zero(A.sticket, (size_t)A.count * sizeof(unsigned));
+    }
+    float best = 0.f;
+    int pick = 1;
+    for (int sp : {1, 2, 4, 8}) {
+      A.split = sp;
+      const float t = time_launches([&] { launch_symv(A, voff, in, out, w.err, s); }, s);
+      if (sp == 1 || t < best) {
+        best = t;
+        pick = sp;
+      }
+    }
+    A.split = pick;
+  };
+  zero(w.uC, c->b1.n_coarse * sizeof(double));
+  tune_rows(c->b1.PhiT, c->b1.goff, nullptr, w.rloc, c->b1.coff, w.gloc, 1.0, nullptr);
+  tune_cols(c->b1.PhiT, c->b1.coff, c->b1.cmap, w.uC, c->b1.goff, w.vloc, 1.0, nullptr);
+  if (c->levels == 3) {
+    DevLevel2& L = c->l2;
+    zero(w.gI2, L.n_int * sizeof(double));
+    zero(w.z2, L.b.n_gamma * sizeof(double));
+    zero(w.u0I2, L.n_int * sizeof(double));
+    zero(w.rloc2, L.b.n_flat * sizeof(double));
+    zero(w.u3, L.n3 * sizeof(double));
+    tune_cols(L.E, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr);
+    tune_rows(L.E, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2);
+    tune_rows(L.b.PhiT, L.b.goff, nullptr, w.rloc2, L.b.coff, w.gloc2, 1.0, nullptr);
+    tune_cols(L.b.PhiT, L.b.coff, L.b.cmap, w.u3, L.b.goff, w.vloc2, 1.0, nullptr);
+    tune_split(L.KIIinv, L.ioff, w.gI2, w.u0I2);
+    tune_split(L.b.N, L.b.goff, w.rloc2, w.uloc2);
+  }
   c->info.symv_slots = c->b1.N.slots;
   c->info.schur_threads = schur_fused_available(c->mesh) ? c->mesh.schur_threads : 0;
   check_err(c, s);
@@ -712,6 +790,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->partials = A.alloc<double>(NBLK * MAXDOT);
     c->wpart = A.alloc<double>((size_t)std::max<int64_t>(NBLK, defl_df_blocks(c->n_gamma)) * MAXK);
     c->mu = A.alloc<double>(MAXK);
+    c->wticket = A.alloc<unsigned>(1);
+    DD_CUDA(cudaMemsetAsync(c->wticket, 0, sizeof(unsigned), s));
     c->gram_part = A.alloc<double>((size_t)NBLK * 4096);
     c->gram_out = A.alloc<double>(4096);
     c->ybuf = A.alloc<double>(128 * 128);
@@ -1210,7 +1290,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
     vec_sub(n, c->bvec, c->q, c->r, s);
-    defl_mu_df(n, k, Wd, n, c->r, st->Ginv, c->wpart, c->mu, s);
+    defl_mu_df(n, k, Wd, n, c->r, st->Ginv, c->wpart, c->mu, c->wticket, s);
     defl_update_df(n, k, Wd, n, c->mu, nullptr, c->xg, c->sc, -1, 1.0, s);
   }
   schur_apply(c, c->xg, c->q, s);
@@ -1233,7 +1313,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     vec_finalize(c->partials, c->sc, FIN_RZL, flex, bs, &c->ctl->its);
     {
       ProfScope pd(c, k ? DD_PROF_DEFL : DD_PROF_COUNT, bs);
-      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, bs);
+      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, c->wticket, bs);
       defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
     }
     schur_apply(c, c->p, c->q, bs);
@@ -1247,7 +1327,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);
     if (reo) {
       // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
-      defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, bs);
+      defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, c->wticket, bs);
       defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, bs);
       vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
       vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);

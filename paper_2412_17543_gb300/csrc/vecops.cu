@@ -164,37 +164,6 @@ void vec_sub_mean(int64_t n, const double* in, double* out, double* partials, cu
   DD_CHECK_LAUNCH();
 }
 
-// ---------------------------------------------------------------------------
-// deflation
-// ---------------------------------------------------------------------------
-// mu = Ginv * (sum of partials)   (k x k, one block of 1024 threads): warp w sums the
-// block partials w, w + 32, ... with the lanes along the columns (rows of wpart read
-// whole), the 32 warp sums are added in warp order, then a warp per output row forms
-// Ginv d (fixed shuffle tree): a fixed reduction order throughout
-__global__ void __launch_bounds__(1024) k_wfinal(int nblk, int k, const double* __restrict__ wpart,
-                                                const double* __restrict__ Ginv, double* mu) {
-  __shared__ double part[32][MAXK];
-  __shared__ double d[MAXK];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = lane; c < k; c += 32) {
-    double sum = 0.0;
-    for (int b = warp; b < nblk; b += nw) sum += wpart[(int64_t)b * MAXK + c];
-    part[warp][c] = sum;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double sum = 0.0;
-    for (int w = 0; w < nw; ++w) sum += part[w][c];
-    d[c] = sum;
-  }
-  __syncthreads();
-  for (int a = warp; a < k; a += nw) {
-    double sum = 0.0;
-    for (int c = lane; c < k; c += 32) sum = fma(Ginv[a * k + c], d[c], sum);
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) mu[a] = sum;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // deflation with the basis stored as df64 (float pairs): the k-column products run on
@@ -215,80 +184,73 @@ void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s) {
 
 constexpr int PT = 4;  // rows per thread of the row-blocked deflation kernels
 
-// wpart[b][c] = sum over the rows of block b of V_c[i] v[i] with the basis as df64: a block
-// takes RB * PT consecutive rows, each thread holds its PT entries of v (converted once) and
-// walks the columns (each a contiguous piece per block, two columns' loads in flight);
-// warp sums by shuffles in df64, then a fixed-order sum over the warps
-__global__ void __launch_bounds__(RB) k_wdots4(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
-                                               const double* __restrict__ v, double* wpart) {
-  __shared__ df64 sh[RB / 32][MAXK];
+// mu = Ginv (V^T v) with the basis V as df64 (k columns of stride ld), in one launch. Block b
+// owns rows [b * PT * RB, (b + 1) * PT * RB): v's entries there are staged in shared memory as
+// df64 once, warp w takes the columns c = w, w + RB/32, ... and walks the block's rows (each
+// lane 32 of them, coalesced), so each column needs a single warp reduction; the block
+// writes wpart[b][c]. The last block to finish (a ticket counter, reset by that block)
+// sums wpart over the blocks in block order and applies Ginv: the same fixed reduction
+// order whichever block finishes last.
+__global__ void __launch_bounds__(RB) k_wdots5(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
+                                               const double* __restrict__ v, double* wpart,
+                                               unsigned* __restrict__ ticket, const double* __restrict__ Ginv,
+                                               double* __restrict__ mu) {
+  constexpr int ROWS = PT * RB;
+  __shared__ df64 zs[ROWS];
+  __shared__ double d[MAXK];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t i0 = (int64_t)blockIdx.x * PT * RB + threadIdx.x;
-  df64 z[PT];
-#pragma unroll
-  for (int r = 0; r < PT; ++r) {
-    const int64_t i = i0 + (int64_t)r * RB;
-    z[r] = i < n ? dbl_to_df(v[i]) : df64{0.f, 0.f};
-  }
-  auto warp_sum = [&](df64 x) {
+  const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+  for (int t = threadIdx.x; t < ROWS; t += RB) zs[t] = r0 + t < n ? dbl_to_df(v[r0 + t]) : df64{0.f, 0.f};
+  __syncthreads();
+  for (int c = warp; c < k; c += RB / 32) {
+    const df64* col = V + (int64_t)c * ld + r0;
+    df64_acc a0, a1;
+#pragma unroll 8
+    for (int j = 0; j < ROWS / 32; j += 2) {
+      const int t0 = j * 32 + lane, t1 = t0 + 32;
+      const df64 e0 = r0 + t0 < n ? col[t0] : df64{0.f, 0.f};
+      const df64 e1 = r0 + t1 < n ? col[t1] : df64{0.f, 0.f};
+      a0.fma(e0, zs[t0]);
+      a1.fma(e1, zs[t1]);
+    }
+    df64 x = df64_add(a0.get(), a1.get());
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       const df64 y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
       x = df64_add(x, y);
     }
-    return x;
-  };
-  int c = 0;
-  for (; c + 1 < k; c += 2) {
-    const df64* c0 = V + (int64_t)c * ld;
-    const df64* c1 = c0 + ld;
-    df64 v0[PT], v1[PT];
-#pragma unroll
-    for (int r = 0; r < PT; ++r) {
-      const int64_t i = i0 + (int64_t)r * RB;
-      v0[r] = i < n ? c0[i] : df64{0.f, 0.f};
-      v1[r] = i < n ? c1[i] : df64{0.f, 0.f};
-    }
-    df64_acc a0, a1;
-#pragma unroll
-    for (int r = 0; r < PT; ++r) {
-      a0.fma(v0[r], z[r]);
-      a1.fma(v1[r], z[r]);
-    }
-    const df64 s0 = warp_sum(a0.get()), s1 = warp_sum(a1.get());
-    if (lane == 0) {
-      sh[warp][c] = s0;
-      sh[warp][c + 1] = s1;
-    }
+    if (lane == 0) wpart[(int64_t)blockIdx.x * MAXK + c] = df64_to_double_bits(x);
   }
-  if (c < k) {
-    const df64* c0 = V + (int64_t)c * ld;
-    df64_acc a0;
-#pragma unroll
-    for (int r = 0; r < PT; ++r) {
-      const int64_t i = i0 + (int64_t)r * RB;
-      if (i < n) a0.fma(c0[i], z[r]);
-    }
-    const df64 s0 = warp_sum(a0.get());
-    if (lane == 0) sh[warp][c] = s0;
+  // the last block to arrive reduces over the blocks and applies Ginv
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < k; c += RB) {
+    double sum = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(&wpart[(int64_t)b * MAXK + c]);
+    d[c] = sum;
   }
   __syncthreads();
-  for (int cc = threadIdx.x; cc < k; cc += blockDim.x) {
-    df64_acc sum;
-    for (int w = 0; w < RB / 32; ++w) sum.add(sh[w][cc]);
-    wpart[(int64_t)blockIdx.x * MAXK + cc] = df64_to_double_bits(sum.get());
+  for (int a = warp; a < k; a += RB / 32) {
+    double sum = 0.0;
+    for (int c = lane; c < k; c += 32) sum = fma(Ginv[a * k + c], d[c], sum);
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) mu[a] = sum;
   }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 int defl_df_blocks(int64_t n) { return (int)((n + (int64_t)PT * RB - 1) / ((int64_t)PT * RB)); }
 
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
-                double* mu, cudaStream_t s) {
+                double* mu, unsigned* ticket, cudaStream_t s) {
   if (k == 0) return;
   const int nb = defl_df_blocks(n);
-  k_wdots4<<<nb, RB, 0, s>>>(n, k, V, ld, v, wpart);
-  DD_CHECK_LAUNCH();
-  k_wfinal<<<1, 1024, 0, s>>>(nb, k, wpart, Ginv, mu);
+  k_wdots5<<<nb, RB, 0, s>>>(n, k, V, ld, v, wpart, ticket, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 

@@ -31,8 +31,9 @@ void vec_sub_mean(int64_t n, const double* in, double* out, double* partials, cu
 void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s);
 // mu with the basis as df64 (V: k columns, stride ld); wpart: [defl_df_blocks(n)][MAXK]
 int defl_df_blocks(int64_t n);
+// ticket: a device counter that is 0 between launches (the kernel resets it)
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
-                double* mu, cudaStream_t s);
+                double* mu, unsigned* ticket, cudaStream_t s);
 void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
                     const double* sc, int beta_idx, double sign_w, cudaStream_t s);
 void gram(int64_t n, int na, const double* const* X, int nb, const double* const* Y, double* part, double* C,
