@@ -13,6 +13,8 @@ Contents (each function cites the part of the paper it restates):
   pcg       deflated PCG (Algorithm 1), recycling B1-B4, harmonic Ritz (eq. 15),
             freezing criterion (eq. 16), stopping criteria (Sect. 5)
   adjoint   adjoint solve and coefficient gradient of a quadratic loss
+  lobpcg    block LOBPCG for the largest eigenpairs of a symmetric pencil (the paper's face
+            eigensolver, Sect. 3.3), used by dd.adaptive_face_constraints(method="lobpcg")
 
 Parity status: every function is pinned by a `-m "not gpu"` test except the
 adaptive face constraints (`dd.adaptive_face_constraints`), which are

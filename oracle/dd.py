@@ -337,7 +337,8 @@ def face_schur(subs: Substructures, i: int, face_dofs: np.ndarray) -> np.ndarray
 
 
 def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: float, max_per_face: int = 10,
-                              drop_tol: float = 1e-10, kinds=(CORNER, EDGE, FACE)):
+                              drop_tol: float = 1e-10, kinds=(CORNER, EDGE, FACE), method: str = "dense",
+                              lobpcg_iters: int = 15):
     """Extra face constraints from eq. 10, one problem per face shared by two subdomains s, t.
 
     Reading used here: the pair problem lives on the common interface of s and t
@@ -378,11 +379,30 @@ def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: floa
         Lhs = Pi @ IE.T @ A @ IE @ Pi
         Rhs = Pi @ A @ Pi
         Lhs, Rhs = 0.5 * (Lhs + Lhs.T), 0.5 * (Rhs + Rhs.T)
-        # restrict to the range of Rhs (drops ker Pi and the common null space)
-        lam_r, U = np.linalg.eigh(Rhs)
-        keep = lam_r > 1e-12 * lam_r.max()
-        T = U[:, keep] / np.sqrt(lam_r[keep])
-        lam, V = np.linalg.eigh(T.T @ Lhs @ T)
+        if method == "lobpcg":
+            # the paper's solver: block LOBPCG for the largest eigenpairs, max_per_face vectors,
+            # lobpcg_iters steps, on the subspace where Rhs is definite: the range of Pi, less
+            # the common constant (1, 1) when both subdomains float (A_s 1 = A_t 1 = 0), on
+            # which both sides of eq. 10 vanish
+            from . import lobpcg
+            ones = np.ones(m)
+            floating = (np.linalg.norm(As @ ones) <= 1e-10 * np.linalg.norm(As) * np.sqrt(m) and
+                        np.linalg.norm(At @ ones) <= 1e-10 * np.linalg.norm(At) * np.sqrt(m))
+            Nc = np.ones(2 * m) / np.sqrt(2 * m) if floating else None
+
+            def project(V):
+                V = V - Qo @ (Qo.T @ V)
+                return V - np.outer(Nc, Nc @ V) if Nc is not None else V
+
+            lam_l, Xl = lobpcg.lobpcg_largest(Lhs, Rhs, max_per_face, iters=lobpcg_iters, project=project)
+            order = np.argsort(lam_l, kind="stable")
+            lam, V, T = lam_l[order], Xl[:, order], np.eye(2 * m)
+        else:
+            # restrict to the range of Rhs (drops ker Pi and the common null space)
+            lam_r, U = np.linalg.eigh(Rhs)
+            keep = lam_r > 1e-12 * lam_r.max()
+            T = U[:, keep] / np.sqrt(lam_r[keep])
+            lam, V = np.linalg.eigh(T.T @ Lhs @ T)
         sel = np.nonzero(lam > tau)[0][::-1][:max_per_face]
         fpos = np.searchsorted(dofs, gd)
         rows = []
