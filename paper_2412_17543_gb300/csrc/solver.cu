@@ -439,6 +439,8 @@ float time_launches(F&& f, cudaStream_t s) {
 // Launch shapes of the two per-iteration kernels that stream the most, timed on this
 // context's own operators: the bulk-copy ring depth of the batched symmetric products
 // (level-1 N_i, and dense K_II^{-1}) and the block size of the fused Schur kernel.
+constexpr int SYMV_WARPS_HOST = 4;  // warps per CTA of k_symv
+
 void tune_shapes(dd_ctx* c, cudaStream_t s) {
   Work& w = c->w;
   DD_CUDA(cudaMemsetAsync(w.rloc, 0, c->b1.n_flat * sizeof(double), s));
@@ -494,64 +496,47 @@ void tune_shapes(dd_ctx* c, cudaStream_t s) {
     }
     B.rows_per_block = pick;
   };
-  auto tune_cols = [&](BatchedRows& B, const int64_t* in_off, const int* in_map, const double* in,
-                       const int64_t* out_off, double* out, double alpha, const double* add) {
+  // Row parts of the column-wise GEMV and CTAs per matrix of the symmetric products change
+  // the order of the sums, so they follow from the sizes alone (never from timings): runs
+  // and contexts stay bitwise reproducible. Target: about two blocks per SM.
+  auto split_cols = [&](BatchedRows& B) {
     if (B.count == 0) return;
     const int ycols = (B.max_cols + 127) / 128;
-    const size_t eb = B.prec == DD_PREC_FP32 ? 4 : 8;
-    if (!B.zpart) {
+    const int want = (2 * 152 + B.count * ycols - 1) / (B.count * ycols);
+    B.zsplit = std::max(1, std::min({8, want, B.max_rows / 64}));
+    if (B.zsplit > 1 && !B.zpart) {
+      const size_t eb = B.prec == DD_PREC_FP32 ? 4 : 8;
       B.zpart = c->arena.alloc<unsigned char>((size_t)B.count * ycols * 8 * 128 * eb);
       B.zticket = c->arena.alloc<unsigned>((size_t)B.count * ycols);
       zero(B.zticket, (size_t)B.count * ycols * sizeof(unsigned));
     }
-    float best = 0.f;
-    int pick = 1;
-    for (int zs : {1, 2, 4, 8}) {
-      B.zsplit = zs;
-      const float t = time_launches([&] { launch_bgemv_t(B, in_off, in_map, in, out_off, out, alpha, add, s); }, s);
-      if (zs == 1 || t < best) {
-        best = t;
-        pick = zs;
-      }
-    }
-    B.zsplit = pick;
   };
-  auto tune_split = [&](SymTiles& A, const int64_t* voff, const double* in, double* out) {
+  auto split_sym = [&](SymTiles& A) {
     if (A.count == 0 || A.count >= 152) return;
-    const int maxpad = (A.max_n + 31) / 32 * 32;
-    if (!A.spart) {
+    const int nb = (A.max_n + 31) / 32;
+    const int want = (2 * 152 + A.count - 1) / A.count;
+    A.split = std::max(1, std::min({8, want, nb * (nb + 1) / 2 / SYMV_WARPS_HOST}));
+    if (A.split > 1 && !A.spart) {
+      const int maxpad = nb * 32;
       A.spart = c->arena.alloc<unsigned char>((size_t)A.count * 8 * maxpad * 8);
       A.sticket = c->arena.alloc<unsigned>((size_t)A.count);
       zero(A.sticket, (size_t)A.count * sizeof(unsigned));
     }
-    float best = 0.f;
-    int pick = 1;
-    for (int sp : {1, 2, 4, 8}) {
-      A.split = sp;
-      const float t = time_launches([&] { launch_symv(A, voff, in, out, w.err, s); }, s);
-      if (sp == 1 || t < best) {
-        best = t;
-        pick = sp;
-      }
-    }
-    A.split = pick;
   };
   zero(w.uC, c->b1.n_coarse * sizeof(double));
   tune_rows(c->b1.PhiT, c->b1.goff, nullptr, w.rloc, c->b1.coff, w.gloc, 1.0, nullptr);
-  tune_cols(c->b1.PhiT, c->b1.coff, c->b1.cmap, w.uC, c->b1.goff, w.vloc, 1.0, nullptr);
+  split_cols(c->b1.PhiT);
   if (c->levels == 3) {
     DevLevel2& L = c->l2;
-    zero(w.gI2, L.n_int * sizeof(double));
     zero(w.z2, L.b.n_gamma * sizeof(double));
     zero(w.u0I2, L.n_int * sizeof(double));
     zero(w.rloc2, L.b.n_flat * sizeof(double));
-    zero(w.u3, L.n3 * sizeof(double));
-    tune_cols(L.E, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr);
+    split_cols(L.E);
     tune_rows(L.E, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2);
     tune_rows(L.b.PhiT, L.b.goff, nullptr, w.rloc2, L.b.coff, w.gloc2, 1.0, nullptr);
-    tune_cols(L.b.PhiT, L.b.coff, L.b.cmap, w.u3, L.b.goff, w.vloc2, 1.0, nullptr);
-    tune_split(L.KIIinv, L.ioff, w.gI2, w.u0I2);
-    tune_split(L.b.N, L.b.goff, w.rloc2, w.uloc2);
+    split_cols(L.b.PhiT);
+    split_sym(L.KIIinv);
+    split_sym(L.b.N);
   }
   c->info.symv_slots = c->b1.N.slots;
   c->info.schur_threads = schur_fused_available(c->mesh) ? c->mesh.schur_threads : 0;

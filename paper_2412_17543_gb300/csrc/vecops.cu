@@ -229,9 +229,24 @@ __global__ void __launch_bounds__(RB) k_wdots5(int64_t n, int k, const df64* __r
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // warp w sums the blocks b = w, w + RB/32, ... (eight chains per lane, combined in order),
+  // lanes over the columns; then the warps' sums are added in warp order
+  __shared__ double wsum[RB / 32][MAXK];
+  const int nb = (int)gridDim.x;
+  for (int c = lane; c < k; c += 32) {
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b = warp;
+    for (; b + 7 * (RB / 32) < nb; b += 8 * (RB / 32)) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += __ldcg(&wpart[(int64_t)(b + u * (RB / 32)) * MAXK + c]);
+    }
+    for (int u = 0; b < nb; b += RB / 32, ++u) a[u & 7] += __ldcg(&wpart[(int64_t)b * MAXK + c]);
+    wsum[warp][c] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  }
+  __syncthreads();
   for (int c = threadIdx.x; c < k; c += RB) {
     double sum = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(&wpart[(int64_t)b * MAXK + c]);
+    for (int w = 0; w < RB / 32; ++w) sum += wsum[w][c];
     d[c] = sum;
   }
   __syncthreads();
