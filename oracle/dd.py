@@ -394,7 +394,14 @@ def adaptive_face_constraints(subs: Substructures, bddc_weights: list, tau: floa
                 V = V - Qo @ (Qo.T @ V)
                 return V - np.outer(Nc, Nc @ V) if Nc is not None else V
 
-            lam_l, Xl = lobpcg.lobpcg_largest(Lhs, Rhs, max_per_face, iters=lobpcg_iters, project=project)
+            # start block: unit vectors at the largest ratios of the diagonals of
+            # (I-E)^T A (I-E) and A (the pencil before Pi; they need only diagonals of A)
+            da = np.concatenate([np.diag(As), np.diag(At)])
+            a1 = np.concatenate([(1 - ws) ** 2 * np.diag(As) + ws ** 2 * np.diag(At),
+                                 wt ** 2 * np.diag(As) + (1 - wt) ** 2 * np.diag(At)])
+            X0 = lobpcg.start_block(np.diag(a1), np.diag(da), min(max_per_face, 2 * m))
+            lam_l, Xl = lobpcg.lobpcg_largest(Lhs, Rhs, max_per_face, iters=lobpcg_iters, X0=X0,
+                                              project=project)
             order = np.argsort(lam_l, kind="stable")
             lam, V, T = lam_l[order], Xl[:, order], np.eye(2 * m)
         else:

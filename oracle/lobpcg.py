@@ -11,8 +11,11 @@ maximizing the Rayleigh quotient, without a preconditioner (T = I), in this form
     W- and P-components (the "conjugate" directions);
   * each step runs Rayleigh-Ritz on S = [X, W, P] (first step [X, W]): the columns are
     scaled to unit B-norm, an in-order Cholesky of S^T B S drops columns whose pivot is
-    below drop_tol of the largest diagonal entry (numerically dependent ones), and the k
-    largest eigenpairs of L^{-1} (S^T A S) L^{-T} give the next X;
+    below drop_tol (1e-8) of the largest diagonal entry, and the k largest eigenpairs of
+    L^{-1} (S^T A S) L^{-T} give the next X. A Cholesky factor of a Gram matrix carries
+    about half the working digits, so columns independent of the others by less than
+    1e-4 (pivot 1e-8) are treated as dependent: with smaller thresholds the B-orthogonality
+    of the iterates decays once residuals reach rounding level;
   * the start block is the unit vectors of the k largest ratios A_ii / B_ii (a stable
     order: ties by index), and exactly `iters` steps are taken.
 
@@ -73,7 +76,7 @@ def _rayleigh_ritz(S, AS, BS, k, drop_tol):
     return theta, Y
 
 
-def lobpcg_largest(A, B, k, iters=15, drop_tol=1e-12, X0=None, history=None, project=None):
+def lobpcg_largest(A, B, k, iters=15, drop_tol=1e-8, X0=None, history=None, project=None):
     """theta (descending, k values) and X (n x k, B-orthonormal) after `iters` steps.
 
     project (optional): a projector onto a subspace on which B is definite, applied to the
