@@ -75,6 +75,7 @@ enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_DF64 = 2 };     /* arithmetic
 enum { DD_B1 = 1, DD_B2 = 2, DD_B3 = 3, DD_B4 = 4 };                /* Sect. 4.2 recycling strategies */
 enum { DD_LOCAL_AUTO = 0, DD_LOCAL_DENSE = 1, DD_LOCAL_FDM = 2 };   /* K_II^{-1} representation */
 enum { DD_ENS_AUTO = 0, DD_ENS_SIMT = 1, DD_ENS_TC = 2, DD_ENS_BF16X3 = 3 };  /* ensemble N_i products */
+enum { DD_EIG_DENSE = 0, DD_EIG_LOBPCG = 1 };   /* solver of the adaptive face eigenproblems (Sect. 3.3) */
 
 typedef struct {
   int32_t levels;           /* 2: exact coarse solve; 3: coarse problem preconditioned by BDDC (Sect. 3.2) */
@@ -108,6 +109,11 @@ typedef struct {
                                profiling (dd_profile) the host-issued form is used */
   int32_t zero_initial_guess; /* 1: every dd_solve starts from x = 0; 0 (default): from the previous
                                solution of the recycle state (Sect. 5 compares the two) */
+  int32_t adaptive_solver;  /* face eigenproblems of eq. 10: DD_EIG_DENSE (default: dense generalized
+                               eigensolver on the host) or DD_EIG_LOBPCG (the paper's solver: block
+                               LOBPCG for the max_eig_per_face <= 10 largest pairs, lobpcg_iters steps,
+                               batched over the faces on the device; dd_setup only, dd_plan rejects it) */
+  int32_t lobpcg_iters;     /* LOBPCG steps per face (default 15, the paper's limit) */
 } dd_options;
 
 typedef struct {

@@ -15,6 +15,7 @@ PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 STRATEGY = {"B1": 1, "B2": 2, "B3": 3, "B4": 4}
 LOCAL = {"auto": 0, "dense": 1, "fdm": 2}
 ENS_NMM = {"auto": 0, "simt": 1, "tc": 2, "bf16x3": 3}
+EIG = {"dense": 0, "lobpcg": 1}
 
 
 class MeshDesc(ctypes.Structure):
@@ -33,7 +34,8 @@ class Options(ctypes.Structure):
                 ("flexible", ctypes.c_int32), ("reorth", ctypes.c_int32), ("stop_rhs_norm", ctypes.c_int32),
                 ("maxit", ctypes.c_int32), ("local_solver", ctypes.c_int32),
                 ("ens_nmm", ctypes.c_int32), ("ens_elem_rc", ctypes.c_int32), ("ens_fdm_rc", ctypes.c_int32),
-                ("loop_graph", ctypes.c_int32), ("zero_initial_guess", ctypes.c_int32)]
+                ("loop_graph", ctypes.c_int32), ("zero_initial_guess", ctypes.c_int32),
+                ("adaptive_solver", ctypes.c_int32), ("lobpcg_iters", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -41,6 +41,8 @@ def make_options(**kw) -> nat.Options:
             v = nat.LOCAL[v]
         if k == "ens_nmm" and isinstance(v, str):
             v = nat.ENS_NMM[v]
+        if k == "adaptive_solver" and isinstance(v, str):
+            v = nat.EIG[v]
         if not hasattr(o, k):
             raise KeyError(f"unknown option {k}")
         setattr(o, k, v)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdd_gb300.so")
-SOURCES = ["hostla.cpp", "setup.cpp", "kernels.cu", "vecops.cu", "solver.cu", "noalloc.cu", "batch.cu", "ensemble.cu", "recycle.cu",
+SOURCES = ["hostla.cpp", "setup.cpp", "kernels.cu", "vecops.cu", "solver.cu", "noalloc.cu", "batch.cu", "ensemble.cu", "recycle.cu", "lobpcg.cu",
            "tc_nmm.cu", "loop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -15,6 +15,7 @@
 
 #include "common.h"
 #include "hostla.h"
+#include "lobpcg.h"
 
 namespace dd {
 
@@ -393,7 +394,70 @@ struct AdaptiveOpts {
   bool on = false;
   double tau = 10.0;
   int max_per_face = 10;
+  bool lobpcg = false;  // face eigenproblems by the batched device LOBPCG (else dense, on the host)
+  int lobpcg_iters = 15;
 };
+
+// Orthonormal basis (modified Gram-Schmidt, dependent columns dropped) of the jumps (c, -c)
+// of the initial coarse dofs c of a common interface of m dofs: the span that Pi removes.
+std::vector<std::vector<double>> jump_basis(int m, const std::vector<std::vector<double>>& cq) {
+  const int n = 2 * m;
+  std::vector<std::vector<double>> Qo;
+  for (const auto& c : cq) {
+    std::vector<double> q(n);
+    for (int a = 0; a < m; ++a) {
+      q[a] = c[a];
+      q[m + a] = -c[a];
+    }
+    double n0 = 0.0;
+    for (double v : q) n0 += v * v;
+    n0 = std::sqrt(n0);
+    for (const auto& b : Qo) {
+      double d = 0.0;
+      for (int a = 0; a < n; ++a) d += b[a] * q[a];
+      for (int a = 0; a < n; ++a) q[a] -= d * b[a];
+    }
+    double n1 = 0.0;
+    for (double v : q) n1 += v * v;
+    n1 = std::sqrt(n1);
+    if (n1 <= 1e-12 * n0) continue;
+    for (double& v : q) v /= n1;
+    Qo.push_back(q);
+  }
+  return Qo;
+}
+
+// Constraint rows of one face from eigenpairs of eq. 10 (theta descending): for theta_j > tau
+// (at most maxr), c = w_j^T Lhs, i.e. (Lhs w_j) on the face dofs of the first copy (fpos),
+// orthogonalized against the face average and the rows before it (dropped below 1e-10).
+std::vector<std::vector<double>> rows_from_pairs(const std::vector<double>& theta, const std::vector<double>& LW,
+                                                 int n, const std::vector<int>& fpos, double tau, int maxr) {
+  const int mf = (int)fpos.size();
+  std::vector<std::vector<double>> basis, rows;
+  basis.push_back(std::vector<double>(mf, 1.0 / std::sqrt((double)mf)));
+  for (size_t j = 0; j < theta.size() && (int)rows.size() < maxr; ++j) {
+    if (!(theta[j] > tau)) break;
+    std::vector<double> row(mf);
+    for (int b = 0; b < mf; ++b) row[b] = LW[j * n + fpos[b]];
+    double n0 = 0.0;
+    for (double v : row) n0 += v * v;
+    n0 = std::sqrt(n0);
+    if (n0 == 0.0) continue;
+    for (const auto& bv : basis) {
+      double d = 0.0;
+      for (int b = 0; b < mf; ++b) d += bv[b] * row[b];
+      for (int b = 0; b < mf; ++b) row[b] -= d * bv[b];
+    }
+    double n1 = 0.0;
+    for (double v : row) n1 += v * v;
+    n1 = std::sqrt(n1);
+    if (n1 < 1e-10 * n0) continue;
+    for (double& v : row) v /= n1;
+    basis.push_back(row);
+    rows.push_back(row);
+  }
+  return rows;
+}
 
 // Weights, constraints and dense pipelines of a level whose subdomain matrices are given:
 // phase A (Schur complements), weights, optional adaptive face constraints, phase C (BDDC).
@@ -444,6 +508,8 @@ void finish_level(Level& L, const Globs& gl, std::vector<CoarseDof> cd, int weig
     std::vector<char> initial(gl.kind.size(), 0);
     for (const CoarseDof& c : cd) initial[c.glob] = 1;
     std::vector<std::vector<std::vector<double>>> extra(faces.size());
+    std::vector<FaceProblem> fprob(ad.lobpcg ? faces.size() : 0);
+    std::vector<std::vector<int>> fposs(ad.lobpcg ? faces.size() : 0);
     int bad = -1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int f = 0; f < (int)faces.size(); ++f) {
@@ -479,9 +545,42 @@ void finish_level(Level& L, const Globs& gl, std::vector<CoarseDof> cd, int weig
       }
       std::vector<int> fpos;
       for (int64_t d : gl.dofs[g]) fpos.push_back((int)(std::lower_bound(dofs.begin(), dofs.end(), d) - dofs.begin()));
-      extra[f] = face_eigen_rows(As, At, ws, wt, cq, fpos, ad.tau, ad.max_per_face);
+      if (!ad.lobpcg) {
+        extra[f] = face_eigen_rows(As, At, ws, wt, cq, fpos, ad.tau, ad.max_per_face);
+        continue;
+      }
+      // the pencil for the device LOBPCG: both Schur complements, weights, jump basis, and
+      // whether both subdomains float (A_s 1 = A_t 1 = 0: the common constant is removed too)
+      FaceProblem& P = fprob[f];
+      P.m = m;
+      auto annihilates_constants = [&](const std::vector<double>& M) {
+        double fro = 0.0, r2 = 0.0;
+        for (double v : M) fro += v * v;
+        for (int a = 0; a < m; ++a) {
+          double r = 0.0;
+          for (int b = 0; b < m; ++b) r += M[(size_t)a * m + b];
+          r2 += r * r;
+        }
+        return std::sqrt(r2) <= 1e-10 * std::sqrt(fro) * std::sqrt((double)m);
+      };
+      P.floating = annihilates_constants(As) && annihilates_constants(At) ? 1 : 0;
+      auto Qo = jump_basis(m, cq);
+      P.nq = (int)Qo.size();
+      for (const auto& q : Qo) P.Q.insert(P.Q.end(), q.begin(), q.end());
+      P.As = std::move(As);
+      P.At = std::move(At);
+      P.ws = std::move(ws);
+      P.wt = std::move(wt);
+      fposs[f] = std::move(fpos);
     }
     if (bad >= 0) throw Error(DD_SINGULAR_LOCAL, std::string(what) + ": singular face Schur complement");
+    if (ad.lobpcg) {
+      std::vector<FaceResult> res;
+      face_lobpcg_batch(fprob, std::min(ad.max_per_face, LOBPCG_MAXK), ad.lobpcg_iters, res);
+#pragma omp parallel for schedule(dynamic, 8)
+      for (int f = 0; f < (int)faces.size(); ++f)
+        extra[f] = rows_from_pairs(res[f].theta, res[f].LX, 2 * fprob[f].m, fposs[f], ad.tau, ad.max_per_face);
+    }
     std::vector<std::vector<std::vector<double>>> by_glob(gl.kind.size());
     for (size_t f = 0; f < faces.size(); ++f) by_glob[faces[f]] = std::move(extra[f]);
     std::vector<CoarseDof> cd2;
@@ -709,6 +808,12 @@ void build_host_setup(const dd_mesh_desc& md, const dd_options& opt, HostSetup& 
   ad.on = opt.adaptive != 0;
   ad.tau = opt.tau;
   ad.max_per_face = opt.max_eig_per_face > 0 ? opt.max_eig_per_face : 10;
+  ad.lobpcg = opt.adaptive_solver == DD_EIG_LOBPCG;
+  ad.lobpcg_iters = opt.lobpcg_iters;
+  DD_REQUIRE(opt.adaptive_solver == DD_EIG_DENSE || opt.adaptive_solver == DD_EIG_LOBPCG,
+             "adaptive_solver must be DENSE or LOBPCG");
+  DD_REQUIRE(!ad.lobpcg || (opt.lobpcg_iters >= 1 && opt.max_eig_per_face <= LOBPCG_MAXK),
+             "adaptive_solver LOBPCG: lobpcg_iters >= 1 and max_eig_per_face <= 10");
   DD_REQUIRE(!ad.on || opt.tau > 1.0, "adaptive threshold tau must exceed 1");
   finish_level(L1, gl, cd, opt.weights, kloc_fn, kdiag_fn, nloc, Iloc, Gloc, false, ad, "level 1");
 

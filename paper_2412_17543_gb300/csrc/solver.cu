@@ -574,6 +574,8 @@ dd_status dd_default_options(dd_options* o) {
   o->ens_fdm_rc = 0;
   o->loop_graph = 1;
   o->zero_initial_guess = 0;
+  o->adaptive_solver = DD_EIG_DENSE;
+  o->lobpcg_iters = 15;
   return DD_OK;
 }
 
@@ -880,6 +882,8 @@ dd_status dd_plan(const dd_mesh_desc* md, const dd_options* opt, dd_info_t* info
     return DD_INVALID_ARG;
   }
   return guard([&] {
+    DD_REQUIRE(!(opt->adaptive && opt->adaptive_solver == DD_EIG_LOBPCG),
+               "dd_plan: adaptive_solver LOBPCG runs on the device (use dd_setup)");
     HostSetup H;
     build_host_setup(*md, *opt, H);
     std::memset(info, 0, sizeof(*info));

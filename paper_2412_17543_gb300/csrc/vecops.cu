@@ -184,53 +184,59 @@ void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s) {
 
 constexpr int PT = 4;  // rows per thread of the row-blocked deflation kernels
 
-// mu = Ginv (V^T v) with the basis V as df64 (k columns of stride ld), in one launch. Block b
-// owns rows [b * PT * RB, (b + 1) * PT * RB): v's entries there are staged in shared memory as
-// df64 once, warp w takes the columns c = w, w + RB/32, ... and walks the block's rows (each
-// lane 32 of them, coalesced), so each column needs a single warp reduction; the block
-// writes wpart[b][c]. The last block to finish (a ticket counter, reset by that block)
-// sums wpart over the blocks in block order and applies Ginv: the same fixed reduction
-// order whichever block finishes last.
-__global__ void __launch_bounds__(RB) k_wdots5(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
+// mu = Ginv (V^T v) with the basis V as df64 (k columns of stride ld), in one launch.
+// Block (b, g) takes the column group g (WD_COLS columns) over a grid-stride share of the
+// rows: every thread keeps the group's sums for its rows in registers (each row: one entry
+// of v, WD_COLS independent coalesced loads), so a column needs one warp reduction per
+// warp at the end; the block's sums go to wpart[b][c]. The last block to finish (a ticket
+// counter, reset by that block) sums wpart over the blocks in block order and applies Ginv.
+constexpr int WD_COLS = 20;
+constexpr int WD_BLOCKS = 2 * 152;
+__global__ void __launch_bounds__(RB) k_wdots6(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
                                                const double* __restrict__ v, double* wpart,
                                                unsigned* __restrict__ ticket, const double* __restrict__ Ginv,
                                                double* __restrict__ mu) {
-  constexpr int ROWS = PT * RB;
-  __shared__ df64 zs[ROWS];
+  __shared__ df64 sh[RB / 32][WD_COLS];
   __shared__ double d[MAXK];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t r0 = (int64_t)blockIdx.x * ROWS;
-  for (int t = threadIdx.x; t < ROWS; t += RB) zs[t] = r0 + t < n ? dbl_to_df(v[r0 + t]) : df64{0.f, 0.f};
-  __syncthreads();
-  for (int c = warp; c < k; c += RB / 32) {
-    const df64* col = V + (int64_t)c * ld + r0;
-    df64_acc a0, a1;
-#pragma unroll 8
-    for (int j = 0; j < ROWS / 32; j += 2) {
-      const int t0 = j * 32 + lane, t1 = t0 + 32;
-      const df64 e0 = r0 + t0 < n ? col[t0] : df64{0.f, 0.f};
-      const df64 e1 = r0 + t1 < n ? col[t1] : df64{0.f, 0.f};
-      a0.fma(e0, zs[t0]);
-      a1.fma(e1, zs[t1]);
-    }
-    df64 x = df64_add(a0.get(), a1.get());
+  const int c0 = blockIdx.y * WD_COLS;
+  const int nc = min(WD_COLS, k - c0);
+  df64_acc acc[WD_COLS];
+  const int64_t stride = (int64_t)gridDim.x * RB;
+  for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
+    const df64 z = dbl_to_df(v[i]);
+    const df64* col = V + (int64_t)c0 * ld + i;
+#pragma unroll
+    for (int c = 0; c < WD_COLS; ++c)
+      if (c < nc) acc[c].fma(col[(int64_t)c * ld], z);
+  }
+#pragma unroll
+  for (int c = 0; c < WD_COLS; ++c) {
+    if (c >= nc) break;
+    df64 x = acc[c].get();
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       const df64 y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
       x = df64_add(x, y);
     }
-    if (lane == 0) wpart[(int64_t)blockIdx.x * MAXK + c] = df64_to_double_bits(x);
+    if (lane == 0) sh[warp][c] = x;
   }
-  // the last block to arrive reduces over the blocks and applies Ginv
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    df64_acc sum;
+    for (int w = 0; w < RB / 32; ++w) sum.add(sh[w][c]);
+    wpart[(int64_t)blockIdx.x * MAXK + c0 + c] = df64_to_double_bits(sum.get());
+  }
+  // the last block of the whole grid reduces over the blocks and applies Ginv
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // warp w sums the blocks b = w, w + RB/32, ... (eight chains per lane, combined in order),
-  // lanes over the columns; then the warps' sums are added in warp order
+  // warp w sums the blocks b = w, w + RB/32, ... (eight chains per lane), lanes over the
+  // columns; then the warps' sums are added in warp order
   __shared__ double wsum[RB / 32][MAXK];
   const int nb = (int)gridDim.x;
   for (int c = lane; c < k; c += 32) {
@@ -264,8 +270,8 @@ int defl_df_blocks(int64_t n) { return (int)((n + (int64_t)PT * RB - 1) / ((int6
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
                 double* mu, unsigned* ticket, cudaStream_t s) {
   if (k == 0) return;
-  const int nb = defl_df_blocks(n);
-  k_wdots5<<<nb, RB, 0, s>>>(n, k, V, ld, v, wpart, ticket, Ginv, mu);
+  const int nb = (int)std::min<int64_t>(WD_BLOCKS, (n + RB - 1) / RB);
+  k_wdots6<<<dim3(nb, (k + WD_COLS - 1) / WD_COLS), RB, 0, s>>>(n, k, V, ld, v, wpart, ticket, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 

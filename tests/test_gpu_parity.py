@@ -168,8 +168,12 @@ def test_solve_mixed_recycled_three_level(local):
 
 
 @pytest.mark.parametrize("tau", [1.5, 3.0])
-def test_precond_apply_adaptive(tau):
-    # random coefficients make some faces need extra constraints (Sect. 3.3)
+@pytest.mark.parametrize("solver,tol", [("dense", 1e-9), ("lobpcg", 1e-6)])
+def test_precond_apply_adaptive(tau, solver, tol):
+    # random coefficients make some faces need extra constraints (Sect. 3.3); the face
+    # eigenproblems by the dense eigensolver, or by the paper's LOBPCG (15 steps, 10 vectors)
+    # batched on the device against the oracle's LOBPCG with the same steps (the tolerance
+    # allows for the rounding that 15 steps of an inexact eigensolver carry into the rows)
     rng = np.random.default_rng(5)
     n = 8
     coef = np.exp(2.0 * rng.standard_normal((n, n, n)))
@@ -177,14 +181,36 @@ def test_precond_apply_adaptive(tau):
     subs = dd.q1_substructures(m)
     kinds = (dd.CORNER, dd.EDGE, dd.FACE)
     base = dd.Preconditioner(subs, 2, kinds, "diag")
-    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau)
+    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=tau, method=solver, lobpcg_iters=15)
     Po = dd.Preconditioner(subs, 2, kinds, "diag", extra_rows=rows)
-    S = P.Solver(m, **_opts(2, kinds, adaptive=1, tau=tau))
+    S = P.Solver(m, **_opts(2, kinds, adaptive=1, tau=tau, adaptive_solver=solver, lobpcg_iters=15))
     assert S.info["n_adaptive"] == sum(len(r) for r in rows.values()) > 0
     r = np.random.default_rng(3).standard_normal(len(subs.gamma))
     z = N(S.precond_apply(T(r)))
     zo = Po.apply(r)
-    assert np.abs(z - zo).max() <= 1e-9 * np.abs(zo).max()
+    assert np.abs(z - zo).max() <= tol * np.abs(zo).max()
+
+
+def test_adaptive_lobpcg_on_the_bench_mesh_family():
+    """Device LOBPCG constraints on a graded 32^3 member of the timed workload's family (FDM
+    local solves, three levels): the count equals the oracle's LOBPCG count, and the solution
+    sequence still matches the sparse Cholesky."""
+    m = make_mesh(32, 8, 1.3, 40.0)
+    subs = dd.q1_substructures(m)
+    kinds = (dd.CORNER, dd.EDGE, dd.FACE)
+    base = dd.Preconditioner(subs, 2, kinds, "diag")
+    rows = dd.adaptive_face_constraints(subs, base.l1.D, tau=4.0, method="lobpcg", lobpcg_iters=15)
+    S = P.Solver(m, levels=3, coarse_group=2, use_corners=1, use_edges=1, use_faces=1, weights="diag", adaptive=1,
+                 tau=4.0, adaptive_solver="lobpcg", schur_prec="df64", precond_prec="fp32", flexible=1)
+    assert S.info["n_adaptive"] == sum(len(r) for r in rows.values()) > 0
+    F = load_sequence(m, 3, 3)
+    ch = cholesky.factor_mesh(m)
+    rec = S.recycler(8, "B4")
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        xe = ch.solve(f)
+        assert np.linalg.norm(N(x) - xe) <= 1e-7 * np.linalg.norm(xe), t
+    S.close()
 
 
 def test_adjoint_and_autograd_match_oracle():
