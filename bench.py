@@ -609,10 +609,10 @@ def main():
     nn = prof["symv_N"]
     nn_ms = nn[0] / max(nn[1], 1)
     achieved = nn[2] / (nn_ms / 1e3) / 1e9 if nn[1] else None
-    # DRAM bytes of one launch from the ncu capture summarized in
-    # profiles/k_symv_fp32_graded64.md (64^3, 512 subdomains: 155.3 MB read + written),
-    # scaled by subdomains to a full 128^3 launch; None for another workload
-    traffic = 155282688.0 * mixed.info["n_sub"] / 512 if args.workload == "graded128" and args.n is None else None
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of this kernel
+    # on the default workload (128^3, 4096 subdomains), from an ncu capture of this bench:
+    # 1131.25 MB read + 13.22 MB written against 1129.2 MB algorithmic; None elsewhere
+    traffic = 1144475392.0 if args.workload == "graded128" and args.n is None else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
             "kernel": "k_symv<FP32> (batched constrained-Neumann N_i GEMV, eq. 9)",

@@ -182,96 +182,117 @@ void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s) {
   DD_CHECK_LAUNCH();
 }
 
-constexpr int PT = 4;  // rows per thread of the row-blocked deflation kernels
+constexpr int PT = 4;  // rows per thread of the row-blocked deflation update
 
 // mu = Ginv (V^T v) with the basis V as df64 (k columns of stride ld), in one launch.
-// Block (b, g) takes the column group g (WD_COLS columns) over a grid-stride share of the
-// rows: every thread keeps the group's sums for its rows in registers (each row: one entry
-// of v, WD_COLS independent coalesced loads), so a column needs one warp reduction per
-// warp at the end; the block's sums go to wpart[b][c]. The last block to finish (a ticket
-// counter, reset by that block) sums wpart over the blocks in block order and applies Ginv.
-constexpr int WD_COLS = 20;
-constexpr int WD_BLOCKS = 2 * 152;
-__global__ void __launch_bounds__(RB) k_wdots6(int64_t n, int k, const df64* __restrict__ V, int64_t ld,
-                                               const double* __restrict__ v, double* wpart,
+// Block b owns a contiguous range of `rows` rows (a multiple of 32, fixed by n alone): v's
+// entries there are staged in shared memory as df64, warp w walks the columns
+// c = w, w + RB/32, ... over the block's rows (eight coalesced loads in flight per lane,
+// two sums per lane) and needs one warp reduction per column; the block writes wpart[b][c].
+// The last block to finish (a ticket counter, reset by that block) reduces wpart with all
+// of its threads: thread (c, s) sums column c over a fixed segment s of the blocks, sixteen
+// loads in flight at a time, and the segments are added in order; then Ginv is applied the
+// same way. The reduction order depends only on n and k, not on which block ends last.
+constexpr int WD_GRID = 4 * 152;   // blocks of the deflation dots: four per SM, one wave
+constexpr int WD_MAXROWS = 4096;   // rows per block at most (32 KiB of staged df64)
+
+static int64_t wd_rows(int64_t n, int nb) { return ((n + nb - 1) / nb + 31) / 32 * 32; }
+
+int defl_df_blocks(int64_t n) {
+  int64_t nb = std::min<int64_t>(WD_GRID, (n + 255) / 256);
+  nb = std::max<int64_t>(nb, (n + WD_MAXROWS - 1) / WD_MAXROWS);
+  return (int)std::max<int64_t>(nb, 1);
+}
+
+__global__ void __launch_bounds__(RB) k_wdots7(int64_t n, int64_t rows, int k, const df64* __restrict__ V,
+                                               int64_t ld, const double* __restrict__ v, double* wpart,
                                                unsigned* __restrict__ ticket, const double* __restrict__ Ginv,
                                                double* __restrict__ mu) {
-  __shared__ df64 sh[RB / 32][WD_COLS];
+  __shared__ df64 zs[WD_MAXROWS];
+  __shared__ double part[RB];
   __shared__ double d[MAXK];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c0 = blockIdx.y * WD_COLS;
-  const int nc = min(WD_COLS, k - c0);
-  df64_acc acc[WD_COLS];
-  const int64_t stride = (int64_t)gridDim.x * RB;
-  for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < n; i += stride) {
-    const df64 z = dbl_to_df(v[i]);
-    const df64* col = V + (int64_t)c0 * ld + i;
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int64_t left = n - r0 < rows ? n - r0 : rows;
+  const int nr = left > 0 ? (int)left : 0;
+  for (int t = threadIdx.x; t < nr; t += RB) zs[t] = dbl_to_df(v[r0 + t]);
+  __syncthreads();
+  for (int c = warp; c < k; c += RB / 32) {
+    const df64* col = V + (int64_t)c * ld + r0;
+    df64_acc a0, a1;
+    int j = lane;
+    for (; j + 7 * 32 < nr; j += 8 * 32) {
+      df64 e[8];
 #pragma unroll
-    for (int c = 0; c < WD_COLS; ++c)
-      if (c < nc) acc[c].fma(col[(int64_t)c * ld], z);
-  }
+      for (int u = 0; u < 8; ++u) e[u] = col[j + 32 * u];
 #pragma unroll
-  for (int c = 0; c < WD_COLS; ++c) {
-    if (c >= nc) break;
-    df64 x = acc[c].get();
+      for (int u = 0; u < 8; u += 2) {
+        a0.fma(e[u], zs[j + 32 * u]);
+        a1.fma(e[u + 1], zs[j + 32 * (u + 1)]);
+      }
+    }
+    for (; j < nr; j += 32) a0.fma(col[j], zs[j]);
+    df64 x = df64_add(a0.get(), a1.get());
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       const df64 y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
       x = df64_add(x, y);
     }
-    if (lane == 0) sh[warp][c] = x;
+    if (lane == 0) wpart[(int64_t)blockIdx.x * MAXK + c] = df64_to_double_bits(x);
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    df64_acc sum;
-    for (int w = 0; w < RB / 32; ++w) sum.add(sh[w][c]);
-    wpart[(int64_t)blockIdx.x * MAXK + c0 + c] = df64_to_double_bits(sum.get());
-  }
-  // the last block of the whole grid reduces over the blocks and applies Ginv
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // warp w sums the blocks b = w, w + RB/32, ... (eight chains per lane), lanes over the
-  // columns; then the warps' sums are added in warp order
-  __shared__ double wsum[RB / 32][MAXK];
   const int nb = (int)gridDim.x;
-  for (int c = lane; c < k; c += 32) {
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int b = warp;
-    for (; b + 7 * (RB / 32) < nb; b += 8 * (RB / 32)) {
+  const int ns = max(1, min(8, RB / k));  // segments per column
+  const int t = threadIdx.x;
+  if (t < ns * k) {
+    const int c = t % k, s = t / k;
+    const int b1 = (s + 1) * nb / ns;
+    int b = s * nb / ns;
+    double sum = 0.0;
+    for (; b + 16 <= b1; b += 16) {
+      double e[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] += __ldcg(&wpart[(int64_t)(b + u * (RB / 32)) * MAXK + c]);
+      for (int u = 0; u < 16; ++u) e[u] = __ldcg(&wpart[(int64_t)(b + u) * MAXK + c]);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sum += e[u];
     }
-    for (int u = 0; b < nb; b += RB / 32, ++u) a[u & 7] += __ldcg(&wpart[(int64_t)b * MAXK + c]);
-    wsum[warp][c] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (; b < b1; ++b) sum += __ldcg(&wpart[(int64_t)b * MAXK + c]);
+    part[t] = sum;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < k; c += RB) {
+  if (t < k) {
     double sum = 0.0;
-    for (int w = 0; w < RB / 32; ++w) sum += wsum[w][c];
-    d[c] = sum;
+    for (int s = 0; s < ns; ++s) sum += part[s * k + t];
+    d[t] = sum;
   }
   __syncthreads();
-  for (int a = warp; a < k; a += RB / 32) {
+  if (t < ns * k) {
+    const int a = t % k, s = t / k;
+    const int c1 = (s + 1) * k / ns;
     double sum = 0.0;
-    for (int c = lane; c < k; c += 32) sum = fma(Ginv[a * k + c], d[c], sum);
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) mu[a] = sum;
+    for (int c = s * k / ns; c < c1; ++c) sum = fma(Ginv[a * k + c], d[c], sum);
+    part[t] = sum;
   }
-  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
+  if (t < k) {
+    double sum = 0.0;
+    for (int s = 0; s < ns; ++s) sum += part[s * k + t];
+    mu[t] = sum;
+  }
+  if (t == 0) *ticket = 0u;
 }
-
-int defl_df_blocks(int64_t n) { return (int)((n + (int64_t)PT * RB - 1) / ((int64_t)PT * RB)); }
 
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
                 double* mu, unsigned* ticket, cudaStream_t s) {
   if (k == 0) return;
-  const int nb = (int)std::min<int64_t>(WD_BLOCKS, (n + RB - 1) / RB);
-  k_wdots6<<<dim3(nb, (k + WD_COLS - 1) / WD_COLS), RB, 0, s>>>(n, k, V, ld, v, wpart, ticket, Ginv, mu);
+  const int nb = defl_df_blocks(n);
+  k_wdots7<<<nb, RB, 0, s>>>(n, wd_rows(n, nb), k, V, ld, v, wpart, ticket, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 
