@@ -50,11 +50,15 @@ struct dd_ctx {
   double* wpart = nullptr;     // [NBLK*MAXK]
   double* mu = nullptr;        // [MAXK]
   unsigned* wticket = nullptr;  // block ticket of the one-launch deflation dots (0 between launches)
+  unsigned* fticket = nullptr;  // block ticket of the dot products that finalize in the same launch
   double* gram_part = nullptr; // [NBLK*4096]
   double* gram_out = nullptr;  // [4096]
   double* ybuf = nullptr;      // [128*128] combination coefficients
   const double** ptrs = nullptr;  // device pointer table for gram / lincomb
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // second (high-priority) stream of the BDDC coarse correction and its fork/join events
+  cudaStream_t s_coarse = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // profiling: events around timed launches, harvested after a synchronization
   bool prof_on = false;
   struct Pending {
@@ -95,6 +99,9 @@ struct dd_ctx {
     if (ctl_host) cudaFreeHost(ctl_host);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (s_coarse) cudaStreamDestroy(s_coarse);
     for (auto& p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);

@@ -209,7 +209,9 @@ void LoopGraph::run(const std::vector<uint64_t>& key, const Body& body, LoopCtl*
       add_launches(-body_launches_);
       cudaGraph_t g2 = nullptr;
       DD_CUDA(cudaStreamEndCapture(cap_, &g2));
-      DD_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+      // kernel nodes keep the priority of the stream they were captured from (the BDDC
+      // coarse branch runs ahead of the level-1 N_i blocks, as in the host-issued loop)
+      DD_CUDA(cudaGraphInstantiate(&exec_, graph_, cudaGraphInstantiateFlagUseNodePriority));
       key_ = key;
       ++captures_;
     }

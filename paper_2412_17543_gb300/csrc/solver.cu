@@ -242,19 +242,34 @@ void recover(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream
   launch_scatter_recover(c->mesh, xg, c->w.sI, x, s);
 }
 
-// BDDC of one level on an interface residual r -> z, with a coarse solver callback
+// BDDC of one level on an interface residual r -> z, with a coarse solver callback.
+// The coarse correction (Phi_i^T D_i R_i r, the coarse solve, Phi_i u_C) does not depend on
+// the local products N_i D_i R_i r: with `fork` it is issued on the context's high-priority
+// stream, so that its short, latency-bound launches run while the N_i product streams from
+// HBM, and the two branches meet before the weighted gather. Each kernel computes the same
+// values in either order.
 template <class CoarseFn>
 void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* vloc,
-                double* gloc, double* gC, double* uC, CoarseFn coarse, cudaStream_t s) {
+                double* gloc, double* gC, double* uC, CoarseFn coarse, cudaStream_t s, bool fork) {
   launch_restrict(b.n_flat, b.gmap, b.D, r, rloc, s);
+  cudaStream_t sc = s;
+  if (fork) {
+    DD_CUDA(cudaEventRecord(c->ev_fork, s));
+    DD_CUDA(cudaStreamWaitEvent(c->s_coarse, c->ev_fork, 0));
+    sc = c->s_coarse;
+  }
+  launch_bgemv(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, sc);  // Phi_i^T D_i R_i r
+  launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, sc);
+  coarse(gC, uC, sc);
+  launch_bgemv_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, sc);  // Phi_i R_Ci u_C
   {
     ProfScope pk(c, &b == &c->b1 ? DD_PROF_SYMV_N : DD_PROF_COUNT, s);
     launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
   }
-  launch_bgemv(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);  // Phi_i^T D_i R_i r
-  launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
-  coarse(gC, uC);
-  launch_bgemv_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);  // Phi_i R_Ci u_C
+  if (fork) {
+    DD_CUDA(cudaEventRecord(c->ev_join, sc));
+    DD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+  }
   launch_wgather(b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
 }
 
@@ -267,7 +282,8 @@ void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
   launch_bgemv_t(L.E, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather(L.b.n_gamma, L.b.gptr, L.b.gidx, w.rl2, g, L.gam_c64, w.r2, s);  // g[gam_c] + sum of copies
   bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.vloc2, w.gloc2, w.g3, w.u3,
-             [&](const double* g3, double* u3) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, s); }, s);
+             [&](const double* g3, double* u3, cudaStream_t ss) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, ss); },
+             s, false);
   launch_bgemv(L.E, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2, s);  // u0 - K_II^{-1} K_IG z
   launch_map_scatter(L.n_int, L.imap, w.uI2, u, s);
   launch_map_scatter(L.b.n_gamma, L.gam_c, w.z2, u, s);
@@ -277,13 +293,13 @@ void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_PRECOND, s);
   Work& w = c->w;
   bddc_apply(c, c->b1, r, z, w.rloc, w.uloc, w.vloc, w.gloc, w.gC, w.uC,
-             [&](const double* g, double* u) {
+             [&](const double* g, double* u, cudaStream_t ss) {
                if (c->levels == 2)
-                 launch_dense_gemv(c->b1.n_coarse, c->b1.prec, c->KCinv, g, u, s);
+                 launch_dense_gemv(c->b1.n_coarse, c->b1.prec, c->KCinv, g, u, ss);
                else
-                 level2_apply(c, g, u, s);
+                 level2_apply(c, g, u, ss);
              },
-             s);
+             s, c->s_coarse != nullptr);
 }
 
 // z = M^{-1} r as the PCG sees it: without a Dirichlet face the constant interface vector
@@ -775,10 +791,12 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     c->ctl = A.alloc<LoopCtl>(1);
     c->alphas = A.alloc<double>((size_t)opt->maxit);
     c->partials = A.alloc<double>(NBLK * MAXDOT);
-    c->wpart = A.alloc<double>((size_t)std::max<int64_t>(NBLK, defl_df_blocks(c->n_gamma)) * MAXK);
+    c->wpart = A.alloc<double>((size_t)std::max<int64_t>(NBLK, defl_df_part_rows(c->n_gamma)) * MAXK);
     c->mu = A.alloc<double>(MAXK);
-    c->wticket = A.alloc<unsigned>(1);
-    DD_CUDA(cudaMemsetAsync(c->wticket, 0, sizeof(unsigned), s));
+    c->fticket = A.alloc<unsigned>(1);
+    DD_CUDA(cudaMemsetAsync(c->fticket, 0, sizeof(unsigned), s));
+    c->wticket = A.alloc<unsigned>(defl_df_tickets(c->n_gamma));
+    DD_CUDA(cudaMemsetAsync(c->wticket, 0, defl_df_tickets(c->n_gamma) * sizeof(unsigned), s));
     c->gram_part = A.alloc<double>((size_t)NBLK * 4096);
     c->gram_out = A.alloc<double>(4096);
     c->ybuf = A.alloc<double>(128 * 128);
@@ -787,6 +805,13 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
     DD_CUDA(cudaMallocHost(&c->ctl_host, sizeof(LoopCtl)));
     DD_CUDA(cudaEventCreate(&c->ev0));
     DD_CUDA(cudaEventCreate(&c->ev1));
+    {
+      int least = 0, greatest = 0;
+      DD_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      DD_CUDA(cudaStreamCreateWithPriority(&c->s_coarse, cudaStreamNonBlocking, greatest));
+      DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
     DD_CUDA(cudaStreamSynchronize(s));
     {
       // algorithmic bytes of one K_II^{-1} application: the operator data read once and the
@@ -1298,28 +1323,25 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     if (flex) DD_CUDA(cudaMemcpyAsync(c->zold, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, bs));
     precond_z(c, c->r, c->z, bs);
     if (rec) launch_record(c->ctl, c->z, st->Z, n, st->hmax, 1, bs);
-    vec_dots(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, nullptr, nullptr, c->partials, bs);
-    vec_finalize(c->partials, c->sc, FIN_RZL, flex, bs, &c->ctl->its);
+    vec_dots_fin(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, c->partials, c->sc, FIN_RZL, flex,
+                 c->fticket, bs, &c->ctl->its);
     {
       ProfScope pd(c, k ? DD_PROF_DEFL : DD_PROF_COUNT, bs);
       if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, c->wticket, bs);
       defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
     }
     schur_apply(c, c->p, c->q, bs);
-    vec_dots(n, c->p, c->q, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
-    vec_finalize(c->partials, c->sc, FIN_PQ, 0, bs);
+    vec_dots_fin(n, c->p, c->q, nullptr, nullptr, c->partials, c->sc, FIN_PQ, 0, c->fticket, bs);
     if (rec) {
       launch_record(c->ctl, c->p, st->P, n, st->hmax, 0, bs);
       launch_record(c->ctl, c->q, st->AP, n, st->hmax, 0, bs);
     }
-    vec_axpy2(n, c->sc, c->xg, c->p, c->r, c->q, c->partials, bs);
-    vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);
+    vec_axpy2_fin(n, c->sc, c->xg, c->p, c->r, c->q, c->partials, c->fticket, bs);
     if (reo) {
       // r -= W (W^T W)^{-1} W^T r  (Algorithm 1, optional re-orthogonalization), then ||r||^2 again
       defl_mu_df(n, k, Wd, n, c->r, st->WWinv, c->wpart, c->mu, c->wticket, bs);
       defl_update_df(n, k, Wd, n, c->mu, nullptr, c->r, c->sc, -1, -1.0, bs);
-      vec_dots(n, c->r, c->r, nullptr, nullptr, nullptr, nullptr, c->partials, bs);
-      vec_finalize(c->partials, c->sc, FIN_RR, 0, bs);
+      vec_dots_fin(n, c->r, c->r, nullptr, nullptr, c->partials, c->sc, FIN_RR, 0, c->fticket, bs);
     }
     launch_loop_check(c->ctl, c->sc, c->alphas, h, in_graph, bs);
   };

@@ -29,44 +29,17 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[ND], double* part
   }
 }
 
-// partial dots: d0 = a0.b0, d1 = a1.b1, d2 = a2.b2 (null pairs skipped)
-__global__ void __launch_bounds__(RB) k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
-                                             const double* __restrict__ a1, const double* __restrict__ b1,
-                                             const double* __restrict__ a2, const double* __restrict__ b2,
-                                             double* partials) {
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
-    v[0] = fma(a0[i], b0[i], v[0]);
-    if (a1) v[1] = fma(a1[i], b1[i], v[1]);
-    if (a2) v[2] = fma(a2[i], b2[i], v[2]);
-  }
-  block_reduce_store<3>(v, partials);
-}
-
-// x += alpha p ; r -= alpha q ; partial ||r||^2
-__global__ void __launch_bounds__(RB) k_axpy2(int64_t n, const double* __restrict__ sc, double* __restrict__ x,
-                                              const double* __restrict__ p, double* __restrict__ r,
-                                              const double* __restrict__ q, double* partials) {
-  const double alpha = sc[SC_ALPHA];
-  double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
-    x[i] = fma(alpha, p[i], x[i]);
-    double ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    v[0] = fma(ri, ri, v[0]);
-  }
-  block_reduce_store<1>(v, partials);
-}
-
 // single-block finalization: sums the partials in a fixed order (a warp per dot product,
-// fixed lane assignment and shuffle tree) and updates the scalars
-__global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible,
-                           const int* __restrict__ its) {
+// fixed lane assignment and shuffle tree) and updates the scalars. CG: the partials were
+// written by other blocks of the same launch (read through L2).
+template <bool CG>
+__device__ __forceinline__ void finalize_block(int nblk, const double* partials, double* sc, int op, int flexible,
+                                               const int* its) {
   __shared__ double tot[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp < 3) {
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += partials[b * MAXDOT + warp];
+    for (int b = lane; b < nblk; b += 32) s += CG ? __ldcg(&partials[b * MAXDOT + warp]) : partials[b * MAXDOT + warp];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) tot[warp] = s;
   }
@@ -111,9 +84,75 @@ __global__ void k_finalize(int nblk, const double* __restrict__ partials, double
   }
 }
 
+__global__ void k_finalize(int nblk, const double* __restrict__ partials, double* sc, int op, int flexible,
+                           const int* __restrict__ its) {
+  finalize_block<false>(nblk, partials, sc, op, flexible, its);
+}
+
+// Finalization by the last block of a reduction launch (ticket counter, reset by that
+// block): the same sums in the same order as k_finalize, without a second launch.
+struct FinArgs {
+  double* sc;
+  int op, flexible;
+  const int* its;
+  unsigned* ticket;
+};
+__device__ __forceinline__ void finalize_last(const double* partials, const FinArgs& f) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(f.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *f.ticket = 0u;
+  finalize_block<true>((int)gridDim.x, partials, f.sc, f.op, f.flexible, f.its);
+}
+
+// partial dots: d0 = a0.b0, d1 = a1.b1, d2 = a2.b2 (null pairs skipped); FIN: the last
+// block finalizes (FinArgs)
+template <bool FIN>
+__global__ void __launch_bounds__(RB) k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
+                                             const double* __restrict__ a1, const double* __restrict__ b1,
+                                             const double* __restrict__ a2, const double* __restrict__ b2,
+                                             double* partials, FinArgs fin) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    v[0] = fma(a0[i], b0[i], v[0]);
+    if (a1) v[1] = fma(a1[i], b1[i], v[1]);
+    if (a2) v[2] = fma(a2[i], b2[i], v[2]);
+  }
+  block_reduce_store<3>(v, partials);
+  if (FIN) finalize_last(partials, fin);
+}
+
+// x += alpha p ; r -= alpha q ; partial ||r||^2 (FIN: the last block finalizes)
+template <bool FIN>
+__global__ void __launch_bounds__(RB) k_axpy2(int64_t n, const double* __restrict__ sc, double* __restrict__ x,
+                                              const double* __restrict__ p, double* __restrict__ r,
+                                              const double* __restrict__ q, double* partials, FinArgs fin) {
+  const double alpha = sc[SC_ALPHA];
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    x[i] = fma(alpha, p[i], x[i]);
+    double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    v[0] = fma(ri, ri, v[0]);
+  }
+  block_reduce_store<1>(v, partials);
+  if (FIN) finalize_last(partials, fin);
+}
+
 void vec_dots(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1, const double* a2,
               const double* b2, double* partials, cudaStream_t s) {
-  k_dots<<<NBLK, RB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, partials);
+  k_dots<false><<<NBLK, RB, 0, s>>>(n, a0, b0, a1, b1, a2, b2, partials, FinArgs{});
+  DD_CHECK_LAUNCH();
+}
+void vec_dots_fin(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1,
+                  double* partials, double* sc, int op, int flexible, unsigned* ticket, cudaStream_t s,
+                  const int* its) {
+  k_dots<true><<<NBLK, RB, 0, s>>>(n, a0, b0, a1, b1, nullptr, nullptr, partials,
+                                   FinArgs{sc, op, flexible, its, ticket});
   DD_CHECK_LAUNCH();
 }
 void vec_finalize(const double* partials, double* sc, int op, int flexible, cudaStream_t s, const int* its) {
@@ -122,7 +161,12 @@ void vec_finalize(const double* partials, double* sc, int op, int flexible, cuda
 }
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
                cudaStream_t s) {
-  k_axpy2<<<NBLK, RB, 0, s>>>(n, sc, x, p, r, q, partials);
+  k_axpy2<false><<<NBLK, RB, 0, s>>>(n, sc, x, p, r, q, partials, FinArgs{});
+  DD_CHECK_LAUNCH();
+}
+void vec_axpy2_fin(int64_t n, double* sc, double* x, const double* p, double* r, const double* q, double* partials,
+                   unsigned* ticket, cudaStream_t s) {
+  k_axpy2<true><<<NBLK, RB, 0, s>>>(n, sc, x, p, r, q, partials, FinArgs{sc, FIN_RR, 0, nullptr, ticket});
   DD_CHECK_LAUNCH();
 }
 
@@ -189,12 +233,15 @@ constexpr int PT = 4;  // rows per thread of the row-blocked deflation update
 // entries there are staged in shared memory as df64, warp w walks the columns
 // c = w, w + RB/32, ... over the block's rows (eight coalesced loads in flight per lane,
 // two sums per lane) and needs one warp reduction per column; the block writes wpart[b][c].
-// The last block to finish (a ticket counter, reset by that block) reduces wpart with all
-// of its threads: thread (c, s) sums column c over a fixed segment s of the blocks, sixteen
-// loads in flight at a time, and the segments are added in order; then Ginv is applied the
-// same way. The reduction order depends only on n and k, not on which block ends last.
-constexpr int WD_GRID = 4 * 152;   // blocks of the deflation dots: four per SM, one wave
+// The partials are then reduced in two levels, each by the last block to arrive (ticket
+// counters, reset by that block): the last block of each group of WD_GROUP blocks sums
+// the group's partials, and the last group sums the groups' sums and applies Ginv. In
+// both, thread (c, s) adds column c over a fixed segment s of its inputs with all loads
+// in flight, and the segments are added in order, so the reduction order depends only on
+// n and k, not on which blocks end last.
+constexpr int WD_GRID = 6 * 152;   // blocks of the deflation dots: six per SM, one wave
 constexpr int WD_MAXROWS = 4096;   // rows per block at most (32 KiB of staged df64)
+constexpr int WD_GROUP = 32;       // blocks per first-level reduction group
 
 static int64_t wd_rows(int64_t n, int nb) { return ((n + nb - 1) / nb + 31) / 32 * 32; }
 
@@ -203,8 +250,44 @@ int defl_df_blocks(int64_t n) {
   nb = std::max<int64_t>(nb, (n + WD_MAXROWS - 1) / WD_MAXROWS);
   return (int)std::max<int64_t>(nb, 1);
 }
+__host__ __device__ static int wd_groups(int nb) { return (nb + WD_GROUP - 1) / WD_GROUP; }
+int defl_df_part_rows(int64_t n) {
+  const int nb = defl_df_blocks(n);
+  return nb + wd_groups(nb);
+}
+int defl_df_tickets(int64_t n) { return 1 + wd_groups(defl_df_blocks(n)); }
 
-__global__ void __launch_bounds__(RB) k_wdots7(int64_t n, int64_t rows, int k, const df64* __restrict__ V,
+// sum over i in [i0, i1) of src[i * MAXK + c], sixteen loads in flight, added in index order
+__device__ __forceinline__ double wd_segment_sum(const double* src, int c, int i0, int i1) {
+  double sum = 0.0;
+  for (int i = i0; i < i1; i += 16) {
+    double e[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) e[u] = i + u < i1 ? __ldcg(&src[(int64_t)(i + u) * MAXK + c]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) sum += e[u];
+  }
+  return sum;
+}
+
+// d[c] = sum over i in [0, m) of src[i][c] for c < k by the whole block (see above)
+__device__ __forceinline__ void wd_reduce(const double* src, int m, int k, double* part, double* d) {
+  const int t = threadIdx.x;
+  const int ns = max(1, min(8, RB / k));
+  if (t < ns * k) {
+    const int c = t % k, sg = t / k;
+    part[t] = wd_segment_sum(src, c, sg * m / ns, (sg + 1) * m / ns);
+  }
+  __syncthreads();
+  if (t < k) {
+    double sum = 0.0;
+    for (int sg = 0; sg < ns; ++sg) sum += part[sg * k + t];
+    d[t] = sum;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(RB) k_wdots8(int64_t n, int64_t rows, int k, const df64* __restrict__ V,
                                                int64_t ld, const double* __restrict__ v, double* wpart,
                                                unsigned* __restrict__ ticket, const double* __restrict__ Ginv,
                                                double* __restrict__ mu) {
@@ -241,58 +324,58 @@ __global__ void __launch_bounds__(RB) k_wdots7(int64_t n, int64_t rows, int k, c
     }
     if (lane == 0) wpart[(int64_t)blockIdx.x * MAXK + c] = df64_to_double_bits(x);
   }
+  // first level: the last block of the group sums the group's partials
+  const int nb = (int)gridDim.x, ng = wd_groups(nb);
+  const int g = blockIdx.x / WD_GROUP, gb0 = g * WD_GROUP, gn = min(nb, gb0 + WD_GROUP) - gb0;
+  double* gpart = wpart + (int64_t)nb * MAXK;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(&ticket[1 + g], 1u) == (unsigned)gn - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const int nb = (int)gridDim.x;
-  const int ns = max(1, min(8, RB / k));  // segments per column
+  wd_reduce(wpart + (int64_t)gb0 * MAXK, gn, k, part, d);
+  for (int c = threadIdx.x; c < k; c += RB) gpart[(int64_t)g * MAXK + c] = d[c];
+  if (threadIdx.x == 0) ticket[1 + g] = 0u;
+  // second level: the last group sums the groups and applies Ginv
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ticket[0], 1u) == (unsigned)ng - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  wd_reduce(gpart, ng, k, part, d);
   const int t = threadIdx.x;
+  const int ns = max(1, min(8, RB / k));
   if (t < ns * k) {
-    const int c = t % k, s = t / k;
-    const int b1 = (s + 1) * nb / ns;
-    int b = s * nb / ns;
+    // row a of Ginv over the c-segment sg, all loads in flight
+    const int a = t % k, sg = t / k;
+    const int c0 = sg * k / ns, c1 = (sg + 1) * k / ns;
     double sum = 0.0;
-    for (; b + 16 <= b1; b += 16) {
+    for (int c = c0; c < c1; c += 16) {
       double e[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) e[u] = __ldcg(&wpart[(int64_t)(b + u) * MAXK + c]);
+      for (int u = 0; u < 16; ++u) e[u] = c + u < c1 ? Ginv[a * k + c + u] : 0.0;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) sum += e[u];
+      for (int u = 0; u < 16; ++u)
+        if (c + u < c1) sum = fma(e[u], d[c + u], sum);
     }
-    for (; b < b1; ++b) sum += __ldcg(&wpart[(int64_t)b * MAXK + c]);
     part[t] = sum;
   }
   __syncthreads();
   if (t < k) {
     double sum = 0.0;
-    for (int s = 0; s < ns; ++s) sum += part[s * k + t];
-    d[t] = sum;
-  }
-  __syncthreads();
-  if (t < ns * k) {
-    const int a = t % k, s = t / k;
-    const int c1 = (s + 1) * k / ns;
-    double sum = 0.0;
-    for (int c = s * k / ns; c < c1; ++c) sum = fma(Ginv[a * k + c], d[c], sum);
-    part[t] = sum;
-  }
-  __syncthreads();
-  if (t < k) {
-    double sum = 0.0;
-    for (int s = 0; s < ns; ++s) sum += part[s * k + t];
+    for (int sg = 0; sg < ns; ++sg) sum += part[sg * k + t];
     mu[t] = sum;
   }
-  if (t == 0) *ticket = 0u;
+  if (t == 0) ticket[0] = 0u;
 }
 
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
                 double* mu, unsigned* ticket, cudaStream_t s) {
   if (k == 0) return;
   const int nb = defl_df_blocks(n);
-  k_wdots7<<<nb, RB, 0, s>>>(n, wd_rows(n, nb), k, V, ld, v, wpart, ticket, Ginv, mu);
+  k_wdots8<<<nb, RB, 0, s>>>(n, wd_rows(n, nb), k, V, ld, v, wpart, ticket, Ginv, mu);
   DD_CHECK_LAUNCH();
 }
 

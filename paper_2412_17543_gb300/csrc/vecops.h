@@ -24,14 +24,23 @@ void vec_finalize(const double* partials, double* sc, int op, int flexible, cuda
                   const int* its = nullptr);
 void vec_axpy2(int64_t n, const double* sc, double* x, const double* p, double* r, const double* q, double* partials,
                cudaStream_t s);
+// the same with vec_finalize done by the last block of the launch (ticket: a device counter,
+// zero between launches; the calls sharing one ticket must be ordered on one stream)
+void vec_dots_fin(int64_t n, const double* a0, const double* b0, const double* a1, const double* b1,
+                  double* partials, double* sc, int op, int flexible, unsigned* ticket, cudaStream_t s,
+                  const int* its = nullptr);
+void vec_axpy2_fin(int64_t n, double* sc, double* x, const double* p, double* r, const double* q, double* partials,
+                   unsigned* ticket, cudaStream_t s);
 void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
 // out = in - mean(in) (in == out allowed); partials: [NBLK * MAXDOT] scratch
 void vec_sub_mean(int64_t n, const double* in, double* out, double* partials, cudaStream_t s);
 // deflation with the basis stored as df64 (float pairs), and the conversion
 void to_df64(int64_t n, const double* in, df64* out, cudaStream_t s);
-// mu with the basis as df64 (V: k columns, stride ld); wpart: [defl_df_blocks(n)][MAXK]
+// mu with the basis as df64 (V: k columns, stride ld); wpart: [defl_df_part_rows(n)][MAXK],
+// ticket: [defl_df_tickets(n)] counters, zero before the first call (each call leaves them zero)
 int defl_df_blocks(int64_t n);
-// ticket: a device counter that is 0 between launches (the kernel resets it)
+int defl_df_part_rows(int64_t n);  // rows of MAXK doubles that wpart needs
+int defl_df_tickets(int64_t n);    // ticket counters (zeroed once) that the dots need
 void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, const double* Ginv, double* wpart,
                 double* mu, unsigned* ticket, cudaStream_t s);
 void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
