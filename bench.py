@@ -189,14 +189,13 @@ class OracleSample:
     GPU arm's setup is); one step solves one right-hand side of the workload's sequence (two
     triangular solves that stream the factor once)."""
 
-    def __init__(self, workload: str, wl, sample_n: int = 48):
+    def __init__(self, workload: str, wl, sample_n: int = 48, n: int | None = None):
         from oracle import cholesky, q1
-        from workload import make_mesh
-        full = workload_mesh(workload)
+        full = workload_mesh(workload, n=n)  # the mesh the GPU arm solves (--n overrides the size)
         self.n_full = full.nx
         self.sample_n = min(sample_n, full.nx)
         self.is_full = self.sample_n == full.nx
-        self.mesh = full if self.is_full else make_mesh(self.sample_n, wl["sub"], wl["ratio"], wl["max_aspect"])
+        self.mesh = full if self.is_full else workload_mesh(workload, n=self.sample_n)
         t0 = time.perf_counter()
         self.ch = cholesky.factor_mesh(self.mesh, q1.assemble(self.mesh))
         self.t_fac = time.perf_counter() - t0
@@ -252,7 +251,7 @@ def cpu_baseline(args, wl, nsolve=3, gpu_x=None, steps_from=0):
     measured sample rate scaled to the workload (marked as an estimate). When the sample is
     the workload, the same time steps' GPU solutions (gpu_x) are compared with the oracle's:
     relative 2-norm error of the full free-node solution per step."""
-    smp = OracleSample(args.workload, wl, args.cpu_baseline_n)
+    smp = OracleSample(args.workload, wl, args.cpu_baseline_n, args.n)
     t_sol, xs = smp.run(nsolve, start=steps_from)
     ext = smp.extrapolation(t_sol)
     out = {"value": ext["solves_per_s"] if ext else 1.0 / t_sol, "unit": "solves/s", "cores": oracle_threads(),
@@ -276,7 +275,7 @@ def reference_arm(args, wl, world, rank):
     estimate."""
     if rank != 0:
         return None
-    smp = OracleSample(args.workload, wl, args.cpu_baseline_n)
+    smp = OracleSample(args.workload, wl, args.cpu_baseline_n, args.n)
     t_sol, _ = smp.run(args.steps, warmup=args.warmup)
     sec = t_sol * args.steps
     value = args.steps / sec
@@ -319,9 +318,19 @@ DF64_MADD_INSTR = 12
 DF64_TFLOPS_PEAK = 2 * FP32_INSTR_PEAK / DF64_MADD_INSTR / 1e12
 
 
-def kernel_table(prof, hbm):
+def tensor_peak(kind: str):
+    """Dense tensor peak of the ensemble N_i kernel's operand type: the measured bf16 cuBLAS
+    rate (burst), times the nominal tf32 : bf16 ratio (1.1 : 2.25 PFLOP/s) for tf32."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = float(json.load(open(p))["bf16_tflops"]) if os.path.exists(p) else 1900.0
+    return bf16 * (1.1 / 2.25) if kind == "tf32" else bf16
+
+
+def kernel_table(prof, hbm, tensor_kind=None):
     """Per profiled class: device time, and against its roofline the achieved rate on
-    algorithmic bytes (HBM) or algorithmic flops (df64 arithmetic on the FP32 pipes)."""
+    algorithmic bytes (HBM) or algorithmic flops (df64 arithmetic on the FP32 pipes; for the
+    ensemble N_i products the tensor-core work as issued, against the tensor peak of its
+    operand type)."""
     out = {}
     for name, v in prof.items():
         ms, n, ab, af = v
@@ -332,7 +341,13 @@ def kernel_table(prof, hbm):
             e.update(alg_bytes=ab, achieved_gbs=gbs, hbm_frac=gbs / hbm)
         if n and af:
             tf = af / (avg / 1e3) / 1e12
-            e.update(alg_flops=af, achieved_tflops=tf, alu_peak_tflops=DF64_TFLOPS_PEAK, alu_frac=tf / DF64_TFLOPS_PEAK)
+            if name == "ens_N" and tensor_kind:
+                pk = tensor_peak(tensor_kind)
+                e.update(tensor_flops_issued=af, tensor_tflops=tf, tensor_peak_tflops=pk,
+                         tensor_kind=tensor_kind, tensor_frac=tf / pk)
+            else:
+                e.update(alg_flops=af, achieved_tflops=tf, alu_peak_tflops=DF64_TFLOPS_PEAK,
+                         alu_frac=tf / DF64_TFLOPS_PEAK)
         out[name] = e
     return out
 
@@ -455,7 +470,7 @@ def ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, see
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl, args.cpu_baseline_steps)
     if rank == 0:
-        per_kernel = kernel_table(prof, hbm)
+        per_kernel = kernel_table(prof, hbm, {2: "tf32", 3: "bf16"}.get(S.info["ens_nmm"]))
         line = {"metric": ENS_METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64 (df64 Schur, f32 BDDC)", "data": "synthetic",

@@ -144,6 +144,9 @@ struct dd_recycle {
   double *W = nullptr, *AW = nullptr, *MAW = nullptr;       // [kmax][n_gamma]
   double *W2 = nullptr, *AW2 = nullptr, *MAW2 = nullptr;    // next basis
   dd::df64 *Wd = nullptr, *AWd = nullptr;                   // df64 copies of W, AW (deflation kernels)
+  float* Wf = nullptr;        // FP32 copy of W when W holds FP32-representable values (FP32 preconditioner)
+  bool wf_valid = false;      // the per-iteration update streams Wf
+  int* rflag = nullptr;       // device flag of the rounding kernel
   double* Ginv = nullptr;                                   // [kmax*kmax] (W^T A W)^{-1}
   double* WWinv = nullptr;                                  // [kmax*kmax] (W^T W)^{-1}
   std::vector<double> theta;

@@ -88,6 +88,16 @@ void select_op(dd_ctx* c, int which, const SymTiles& S, const int64_t* voff, voi
   }
   check_err(c, s);
   o.kind = kinds[best];
+  if (which == BOP_N1 && o.kind != DD_ENS_SIMT) {
+    // tensor-core work of one level-1 launch as issued: per (subdomain, 128-row block) and
+    // 32-wide k chunk, 128 x 32 x N multiply-adds with N = 64 + 32 (3xTF32: a_hi [b_hi b_lo],
+    // a_lo b_hi) or 96 + 64 + 32 (BF16x3: the six slice products i + j <= 2)
+    const double nsum = o.kind == DD_ENS_BF16X3 ? 192.0 : 96.0;
+    double fl = 0.0;
+    for (int i = 0; i < S.count; ++i)
+      fl += (double)((nh[i] + 127) / 128) * ((nh[i] + 31) / 32) * 128.0 * 32.0 * nsum * 2.0;
+    c->prof_flops[DD_PROF_ENS_N] = fl;
+  }
 }
 
 

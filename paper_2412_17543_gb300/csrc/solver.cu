@@ -1030,6 +1030,33 @@ void refresh_df(dd_ctx* c, dd_recycle* st, cudaStream_t s) {
   to_df64(kn, st->AW, st->AWd, s);
 }
 
+// With an FP32 preconditioner the per-iteration update p = z + beta p - W mu streams the
+// basis as FP32: W is rounded to FP32-representable values (another basis of the same span
+// up to rounding; deflation is exact for whichever basis it uses) and A W is recomputed for
+// the rounded basis by the Schur operator (df64), so that the projection stays exact for
+// the stored W. Single sequences only (the ensemble streams W in df64). Returns whether W
+// changed; with `force` A W is recomputed in any case.
+bool use_f32_basis(const dd_ctx* c, const dd_recycle* st) {
+  return c->opt.precond_prec == DD_PREC_FP32 && st->nrhs == 0;
+}
+bool basis_to_f32(dd_ctx* c, dd_recycle* st, cudaStream_t s, bool force) {
+  const int64_t n = c->n_gamma;
+  const int k = st->k;
+  if (!st->Wf) {
+    st->Wf = st->arena.alloc<float>((size_t)st->kmax * n);
+    st->rflag = st->arena.alloc<int>(1);
+  }
+  DD_CUDA(cudaMemsetAsync(st->rflag, 0, sizeof(int), s));
+  round_to_f32((int64_t)k * n, st->W, st->Wf, st->rflag, s);
+  int changed = 0;
+  DD_CUDA(cudaMemcpyAsync(&changed, st->rflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  if (changed || force)
+    for (int j = 0; j < k; ++j) schur_apply(c, st->W + (size_t)j * n, st->AW + (size_t)j * n, s);
+  st->wf_valid = true;
+  return changed != 0;
+}
+
 // Device work space of the recycling update, allocated once per recycle state.
 void recycle_work(dd_recycle* st) {
   if (st->rptr) return;
@@ -1138,6 +1165,7 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
     std::swap(st->W, st->W2);
     std::swap(st->AW, st->AW2);
     st->k = kn;
+    st->wf_valid = false;
     if (st->strategy == DD_B1 && kn >= R) st->frozen = true;
     refresh_gram(c, st, s);
     return;
@@ -1278,14 +1306,23 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
   double* const* PO = reinterpret_cast<double* const*>(st->rptr);
   df64* const* PD = reinterpret_cast<df64* const*>(st->rptr);
-  lincomb_src(n, m, kn, PV, st->rY, PO + 3 * REC_MAXM, PD + 6 * REC_MAXM, true, s);
-  lincomb_src(n, m, kn, PV + REC_MAXM, st->rY, PO + 4 * REC_MAXM, PD + 7 * REC_MAXM, true, s);
+  const bool f32 = use_f32_basis(c, st);
+  lincomb_src(n, m, kn, PV, st->rY, PO + 3 * REC_MAXM, f32 ? nullptr : PD + 6 * REC_MAXM, true, s);
+  if (!f32) lincomb_src(n, m, kn, PV + REC_MAXM, st->rY, PO + 4 * REC_MAXM, PD + 7 * REC_MAXM, true, s);
   lincomb_src(n, m, kn, PV + 2 * REC_MAXM, st->rY, PO + 5 * REC_MAXM, nullptr, gh_df, s);
   std::swap(st->W, st->W2);
   std::swap(st->AW, st->AW2);
   std::swap(st->MAW, st->MAW2);
   st->k = kn;
-  refresh_gram(c, st, s, true);
+  if (f32) {
+    // W rounded to FP32 values and A W recomputed for it; M^{-1} A W stays the combination
+    // (it only enters the next harmonic Ritz problem, at the FP32 preconditioner's accuracy)
+    basis_to_f32(c, st, s, true);
+    refresh_gram(c, st, s);
+  } else {
+    st->wf_valid = false;
+    refresh_gram(c, st, s, true);
+  }
 }
 
 
@@ -1296,10 +1333,11 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   const int k = st ? st->k : 0;
   const df64* Wd = k ? st->Wd : nullptr;
   const df64* AWd = k ? st->AWd : nullptr;
+  const float* Wf = (k && st->wf_valid) ? st->Wf : nullptr;
   DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
   // deflation of one iteration streams the df64 copies of A W and W once each, and z, p
   // (read) and p (written)
-  c->prof_bytes[DD_PROF_DEFL] = (2.0 * k + 3.0) * 8.0 * (double)n;
+  c->prof_bytes[DD_PROF_DEFL] = ((double)k * (8.0 + (Wf ? 4.0 : 8.0)) + 3.0 * 8.0) * (double)n;
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
@@ -1328,7 +1366,10 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     {
       ProfScope pd(c, k ? DD_PROF_DEFL : DD_PROF_COUNT, bs);
       if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, c->wticket, bs);
-      defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
+      if (Wf)
+        defl_update_f(n, k, Wf, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
+      else
+        defl_update_df(n, k, Wd, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
     }
     schur_apply(c, c->p, c->q, bs);
     vec_dots_fin(n, c->p, c->q, nullptr, nullptr, c->partials, c->sc, FIN_PQ, 0, c->fticket, bs);
@@ -1354,6 +1395,7 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
                                      (uint64_t)flex,
                                      (uint64_t)(uintptr_t)Wd,
                                      (uint64_t)(uintptr_t)AWd,
+                                     (uint64_t)(uintptr_t)Wf,
                                      (uint64_t)(uintptr_t)(st ? st->Ginv : nullptr),
                                      (uint64_t)(uintptr_t)(st ? st->WWinv : nullptr),
                                      (uint64_t)(uintptr_t)(st ? st->P : nullptr),
@@ -1604,7 +1646,13 @@ dd_status dd_recycle_import(dd_ctx* c, const void* host_buf, size_t bytes, dd_re
       DD_CUDA(cudaMemcpy(st->Ginv, p, k * k * 8, cudaMemcpyHostToDevice));
       p += k * k * 8;
       DD_CUDA(cudaMemcpy(st->WWinv, p, k * k * 8, cudaMemcpyHostToDevice));
-      refresh_df(c, st, nullptr);
+      // a basis saved from an FP32-basis state is FP32-representable and comes back as it
+      // was; any other is rounded here and its A W and Gram matrices recomputed
+      if (use_f32_basis(c, st) && (st->strategy == DD_B3 || st->strategy == DD_B4) &&
+          basis_to_f32(c, st, nullptr, false))
+        refresh_gram(c, st, nullptr);
+      else
+        refresh_df(c, st, nullptr);
       DD_CUDA(cudaStreamSynchronize(nullptr));
     }
   });

@@ -436,6 +436,83 @@ void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* m
   DD_CHECK_LAUNCH();
 }
 
+// The same update with the basis stored as FP32 values (the basis is rounded to
+// FP32-representable numbers when it is formed, so these are its exact entries): the
+// products w * mu run as float x df64 in df64 accumulation.
+__global__ void __launch_bounds__(RB) k_pupdate_f(int64_t n, int k, const float* __restrict__ W, int64_t ld,
+                                                  const double* __restrict__ mu, const double* __restrict__ z,
+                                                  double* __restrict__ y, const double* __restrict__ sc, int beta_idx,
+                                                  double sign_w) {
+  __shared__ df64 m[MAXK];
+  for (int c = threadIdx.x; c < k; c += blockDim.x) m[c] = dbl_to_df(sign_w * mu[c]);
+  __syncthreads();
+  const double beta = beta_idx >= 0 ? sc[beta_idx] : 0.0;
+  const int64_t i0 = (int64_t)blockIdx.x * PT * RB + threadIdx.x;
+  df64_acc acc[PT];
+  int c = 0;
+  for (; c + 3 < k; c += 4) {
+    // the four columns' entries are loaded before any product
+    float e[4][PT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float* col = W + (int64_t)(c + q) * ld;
+#pragma unroll
+      for (int r = 0; r < PT; ++r) {
+        const int64_t i = i0 + (int64_t)r * RB;
+        e[q][r] = i < n ? col[i] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const df64 mq = m[c + q];
+#pragma unroll
+      for (int r = 0; r < PT; ++r) acc[r].fma(df64{e[q][r], 0.f}, mq);
+    }
+  }
+  for (; c < k; ++c) {
+    const float* col = W + (int64_t)c * ld;
+    const df64 mc = m[c];
+#pragma unroll
+    for (int r = 0; r < PT; ++r) {
+      const int64_t i = i0 + (int64_t)r * RB;
+      if (i < n) acc[r].fma(df64{col[i], 0.f}, mc);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PT; ++r) {
+    const int64_t i = i0 + (int64_t)r * RB;
+    if (i < n) {
+      const double v = (z ? z[i] : 0.0) + (beta_idx >= 0 ? beta * y[i] : (z ? 0.0 : y[i]));
+      y[i] = v + df64_to_double(acc[r].get());
+    }
+  }
+}
+
+void defl_update_f(int64_t n, int k, const float* W, int64_t ld, const double* mu, const double* z, double* y,
+                   const double* sc, int beta_idx, double sign_w, cudaStream_t s) {
+  const int64_t blocks = (n + (int64_t)PT * RB - 1) / ((int64_t)PT * RB);
+  k_pupdate_f<<<(unsigned)std::max<int64_t>(blocks, 1), RB, 0, s>>>(n, k, W, ld, mu, z, y, sc, beta_idx, sign_w);
+  DD_CHECK_LAUNCH();
+}
+
+// wf = w rounded to FP32; where that changes w, w takes the rounded value and *changed = 1
+__global__ void k_round_f32(int64_t n, double* __restrict__ w, float* __restrict__ wf, int* __restrict__ changed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i];
+    const float f = (float)v;
+    wf[i] = f;
+    if ((double)f != v) {
+      w[i] = (double)f;
+      *changed = 1;
+    }
+  }
+}
+void round_to_f32(int64_t n, double* w, float* wf, int* changed, cudaStream_t s) {
+  if (n == 0) return;
+  k_round_f32<<<NBLK * 2, RB, 0, s>>>(n, w, wf, changed);
+  DD_CHECK_LAUNCH();
+}
+
 // ---------------------------------------------------------------------------
 // tall-skinny products for the recycling update
 // ---------------------------------------------------------------------------

@@ -45,6 +45,11 @@ void defl_mu_df(int64_t n, int k, const df64* V, int64_t ld, const double* v, co
                 double* mu, unsigned* ticket, cudaStream_t s);
 void defl_update_df(int64_t n, int k, const df64* W, int64_t ld, const double* mu, const double* z, double* y,
                     const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+// the update with an FP32-stored basis (exact entries of a basis rounded to FP32 values)
+void defl_update_f(int64_t n, int k, const float* W, int64_t ld, const double* mu, const double* z, double* y,
+                   const double* sc, int beta_idx, double sign_w, cudaStream_t s);
+// wf = (float)w; w takes the rounded values; *changed = 1 if any entry changed (not cleared here)
+void round_to_f32(int64_t n, double* w, float* wf, int* changed, cudaStream_t s);
 void gram(int64_t n, int na, const double* const* X, int nb, const double* const* Y, double* part, double* C,
           cudaStream_t s);
 void lincomb(int64_t n, int m, const double* const* V, const double* Yc, int kc, double* const* out, cudaStream_t s);
