@@ -526,6 +526,40 @@ def ablation(args, wl, torch, pkg, dev, mesh, seed, rtol):
     print(json.dumps(line), flush=True)
 
 
+def tau_sweep(args, wl, torch, pkg, dev, mesh, seed, rtol):
+    """The adaptivity study of Sect. 6 on this workload: the threshold tau of the face
+    eigenproblems (eq. 10) in {2, 2.5, 3, 3.5} and the workload's own, with cardinality and
+    diagonal-stiffness weights, each with B4 recycling (k of the workload) on the mixed-
+    precision path; its own setup per row, W untimed and K timed steps of the same sequence.
+    Reports the adaptive constraints, the coarse problem size, iterations min-max(avg), ms per
+    step (time per iteration), setup seconds and the largest kept harmonic Ritz value."""
+    nsteps = args.warmup + args.steps
+    F_dev = torch.from_numpy(load_sequence(mesh, seed, nsteps)).to(dev)
+    rows = []
+    taus = sorted({2.0, 2.5, 3.0, 3.5, float(wl.get("tau", 10.0))})
+    for weights in ("card", "diag"):
+        for tau in taus:
+            o = dict(solver_options(dict(wl, adaptive=1, tau=tau), True), weights=weights)
+            t0 = time.perf_counter()
+            S = pkg.Solver(mesh, **o)
+            setup_s = time.perf_counter() - t0
+            keep = {}
+            sec, stats, _ = run_arm(torch, S, F_dev, args.warmup, args.steps, wl["k"], "B4", rtol, 1, None,
+                                    keep_state=keep)
+            its = [st["iters"] for st in stats]
+            th = keep["recycle"]["theta"]
+            rows.append({"weights": weights, "tau": tau, "n_adaptive": S.info["n_adaptive"],
+                         "n_coarse": S.info["n_coarse"], "iters_min_max_avg": [min(its), max(its), sum(its) / len(its)],
+                         "ms_per_step": 1e3 * sec / args.steps, "ms_per_iter": 1e3 * sec / sum(its),
+                         "solves_per_s": args.steps / sec, "setup_s": setup_s,
+                         "theta_max": float(th.max()) if len(th) else None})
+            S.close()
+    line = {"metric": "tau sweep: adaptive BDDC threshold x weights with B4 recycling (mixed precision)",
+            "workload": args.workload, "n": wl["n"], "k": wl["k"], "steps": args.steps, "warmup": args.warmup,
+            "rtol": rtol, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,6 +577,8 @@ def main():
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
     ap.add_argument("--ablation", action="store_true",
                     help="print the adaptive x recycling table at equal precision instead of the bench line")
+    ap.add_argument("--tau-sweep", action="store_true",
+                    help="print the adaptivity threshold x weights table (Sect. 6) instead of the bench line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--ens-nmm", default="auto", choices=["auto", "simt", "tc", "bf16x3"],
@@ -575,6 +611,8 @@ def main():
         return ensemble_main(args, wl, torch, pkg, dist, world, rank, local, dev, mesh, seed, rtol)
     if args.ablation:
         return ablation(args, wl, torch, pkg, dev, mesh, seed, rtol)
+    if args.tau_sweep:
+        return tau_sweep(args, wl, torch, pkg, dev, mesh, seed, rtol)
     nsteps = args.warmup + args.steps
     t0 = time.perf_counter()
     F_host = torch.from_numpy(load_sequence(mesh, seed, nsteps))

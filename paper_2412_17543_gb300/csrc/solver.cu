@@ -1307,7 +1307,9 @@ void recycle_update(dd_ctx* c, dd_recycle* st, int l, cudaStream_t s) {
   double* const* PO = reinterpret_cast<double* const*>(st->rptr);
   df64* const* PD = reinterpret_cast<df64* const*>(st->rptr);
   const bool f32 = use_f32_basis(c, st);
-  lincomb_src(n, m, kn, PV, st->rY, PO + 3 * REC_MAXM, f32 ? nullptr : PD + 6 * REC_MAXM, true, s);
+  // an FP32-valued basis is formed in FP32 accumulation: it is rounded to floats next, and
+  // whichever basis results, A W is then computed for exactly it
+  lincomb_src(n, m, kn, PV, st->rY, PO + 3 * REC_MAXM, f32 ? nullptr : PD + 6 * REC_MAXM, !f32, s);
   if (!f32) lincomb_src(n, m, kn, PV + REC_MAXM, st->rY, PO + 4 * REC_MAXM, PD + 7 * REC_MAXM, true, s);
   lincomb_src(n, m, kn, PV + 2 * REC_MAXM, st->rY, PO + 5 * REC_MAXM, nullptr, gh_df, s);
   std::swap(st->W, st->W2);

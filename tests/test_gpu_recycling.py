@@ -100,3 +100,33 @@ def test_reorthogonalized_recycled_solves_match_oracle(schur, pre, flex):
         if schur == "fp64":
             assert abs(st["iters"] - info.iters) <= 1, (t, st["iters"], info.iters)
     S.close()
+
+
+def test_fp32_valued_basis_is_exact_for_its_own_span():
+    """With an FP32 preconditioner the recycled basis is rounded to FP32-representable values
+    when it is formed and A W recomputed for it (the update streams W as floats). The
+    checkpoint holds the state as the solver uses it: every entry of W is a float, A W is
+    the Schur operator applied to that W bit for bit, and the solves match the oracle."""
+    import struct
+    m = make_mesh(16, 8, 1.08, 20.0)
+    F = load_sequence(m, 4, 5)
+    ch = cholesky.factor_mesh(m)
+    S = P.Solver(m, **dict(KINDS, schur_prec="df64", precond_prec="fp32", flexible=1))
+    rec = S.recycler(6, "B4")
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        xe = ch.solve(f)
+        assert np.linalg.norm(x.cpu().numpy() - xe) <= 1e-7 * np.linalg.norm(xe), t
+    blob = rec.export()
+    fmt = "<8sq6id"
+    _, n, kmax, _, k, _, _, ntheta, _ = struct.unpack_from(fmt, blob, 0)
+    assert k > 0
+    off = struct.calcsize(fmt) + 8 * ntheta + 8 * n  # theta, previous solution
+    W = np.frombuffer(blob, dtype=np.float64, count=k * n, offset=off).reshape(k, n)
+    AW = np.frombuffer(blob, dtype=np.float64, count=k * n, offset=off + 8 * k * n).reshape(k, n)
+    assert np.array_equal(W, W.astype(np.float32).astype(np.float64))
+    for j in range(k):
+        y = S.schur_apply(T(W[j])).cpu().numpy()
+        assert np.array_equal(y, AW[j]), j
+    rec.close()
+    S.close()
