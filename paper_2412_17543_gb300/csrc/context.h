@@ -59,6 +59,9 @@ struct dd_ctx {
   // second (high-priority) stream of the BDDC coarse correction and its fork/join events
   cudaStream_t s_coarse = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // two more side streams for the independent pieces of the level-2 BDDC, and their events
+  cudaStream_t s_aux[2] = {nullptr, nullptr};
+  cudaEvent_t ev_aux[4] = {nullptr, nullptr, nullptr, nullptr};
   // profiling: events around timed launches, harvested after a synchronization
   bool prof_on = false;
   struct Pending {
@@ -102,6 +105,10 @@ struct dd_ctx {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (s_coarse) cudaStreamDestroy(s_coarse);
+    for (auto e : ev_aux)
+      if (e) cudaEventDestroy(e);
+    for (auto a : s_aux)
+      if (a) cudaStreamDestroy(a);
     for (auto& p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);

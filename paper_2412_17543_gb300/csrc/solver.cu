@@ -242,22 +242,34 @@ void recover(dd_ctx* c, const double* f, const double* xg, double* x, cudaStream
   launch_scatter_recover(c->mesh, xg, c->w.sI, x, s);
 }
 
+// A side stream and the two events that fork work onto it and join it back.
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t f = nullptr, j = nullptr;
+  cudaStream_t begin(cudaStream_t s) const {
+    if (!side) return s;
+    DD_CUDA(cudaEventRecord(f, s));
+    DD_CUDA(cudaStreamWaitEvent(side, f, 0));
+    return side;
+  }
+  void end(cudaStream_t s) const {
+    if (!side) return;
+    DD_CUDA(cudaEventRecord(j, side));
+    DD_CUDA(cudaStreamWaitEvent(s, j, 0));
+  }
+};
+
 // BDDC of one level on an interface residual r -> z, with a coarse solver callback.
 // The coarse correction (Phi_i^T D_i R_i r, the coarse solve, Phi_i u_C) does not depend on
-// the local products N_i D_i R_i r: with `fork` it is issued on the context's high-priority
+// the local products N_i D_i R_i r: with a fork it is issued on a high-priority side
 // stream, so that its short, latency-bound launches run while the N_i product streams from
 // HBM, and the two branches meet before the weighted gather. Each kernel computes the same
 // values in either order.
 template <class CoarseFn>
 void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double* rloc, double* uloc, double* vloc,
-                double* gloc, double* gC, double* uC, CoarseFn coarse, cudaStream_t s, bool fork) {
+                double* gloc, double* gC, double* uC, CoarseFn coarse, cudaStream_t s, const Fork& fk) {
   launch_restrict(b.n_flat, b.gmap, b.D, r, rloc, s);
-  cudaStream_t sc = s;
-  if (fork) {
-    DD_CUDA(cudaEventRecord(c->ev_fork, s));
-    DD_CUDA(cudaStreamWaitEvent(c->s_coarse, c->ev_fork, 0));
-    sc = c->s_coarse;
-  }
+  cudaStream_t sc = fk.begin(s);
   launch_bgemv(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, sc);  // Phi_i^T D_i R_i r
   launch_gather(b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, sc);
   coarse(gC, uC, sc);
@@ -266,24 +278,30 @@ void bddc_apply(dd_ctx* c, const DevBDDC& b, const double* r, double* z, double*
     ProfScope pk(c, &b == &c->b1 ? DD_PROF_SYMV_N : DD_PROF_COUNT, s);
     launch_symv(b.N, b.goff, rloc, uloc, c->w.err, s);
   }
-  if (fork) {
-    DD_CUDA(cudaEventRecord(c->ev_join, sc));
-    DD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-  }
+  fk.end(s);
   launch_wgather(b.n_gamma, b.gptr, b.gidx, b.D, uloc, vloc, z, s);
 }
 
-// three-level: BDDC for the whole coarse system K_C u = g (interior correction, interface BDDC, extension)
+// three-level: BDDC for the whole coarse system K_C u = g (interior correction, interface BDDC,
+// extension). On the coarse branch it is the critical path of the preconditioner, so its
+// independent pieces run on two more side streams: u0 = K_II^{-1} g_I beside the interface
+// correction and the level-2 BDDC, and the level-3 coarse correction beside the level-2
+// local products.
 void level2_apply(dd_ctx* c, const double* g, double* u, cudaStream_t s) {
   DevLevel2& L = c->l2;
   Work& w = c->w;
+  const bool par = c->s_aux[0] != nullptr;
+  const Fork f0{par ? c->s_aux[0] : nullptr, c->ev_aux[0], c->ev_aux[1]};
+  const Fork f1{par ? c->s_aux[1] : nullptr, c->ev_aux[2], c->ev_aux[3]};
   launch_map_gather(L.n_int, L.imap, g, w.gI2, s);
-  launch_symv(L.KIIinv, L.ioff, w.gI2, w.u0I2, w.err, s);
+  const cudaStream_t s0 = f0.begin(s);
+  launch_symv(L.KIIinv, L.ioff, w.gI2, w.u0I2, w.err, s0);
   launch_bgemv_t(L.E, L.ioff, nullptr, w.gI2, L.b.goff, w.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather(L.b.n_gamma, L.b.gptr, L.b.gidx, w.rl2, g, L.gam_c64, w.r2, s);  // g[gam_c] + sum of copies
   bddc_apply(c, L.b, w.r2, w.z2, w.rloc2, w.uloc2, w.vloc2, w.gloc2, w.g3, w.u3,
              [&](const double* g3, double* u3, cudaStream_t ss) { launch_dense_gemv(L.n3, L.b.prec, L.KC3inv, g3, u3, ss); },
-             s, false);
+             s, f1);
+  f0.end(s);
   launch_bgemv(L.E, L.b.goff, L.b.gmap, w.z2, L.ioff, w.uI2, -1.0, w.u0I2, s);  // u0 - K_II^{-1} K_IG z
   launch_map_scatter(L.n_int, L.imap, w.uI2, u, s);
   launch_map_scatter(L.b.n_gamma, L.gam_c, w.z2, u, s);
@@ -299,7 +317,7 @@ void precond_apply(dd_ctx* c, const double* r, double* z, cudaStream_t s) {
                else
                  level2_apply(c, g, u, ss);
              },
-             s, c->s_coarse != nullptr);
+             s, Fork{c->s_coarse, c->ev_fork, c->ev_join});
 }
 
 // z = M^{-1} r as the PCG sees it: without a Dirichlet face the constant interface vector
@@ -811,6 +829,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       DD_CUDA(cudaStreamCreateWithPriority(&c->s_coarse, cudaStreamNonBlocking, greatest));
       DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
       DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+      for (auto& a : c->s_aux) DD_CUDA(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, greatest));
+      for (auto& e : c->ev_aux) DD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     DD_CUDA(cudaStreamSynchronize(s));
     {
