@@ -671,7 +671,17 @@ def main():
             "kernel": "k_symv<FP32> (batched constrained-Neumann N_i GEMV, eq. 9)",
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "alg_bytes_per_launch": nn[2],
             "avg_launch_ms": nn_ms, "launches": nn[1], "timing": PROF_TIMING,
-            "replay_ms_per_step": 1e3 * prof_sec / args.steps}
+            "replay_ms_per_step": 1e3 * prof_sec / args.steps,
+            "sharing": "in each BDDC application the coarse branch runs on a second stream beside this "
+                       "kernel, so the launch time above includes that sharing of the SMs and of HBM"}
+    # the same kernel alone: the setup's launch-shape tuning times back-to-back launches of it
+    # on the context's own operators (1.13 GB per launch, larger than L2) for each ring depth
+    tms = [t for t in mixed.info.get("tune_symv_ms", []) if t > 0]
+    if tms and nn[2]:
+        t_alone = min(tms)
+        a_alone = nn[2] / (t_alone / 1e3) / 1e9
+        roof["alone"] = {"avg_launch_ms": t_alone, "achieved": a_alone, "frac": a_alone / hbm,
+                         "timing": "CUDA events around back-to-back launches at setup (the tuned ring depth)"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, wl, args.cpu_baseline_steps, keep.get("x"), args.warmup)

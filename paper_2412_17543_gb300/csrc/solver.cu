@@ -1357,9 +1357,10 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
   const df64* AWd = k ? st->AWd : nullptr;
   const float* Wf = (k && st->wf_valid) ? st->Wf : nullptr;
   DD_CUDA(cudaMemsetAsync(c->sc, 0, SC_COUNT * sizeof(double), s));
-  // deflation of one iteration streams the df64 copies of A W and W once each, and z, p
-  // (read) and p (written)
-  c->prof_bytes[DD_PROF_DEFL] = ((double)k * (8.0 + (Wf ? 4.0 : 8.0)) + 3.0 * 8.0) * (double)n;
+  // deflation of one iteration streams A W (df64) and W (df64 or FP32) once each, and z, p
+  // (read) and p (written); the Krylov dots r^T z (and r^T z_old) run in the same window
+  c->prof_bytes[DD_PROF_DEFL] =
+      ((double)k * (8.0 + (Wf ? 4.0 : 8.0)) + 3.0 * 8.0 + (o.flexible ? 4.0 : 2.0) * 8.0) * (double)n;
   if (k) {
     // x_0 = x_{-1} + W (W^T A W)^{-1} W^T (b - A x_{-1})   (assures W^T r_0 = 0)
     schur_apply(c, c->xg, c->q, s);
@@ -1383,11 +1384,16 @@ dd_status pcg_solve(dd_ctx* c, dd_recycle* st, double rtol, bool record, dd_stat
     if (flex) DD_CUDA(cudaMemcpyAsync(c->zold, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, bs));
     precond_z(c, c->r, c->z, bs);
     if (rec) launch_record(c->ctl, c->z, st->Z, n, st->hmax, 1, bs);
-    vec_dots_fin(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, c->partials, c->sc, FIN_RZL, flex,
-                 c->fticket, bs, &c->ctl->its);
     {
+      // the deflation dots (AW)^T z and the Krylov dots r^T z (r^T z_old) only read z: the
+      // former run on the side stream while the latter finalize beta on the main stream
       ProfScope pd(c, k ? DD_PROF_DEFL : DD_PROF_COUNT, bs);
-      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, c->wticket, bs);
+      const Fork fk{k ? c->s_coarse : nullptr, c->ev_fork, c->ev_join};
+      const cudaStream_t sd = fk.begin(bs);
+      if (k) defl_mu_df(n, k, AWd, n, c->z, st->Ginv, c->wpart, c->mu, c->wticket, sd);
+      vec_dots_fin(n, c->r, c->z, flex ? c->r : nullptr, flex ? c->zold : nullptr, c->partials, c->sc, FIN_RZL, flex,
+                   c->fticket, bs, &c->ctl->its);
+      fk.end(bs);
       if (Wf)
         defl_update_f(n, k, Wf, n, c->mu, c->z, c->p, c->sc, SC_BETA, -1.0, bs);
       else
