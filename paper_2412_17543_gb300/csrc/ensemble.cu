@@ -241,18 +241,40 @@ void recover_b(dd_ctx* c, const df64* f, const df64* xg, df64* x, cudaStream_t s
   launch_scatter_recover_b(c->mesh, xg, B.sI, x, s);
 }
 
+// The same fork as the single path: the coarse correction (Phi_i^T r_i, the coarse solve,
+// Phi_i u_C) on the context's high-priority side stream beside the local products N_i r_i;
+// in level 2, K_II^{-1} g_I and the level-3 correction on two more side streams.
+struct ForkB {
+  cudaStream_t side;
+  cudaEvent_t f, j;
+  cudaStream_t begin(cudaStream_t s) const {
+    if (!side) return s;
+    DD_CUDA(cudaEventRecord(f, s));
+    DD_CUDA(cudaStreamWaitEvent(side, f, 0));
+    return side;
+  }
+  void end(cudaStream_t s) const {
+    if (!side) return;
+    DD_CUDA(cudaEventRecord(j, side));
+    DD_CUDA(cudaStreamWaitEvent(s, j, 0));
+  }
+};
+
 template <class CoarseFn>
 void bddc_b(dd_ctx* c, const DevBDDC& b, const df64* r, df64* z, void* rloc, void* uloc, void* vloc, void* gloc,
             void* gC, void* uC, CoarseFn coarse, cudaStream_t s) {
   launch_restrict_b(b.prec, b.n_flat, b.gmap, c->bw->D1f, b.D, r, rloc, s);
+  const ForkB fk{c->s_coarse, c->ev_fork, c->ev_join};
+  const cudaStream_t sc = fk.begin(s);
+  launch_bmm(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, sc);    // Phi_i^T r_i
+  launch_gather_tb(b.prec, b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, sc);
+  coarse(gC, uC, sc);
+  launch_bmm_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, sc);     // Phi_i R_Ci u_C
   {
     ProfScope pk(c, DD_PROF_ENS_N, s);
     apply_sym_b(c, BOP_N1, b.N, b.goff, rloc, uloc, s);                        // u_i = N_i r_i
   }
-  launch_bmm(b.PhiT, b.goff, nullptr, rloc, b.coff, gloc, 1.0, nullptr, s);    // Phi_i^T r_i
-  launch_gather_tb(b.prec, b.n_coarse, b.cptr, b.cidx, gloc, nullptr, nullptr, gC, s);
-  coarse(gC, uC);
-  launch_bmm_t(b.PhiT, b.coff, b.cmap, uC, b.goff, vloc, 1.0, nullptr, s);     // Phi_i R_Ci u_C
+  fk.end(s);
   launch_wgather_b(b.prec, b.n_gamma, b.gptr, b.gidx, c->bw->D1f, b.D, uloc, vloc, z, s);
 }
 
@@ -261,21 +283,27 @@ void level2_b(dd_ctx* c, const void* g, void* u, cudaStream_t s) {
   DevLevel2& L = c->l2;
   BatchWork& B = *c->bw;
   const int p2 = L.b.prec;
+  const ForkB f0{c->s_aux[0], c->ev_aux[0], c->ev_aux[1]};
+  const ForkB f1{c->s_aux[1], c->ev_aux[2], c->ev_aux[3]};
   launch_map_gather_b(p2, L.n_int, L.imap, g, B.gI2, s);
-  apply_sym_b(c, BOP_KII2, L.KIIinv, L.ioff, B.gI2, B.u0I2, s);
+  const cudaStream_t s0 = f0.begin(s);
+  apply_sym_b(c, BOP_KII2, L.KIIinv, L.ioff, B.gI2, B.u0I2, s0);
   launch_bmm_t(L.E, L.ioff, nullptr, B.gI2, L.b.goff, B.rl2, -1.0, nullptr, s);  // -K_GI K_II^{-1} g_I
   launch_gather_tb(p2, L.b.n_gamma, L.b.gptr, L.b.gidx, B.rl2, g, L.gam_c64, B.r2, s);
   {
     // level-2 interface BDDC on r2 (vectors in the preconditioner type), exact level 3
     const DevBDDC& b = L.b;
     launch_restrict_tb(p2, b.n_flat, b.gmap, b.D, B.r2, B.rloc2, s);
+    const cudaStream_t s1 = f1.begin(s);
+    launch_bmm(b.PhiT, b.goff, nullptr, B.rloc2, b.coff, B.gloc2, 1.0, nullptr, s1);
+    launch_gather_tb(p2, b.n_coarse, b.cptr, b.cidx, B.gloc2, nullptr, nullptr, B.g3, s1);
+    launch_dense_mm(p2, L.n3, L.KC3inv, B.g3, B.u3, s1);
+    launch_bmm_t(b.PhiT, b.coff, b.cmap, B.u3, b.goff, B.vloc2, 1.0, nullptr, s1);
     apply_sym_b(c, BOP_N2, b.N, b.goff, B.rloc2, B.uloc2, s);
-    launch_bmm(b.PhiT, b.goff, nullptr, B.rloc2, b.coff, B.gloc2, 1.0, nullptr, s);
-    launch_gather_tb(p2, b.n_coarse, b.cptr, b.cidx, B.gloc2, nullptr, nullptr, B.g3, s);
-    launch_dense_mm(p2, L.n3, L.KC3inv, B.g3, B.u3, s);
-    launch_bmm_t(b.PhiT, b.coff, b.cmap, B.u3, b.goff, B.vloc2, 1.0, nullptr, s);
+    f1.end(s);
     launch_wgather_tb(p2, b.n_gamma, b.gptr, b.gidx, b.D, B.uloc2, B.vloc2, B.z2, s);
   }
+  f0.end(s);
   launch_bmm(L.E, L.b.goff, L.b.gmap, B.z2, L.ioff, B.uI2, -1.0, B.u0I2, s);  // u0 - K_II^{-1} K_IG z
   launch_map_scatter_b(p2, L.n_int, L.imap, B.uI2, u, s);
   launch_map_scatter_b(p2, L.b.n_gamma, L.gam_c, B.z2, u, s);
@@ -285,11 +313,11 @@ void precond_b(dd_ctx* c, const df64* r, df64* z, cudaStream_t s) {
   ProfScope ps(c, DD_PROF_ENS_PRECOND, s);
   BatchWork& B = *c->bw;
   bddc_b(c, c->b1, r, z, B.rloc, B.uloc, B.vloc, B.gloc, B.gC, B.uC,
-         [&](const void* g, void* u) {
+         [&](const void* g, void* u, cudaStream_t ss) {
            if (c->levels == 2)
-             launch_dense_mm(c->b1.prec, c->b1.n_coarse, c->KCinv, g, u, s);
+             launch_dense_mm(c->b1.prec, c->b1.n_coarse, c->KCinv, g, u, ss);
            else
-             level2_b(c, g, u, s);
+             level2_b(c, g, u, ss);
          },
          s);
 }
