@@ -29,6 +29,11 @@
  *     Interface vectors (length n_gamma) list the interface nodes (nodes of
  *     more than one subdomain) in increasing free-node index.
  *   - All floating-point vectors crossing the ABI are float64.
+ *   - A context and its recycle states are used by one host thread at a time, with
+ *     their calls issued in order: they own work space and side streams. Work that a
+ *     call puts on a side stream (the BDDC coarse correction, the deflation dots) is
+ *     forked from and joined back into `stream` by events, so for the caller every
+ *     call stays ordered on `stream` (also under stream capture).
  */
 #ifndef DD_SOLVER_H
 #define DD_SOLVER_H
