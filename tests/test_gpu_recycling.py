@@ -130,3 +130,24 @@ def test_fp32_valued_basis_is_exact_for_its_own_span():
         assert np.array_equal(y, AW[j]), j
     rec.close()
     S.close()
+
+
+@pytest.mark.parametrize("pre", ["fp64", "fp32"])
+def test_wide_recycled_basis_matches_oracle(pre):
+    """A basis of 100 columns (the deflation dots' last-block reduction then gives each thread
+    a segment of half the blocks, and the update walks 25 groups of four columns) on the
+    FP64 and the mixed-precision path: every step's solution against the sparse Cholesky."""
+    m = make_mesh(16, 4, 1.08, 20.0)
+    F = load_sequence(m, 8, 6)
+    ch = cholesky.factor_mesh(m)
+    mixed = pre == "fp32"
+    S = P.Solver(m, **dict(KINDS, schur_prec="df64" if mixed else "fp64", precond_prec=pre, flexible=int(mixed)))
+    rec = S.recycler(100, "B4")
+    for t, f in enumerate(F):
+        x, st = S.solve(T(f), rec, rtol=1e-9)
+        xe = ch.solve(f)
+        err = np.linalg.norm(x.cpu().numpy() - xe) / np.linalg.norm(xe)
+        assert err <= 1e-7, (t, err)
+    assert rec.state()["k"] > 40
+    rec.close()
+    S.close()
