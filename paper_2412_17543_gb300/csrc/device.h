@@ -116,6 +116,11 @@ struct DevMesh {
   const int* fdm_n;         // [S][3] sizes of the interior index sets per axis (<= 9)
   const void* fdm_V;        // [S][3][81] 1D generalized eigenvectors, stride 9 (df64 or double)
   const void* fdm_Dinv;     // [n_int] inverse eigenvalue sums, indexed like interior vectors
+  // per-subdomain copies read by the fused Schur kernel in one coalesced level each
+  // (8^3-element subdomains with the fast-diagonalization solver only; else null):
+  const int* sxg = nullptr;     // [S][NL] interface index of each local node (-1: not on the interface)
+  const void* sfac = nullptr;   // [S][max_nbl][3] factors of the boundary-layer elements in the
+                                // order of the type's list (df64 or double, as schur_prec)
 };
 
 // One BDDC level (Sect. 3.2): weights, constrained Neumann operator N, coarse basis

@@ -786,25 +786,26 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
   const int64_t io = m.ioff[s], go = m.goff[s];
   if (threadIdx.x < 3) n[threadIdx.x] = m.fdm_n[3 * s + threadIdx.x];
   for (int t = threadIdx.x; t < 243; t += blockDim.x) Vs[t] = ld_fdm<P>(m.fdm_V, (int64_t)s * 243 + t);
+  // the subdomain's own copies (setup): interface index per local node, the interior entries
+  // of D^{-1} (contiguous from ioff[s]) and the boundary-layer element factors in list order,
+  // so that every load here is one coalesced level (x_G then one gather through the indices)
+  const int* gix = m.sxg + (size_t)s * m.NL;
   for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
     const int cd = code[l];
-    xl[l] = (cd < 0 && cd != INT16_MIN) ? P::from_d(xg[m.gmap[go + (-1 - cd)]]) : P::zero();
+    const int gi = gix[l];
+    xl[l] = gi >= 0 ? P::from_d(xg[gi]) : P::zero();
     if (cd >= 0) {
       f0[cd] = P::zero();
-      dv[cd] = ld_fdm<P>(m.fdm_Dinv, io + cd);
       il[cd] = (int16_t)l;
     }
   }
+  const int nint = (int)(m.ioff[s + 1] - io);
+  for (int t = threadIdx.x; t < nint; t += blockDim.x) dv[t] = ld_fdm<P>(m.fdm_Dinv, io + t);
   {
-    const int sx = S ? S : m.sx, sy = S ? S : m.sy, sz = S ? S : m.sz;
-    const int I = s % m.Sx, J = (s / m.Sx) % m.Sy, K = s / (m.Sx * m.Sy);
+    const V* fac = static_cast<const V*>(m.sfac) + (size_t)s * m.max_nbl * 3;
     for (int t = threadIdx.x; t < nbl; t += blockDim.x) {
-      const int el = m.type_bl[to[4] + t];
-      bll[t] = (int16_t)el;
-      const int ea = el % sx, eb = (el / sx) % sy, ec = el / (sx * sy);
-      const int64_t e = (int64_t)(I * sx + ea) + (int64_t)m.nx * ((J * sy + eb) + (int64_t)m.ny * (K * sz + ec));
-      V c[3];
-      load_factors<P>(m, e, c);
+      bll[t] = m.type_bl[to[4] + t];
+      V c[3] = {fac[3 * t], fac[3 * t + 1], fac[3 * t + 2]};
 #pragma unroll
       for (int d = 0; d < 8; ++d) kd[d * nbl + t] = P::entry(c, d);
     }
@@ -831,7 +832,8 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
 }
 
 bool schur_fused_available(const DevMesh& m) {
-  return m.local_solver == DD_LOCAL_FDM && m.sx == 8 && m.sy == 8 && m.sz == 8 && m.type_citems != nullptr;
+  return m.local_solver == DD_LOCAL_FDM && m.sx == 8 && m.sy == 8 && m.sz == 8 && m.type_citems != nullptr &&
+         m.sxg != nullptr && m.sfac != nullptr;
 }
 
 template <class P, int BS>

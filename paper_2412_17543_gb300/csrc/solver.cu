@@ -689,6 +689,36 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       dm.type_citems = A.upload(W.citems, s);
       dm.max_nbl = W.max_nbl;
       dm.schur_threads = 256;
+      if (H->local_solver == DD_LOCAL_FDM && M.sx == 8 && M.sy == 8 && M.sz == 8) {
+        // the fused Schur kernel's per-subdomain copies: each local node's interface index, and
+        // the factors of the boundary-layer elements in the order of the type's list
+        std::vector<int> sxg((size_t)M.S * M.NL, -1);
+        std::vector<double> sf((size_t)M.S * W.max_nbl * 3, 0.0);
+        for (int i = 0; i < M.S; ++i) {
+          const int16_t* code = M.lidx.data() + (size_t)i * M.NL;
+          for (int l = 0; l < M.NL; ++l)
+            if (code[l] < 0 && code[l] != INT16_MIN)
+              sxg[(size_t)i * M.NL + l] = H->l1.gmap[H->l1.goff[i] + (-1 - code[l])];
+          const int* o = W.type_off.data() + 6 * W.sub_type[i];
+          const int I = i % M.Sx, J = (i / M.Sx) % M.Sy, K = i / (M.Sx * M.Sy);
+          for (int t = o[4]; t < o[5]; ++t) {
+            const int el = W.bl[t], ea = el % M.sx, eb = (el / M.sx) % M.sy, ec = el / (M.sx * M.sy);
+            const size_t e = (size_t)(I * M.sx + ea) + (size_t)M.nx * ((J * M.sy + eb) + (size_t)M.ny * (K * M.sz + ec));
+            double* d = sf.data() + ((size_t)i * W.max_nbl + (t - o[4])) * 3;
+            d[0] = M.ecx[e];
+            d[1] = M.ecy[e];
+            d[2] = M.ecz[e];
+          }
+        }
+        dm.sxg = A.upload(sxg, s);
+        if (opt->schur_prec == DD_PREC_DF64) {
+          std::vector<df64> sfd(sf.size());
+          for (size_t t = 0; t < sf.size(); ++t) sfd[t] = df64_from_double(sf[t]);
+          dm.sfac = A.upload(sfd, s);
+        } else {
+          dm.sfac = A.upload(sf, s);
+        }
+      }
     }
     dm.ioff = A.upload(H->l1.ioff, s);
     dm.goff = A.upload(H->l1.goff, s);
