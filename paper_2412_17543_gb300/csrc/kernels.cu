@@ -701,10 +701,13 @@ __device__ __forceinline__ void fdm_contract_epi(const typename P::V* A, int ax,
         P::fma(acc[i & 1], a, in[base + i * stride]);
       }
     } else {
-      for (int i = 0; i < na; ++i) {
-        typename P::V a = trans ? A[i * 9 + j] : A[j * 9 + i];
-        P::fma(acc[i & 1], a, in[base + i * stride]);
+      // pairs of terms, so that the accumulators stay in registers
+      int i = 0;
+      for (; i + 1 < na; i += 2) {
+        P::fma(acc[0], trans ? A[i * 9 + j] : A[j * 9 + i], in[base + i * stride]);
+        P::fma(acc[1], trans ? A[(i + 1) * 9 + j] : A[j * 9 + i + 1], in[base + (i + 1) * stride]);
       }
+      if (i < na) P::fma(acc[0], trans ? A[i * 9 + j] : A[j * 9 + i], in[base + i * stride]);
     }
     const typename P::V v = P::add(P::get(acc[0]), P::get(acc[1]));
     if (EPI == 0) {
@@ -790,24 +793,58 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
   // of D^{-1} (contiguous from ioff[s]) and the boundary-layer element factors in list order,
   // so that every load here is one coalesced level (x_G then one gather through the indices)
   const int* gix = m.sxg + (size_t)s * m.NL;
-  for (int l = threadIdx.x; l < m.NL; l += blockDim.x) {
-    const int cd = code[l];
-    const int gi = gix[l];
-    xl[l] = gi >= 0 ? P::from_d(xg[gi]) : P::zero();
-    if (cd >= 0) {
-      f0[cd] = P::zero();
-      il[cd] = (int16_t)l;
+  constexpr int NLC = (S + 1) * (S + 1) * (S + 1), NLT = (NLC + BS - 1) / BS;
+  {
+    // all of a thread's codes and indices first, then its x_G values, then the stores
+    int cd[NLT], gi[NLT];
+#pragma unroll
+    for (int u = 0; u < NLT; ++u) {
+      const int l = threadIdx.x + u * BS;
+      cd[u] = l < NLC ? code[l] : INT16_MIN;
+      gi[u] = l < NLC ? gix[l] : -1;
+    }
+    V xv[NLT];
+#pragma unroll
+    for (int u = 0; u < NLT; ++u) xv[u] = gi[u] >= 0 ? P::from_d(xg[gi[u]]) : P::zero();
+#pragma unroll
+    for (int u = 0; u < NLT; ++u) {
+      const int l = threadIdx.x + u * BS;
+      if (l < NLC) {
+        xl[l] = xv[u];
+        if (cd[u] >= 0) {
+          f0[cd[u]] = P::zero();
+          il[cd[u]] = (int16_t)l;
+        }
+      }
     }
   }
   const int nint = (int)(m.ioff[s + 1] - io);
-  for (int t = threadIdx.x; t < nint; t += blockDim.x) dv[t] = ld_fdm<P>(m.fdm_Dinv, io + t);
-  {
-    const V* fac = static_cast<const V*>(m.sfac) + (size_t)s * m.max_nbl * 3;
-    for (int t = threadIdx.x; t < nbl; t += blockDim.x) {
-      bll[t] = m.type_bl[to[4] + t];
-      V c[3] = {fac[3 * t], fac[3 * t + 1], fac[3 * t + 2]};
 #pragma unroll
-      for (int d = 0; d < 8; ++d) kd[d * nbl + t] = P::entry(c, d);
+  for (int u = 0; u < NLT; ++u) {
+    const int t = threadIdx.x + u * BS;
+    if (t < nint) dv[t] = ld_fdm<P>(m.fdm_Dinv, io + t);
+  }
+  {
+    constexpr int NBT = (S * S * S + BS - 1) / BS;  // boundary-layer elements per thread at most
+    const V* fac = static_cast<const V*>(m.sfac) + (size_t)s * m.max_nbl * 3;
+    V c[NBT][3];
+#pragma unroll
+    for (int u = 0; u < NBT; ++u) {
+      const int t = threadIdx.x + u * BS;
+      if (t < nbl) {
+        c[u][0] = fac[3 * t];
+        c[u][1] = fac[3 * t + 1];
+        c[u][2] = fac[3 * t + 2];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NBT; ++u) {
+      const int t = threadIdx.x + u * BS;
+      if (t < nbl) {
+        bll[t] = m.type_bl[to[4] + t];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) kd[d * nbl + t] = P::entry(c[u], d);
+      }
     }
   }
   __syncthreads();
