@@ -100,6 +100,7 @@ struct DevMesh {
   const int16_t* type_bl;     // boundary-layer element ids
   const int16_t* type_citems; // the items with slots (position in the type's boundary-layer list) * 8 + corner
   int max_nbl;                // largest boundary-layer list of a subdomain type
+  int max_nint = 0;           // largest interior (unknowns not on the interface) of a subdomain
   int schur_threads;          // threads per CTA of the fused Schur kernel (256, 352 or 416; tuned at setup)
   const int64_t* ioff;
   const int64_t* goff;

@@ -774,13 +774,13 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* xl = reinterpret_cast<V*>(smem_raw);  // [NL] local nodal vector
-  V* f0 = xl + m.NL;                        // [NL] interior vector buffers of the fast diagonalization
-  V* f1 = f0 + m.NL;
-  V* dv = f1 + m.NL;                        // [NL] D^{-1} of the fast diagonalization
-  V* Vs = dv + m.NL;                        // [3][81] 1D eigenbases (stride 9)
+  V* f0 = xl + m.NL;                        // [max_nint] interior vector buffers of the fast diagonalization
+  V* f1 = f0 + m.max_nint;
+  V* dv = f1 + m.max_nint;                  // [max_nint] D^{-1} of the fast diagonalization
+  V* Vs = dv + m.max_nint;                  // [3][81] 1D eigenbases (stride 9)
   V* kd = Vs + 243;                         // [8][nbl] entry classes of the boundary-layer elements
   int16_t* bll = reinterpret_cast<int16_t*>(kd + 8 * m.max_nbl);  // [nbl] boundary-layer elements
-  int16_t* il = bll + m.max_nbl;                                   // [NL] local node of interior index
+  int16_t* il = bll + m.max_nbl;                                   // [max_nint] local node of interior index
   __shared__ int n[3];
   const int s = blockIdx.x;
   const int16_t* code = m.lidx + (size_t)s * m.NL;
@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(BS) k_schur_fused(DevMesh m, const double* __r
 
 bool schur_fused_available(const DevMesh& m) {
   return m.local_solver == DD_LOCAL_FDM && m.sx == 8 && m.sy == 8 && m.sz == 8 && m.type_citems != nullptr &&
-         m.sxg != nullptr && m.sfac != nullptr;
+         m.sxg != nullptr && m.sfac != nullptr && m.max_nint > 0 && m.max_nint <= m.NL;
 }
 
 template <class P, int BS>
@@ -881,7 +881,10 @@ static void schur_fused_bs(const DevMesh& m, const double* xg, double* yloc, siz
 
 void launch_schur_fused(const DevMesh& m, const double* xg, double* yloc, cudaStream_t s) {
   const size_t vb = m.schur_prec == DD_PREC_DF64 ? sizeof(df64) : sizeof(double);
-  const size_t smem = vb * ((size_t)4 * m.NL + 243 + 8 * (size_t)m.max_nbl) + 2 * ((size_t)m.max_nbl + m.NL);
+  // interior buffers sized by the largest interior of a subdomain (up to 8^3 on the Neumann
+  // boundary, whose face nodes are interior unknowns), so that more CTAs fit on an SM
+  const size_t ni = (size_t)m.max_nint;
+  const size_t smem = vb * ((size_t)m.NL + 3 * ni + 243 + 8 * (size_t)m.max_nbl) + 2 * ((size_t)m.max_nbl + ni);
   if (m.schur_prec == DD_PREC_DF64) {
     switch (m.schur_threads) {
       case 352: schur_fused_bs<PolDF, 352>(m, xg, yloc, smem, s); break;

@@ -688,6 +688,8 @@ dd_status dd_setup(const dd_mesh_desc* md, const dd_options* opt, void* stream, 
       dm.type_bl = A.upload(W.bl, s);
       dm.type_citems = A.upload(W.citems, s);
       dm.max_nbl = W.max_nbl;
+      for (int i = 0; i < M.S; ++i)
+        dm.max_nint = std::max(dm.max_nint, (int)(H->l1.ioff[i + 1] - H->l1.ioff[i]));
       dm.schur_threads = 256;
       if (H->local_solver == DD_LOCAL_FDM && M.sx == 8 && M.sy == 8 && M.sz == 8) {
         // the fused Schur kernel's per-subdomain copies: each local node's interface index, and
