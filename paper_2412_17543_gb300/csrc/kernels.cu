@@ -375,7 +375,7 @@ __device__ __forceinline__ void packed_ragged_parts(const unsigned char* T, int 
 // copies completing on mbarriers; an off-diagonal block serves its block row and (by
 // symmetry) its block column, so every stored entry is read from HBM once.
 template <int PREC, int SYMV_SLOTS>
-__global__ void __launch_bounds__(SYMV_WARPS * 32) k_symv(SymTiles A, const int64_t* __restrict__ voff,
+__global__ void __launch_bounds__(SYMV_WARPS * 32, 5) k_symv(SymTiles A, const int64_t* __restrict__ voff,
                                                           const double* __restrict__ in,
                                                           double* __restrict__ out, int* err) {
   // A.split CTAs per matrix (small batches): CTA q of matrix m takes the blocks of warps
